@@ -1,0 +1,324 @@
+"""Benchmark: restarted-PDHG iterations per second on the large mixed LP.
+
+Workload: m = 200,000 rows (70% EQ, 30% GE), n = 1,000,000 columns (40%
+[0,inf), 40% [0,U(1,10)], 20% free), power-law column degree on 2..200
+(~10.07M nonzeros), N(0,1) values, planted optimum; seeded (seed 1).
+A step is one block of K = 64 PDHG iterations followed by one check (KKT
+of average and current iterate, normalized duality gap by the multiplier
+search, adaptive restart decision): every row of the hot path.
+
+value = PDHG iterations / second (device-timed, inputs resident in HBM;
+the working set, ~330 MB, exceeds the 129 MB L2, so no flush is needed).
+e2e   = the same metric through the C ABI from HOST buffers: lp_create
+        (host arrays, H2D inside), lp_solve for a fixed iteration budget,
+        lp_get_solution into host memory, lp_destroy, per step.
+
+--impl reference times the CPU oracle (plain C, FP64, 1 thread) on a
+bounded sample of the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+K_CHECK = 64
+FALLBACK_HBM_GBS = 6800.0
+# dram__bytes_read.sum + dram__bytes_write.sum of one primal_kernel launch on
+# this workload, from profiles/primal_kernel_large_mixed.md (None until taken
+# for the current kernel).
+PRIMAL_TRAFFIC_BYTES = None
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=60)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--m", type=int, default=200_000)
+    p.add_argument("--n", type=int, default=1_000_000)
+    p.add_argument("--seed", type=int, default=1)
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--e2e-iters", type=int, default=6400)
+    p.add_argument("--cpu-iters", type=int, default=64)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--kernel-reps", type=int, default=50)  # >= 1
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(args):
+    from paper_2105_12715_gb300 import lpgen
+
+    return lpgen.large_mixed(args.seed, m=args.m, n=args.n)
+
+
+def config_of(args, data):
+    return {"workload": f"large_mixed LP m={data.m} n={data.n} nnz={data.nnz} "
+                        f"(70% EQ/30% GE rows; 40% [0,inf), 40% [0,U], 20% free cols; "
+                        f"power-law col degree 2..200; seed {args.seed})",
+            "m": data.m, "n": data.n, "nnz": data.nnz, "check_every": K_CHECK,
+            "restart": "adaptive beta=e^-1", "precision": "fp64",
+            "l2": "working set > L2 (129 MB); no flush"}
+
+
+def algorithmic_bytes(m, n, nnz):
+    """Bytes one PDHG iteration must move (each array once, gathers once)."""
+    primal = 12 * nnz + 64 * n + 8 * m  # A^T values+indices; c,l,u,x,xbar in; x,xhat,xbar out; y gathered
+    dual = 12 * nnz + 41 * m + 8 * n    # A values+indices; b,y,ybar,rowtype in; y,ybar out; xhat gathered
+    return primal, dual
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for k in ("hbm_gbs_sustained", "hbm_gbs"):
+                if k in d and d[k]:
+                    return float(d[k]), f"measured ({k})"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.remove(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(args, data):
+    """The oracle (plain C, 1 thread) on a bounded sample: cpu_iters iterations
+    with one check every 64 (the same workload)."""
+    import oracle
+
+    eta = 0.9 / 11.0
+    t = time.perf_counter()
+    res = oracle.solve(data, eta, tol=1e-300, max_iter=args.cpu_iters, check_every=K_CHECK)
+    dt = time.perf_counter() - t
+    return {"value": res.iters / dt, "unit": "iters/s", "cores": 1, "kind": "oracle",
+            "sample": f"{res.iters} oracle iterations incl. {res.n_checks} check(s) on the full "
+                      f"workload, {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    data = workload(args)
+    import oracle
+
+    oracle.build()
+    eta = 0.9 / 11.0
+    per_step = 4  # oracle iterations per step (bounded sample; a check every 64 iterations)
+    olp = oracle.OracleLP(data)
+    oracle.solve(olp, eta, tol=1e-300, max_iter=per_step * args.warmup, check_every=K_CHECK)
+    total = per_step * args.steps
+    t = time.perf_counter()
+    res = oracle.solve(olp, eta, tol=1e-300, max_iter=total, check_every=K_CHECK)
+    dt = time.perf_counter() - t
+    v = res.iters / dt
+    line = {"metric": "PDHG iterations/s (fp64 restarted PDHG, large mixed LP)", "value": v,
+            "unit": "iters/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": config_of(args, data),
+            "cpu_baseline": {"value": v, "unit": "iters/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{res.iters} oracle iterations ({per_step} per step), "
+                                       f"{res.n_checks} check(s)"},
+            "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    from paper_2105_12715_gb300 import lp
+
+    lp.load()
+    data = workload(args)
+    stream = torch.cuda.current_stream()
+    g = lp.LP(data, stream=stream, check_every=K_CHECK)
+    info0 = g.info()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    # warm-up
+    g.iterate(args.warmup, 1e-300)
+    barrier()
+    sampler = ClockSampler(dev)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.iterate(args.steps, 1e-300)
+    e1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    iters = args.steps * K_CHECK
+    value = ws * iters / (ms / 1000.0)
+    info = g.info()
+    # per step: 2 K iteration kernels + 2 check passes, finalize, 8 x (hist, select), decide, copy
+    launches_per_step = 2 * K_CHECK + 21
+
+    # dominant kernel timed alone with CUDA events (same stream, same data)
+    primal_b, dual_b = algorithmic_bytes(data.m, data.n, data.nnz)
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    lp.lp_profile_kernel(g.h, 0, args.kernel_reps, stream)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    primal_ms = k0.elapsed_time(k1) / args.kernel_reps
+    k0.record(stream)
+    lp.lp_profile_kernel(g.h, 1, args.kernel_reps, stream)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    dual_ms = k0.elapsed_time(k1) / args.kernel_reps
+    peak, peak_kind = peaks()
+    achieved = primal_b / (primal_ms / 1000.0) / 1e9
+    g.close()
+
+    # end to end through the C ABI from host buffers
+    e2e_vals, h2d = [], 0
+    host = [np.ascontiguousarray(a) for a in (data.row_ptr, data.col_idx, data.val, data.c, data.b,
+                                              data.lb, data.ub, data.row_type)]
+    pinned = [torch.from_numpy(a).pin_memory() for a in host]
+    h2d = sum(a.numel() * a.element_size() for a in pinned)
+    xo = torch.empty(data.n, dtype=torch.float64).pin_memory()
+    yo = torch.empty(data.m, dtype=torch.float64).pin_memory()
+    d2h = (data.n + data.m) * 8
+    for _ in range(args.e2e_steps):
+        barrier()
+        t = time.perf_counter()
+        opt = lp.lp_default_options()
+        opt.check_every = K_CHECK
+        opt.max_iter = args.e2e_iters
+        h = lp.lp_create(data.m, data.n, data.nnz, *pinned, opt=opt, stream=stream)
+        lp.lp_solve(h, 1e-300, stream)
+        lp.lp_get_solution(h, xo, yo, stream)
+        lp.lp_destroy(h)
+        barrier()
+        e2e_vals.append(args.e2e_iters / (time.perf_counter() - t))
+    e2e = {"value": ws * float(np.median(e2e_vals)), "unit": "iters/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h,
+           "what": f"lp_create(host arrays)+lp_solve({args.e2e_iters} iters)+lp_get_solution(host)"}
+
+    out = None
+    if rank == 0:
+        out = {"metric": "PDHG iterations/s (fp64 restarted PDHG, large mixed LP)", "value": value,
+               "unit": "iters/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": config_of(args, data),
+               "parallelism": "replicas" if ws > 1 else "single",
+               "gpu_launches": launches_per_step * args.steps,
+               "iters_per_step": K_CHECK,
+               "bytes_per_iter_algorithmic": primal_b + dual_b,
+               "achieved_gbs_per_iter": (primal_b + dual_b) * value / ws / 1e9,
+               "roofline": {"bound": "hbm", "kernel": "primal_kernel", "achieved": achieved,
+                            "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                            "peak_kind": peak_kind, "traffic": PRIMAL_TRAFFIC_BYTES,
+                            "algorithmic_bytes": primal_b, "avg_launch_ms": primal_ms,
+                            "dual_kernel_ms": dual_ms, "dual_algorithmic_bytes": dual_b},
+               "clocks": clocks, "e2e": e2e,
+               "solver": {"eta": info0.eta, "sigma_max": info0.sigma_max,
+                          "iters_done": info.iters, "restarts": info.restarts,
+                          "rel_kkt_avg": info.kkt_avg[4], "rel_kkt_cur": info.kkt_cur[4],
+                          "nnz_padded": info.nnz_padded}}
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args, data)
+        print(json.dumps(out))
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    args.kernel_reps = max(1, args.kernel_reps)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,193 @@
+/*
+ * lp.h -- C ABI of the GB300 restarted-PDHG linear-programming library
+ * (liblp.so, built for sm_103a).
+ *
+ * Method: Applegate, Hinder, Lu, Lubin, "Faster first-order primal-dual
+ * methods for linear programming using restarts and sharpness".
+ *
+ * Problem (Eq. LP-Lag, widened to box bounds and signed rows):
+ *     min_{x in X} max_{y in Y}  L(x, y) = c^T x - y^T A x + b^T y,
+ *     X = prod_j [lb_j, ub_j],  Y = prod_i Y_i with
+ *     Y_i = R          for LP_ROW_EQ  ((A x)_i =  b_i),
+ *     Y_i = [0, inf)   for LP_ROW_GE  ((A x)_i >= b_i),
+ *     Y_i = (-inf, 0]  for LP_ROW_LE  ((A x)_i <= b_i).
+ *
+ * Conventions for every entry point:
+ *   - A is m x n, given in CSR form with int32 indices; nnz < 2^31.
+ *   - Array arguments of lp_create may be host or device memory (detected
+ *     per pointer); all other array arguments are DEVICE pointers unless
+ *     the name starts with host_.  Device arrays are read/written in stream
+ *     order on the given stream.
+ *   - cuda_stream is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.
+ *   - The library copies every input at lp_create; the caller may free or
+ *     reuse its buffers once lp_create returns.  Outputs go to caller
+ *     buffers.  The handle owns all device memory it allocates.
+ *   - Errors are reported as lp_status codes, never as exceptions; the
+ *     message of the last error on the calling thread is lp_last_error().
+ *   - A handle may be used by one host thread at a time.
+ */
+#ifndef LP_GB300_LP_H
+#define LP_GB300_LP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lp_problem *lp_handle;
+
+typedef enum {
+  LP_OK = 0,
+  LP_ERR_INVALID_ARG = 1, /* bad size, pointer, CSR structure, NaN, bound */
+  LP_ERR_CUDA = 2,        /* a CUDA runtime call failed                  */
+  LP_ERR_OOM = 3,         /* device or host allocation failed            */
+  LP_ITER_LIMIT = 4,      /* max_iter reached before the tolerance       */
+  LP_ERR_NUMERICAL = 5,   /* NaN or Inf met in an iterate or residual    */
+  LP_ERR_TIMEOUT = 6,     /* reserved: a bounded device wait expired     */
+  LP_ERR_NOT_SOLVED = 7   /* no solve has run on this handle yet         */
+} lp_status;
+
+enum { LP_ROW_EQ = 0, LP_ROW_GE = 1, LP_ROW_LE = 2 };
+
+/* Restart schemes of Section 4 (fixed frequency, Eq. define:t-star;
+ * adaptive, Eq. adaptive-restart-scheme) and Section 7 (no restarts; the
+ * flexible scheme of Remark "Flexible restarts"). */
+enum {
+  LP_RESTART_NONE = 0,
+  LP_RESTART_FIXED = 1,
+  LP_RESTART_ADAPTIVE = 2,
+  LP_RESTART_FLEXIBLE = 3
+};
+
+typedef struct {
+  double beta;            /* restart contraction factor (Remark on the choice of beta: e^-1) */
+  int32_t check_every;    /* K: restart/termination checks every K iterations (Section 7 uses 30) */
+  int32_t restart_scheme; /* LP_RESTART_* */
+  int64_t tau0;           /* first restart length for n = 0 (iterations; 0 = K) */
+  int64_t fixed_len;      /* restart length of LP_RESTART_FIXED (iterations) */
+  double omega;           /* primal weight: tau = eta/omega, sigma = eta*omega (Section 7) */
+  double eta;             /* base step; 0 = 0.9 / sigma_max(A) by power iteration */
+  int32_t power_iters;    /* power-iteration cap for sigma_max (default 5000) */
+  double power_tol;       /* relative change of the Rayleigh estimate to stop (1e-10) */
+  int64_t max_iter;       /* iteration limit of one lp_solve call */
+  int32_t long_row_threshold; /* rows longer than this use the warp-per-row path (512) */
+  int32_t trace_capacity; /* per-check trace rows kept on device (65536) */
+  int32_t reserved[6];
+} lp_options;
+
+typedef struct {
+  int64_t iters;        /* iterations since the last lp_create / lp_set_state */
+  int64_t restarts;     /* outer-loop count n of Algorithm 1 */
+  int64_t checks;       /* restart/termination checks run */
+  int32_t status;       /* lp_status of the last lp_solve / lp_iterate */
+  int32_t returned;     /* solution candidate: 0 = running average, 1 = current iterate */
+  double kkt_avg[5];    /* at the last check, average:  r_p, r_d, p, d, relative KKT */
+  double kkt_cur[5];    /* at the last check, current iterate: same layout */
+  double eta, sigma_max, omega, tau, sigma;
+  double rho_stored;    /* gap stored at the last restart, Eq. (adaptive-restart-scheme) */
+  double last_rho;      /* normalized duality gap at the last check */
+  double last_radius;   /* its radius ||zbar - z^{n,0}|| */
+  int64_t nnz_padded;   /* stored nonzeros of one copy of A including padding */
+  int32_t n_long_rows, n_long_cols; /* rows/cols on the warp-per-row path */
+} lp_info;
+
+/* Defaults: beta = e^-1, K = 64, ADAPTIVE, tau0 = K, omega = 1, eta = 0
+ * (auto), power_iters = 5000, power_tol = 1e-10, max_iter = 1e7. */
+void lp_default_options(lp_options *opt);
+
+/*
+ * Creates a problem handle (the LP data of Eq. LP-Lag and the setup of
+ * Section 7: eta = 0.9 / sigma_max(A) by power iteration unless opt->eta > 0).
+ *   row_ptr[m+1], col_idx[nnz], val[nnz]: CSR of A; row_ptr[0] = 0,
+ *     nondecreasing, row_ptr[m] = nnz; col_idx in [0, n); a column may
+ *     appear at most once per row (duplicates are rejected).
+ *   c[n], lb[n], ub[n]: objective and bounds; lb = -INFINITY / ub = INFINITY
+ *     mean no bound; lb <= ub, lb < INFINITY, ub > -INFINITY.
+ *   b[m], row_type[m] (LP_ROW_*): right-hand side and row sense.
+ *   opt: may be NULL for defaults.
+ * Every value must be finite except the infinite bounds.  The starting
+ * point z^{0,0} is zero projected onto X x Y.  Returns LP_ERR_INVALID_ARG
+ * on any violation (message in lp_last_error), LP_ERR_OOM, LP_ERR_CUDA.
+ */
+lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
+                    const int32_t *col_idx, const double *val, const double *c,
+                    const double *b, const double *lb, const double *ub,
+                    const int8_t *row_type, const lp_options *opt,
+                    void *cuda_stream, lp_handle *out);
+
+/*
+ * Runs Algorithm 1 (restarted PDHG) from the handle's current state until
+ * the relative KKT error of the running average or of the current iterate
+ * is <= tol at a check (every K iterations; the average wins ties), or
+ * until opt.max_iter further iterations.  Returns LP_OK, LP_ITER_LIMIT,
+ * LP_ERR_NUMERICAL, LP_ERR_INVALID_ARG (tol <= 0) or LP_ERR_CUDA.  Blocks
+ * the host until the solve ends (one 4-byte read per check).
+ */
+lp_status lp_solve(lp_handle h, double tol, void *cuda_stream);
+
+/*
+ * Enqueues n_checks blocks of K PDHG iterations, each followed by a check
+ * (KKT, normalized gap, restart decision), without any host
+ * synchronization.  Blocks after convergence (relative KKT <= tol) do no
+ * work.  The iteration count is not capped by max_iter.  Returns LP_OK or
+ * an error of the enqueue.
+ */
+lp_status lp_iterate(lp_handle h, int32_t n_checks, double tol, void *cuda_stream);
+
+/* Copies the solution candidate (see lp_info.returned) into x[n], y[m]
+ * (device or host pointers); LP_ERR_NOT_SOLVED before any solve. */
+lp_status lp_get_solution(lp_handle h, double *x, double *y, void *cuda_stream);
+
+/* Copies the full iteration state of Algorithm 1 -- current iterate (x, y),
+ * running average (xbar, ybar), restart point (x0, y0) -- in the caller's
+ * (unpermuted) order; any pointer may be NULL to skip it.  Host or device
+ * pointers.  Synchronizes the stream. */
+lp_status lp_get_state(lp_handle h, double *x, double *y, double *xbar,
+                       double *ybar, double *x0, double *y0, void *cuda_stream);
+
+/* Warm start: sets z^{0,0} = proj_{X x Y}(x, y) (host or device pointers,
+ * NULL = zero) and resets the restart state and counters. */
+lp_status lp_set_state(lp_handle h, const double *x, const double *y, void *cuda_stream);
+
+/* Counters, step sizes and the residuals of the last check (host struct). */
+lp_status lp_get_info(lp_handle h, lp_info *host_info);
+
+/* Per-check log (Figure 2's series): 6 doubles per check
+ * {iteration, rho, restarted, relKKT(avg), relKKT(cur), radius}, oldest
+ * first, at most capacity rows; *host_count receives the number written. */
+lp_status lp_get_trace(lp_handle h, double *host_rows, int64_t capacity,
+                       int64_t *host_count);
+
+/*
+ * Normalized duality gap, Eq. (rhorz), of the LP at (x, y) for radius r
+ * under the weighted norm ||(x, y)||^2 = omega ||x||^2 + ||y||^2 / omega:
+ * the linear trust region of Section 6.3 solved by a parallel search over
+ * the multiplier (Algorithm 2's answer).  x[n], y[m] (host or device) in the
+ * caller's order, inside X x Y.  *host_rho receives rho_r; r = 0 gives 0.
+ * Allocates and frees its own scratch.  Synchronizes the stream.
+ */
+lp_status lp_normalized_gap(lp_handle h, const double *x, const double *y,
+                            double r, double *host_rho, void *cuda_stream);
+
+/*
+ * Profiling hook: enqueues reps launches of one hot-path kernel alone --
+ * which = 0: the primal step (column pass, Eq. PDHG-update first line),
+ * which = 1: the dual step (row pass, second line) -- on the stream, with
+ * the averaging weight of the block's first iteration.  It advances the
+ * iterate like real steps do (without checks), so use it on a handle whose
+ * solve state no longer matters.  Bracket it with events to time a kernel.
+ */
+lp_status lp_profile_kernel(lp_handle h, int32_t which, int32_t reps, void *cuda_stream);
+
+/* Releases every resource of the handle (NULL is a no-op). */
+void lp_destroy(lp_handle h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *lp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LP_GB300_LP_H */

@@ -1,0 +1,762 @@
+// C ABI of liblp.so (declared in include/lp.h): problem setup, the
+// restarted-PDHG driver around CUDA graphs, and state I/O.
+//
+// Setup (lp_create) builds the library's device layout on the host:
+//   * a CSC copy of A by a stable counting sort (rows ascending per column);
+//   * row and column permutations sorting rows of A and rows of A^T by
+//     length, longest first (stable), so that each SELL-32 slice holds 32
+//     rows of nearly equal length and long rows come first;
+//   * both operators relabeled into the permuted index spaces, so every
+//     vector (x, xhat, xbar, x0, c, l, u and y, ybar, y0, b, row sense) is
+//     stored permuted and accessed with unit stride; only the gathered
+//     operand of each SpMV is indexed.
+// The solve (lp_solve / lp_iterate) replays one captured CUDA graph per
+// block of K iterations + check; lp_solve keeps two blocks in flight and
+// reads a 4-byte status per check.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/lp.h"
+#include "lp_internal.h"
+
+using namespace lpg;
+
+namespace {
+
+thread_local std::string g_err;
+
+lp_status fail(lp_status s, const std::string &msg) {
+  g_err = msg;
+  return s;
+}
+
+lp_status cuda_fail(cudaError_t e, const char *what) {
+  cudaGetLastError();
+  return fail(e == cudaErrorMemoryAllocation ? LP_ERR_OOM : LP_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define LP_CU(call)                                   \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+struct HostSell {
+  int32_t nrows = 0, ncols = 0, nlong = 0, nslices = 0;
+  std::vector<int64_t> long_ptr, slice_ptr;
+  std::vector<int32_t> long_idx, idx;
+  std::vector<double> long_val, val;
+};
+
+// SELL-32 layout of the operator whose row r (permuted order) is original
+// row perm[r] of the CSR (ptr, ind, v); column indices relabeled by relabel.
+void build_sell(int32_t nrows, int32_t ncols, const std::vector<int64_t> &ptr,
+                const std::vector<int32_t> &ind, const std::vector<double> &v,
+                const std::vector<int32_t> &perm, const std::vector<int32_t> &relabel,
+                int32_t long_threshold, HostSell &S) {
+  S.nrows = nrows;
+  S.ncols = ncols;
+  auto len = [&](int32_t r) { return ptr[perm[r] + 1] - ptr[perm[r]]; };
+  int32_t nlong = 0;
+  while (nlong < nrows && len(nlong) > long_threshold) ++nlong;
+  S.nlong = nlong;
+  S.long_ptr.assign(nlong + 1, 0);
+  for (int32_t r = 0; r < nlong; ++r) S.long_ptr[r + 1] = S.long_ptr[r] + len(r);
+  S.long_idx.resize(S.long_ptr[nlong]);
+  S.long_val.resize(S.long_ptr[nlong]);
+  for (int32_t r = 0; r < nlong; ++r) {
+    const int64_t src = ptr[perm[r]], dst = S.long_ptr[r];
+    for (int64_t k = 0; k < len(r); ++k) {
+      S.long_idx[dst + k] = relabel[ind[src + k]];
+      S.long_val[dst + k] = v[src + k];
+    }
+  }
+  const int32_t nsell = nrows - nlong;
+  S.nslices = (nsell + kWarp - 1) / kWarp;
+  S.slice_ptr.assign(S.nslices + 1, 0);
+  for (int32_t s = 0; s < S.nslices; ++s) {
+    int64_t mx = 0;
+    for (int32_t l = 0; l < kWarp; ++l) {
+      const int32_t r = nlong + s * kWarp + l;
+      if (r < nrows) mx = std::max<int64_t>(mx, len(r));
+    }
+    S.slice_ptr[s + 1] = S.slice_ptr[s] + mx * kWarp;
+  }
+  S.idx.assign(S.slice_ptr[S.nslices], 0);
+  S.val.assign(S.slice_ptr[S.nslices], 0.0);
+  for (int32_t s = 0; s < S.nslices; ++s) {
+    for (int32_t l = 0; l < kWarp; ++l) {
+      const int32_t r = nlong + s * kWarp + l;
+      if (r >= nrows) break;
+      const int64_t src = ptr[perm[r]];
+      for (int64_t k = 0; k < len(r); ++k) {
+        const int64_t dst = S.slice_ptr[s] + k * kWarp + l;
+        S.idx[dst] = relabel[ind[src + k]];
+        S.val[dst] = v[src + k];
+      }
+    }
+  }
+}
+
+double now_seconds() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+}  // namespace
+
+struct lp_problem {
+  int32_t m = 0, n = 0;
+  int64_t nnz = 0;
+  lp_options opt{};
+  int device = 0;
+  int nsm = 0;
+  std::vector<void *> allocs;
+  SellMat A{}, AT{};
+  DevVecs v{};
+  DevState *st = nullptr;
+  double *w = nullptr;
+  CheckScratch cs{};
+  double *trace = nullptr;
+  int32_t *perm_x = nullptr, *perm_y = nullptr;
+  double *tmp = nullptr;
+  int64_t nnz_padded = 0;
+  double eta = 0, sigma_max = NAN;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int32_t *h_status = nullptr;  // pinned [2]
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  bool solved = false;
+  int nsearch = 1;
+
+  ~lp_problem() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (auto &e : ev)
+      if (e) cudaEventDestroy(e);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (h_status) cudaFreeHost(h_status);
+    for (void *p : allocs) cudaFree(p);
+  }
+
+  template <class T>
+  lp_status alloc(T **p, int64_t count) {
+    void *q = nullptr;
+    const size_t bytes = std::max<size_t>(16, sizeof(T) * (size_t)std::max<int64_t>(count, 1));
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    allocs.push_back(q);
+    *p = static_cast<T *>(q);
+    return LP_OK;
+  }
+
+  template <class T>
+  lp_status upload(T **p, const std::vector<T> &h) {
+    lp_status s = alloc(p, (int64_t)h.size());
+    if (s != LP_OK) return s;
+    if (!h.empty()) LP_CU(cudaMemcpy(*p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+    return LP_OK;
+  }
+
+  lp_status upload_sell(const HostSell &H, SellMat &M) {
+    int64_t *lp = nullptr, *sp = nullptr;
+    int32_t *li = nullptr, *ix = nullptr;
+    double *lv = nullptr, *vv = nullptr;
+    lp_status s;
+    if ((s = upload(&lp, H.long_ptr)) != LP_OK) return s;
+    if ((s = upload(&li, H.long_idx)) != LP_OK) return s;
+    if ((s = upload(&lv, H.long_val)) != LP_OK) return s;
+    if ((s = upload(&sp, H.slice_ptr)) != LP_OK) return s;
+    if ((s = upload(&ix, H.idx)) != LP_OK) return s;
+    if ((s = upload(&vv, H.val)) != LP_OK) return s;
+    M.nrows = H.nrows;
+    M.ncols = H.ncols;
+    M.nlong = H.nlong;
+    M.nslices = H.nslices;
+    M.long_ptr = lp;
+    M.long_idx = li;
+    M.long_val = lv;
+    M.slice_ptr = sp;
+    M.idx = ix;
+    M.val = vv;
+    return LP_OK;
+  }
+};
+
+namespace {
+
+template <class T>
+bool copy_in(std::vector<T> &dst, const T *src, int64_t count) {
+  dst.resize(count);
+  if (count == 0) return true;
+  return cudaMemcpy(dst.data(), src, sizeof(T) * count, cudaMemcpyDefault) == cudaSuccess;
+}
+
+lp_status validate_options(const lp_options &o) {
+  if (!(o.beta > 0.0 && o.beta < 1.0)) return fail(LP_ERR_INVALID_ARG, "beta must lie in (0, 1)");
+  if (o.check_every < 1 || o.check_every > 65536)
+    return fail(LP_ERR_INVALID_ARG, "check_every must lie in [1, 65536]");
+  if (o.restart_scheme < LP_RESTART_NONE || o.restart_scheme > LP_RESTART_FLEXIBLE)
+    return fail(LP_ERR_INVALID_ARG, "unknown restart_scheme");
+  if (o.tau0 < 0 || o.fixed_len < 0) return fail(LP_ERR_INVALID_ARG, "tau0 and fixed_len must be >= 0");
+  if (!(o.omega > 0.0) || !std::isfinite(o.omega)) return fail(LP_ERR_INVALID_ARG, "omega must be finite and > 0");
+  if (!(o.eta >= 0.0) || !std::isfinite(o.eta)) return fail(LP_ERR_INVALID_ARG, "eta must be finite and >= 0");
+  if (o.power_iters < 1) return fail(LP_ERR_INVALID_ARG, "power_iters must be >= 1");
+  if (!(o.power_tol >= 0.0)) return fail(LP_ERR_INVALID_ARG, "power_tol must be >= 0");
+  if (o.max_iter < 0) return fail(LP_ERR_INVALID_ARG, "max_iter must be >= 0");
+  if (o.long_row_threshold < 1) return fail(LP_ERR_INVALID_ARG, "long_row_threshold must be >= 1");
+  if (o.trace_capacity < 0) return fail(LP_ERR_INVALID_ARG, "trace_capacity must be >= 0");
+  return LP_OK;
+}
+
+// Resets Algorithm 1's counters on the device (status running).
+lp_status reset_state(lp_problem *h, cudaStream_t s) {
+  DevState hs{};
+  LP_CU(cudaMemcpyAsync(&hs, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  LP_CU(cudaStreamSynchronize(s));
+  hs.t0 = 0;
+  hs.iters = 0;
+  hs.checks = 0;
+  hs.restarts = 0;
+  hs.status = kRunning;
+  hs.returned = 0;
+  hs.restart_now = 0;
+  hs.use_cur = 0;
+  hs.rho_stored = NAN;
+  hs.last_rho = NAN;
+  hs.last_r = NAN;
+  for (int i = 0; i < 5; ++i) hs.kkt_a[i] = hs.kkt_c[i] = NAN;
+  hs.kkt_a[4] = hs.kkt_c[4] = INFINITY;
+  hs.ls[0].done = hs.ls[1].done = 1;
+  hs.trace_count = 0;
+  hs.given_radius = 0;
+  LP_CU(cudaMemcpyAsync(h->st, &hs, sizeof(DevState), cudaMemcpyHostToDevice, s));
+  LP_CU(cudaStreamSynchronize(s));
+  launch_weights(h->st, h->w, s);
+  LP_CU(cudaGetLastError());
+  return LP_OK;
+}
+
+lp_status build_graph(lp_problem *h) {
+  if (h->exec) return LP_OK;
+  cudaStream_t s = h->cap_stream;
+  LP_CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < h->opt.check_every; ++k) {
+    launch_primal_step(h->AT, h->v, h->st, h->w, k, s);
+    launch_dual_step(h->A, h->v, h->st, h->w, k, s);
+  }
+  launch_check(h->A, h->AT, h->v, h->st, h->w, h->cs, h->n, h->m, h->nsearch, h->trace, true, s);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  h->graph = g;
+  LP_CU(cudaGraphInstantiate(&h->exec, g, 0));
+  return LP_OK;
+}
+
+lp_status set_run_params(lp_problem *h, double tol, cudaStream_t s) {
+  // status <- running, tol <- tol (two small host-to-device copies)
+  const int32_t running = kRunning;
+  LP_CU(cudaMemcpyAsync(&h->st->tol, &tol, sizeof(double), cudaMemcpyHostToDevice, s));
+  LP_CU(cudaMemcpyAsync(&h->st->status, &running, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  return LP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lp_default_options(lp_options *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->beta = std::exp(-1.0);
+  o->check_every = 64;
+  o->restart_scheme = LP_RESTART_ADAPTIVE;
+  o->tau0 = 0;
+  o->fixed_len = 0;
+  o->omega = 1.0;
+  o->eta = 0.0;
+  o->power_iters = 5000;
+  o->power_tol = 1e-10;
+  o->max_iter = 10000000;
+  o->long_row_threshold = 512;
+  o->trace_capacity = 65536;
+}
+
+const char *lp_last_error(void) { return g_err.c_str(); }
+
+lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
+                    const int32_t *col_idx, const double *val, const double *c, const double *b,
+                    const double *lb, const double *ub, const int8_t *row_type,
+                    const lp_options *opt_in, void *cuda_stream, lp_handle *out) {
+  g_err.clear();
+  if (!out) return fail(LP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (m < 0 || n < 1) return fail(LP_ERR_INVALID_ARG, "need m >= 0 and n >= 1");
+  if (nnz < 0 || nnz >= (int64_t(1) << 31)) return fail(LP_ERR_INVALID_ARG, "nnz must lie in [0, 2^31)");
+  if (!row_ptr || !c || !lb || !ub || (m > 0 && (!b || !row_type)) ||
+      (nnz > 0 && (!col_idx || !val)))
+    return fail(LP_ERR_INVALID_ARG, "NULL array argument");
+  lp_options opt;
+  if (opt_in) opt = *opt_in;
+  else lp_default_options(&opt);
+  lp_status st = validate_options(opt);
+  if (st != LP_OK) return st;
+  if (opt.tau0 == 0) opt.tau0 = opt.check_every;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const double t_start = now_seconds();
+
+  // ---- copy in (host or device pointers) and validate
+  std::vector<int32_t> hrp32, hci;
+  std::vector<double> hv, hc, hb, hl, hu;
+  std::vector<int8_t> hrt;
+  LP_CU(cudaStreamSynchronize(s));
+  if (!copy_in(hrp32, row_ptr, (int64_t)m + 1) || !copy_in(hci, col_idx, nnz) ||
+      !copy_in(hv, val, nnz) || !copy_in(hc, c, n) || !copy_in(hb, b, m) || !copy_in(hl, lb, n) ||
+      !copy_in(hu, ub, n) || !copy_in(hrt, row_type, m)) {
+    cudaGetLastError();
+    return fail(LP_ERR_INVALID_ARG, "could not read an input array (bad pointer?)");
+  }
+  if (hrp32[0] != 0) return fail(LP_ERR_INVALID_ARG, "row_ptr[0] must be 0");
+  for (int32_t i = 0; i < m; ++i)
+    if (hrp32[i + 1] < hrp32[i]) return fail(LP_ERR_INVALID_ARG, "row_ptr must be nondecreasing");
+  if (hrp32[m] != nnz) return fail(LP_ERR_INVALID_ARG, "row_ptr[m] must equal nnz");
+  {
+    std::vector<int32_t> mark(n, -1);
+    for (int32_t i = 0; i < m; ++i) {
+      for (int64_t p = hrp32[i]; p < hrp32[i + 1]; ++p) {
+        const int32_t j = hci[p];
+        if (j < 0 || j >= n) return fail(LP_ERR_INVALID_ARG, "col_idx out of range");
+        if (mark[j] == i) return fail(LP_ERR_INVALID_ARG, "duplicate column in a row");
+        mark[j] = i;
+        if (!std::isfinite(hv[p])) return fail(LP_ERR_INVALID_ARG, "non-finite matrix value");
+      }
+    }
+  }
+  for (int32_t j = 0; j < n; ++j) {
+    if (!std::isfinite(hc[j])) return fail(LP_ERR_INVALID_ARG, "non-finite objective c");
+    if (std::isnan(hl[j]) || std::isnan(hu[j]) || hl[j] > hu[j] || hl[j] == INFINITY ||
+        hu[j] == -INFINITY)
+      return fail(LP_ERR_INVALID_ARG, "invalid bounds (need lb <= ub, lb < inf, ub > -inf)");
+  }
+  for (int32_t i = 0; i < m; ++i) {
+    if (!std::isfinite(hb[i])) return fail(LP_ERR_INVALID_ARG, "non-finite right-hand side b");
+    if (hrt[i] < LP_ROW_EQ || hrt[i] > LP_ROW_LE) return fail(LP_ERR_INVALID_ARG, "row_type must be 0, 1 or 2");
+  }
+
+  std::unique_ptr<lp_problem> h(new lp_problem());
+  h->m = m;
+  h->n = n;
+  h->nnz = nnz;
+  h->opt = opt;
+  LP_CU(cudaGetDevice(&h->device));
+  LP_CU(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device));
+  h->nsearch = (opt.restart_scheme == LP_RESTART_ADAPTIVE) ? 1
+               : (opt.restart_scheme == LP_RESTART_FLEXIBLE) ? 2 : 0;
+
+  // ---- CSC by stable counting sort, permutations, SELL layouts
+  std::vector<int64_t> rp(m + 1), cp(n + 1, 0);
+  for (int32_t i = 0; i <= m; ++i) rp[i] = hrp32[i];
+  for (int64_t p = 0; p < nnz; ++p) cp[hci[p] + 1]++;
+  for (int32_t j = 0; j < n; ++j) cp[j + 1] += cp[j];
+  std::vector<int32_t> ri(nnz);
+  std::vector<double> cv(nnz);
+  {
+    std::vector<int64_t> pos(cp.begin(), cp.end() - 1);
+    for (int32_t i = 0; i < m; ++i)
+      for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+        const int64_t q = pos[hci[p]]++;
+        ri[q] = i;
+        cv[q] = hv[p];
+      }
+  }
+  std::vector<int32_t> perm_y(m), perm_x(n), inv_y(m), inv_x(n);
+  for (int32_t i = 0; i < m; ++i) perm_y[i] = i;
+  for (int32_t j = 0; j < n; ++j) perm_x[j] = j;
+  std::stable_sort(perm_y.begin(), perm_y.end(),
+                   [&](int32_t a, int32_t bb) { return rp[a + 1] - rp[a] > rp[bb + 1] - rp[bb]; });
+  std::stable_sort(perm_x.begin(), perm_x.end(),
+                   [&](int32_t a, int32_t bb) { return cp[a + 1] - cp[a] > cp[bb + 1] - cp[bb]; });
+  for (int32_t r = 0; r < m; ++r) inv_y[perm_y[r]] = r;
+  for (int32_t r = 0; r < n; ++r) inv_x[perm_x[r]] = r;
+  HostSell HA, HAT;
+  build_sell(m, n, rp, hci, hv, perm_y, inv_x, opt.long_row_threshold, HA);
+  build_sell(n, m, cp, ri, cv, perm_x, inv_y, opt.long_row_threshold, HAT);
+  h->nnz_padded = (int64_t)HA.idx.size() + (int64_t)HA.long_idx.size();
+
+  // permuted vectors
+  std::vector<double> pc(n), pl(n), pu(n), pb(m);
+  std::vector<int8_t> prt(m);
+  for (int32_t r = 0; r < n; ++r) {
+    pc[r] = hc[perm_x[r]];
+    pl[r] = hl[perm_x[r]];
+    pu[r] = hu[perm_x[r]];
+  }
+  for (int32_t r = 0; r < m; ++r) {
+    pb[r] = hb[perm_y[r]];
+    prt[r] = hrt[perm_y[r]];
+  }
+
+  // ---- device buffers
+  lp_status e;
+  if ((e = h->upload_sell(HA, h->A)) != LP_OK) return e;
+  if ((e = h->upload_sell(HAT, h->AT)) != LP_OK) return e;
+  if ((e = h->upload(&h->v.c, pc)) != LP_OK) return e;
+  if ((e = h->upload(&h->v.lb, pl)) != LP_OK) return e;
+  if ((e = h->upload(&h->v.ub, pu)) != LP_OK) return e;
+  if ((e = h->upload(&h->v.b, pb)) != LP_OK) return e;
+  if ((e = h->upload(&h->v.row_type, prt)) != LP_OK) return e;
+  if ((e = h->upload(&h->perm_x, perm_x)) != LP_OK) return e;
+  if ((e = h->upload(&h->perm_y, perm_y)) != LP_OK) return e;
+  double **xs[] = {&h->v.x, &h->v.xhat, &h->v.xbar, &h->v.x0};
+  for (double **p : xs)
+    if ((e = h->alloc(p, n)) != LP_OK) return e;
+  double **ys[] = {&h->v.y, &h->v.ybar, &h->v.y0};
+  for (double **p : ys)
+    if ((e = h->alloc(p, m)) != LP_OK) return e;
+  if ((e = h->alloc(&h->tmp, std::max(n, m))) != LP_OK) return e;
+  if ((e = h->alloc(&h->st, 1)) != LP_OK) return e;
+  if ((e = h->alloc(&h->w, opt.check_every)) != LP_OK) return e;
+  if ((e = h->alloc(&h->trace, (int64_t)6 * std::max(1, opt.trace_capacity))) != LP_OK) return e;
+
+  // check scratch
+  CheckScratch &cs = h->cs;
+  cs.cols_grid = check_grid_for(h->AT, h->nsm);
+  cs.rows_grid = check_grid_for(h->A, h->nsm);
+  cs.pstride = std::max(cs.cols_grid + cs.rows_grid, 8 * h->nsm);
+  if ((e = h->alloc(&cs.partials, (int64_t)NQ * cs.pstride)) != LP_OK) return e;
+  const int64_t N = (int64_t)n + m;
+  for (int k = 0; k < 2; ++k) {
+    if (k == 1 && h->nsearch < 2) {
+      cs.keys[1] = cs.keys[0];
+      cs.d2[1] = cs.d2[0];
+      cs.g2[1] = cs.g2[0];
+      cs.gd[1] = cs.gd[0];
+      break;
+    }
+    if ((e = h->alloc(&cs.keys[k], N)) != LP_OK) return e;
+    if ((e = h->alloc(&cs.d2[k], N)) != LP_OK) return e;
+    if ((e = h->alloc(&cs.g2[k], N)) != LP_OK) return e;
+    if ((e = h->alloc(&cs.gd[k], N)) != LP_OK) return e;
+  }
+  cs.hist_grid = (int)std::min<int64_t>(std::max<int64_t>(1, (N + 4095) / 4096), 2 * h->nsm);
+  if ((e = h->alloc(&cs.hpart, (int64_t)2 * cs.hist_grid * 4 * kBuckets)) != LP_OK) return e;
+  LP_CU(cudaMallocHost(&h->h_status, 2 * sizeof(int32_t)));
+  LP_CU(cudaEventCreateWithFlags(&h->ev[0], cudaEventDisableTiming));
+  LP_CU(cudaEventCreateWithFlags(&h->ev[1], cudaEventDisableTiming));
+  LP_CU(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+
+  // ---- device state: step sizes, norms, power iteration
+  DevState hs{};
+  hs.omega = opt.omega;
+  hs.beta = opt.beta;
+  hs.tol = 1e-8;
+  hs.K = opt.check_every;
+  hs.scheme = opt.restart_scheme;
+  hs.tau0 = opt.tau0;
+  hs.fixed_len = opt.fixed_len;
+  hs.status = kRunning;
+  hs.trace_cap = opt.trace_capacity;
+  hs.pw_tol = opt.power_tol;
+  hs.pw_max = opt.power_iters;
+  LP_CU(cudaMemcpy(h->st, &hs, sizeof(DevState), cudaMemcpyHostToDevice));
+  const int rgrid = std::min(std::max(1, (int)((std::max(n, m) + kBlock - 1) / kBlock)), 8 * h->nsm);
+  launch_norms(h->v, h->st, cs.partials, cs.pstride, rgrid, n, m, s);
+  LP_CU(cudaGetLastError());
+  if (opt.eta > 0.0) {
+    h->eta = opt.eta;
+  } else {
+    // Section 7: eta = 0.9 / sigma_max(A), sigma_max by power iteration
+    double *pv = h->v.x, *pav = h->v.y, *pw = h->v.xhat;
+    launch_fill(pv, 1.0 / std::sqrt((double)n), n, s);
+    const int chunk = 25;
+    for (int it = 0; it < opt.power_iters; it += chunk) {
+      for (int k = 0; k < chunk; ++k)
+        launch_power_iteration_step(h->A, h->AT, pv, pav, pw, h->st, cs.partials, cs.pstride,
+                                    rgrid, n, m, s);
+      LP_CU(cudaGetLastError());
+      int32_t done = 0;
+      LP_CU(cudaMemcpyAsync(&done, &h->st->pw_done, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      LP_CU(cudaStreamSynchronize(s));
+      if (done) break;
+    }
+    double est = 0.0;
+    LP_CU(cudaMemcpyAsync(&est, &h->st->pw_est, sizeof(double), cudaMemcpyDeviceToHost, s));
+    LP_CU(cudaStreamSynchronize(s));
+    h->sigma_max = std::sqrt(est);
+    if (!(h->sigma_max > 0.0)) return fail(LP_ERR_NUMERICAL, "sigma_max(A) is zero or not finite; pass eta explicitly");
+    h->eta = 0.9 / h->sigma_max;
+  }
+  const double tau = h->eta / opt.omega, sigma = h->eta * opt.omega;
+  LP_CU(cudaMemcpyAsync(&h->st->tau, &tau, sizeof(double), cudaMemcpyHostToDevice, s));
+  LP_CU(cudaMemcpyAsync(&h->st->sigma, &sigma, sizeof(double), cudaMemcpyHostToDevice, s));
+  // z^{0,0} = proj(0)
+  launch_fill(h->v.x, 0.0, n, s);
+  launch_fill(h->v.y, 0.0, m, s);
+  launch_project(h->v, n, m, s);
+  LP_CU(cudaGetLastError());
+  if ((e = reset_state(h.get(), s)) != LP_OK) return e;
+  LP_CU(cudaStreamSynchronize(s));
+  (void)t_start;
+  *out = h.release();
+  return LP_OK;
+}
+
+lp_status lp_set_state(lp_handle h, const double *x, const double *y, void *cuda_stream) {
+  g_err.clear();
+  if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (x) {
+    LP_CU(cudaMemcpyAsync(h->tmp, x, sizeof(double) * h->n, cudaMemcpyDefault, s));
+    launch_gather(h->v.x, h->tmp, h->perm_x, h->n, s);
+  } else {
+    launch_fill(h->v.x, 0.0, h->n, s);
+  }
+  if (y) {
+    LP_CU(cudaMemcpyAsync(h->tmp, y, sizeof(double) * h->m, cudaMemcpyDefault, s));
+    launch_gather(h->v.y, h->tmp, h->perm_y, h->m, s);
+  } else {
+    launch_fill(h->v.y, 0.0, h->m, s);
+  }
+  launch_project(h->v, h->n, h->m, s);
+  LP_CU(cudaGetLastError());
+  h->solved = false;
+  return reset_state(h, s);
+}
+
+lp_status lp_iterate(lp_handle h, int32_t n_checks, double tol, void *cuda_stream) {
+  g_err.clear();
+  if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
+  if (!(tol > 0.0)) return fail(LP_ERR_INVALID_ARG, "tol must be > 0");
+  if (n_checks < 0) return fail(LP_ERR_INVALID_ARG, "n_checks must be >= 0");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  lp_status e = build_graph(h);
+  if (e != LP_OK) return e;
+  if ((e = set_run_params(h, tol, s)) != LP_OK) return e;
+  for (int32_t i = 0; i < n_checks; ++i) LP_CU(cudaGraphLaunch(h->exec, s));
+  h->solved = true;
+  return LP_OK;
+}
+
+lp_status lp_solve(lp_handle h, double tol, void *cuda_stream) {
+  g_err.clear();
+  if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
+  if (!(tol > 0.0)) return fail(LP_ERR_INVALID_ARG, "tol must be > 0");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  lp_status e = build_graph(h);
+  if (e != LP_OK) return e;
+  if ((e = set_run_params(h, tol, s)) != LP_OK) return e;
+  const int K = h->opt.check_every;
+  int64_t remaining = h->opt.max_iter;
+  int32_t status = kRunning;
+  int inflight = 0, head = 0;  // ring of two (event, status slot)
+  while (true) {
+    while (inflight < 2 && remaining >= K) {
+      const int slot = (head + inflight) & 1;
+      LP_CU(cudaGraphLaunch(h->exec, s));
+      LP_CU(cudaMemcpyAsync(&h->h_status[slot], &h->st->status, sizeof(int32_t),
+                            cudaMemcpyDeviceToHost, s));
+      LP_CU(cudaEventRecord(h->ev[slot], s));
+      remaining -= K;
+      ++inflight;
+    }
+    if (inflight == 0) break;
+    LP_CU(cudaEventSynchronize(h->ev[head]));
+    status = h->h_status[head];
+    head ^= 1;
+    --inflight;
+    if (status != kRunning) break;
+  }
+  LP_CU(cudaStreamSynchronize(s));
+  if (status == kRunning && remaining > 0) {
+    const int r = (int)remaining;
+    for (int k = 0; k < r; ++k) {
+      launch_primal_step(h->AT, h->v, h->st, h->w, k, s);
+      launch_dual_step(h->A, h->v, h->st, h->w, k, s);
+    }
+    launch_advance(h->st, h->w, r, s);
+    LP_CU(cudaGetLastError());
+  }
+  LP_CU(cudaMemcpyAsync(&status, &h->st->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  LP_CU(cudaStreamSynchronize(s));
+  h->solved = true;
+  if (status == kRunning) return fail(LP_ITER_LIMIT, "iteration limit reached");
+  if (status == LP_ERR_NUMERICAL) return fail(LP_ERR_NUMERICAL, "NaN or Inf in the iterates or residuals");
+  return static_cast<lp_status>(status);
+}
+
+lp_status lp_get_solution(lp_handle h, double *x, double *y, void *cuda_stream) {
+  g_err.clear();
+  if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
+  if (!h->solved) return fail(LP_ERR_NOT_SOLVED, "no solve has run on this handle");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  int32_t returned = 0;
+  LP_CU(cudaMemcpyAsync(&returned, &h->st->returned, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  LP_CU(cudaStreamSynchronize(s));
+  if (x) {
+    launch_scatter(h->tmp, returned ? h->v.x : h->v.xbar, h->perm_x, h->n, s);
+    LP_CU(cudaMemcpyAsync(x, h->tmp, sizeof(double) * h->n, cudaMemcpyDefault, s));
+  }
+  if (y) {
+    LP_CU(cudaStreamSynchronize(s));
+    launch_scatter(h->tmp, returned ? h->v.y : h->v.ybar, h->perm_y, h->m, s);
+    LP_CU(cudaMemcpyAsync(y, h->tmp, sizeof(double) * h->m, cudaMemcpyDefault, s));
+  }
+  LP_CU(cudaGetLastError());
+  LP_CU(cudaStreamSynchronize(s));
+  return LP_OK;
+}
+
+lp_status lp_get_state(lp_handle h, double *x, double *y, double *xbar, double *ybar, double *x0,
+                       double *y0, void *cuda_stream) {
+  g_err.clear();
+  if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  struct Item { double *dst; const double *src; const int32_t *perm; int32_t len; };
+  const Item items[] = {{x, h->v.x, h->perm_x, h->n},       {y, h->v.y, h->perm_y, h->m},
+                        {xbar, h->v.xbar, h->perm_x, h->n}, {ybar, h->v.ybar, h->perm_y, h->m},
+                        {x0, h->v.x0, h->perm_x, h->n},     {y0, h->v.y0, h->perm_y, h->m}};
+  for (const Item &it : items) {
+    if (!it.dst) continue;
+    launch_scatter(h->tmp, it.src, it.perm, it.len, s);
+    LP_CU(cudaMemcpyAsync(it.dst, h->tmp, sizeof(double) * it.len, cudaMemcpyDefault, s));
+    LP_CU(cudaStreamSynchronize(s));
+  }
+  LP_CU(cudaGetLastError());
+  return LP_OK;
+}
+
+lp_status lp_get_info(lp_handle h, lp_info *info) {
+  g_err.clear();
+  if (!h || !info) return fail(LP_ERR_INVALID_ARG, "NULL argument");
+  DevState hs{};
+  LP_CU(cudaMemcpy(&hs, h->st, sizeof(DevState), cudaMemcpyDeviceToHost));
+  std::memset(info, 0, sizeof(*info));
+  info->iters = hs.iters;
+  info->restarts = hs.restarts;
+  info->checks = hs.checks;
+  info->status = (hs.status == kRunning) ? (h->solved ? LP_ITER_LIMIT : LP_ERR_NOT_SOLVED) : hs.status;
+  info->returned = hs.returned;
+  for (int i = 0; i < 5; ++i) {
+    info->kkt_avg[i] = hs.kkt_a[i];
+    info->kkt_cur[i] = hs.kkt_c[i];
+  }
+  info->eta = h->eta;
+  info->sigma_max = h->sigma_max;
+  info->omega = hs.omega;
+  info->tau = hs.tau;
+  info->sigma = hs.sigma;
+  info->rho_stored = hs.rho_stored;
+  info->last_rho = hs.last_rho;
+  info->last_radius = hs.last_r;
+  info->nnz_padded = h->nnz_padded;
+  info->n_long_rows = h->A.nlong;
+  info->n_long_cols = h->AT.nlong;
+  return LP_OK;
+}
+
+lp_status lp_get_trace(lp_handle h, double *rows, int64_t capacity, int64_t *count) {
+  g_err.clear();
+  if (!h || !count || (capacity > 0 && !rows)) return fail(LP_ERR_INVALID_ARG, "NULL argument");
+  int64_t tc = 0;
+  LP_CU(cudaMemcpy(&tc, &h->st->trace_count, sizeof(int64_t), cudaMemcpyDeviceToHost));
+  tc = std::min<int64_t>(tc, h->opt.trace_capacity);
+  const int64_t k = std::min(tc, capacity);
+  if (k > 0) LP_CU(cudaMemcpy(rows, h->trace, sizeof(double) * 6 * k, cudaMemcpyDeviceToHost));
+  *count = k;
+  return LP_OK;
+}
+
+lp_status lp_normalized_gap(lp_handle h, const double *x, const double *y, double r,
+                            double *host_rho, void *cuda_stream) {
+  g_err.clear();
+  if (!h || !host_rho || !x || (h->m > 0 && !y)) return fail(LP_ERR_INVALID_ARG, "NULL argument");
+  if (!(r >= 0.0) || !std::isfinite(r)) return fail(LP_ERR_INVALID_ARG, "radius must be finite and >= 0");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const int n = h->n, m = h->m;
+  const int64_t N = (int64_t)n + m;
+  // scratch owned by this call
+  std::vector<void *> mine;
+  struct Guard {
+    std::vector<void *> &v;
+    ~Guard() { for (void *p : v) cudaFree(p); }
+  } guard{mine};
+  auto get = [&](size_t bytes) -> void * {
+    void *p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) return nullptr;
+    mine.push_back(p);
+    return p;
+  };
+  DevVecs v = h->v;
+  double *xp = (double *)get(sizeof(double) * n), *yp = (double *)get(sizeof(double) * std::max(m, 1));
+  DevState *st = (DevState *)get(sizeof(DevState));
+  CheckScratch cs = h->cs;
+  cs.partials = (double *)get(sizeof(double) * NQ * cs.pstride);
+  cs.keys[0] = (uint64_t *)get(sizeof(uint64_t) * N);
+  cs.d2[0] = (double *)get(sizeof(double) * N);
+  cs.g2[0] = (double *)get(sizeof(double) * N);
+  cs.gd[0] = (double *)get(sizeof(double) * N);
+  cs.keys[1] = cs.keys[0];
+  cs.d2[1] = cs.d2[0];
+  cs.g2[1] = cs.g2[0];
+  cs.gd[1] = cs.gd[0];
+  cs.hpart = (double *)get(sizeof(double) * 2 * cs.hist_grid * 4 * kBuckets);
+  double *tmpx = (double *)get(sizeof(double) * std::max(n, m));
+  if (!xp || !yp || !st || !cs.partials || !cs.keys[0] || !cs.d2[0] || !cs.g2[0] || !cs.gd[0] ||
+      !cs.hpart || !tmpx) {
+    cudaGetLastError();
+    return fail(LP_ERR_OOM, "cudaMalloc of gap scratch failed");
+  }
+  LP_CU(cudaMemcpyAsync(tmpx, x, sizeof(double) * n, cudaMemcpyDefault, s));
+  launch_gather(xp, tmpx, h->perm_x, n, s);
+  if (m > 0) {
+    LP_CU(cudaMemcpyAsync(tmpx, y, sizeof(double) * m, cudaMemcpyDefault, s));
+    launch_gather(yp, tmpx, h->perm_y, m, s);
+  }
+  v.x = v.xbar = v.x0 = xp;
+  v.y = v.ybar = v.y0 = yp;
+  DevState hs{};
+  LP_CU(cudaMemcpyAsync(&hs, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  LP_CU(cudaStreamSynchronize(s));
+  hs.status = kRunning;
+  hs.given_radius = 1;
+  hs.r_given = r;
+  LP_CU(cudaMemcpyAsync(st, &hs, sizeof(DevState), cudaMemcpyHostToDevice, s));
+  LP_CU(cudaStreamSynchronize(s));
+  launch_check(h->A, h->AT, v, st, nullptr, cs, n, m, 1, nullptr, false, s);
+  LP_CU(cudaGetLastError());
+  LSearch L{};
+  LP_CU(cudaMemcpyAsync(&L, &st->ls[0], sizeof(LSearch), cudaMemcpyDeviceToHost, s));
+  LP_CU(cudaStreamSynchronize(s));
+  *host_rho = (r == 0.0) ? 0.0 : L.rho_r / r;
+  return LP_OK;
+}
+
+lp_status lp_profile_kernel(lp_handle h, int32_t which, int32_t reps, void *cuda_stream) {
+  g_err.clear();
+  if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
+  if (which < 0 || which > 1 || reps < 0) return fail(LP_ERR_INVALID_ARG, "which must be 0 or 1, reps >= 0");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  for (int32_t r = 0; r < reps; ++r) {
+    if (which == 0) launch_primal_step(h->AT, h->v, h->st, h->w, 0, s);
+    else launch_dual_step(h->A, h->v, h->st, h->w, 0, s);
+  }
+  LP_CU(cudaGetLastError());
+  return LP_OK;
+}
+
+void lp_destroy(lp_handle h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  delete h;
+}
+
+}  // extern "C"

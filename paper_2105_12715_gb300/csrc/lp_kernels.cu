@@ -1,0 +1,971 @@
+// Device code of liblp.so: the restarted-PDHG hot path for sm_103a.
+//
+// Per iteration (Eq. PDHG-update, tau = eta/omega, sigma = eta*omega):
+//   primal_kernel: column pass over A^T (SELL-32 layout, gathers y)
+//       x+ = clamp(x - tau (c - A^T y), l, u), xhat = 2 x+ - x,
+//       xbar += w_t (x+ - xbar)                     (Algorithm 1, average)
+//   dual_kernel:   row pass over A (SELL-32 layout, gathers xhat)
+//       y+ = proj_Y(y + sigma (b - A xhat)),  ybar += w_t (y+ - ybar)
+// Every K iterations, the check (Section 7: restart and termination tests):
+//   check_cols / check_rows: A^T [ybar, y] and A [xbar, x] with fused
+//       epilogues for the KKT residuals, the radius ||zbar - z^{n,0}|| and
+//       the breakpoints of the linear trust region (Section 6.3);
+//   check_finalize: fixed-order reduction, relative KKT, termination;
+//   hist / select (x8): search for the trust-region multiplier lambda* over
+//       the bit patterns of the breakpoints, 8 bits per pass;
+//   check_decide: normalized gap rho = (sum_clamped |g| d + lambda* f_hi)/r,
+//       restart rule of Eq. (adaptive-restart-scheme), next averaging weights;
+//   restart_copy: z^{n+1,0} <- zbar and z <- zbar on restart.
+// All reductions run in a fixed order, so results are bitwise reproducible
+// for a given problem and launch configuration.
+#include <cmath>
+#include <cstdint>
+
+#include "lp_internal.h"
+
+namespace lpg {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kStatusOK = 0;
+constexpr int kStatusNumerical = 5;
+constexpr int kSchemeFixed = 1, kSchemeAdaptive = 2, kSchemeFlexible = 3;
+
+__device__ __forceinline__ double sq(double v) { return v * v; }
+
+// ------------------------------------------------------------------ SpMV core
+//
+// Row sums of one work item of a SellMat: a long row (whole warp, lanes
+// stride over the row, butterfly reduction) or a slice of 32 rows (one
+// lane per row, sequential in the row's stored order).  NV = 1 or 2
+// gathered vectors.  The epilogue's operands are loaded before the row
+// loop so that their latency overlaps the matrix stream.
+template <int NV, class Epi>
+__device__ __forceinline__ void process_item(const SellMat &A,
+                                             const double *__restrict__ v0,
+                                             const double *__restrict__ v1,
+                                             int item, int lane, Epi &epi) {
+  if (item < A.nlong) {
+    const int64_t s = A.long_ptr[item], e = A.long_ptr[item + 1];
+    typename Epi::Pre pre{};
+    if (lane == 0) pre = epi.load(item);
+    double a0 = 0.0, a1 = 0.0;
+    for (int64_t p = s + lane; p < e; p += kWarp) {
+      const int32_t j = __ldcs(A.long_idx + p);
+      const double a = __ldcs(A.long_val + p);
+      a0 = fma(a, __ldg(v0 + j), a0);
+      if (NV == 2) a1 = fma(a, __ldg(v1 + j), a1);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a0 += __shfl_xor_sync(kFull, a0, o);
+      if (NV == 2) a1 += __shfl_xor_sync(kFull, a1, o);
+    }
+    if (lane == 0) epi.store(item, a0, a1, pre);
+    return;
+  }
+  const int s = item - A.nlong;
+  const int row = A.nlong + s * kWarp + lane;
+  const bool valid = row < A.nrows;
+  typename Epi::Pre pre{};
+  if (valid) pre = epi.load(row);
+  const int64_t base = A.slice_ptr[s];
+  const int len = (int)((A.slice_ptr[s + 1] - base) >> 5);
+  const int32_t *ip = A.idx + base + lane;
+  const double *vp = A.val + base + lane;
+  double a0 = 0.0, a1 = 0.0;
+  int k = 0;
+  for (; k + 4 <= len; k += 4) {
+    const int32_t j0 = __ldcs(ip), j1 = __ldcs(ip + 32), j2 = __ldcs(ip + 64),
+                  j3 = __ldcs(ip + 96);
+    const double c0 = __ldcs(vp), c1 = __ldcs(vp + 32), c2 = __ldcs(vp + 64),
+                 c3 = __ldcs(vp + 96);
+    const double g0 = __ldg(v0 + j0), g1 = __ldg(v0 + j1), g2 = __ldg(v0 + j2),
+                 g3 = __ldg(v0 + j3);
+    if (NV == 2) {
+      const double h0 = __ldg(v1 + j0), h1 = __ldg(v1 + j1), h2 = __ldg(v1 + j2),
+                   h3 = __ldg(v1 + j3);
+      a1 = fma(c0, h0, a1);
+      a1 = fma(c1, h1, a1);
+      a1 = fma(c2, h2, a1);
+      a1 = fma(c3, h3, a1);
+    }
+    a0 = fma(c0, g0, a0);
+    a0 = fma(c1, g1, a0);
+    a0 = fma(c2, g2, a0);
+    a0 = fma(c3, g3, a0);
+    ip += 4 * kWarp;
+    vp += 4 * kWarp;
+  }
+  for (; k < len; ++k) {
+    const int32_t j = __ldcs(ip);
+    const double c = __ldcs(vp);
+    a0 = fma(c, __ldg(v0 + j), a0);
+    if (NV == 2) a1 = fma(c, __ldg(v1 + j), a1);
+    ip += kWarp;
+    vp += kWarp;
+  }
+  if (valid) epi.store(row, a0, a1, pre);
+}
+
+template <int NV, class Epi>
+__device__ __forceinline__ void process_all(const SellMat &A, const double *v0,
+                                            const double *v1, Epi &epi) {
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)(gridDim.x * blockDim.x) >> 5;
+  const int items = A.nlong + A.nslices;
+  for (int it = warp; it < items; it += nwarps) process_item<NV>(A, v0, v1, it, lane, epi);
+}
+
+// Fixed-order block reduction of NV2 per-thread values; thread q < NV2 of
+// the block writes the block's value q to partials[q * pstride + col].
+template <int NV2>
+__device__ __forceinline__ void block_reduce_store(const double (&q)[NV2], double *partials,
+                                                   int pstride, int col) {
+  __shared__ double sh[kBlock / kWarp][NV2];
+  const int lane = threadIdx.x & (kWarp - 1), warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV2; ++i) {
+    double v = q[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    if (lane == 0) sh[warp][i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV2) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w][threadIdx.x];
+    partials[(size_t)threadIdx.x * pstride + col] = s;
+  }
+}
+
+// -------------------------------------------------------------- epilogues
+
+// Eq. (PDHG-update), primal half, and Algorithm 1's running average.
+struct PrimalEpi {
+  const double *__restrict__ c;
+  const double *__restrict__ lb;
+  const double *__restrict__ ub;
+  double *x, *xhat, *xbar;
+  double tau, w;
+  struct Pre { double c, lb, ub, x, xb; };
+  __device__ __forceinline__ Pre load(int j) const { return {c[j], lb[j], ub[j], x[j], xbar[j]}; }
+  __device__ __forceinline__ void store(int j, double aty, double, const Pre &p) const {
+    const double g = p.c - aty;
+    const double xn = fmin(fmax(fma(-tau, g, p.x), p.lb), p.ub);
+    x[j] = xn;
+    xhat[j] = fma(2.0, xn, -p.x);
+    xbar[j] = fma(w, xn - p.xb, p.xb);
+  }
+};
+
+// Eq. (PDHG-update), dual half: projection onto Y_i by row sense.
+struct DualEpi {
+  const double *__restrict__ b;
+  const int8_t *__restrict__ rt;
+  double *y, *ybar;
+  double sigma, w;
+  struct Pre { double b, y, yb; int t; };
+  __device__ __forceinline__ Pre load(int i) const { return {b[i], y[i], ybar[i], (int)rt[i]}; }
+  __device__ __forceinline__ void store(int i, double ax, double, const Pre &p) const {
+    double yn = fma(sigma, p.b - ax, p.y);
+    if (p.t == 1) yn = fmax(yn, 0.0);
+    else if (p.t == 2) yn = fmin(yn, 0.0);
+    y[i] = yn;
+    ybar[i] = fma(w, yn - p.yb, p.yb);
+  }
+};
+
+struct StoreEpi {
+  double *out;
+  struct Pre {};
+  __device__ __forceinline__ Pre load(int) const { return {}; }
+  __device__ __forceinline__ void store(int r, double a, double, const Pre &) const { out[r] = a; }
+};
+
+// One coordinate of the linear trust region of Section 6.3 in the
+// omega-rescaled space: objective component G, distance dist >= 0 to the
+// bound it moves toward (INFINITY if none), scales sd (distance) and sg
+// (objective).  Breakpoint lambda_hat = d / g; its bit pattern is the key.
+struct GapOut {
+  uint64_t *keys;
+  double *d2, *g2, *gd;
+};
+
+__device__ __forceinline__ void gap_elem(double G, double dist, double sd, double sg, int64_t e,
+                                         const GapOut &o, double &sum_d2, double &sum_gd,
+                                         double &sum_g2inf) {
+  uint64_t key = kNoKey;
+  if (G != 0.0) {
+    const double g = fabs(G) * sg;
+    if (isinf(dist)) {
+      sum_g2inf += g * g;
+    } else {
+      const double d = dist * sd;
+      const double lam = d / g;
+      if (isinf(lam)) {
+        sum_g2inf += g * g;
+      } else {
+        key = (uint64_t)__double_as_longlong(lam);
+        const double vd2 = d * d, vg2 = g * g, vgd = d * g;
+        sum_d2 += vd2;
+        sum_gd += vgd;
+        o.d2[e] = vd2;
+        o.g2[e] = vg2;
+        o.gd[e] = vgd;
+      }
+    }
+  }
+  o.keys[e] = key;
+}
+
+// Check epilogue over columns (x-space): reduced costs lam = c - A^T y for
+// both candidates, dual residual, dual-objective bound terms, primal
+// objective, and the x-part of the trust region with F_x = lam.
+struct CheckColsEpi {
+  const double *__restrict__ c;
+  const double *__restrict__ lb;
+  const double *__restrict__ ub;
+  const double *__restrict__ xbar;
+  const double *__restrict__ x;
+  const double *__restrict__ x0;
+  GapOut ga, gc;
+  double sw, isw;
+  int gap_a, gap_c;
+  double q[NQ];
+  struct Pre { double c, lb, ub, xb, x, x0; };
+  __device__ __forceinline__ Pre load(int j) const {
+    return {c[j], lb[j], ub[j], xbar[j], x[j], x0[j]};
+  }
+  __device__ __forceinline__ void store(int j, double aty_a, double aty_c, const Pre &p) {
+    const bool lf = p.lb > -INFINITY, uf = p.ub < INFINITY;
+    // Lambda_j: {0} free, [0,inf) only l finite, (-inf,0] only u finite, R both
+    const double lo = uf ? -INFINITY : 0.0;
+    const double hi = lf ? INFINITY : 0.0;
+    const double lam_a = p.c - aty_a, lam_c = p.c - aty_c;
+    const double lt_a = fmin(fmax(lam_a, lo), hi), lt_c = fmin(fmax(lam_c, lo), hi);
+    q[Q_RD2_A] += sq(lam_a - lt_a);
+    q[Q_RD2_C] += sq(lam_c - lt_c);
+    if (lf && lt_a > 0.0) q[Q_DOBJ_A] += p.lb * lt_a;
+    if (uf && lt_a < 0.0) q[Q_DOBJ_A] += p.ub * lt_a;
+    if (lf && lt_c > 0.0) q[Q_DOBJ_C] += p.lb * lt_c;
+    if (uf && lt_c < 0.0) q[Q_DOBJ_C] += p.ub * lt_c;
+    q[Q_POBJ_A] += p.c * p.xb;
+    q[Q_POBJ_C] += p.c * p.x;
+    if (!(isfinite(lam_a) && isfinite(lam_c) && isfinite(p.xb) && isfinite(p.x))) q[Q_BAD] += 1.0;
+    if (gap_a) {
+      const double dx = p.xb - p.x0;
+      q[Q_RRX_A] += dx * dx;
+      double dist = INFINITY;
+      if (lam_a > 0.0 && lf) dist = fmax(p.xb - p.lb, 0.0);
+      if (lam_a < 0.0 && uf) dist = fmax(p.ub - p.xb, 0.0);
+      gap_elem(lam_a, dist, sw, isw, j, ga, q[Q_D2_A], q[Q_GD_A], q[Q_G2INF_A]);
+    }
+    if (gap_c) {
+      const double dx = p.x - p.x0;
+      q[Q_RRX_C] += dx * dx;
+      double dist = INFINITY;
+      if (lam_c > 0.0 && lf) dist = fmax(p.x - p.lb, 0.0);
+      if (lam_c < 0.0 && uf) dist = fmax(p.ub - p.x, 0.0);
+      gap_elem(lam_c, dist, sw, isw, j, gc, q[Q_D2_C], q[Q_GD_C], q[Q_G2INF_C]);
+    }
+  }
+};
+
+// Check epilogue over rows (y-space): primal residual by row sense, b^T y,
+// and the y-part of the trust region with F_y = A x - b.
+struct CheckRowsEpi {
+  const double *__restrict__ b;
+  const int8_t *__restrict__ rt;
+  const double *__restrict__ ybar;
+  const double *__restrict__ y;
+  const double *__restrict__ y0;
+  GapOut ga, gc;
+  double sw, isw;
+  int64_t off;  // element offset of the y-part in the search arrays (= n)
+  int gap_a, gap_c;
+  double q[NQ];
+  struct Pre { double b, yb, y, y0; int t; };
+  __device__ __forceinline__ Pre load(int i) const { return {b[i], ybar[i], y[i], y0[i], (int)rt[i]}; }
+  __device__ __forceinline__ void store(int i, double ax_a, double ax_c, const Pre &p) {
+    double va = ax_a - p.b, vc = ax_c - p.b;
+    if (p.t == 1) { va = fmin(va, 0.0); vc = fmin(vc, 0.0); }
+    if (p.t == 2) { va = fmax(va, 0.0); vc = fmax(vc, 0.0); }
+    q[Q_RP2_A] += va * va;
+    q[Q_RP2_C] += vc * vc;
+    q[Q_DOBJ_A] += p.b * p.yb;
+    q[Q_DOBJ_C] += p.b * p.y;
+    if (!(isfinite(ax_a) && isfinite(ax_c) && isfinite(p.yb) && isfinite(p.y))) q[Q_BAD] += 1.0;
+    if (gap_a) {
+      const double G = ax_a - p.b;
+      const double dy = p.yb - p.y0;
+      q[Q_RRY_A] += dy * dy;
+      double dist = INFINITY;
+      if (G > 0.0 && p.t == 1) dist = fmax(p.yb, 0.0);
+      if (G < 0.0 && p.t == 2) dist = fmax(-p.yb, 0.0);
+      gap_elem(G, dist, isw, sw, off + i, ga, q[Q_D2_A], q[Q_GD_A], q[Q_G2INF_A]);
+    }
+    if (gap_c) {
+      const double G = ax_c - p.b;
+      const double dy = p.y - p.y0;
+      q[Q_RRY_C] += dy * dy;
+      double dist = INFINITY;
+      if (G > 0.0 && p.t == 1) dist = fmax(p.y, 0.0);
+      if (G < 0.0 && p.t == 2) dist = fmax(-p.y, 0.0);
+      gap_elem(G, dist, isw, sw, off + i, gc, q[Q_D2_C], q[Q_GD_C], q[Q_G2INF_C]);
+    }
+  }
+};
+
+// ------------------------------------------------------------ iteration
+
+__global__ void __launch_bounds__(kBlock) primal_kernel(SellMat AT, const double *__restrict__ y,
+                                                        PrimalEpi epi, const DevState *st,
+                                                        const double *__restrict__ w, int k) {
+  if (st->status != kRunning) return;
+  epi.tau = st->tau;
+  epi.w = w[k];
+  process_all<1>(AT, y, nullptr, epi);
+}
+
+__global__ void __launch_bounds__(kBlock) dual_kernel(SellMat A, const double *__restrict__ xhat,
+                                                      DualEpi epi, const DevState *st,
+                                                      const double *__restrict__ w, int k) {
+  if (st->status != kRunning) return;
+  epi.sigma = st->sigma;
+  epi.w = w[k];
+  process_all<1>(A, xhat, nullptr, epi);
+}
+
+__global__ void __launch_bounds__(kBlock) spmv_kernel(SellMat A, const double *__restrict__ v,
+                                                      StoreEpi epi, const DevState *st) {
+  if (st && (st->status != kRunning || st->pw_done)) return;
+  process_all<1>(A, v, nullptr, epi);
+}
+
+// ---------------------------------------------------------------- check
+
+template <class Epi>
+__global__ void __launch_bounds__(kBlock) check_kernel(SellMat A, const double *__restrict__ v0,
+                                                       const double *__restrict__ v1, Epi epi,
+                                                       const DevState *st, double *partials,
+                                                       int pstride, int poff) {
+  if (st->status != kRunning) return;
+  if (!st->given_radius) {
+    epi.gap_a = (st->scheme == kSchemeAdaptive || st->scheme == kSchemeFlexible);
+    epi.gap_c = (st->scheme == kSchemeFlexible);
+  }
+  const double om = st->omega;
+  epi.sw = sqrt(om);
+  epi.isw = 1.0 / epi.sw;
+#pragma unroll
+  for (int i = 0; i < NQ; ++i) epi.q[i] = 0.0;
+  process_all<2>(A, v0, v1, epi);
+  block_reduce_store<NQ>(epi.q, partials, pstride, poff + (int)blockIdx.x);
+}
+
+__device__ void init_search(LSearch &L, double r, double d2, double gd, double g2inf) {
+  L.r2 = r * r;
+  L.f_lo = 0.0;
+  L.e_lo = 0.0;
+  L.f_hi = g2inf;
+  L.prefix = 0ull;
+  L.lambda = 0.0;
+  L.rho_r = 0.0;
+  L.done = 0;
+  if (r == 0.0) {
+    L.done = 1;  // zero radius: rho := 0 (Section 6.1)
+  } else if (g2inf == 0.0 && d2 <= L.r2) {
+    L.done = 1;  // the full clamp is inside the ball (Algorithm 2, first test)
+    L.lambda = INFINITY;
+    L.rho_r = gd;
+  }
+}
+
+__device__ void kkt_from(const double *t, int qp, int qd, int qpo, int qdo, double nb, double nc,
+                         double *out) {
+  const double rp = sqrt(t[qp]), rd = sqrt(t[qd]);
+  const double p = t[qpo], d = t[qdo];
+  double rel = fmax(rp / (1.0 + nb), rd / (1.0 + nc));
+  rel = fmax(rel, fabs(p - d) / (1.0 + fabs(p) + fabs(d)));
+  out[0] = rp; out[1] = rd; out[2] = p; out[3] = d; out[4] = rel;
+}
+
+__global__ void __launch_bounds__(kBlock) check_finalize_kernel(DevState *st,
+                                                                const double *partials,
+                                                                int pstride, int nparts) {
+  if (st->status != kRunning) return;
+  __shared__ double tot[NQ];
+  __shared__ double red[kBlock];
+  for (int qi = 0; qi < NQ; ++qi) {
+    double s = 0.0;
+    for (int p = threadIdx.x; p < nparts; p += kBlock) s += partials[(size_t)qi * pstride + p];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = kBlock / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) tot[qi] = red[0];
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  const double om = st->omega;
+  if (st->given_radius) {  // standalone gap evaluation
+    init_search(st->ls[0], st->r_given, tot[Q_D2_A], tot[Q_GD_A], tot[Q_G2INF_A]);
+    return;
+  }
+  st->iters += st->K;
+  st->checks += 1;
+  kkt_from(tot, Q_RP2_A, Q_RD2_A, Q_POBJ_A, Q_DOBJ_A, st->norm_b, st->norm_c, st->kkt_a);
+  kkt_from(tot, Q_RP2_C, Q_RD2_C, Q_POBJ_C, Q_DOBJ_C, st->norm_b, st->norm_c, st->kkt_c);
+  const double ra = st->kkt_a[4], rc = st->kkt_c[4];
+  st->ls[0].done = 1;
+  st->ls[1].done = 1;
+  if (tot[Q_BAD] > 0.0 || !isfinite(ra) || !isfinite(rc)) {
+    st->status = kStatusNumerical;
+    return;
+  }
+  if (ra <= st->tol) {
+    st->status = kStatusOK;
+    st->returned = 0;
+    return;
+  }
+  if (rc <= st->tol) {
+    st->status = kStatusOK;
+    st->returned = 1;
+    return;
+  }
+  st->returned = (ra <= rc) ? 0 : 1;
+  if (st->scheme == kSchemeAdaptive || st->scheme == kSchemeFlexible) {
+    const double r = sqrt(om * tot[Q_RRX_A] + tot[Q_RRY_A] / om);
+    init_search(st->ls[0], r, tot[Q_D2_A], tot[Q_GD_A], tot[Q_G2INF_A]);
+    st->last_r = r;
+  }
+  if (st->scheme == kSchemeFlexible) {
+    const double r = sqrt(om * tot[Q_RRX_C] + tot[Q_RRY_C] / om);
+    init_search(st->ls[1], r, tot[Q_D2_C], tot[Q_GD_C], tot[Q_G2INF_C]);
+  }
+}
+
+// ----------------------------------------------- multiplier search (Sec. 6.3)
+//
+// f(lambda) = ||zt(lambda) - z||^2 = sum_{lam_i <= lambda} d_i^2
+//           + lambda^2 sum_{lam_i > lambda} g_i^2 is continuous and
+// nondecreasing; lambda* is its largest point with f <= r^2.  Pass p splits
+// the current bracket (keys sharing the fixed prefix) into 256 buckets by
+// bits [56 - 8p, 64 - 8p) of the breakpoint's bit pattern (monotone in the
+// value for nonnegative doubles) and accumulates, per bucket, the count,
+// sum d^2, sum g^2 and sum d g.  Bucket edges e_k are evaluated exactly;
+// the bracket shrinks to the last bucket with f(e_k) <= r^2.  The search
+// ends when that bucket is empty or after the 8th pass, then
+// lambda* = sqrt((r^2 - f_lo) / f_hi), the closed form of Algorithm 2.
+//
+// Within a warp, lanes that fall in the same bucket are summed by the
+// group's lowest lane in lane order (match_any), so the per-bucket sums
+// are deterministic.
+
+__global__ void __launch_bounds__(kHistWarps *kWarp) ls_hist_kernel(
+    const uint64_t *__restrict__ keys0, const double *__restrict__ d20,
+    const double *__restrict__ g20, const double *__restrict__ gd0,
+    const uint64_t *__restrict__ keys1, const double *__restrict__ d21,
+    const double *__restrict__ g21, const double *__restrict__ gd1, int64_t N,
+    const DevState *st, int pass, double *hpart) {
+  const int sidx = blockIdx.y;
+  const LSearch &L = st->ls[sidx];
+  if (L.done) return;
+  const uint64_t *keys = sidx ? keys1 : keys0;
+  const double *d2 = sidx ? d21 : d20;
+  const double *g2 = sidx ? g21 : g20;
+  const double *gd = sidx ? gd1 : gd0;
+  const int shift = 56 - 8 * pass;
+  const uint64_t pre = L.prefix;
+  __shared__ double hist[kHistWarps][kBuckets][3];
+  __shared__ unsigned cnt[kHistWarps][kBuckets];
+  __shared__ double stage[kHistWarps][kWarp][3];
+  for (int i = threadIdx.x; i < kHistWarps * kBuckets; i += blockDim.x) {
+    (&hist[0][0][0])[3 * i] = 0.0;
+    (&hist[0][0][0])[3 * i + 1] = 0.0;
+    (&hist[0][0][0])[3 * i + 2] = 0.0;
+    (&cnt[0][0])[i] = 0u;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & (kWarp - 1), warp = threadIdx.x >> 5;
+  const int64_t stride = (int64_t)gridDim.x * kHistWarps * kWarp;
+  for (int64_t base = ((int64_t)blockIdx.x * kHistWarps + warp) * kWarp; base < N; base += stride) {
+    const int64_t e = base + lane;
+    bool act = false;
+    int bk = -1;
+    if (e < N) {
+      const uint64_t k = keys[e];
+      if (k != kNoKey && (pass == 0 || (k >> (shift + 8)) == (pre >> (shift + 8)))) {
+        act = true;
+        bk = (int)((k >> shift) & 255u);
+      }
+    }
+    if (__ballot_sync(kFull, act) == 0u) continue;
+    if (act) {
+      stage[warp][lane][0] = d2[e];
+      stage[warp][lane][1] = g2[e];
+      stage[warp][lane][2] = gd[e];
+    }
+    __syncwarp();
+    const unsigned grp = __match_any_sync(kFull, bk);
+    if (act && (grp & ((1u << lane) - 1u)) == 0u) {
+      double sd = 0.0, sg = 0.0, se = 0.0;
+      unsigned gm = grp;
+      while (gm) {
+        const int l = __ffs(gm) - 1;
+        gm &= gm - 1u;
+        sd += stage[warp][l][0];
+        sg += stage[warp][l][1];
+        se += stage[warp][l][2];
+      }
+      hist[warp][bk][0] += sd;
+      hist[warp][bk][1] += sg;
+      hist[warp][bk][2] += se;
+      cnt[warp][bk] += (unsigned)__popc(grp);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  double *out = hpart + ((size_t)sidx * gridDim.x + blockIdx.x) * 4 * kBuckets;
+  for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) {
+    double c = 0.0, sd = 0.0, sg = 0.0, se = 0.0;
+    for (int w = 0; w < kHistWarps; ++w) {
+      c += (double)cnt[w][b];
+      sd += hist[w][b][0];
+      sg += hist[w][b][1];
+      se += hist[w][b][2];
+    }
+    out[b] = c;
+    out[kBuckets + b] = sd;
+    out[2 * kBuckets + b] = sg;
+    out[3 * kBuckets + b] = se;
+  }
+}
+
+__global__ void __launch_bounds__(kBuckets) ls_select_kernel(DevState *st, int pass,
+                                                             const double *hpart, int hist_grid) {
+  LSearch &L = st->ls[blockIdx.x];
+  if (L.done) return;
+  const int b = threadIdx.x;
+  __shared__ double cnt[kBuckets], sd[kBuckets], sg[kBuckets], se[kBuckets];
+  __shared__ double cum_d[kBuckets + 1], cum_e[kBuckets + 1], tail_g[kBuckets + 1];
+  __shared__ int kstar;
+  double c = 0.0, d = 0.0, g = 0.0, e = 0.0;
+  for (int blk = 0; blk < hist_grid; ++blk) {
+    const double *p = hpart + ((size_t)blockIdx.x * hist_grid + blk) * 4 * kBuckets;
+    c += p[b];
+    d += p[kBuckets + b];
+    g += p[2 * kBuckets + b];
+    e += p[3 * kBuckets + b];
+  }
+  cnt[b] = c;
+  sd[b] = d;
+  sg[b] = g;
+  se[b] = e;
+  if (b == 0) kstar = -1;
+  __syncthreads();
+  // exclusive prefix sums of d^2 and d g, inclusive suffix sums of g^2
+  if (b == 0) {
+    double s = 0.0;
+    for (int k = 0; k < kBuckets; ++k) { cum_d[k] = s; s += sd[k]; }
+    cum_d[kBuckets] = s;
+  } else if (b == 32) {
+    double s = 0.0;
+    for (int k = 0; k < kBuckets; ++k) { cum_e[k] = s; s += se[k]; }
+    cum_e[kBuckets] = s;
+  } else if (b == 64) {
+    double s = 0.0;
+    tail_g[kBuckets] = 0.0;
+    for (int k = kBuckets - 1; k >= 0; --k) { s += sg[k]; tail_g[k] = s; }
+  }
+  __syncthreads();
+  const int shift = 56 - 8 * pass;
+  const uint64_t edge_bits = L.prefix | ((uint64_t)b << shift);
+  const double edge = __longlong_as_double((long long)edge_bits);
+  bool ok = false;
+  if ((edge_bits >> 63) == 0ull && isfinite(edge)) {  // edges are nonnegative finite doubles
+    const double f = L.f_lo + cum_d[b] + edge * edge * (L.f_hi + tail_g[b]);
+    ok = f <= L.r2;
+  }
+  if (ok) atomicMax(&kstar, b);
+  __syncthreads();
+  if (b != 0) return;
+  const int k = kstar < 0 ? 0 : kstar;
+  L.f_lo += cum_d[k];
+  L.e_lo += cum_e[k];
+  L.f_hi += tail_g[k + 1];
+  L.prefix = L.prefix | ((uint64_t)k << shift);
+  if (cnt[k] == 0.0 || pass == kSearchPasses - 1) {
+    if (cnt[k] != 0.0) {  // last pass: breakpoints equal to the edge are clamped
+      L.f_lo += sd[k];
+      L.e_lo += se[k];
+    }
+    if (L.f_hi > 0.0) {
+      L.lambda = sqrt(fmax(L.r2 - L.f_lo, 0.0) / L.f_hi);
+      L.rho_r = L.e_lo + L.lambda * L.f_hi;
+    } else {
+      L.lambda = INFINITY;
+      L.rho_r = L.e_lo;
+    }
+    L.done = 1;
+  }
+}
+
+// Restart decision (Eq. adaptive-restart-scheme / flexible / fixed), trace
+// row, and the averaging weights w_k = 1 / (t0 + k + 1) of the next block.
+__global__ void __launch_bounds__(kBlock) check_decide_kernel(DevState *st, double *w,
+                                                              double *trace) {
+  __shared__ int64_t t0s;
+  __shared__ int active;
+  if (threadIdx.x == 0) {
+    active = (st->status == kRunning);
+    if (active) {
+      const int scheme = st->scheme;
+      double rho = NAN, r = st->last_r;
+      int use_cur = 0;
+      if (scheme == kSchemeAdaptive || scheme == kSchemeFlexible) {
+        const LSearch &La = st->ls[0];
+        r = sqrt(La.r2);
+        rho = (La.r2 > 0.0) ? La.rho_r / r : 0.0;
+        if (scheme == kSchemeFlexible) {
+          const LSearch &Lc = st->ls[1];
+          const double rc = sqrt(Lc.r2);
+          const double rho_c = (Lc.r2 > 0.0) ? Lc.rho_r / rc : 0.0;
+          if (rho_c < rho) {
+            use_cur = 1;
+            rho = rho_c;
+            r = rc;
+          }
+        }
+      }
+      const int64_t t = st->t0 + st->K;
+      int restart = 0;
+      if (scheme == kSchemeAdaptive || scheme == kSchemeFlexible)
+        restart = (st->restarts == 0) ? (t >= st->tau0) : (rho <= st->beta * st->rho_stored);
+      else if (scheme == kSchemeFixed)
+        restart = (t >= st->fixed_len);
+      if (trace && st->trace_count < st->trace_cap) {
+        double *row = trace + 6 * st->trace_count;
+        row[0] = (double)st->iters;
+        row[1] = rho;
+        row[2] = (double)restart;
+        row[3] = st->kkt_a[4];
+        row[4] = st->kkt_c[4];
+        row[5] = r;
+      }
+      st->trace_count += 1;
+      st->last_rho = rho;
+      st->last_r = r;
+      st->use_cur = use_cur;
+      st->restart_now = restart;
+      if (restart) {
+        st->rho_stored = rho;
+        st->restarts += 1;
+        st->t0 = 0;
+      } else {
+        st->t0 = t;
+      }
+    }
+    t0s = st->t0;
+  }
+  __syncthreads();
+  if (!active) return;
+  for (int k = threadIdx.x; k < st->K; k += blockDim.x) w[k] = 1.0 / (double)(t0s + k + 1);
+}
+
+__global__ void restart_copy_kernel(DevVecs v, const DevState *st, int n, int m) {
+  if (st->status != kRunning) return;
+  const int rs = st->restart_now, uc = st->use_cur;
+  if (!rs && !uc) return;
+  const int64_t total = (int64_t)n + m;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < n) {
+      const double s = uc ? v.x[i] : v.xbar[i];
+      if (rs) {
+        v.x0[i] = s;
+        v.x[i] = s;
+      }
+      v.xbar[i] = s;
+    } else {
+      const int64_t k = i - n;
+      const double s = uc ? v.y[k] : v.ybar[k];
+      if (rs) {
+        v.y0[k] = s;
+        v.y[k] = s;
+      }
+      v.ybar[k] = s;
+    }
+  }
+}
+
+__global__ void advance_kernel(DevState *st, double *w, int r) {
+  __shared__ int64_t t0s;
+  __shared__ int active;
+  if (threadIdx.x == 0) {
+    active = (st->status == kRunning);
+    if (active) {
+      st->iters += r;
+      st->t0 += r;
+    }
+    t0s = st->t0;
+  }
+  __syncthreads();
+  if (!active) return;
+  for (int k = threadIdx.x; k < st->K; k += blockDim.x) w[k] = 1.0 / (double)(t0s + k + 1);
+}
+
+__global__ void weights_kernel(const DevState *st, double *w) {
+  const int64_t t0 = st->t0;
+  for (int k = threadIdx.x; k < st->K; k += blockDim.x) w[k] = 1.0 / (double)(t0 + k + 1);
+}
+
+// ------------------------------------------------------ power iteration
+
+__global__ void __launch_bounds__(kBlock) sumsq_kernel(const double *__restrict__ v, int64_t n,
+                                                       double *partials, int pstride, int slot,
+                                                       const DevState *st) {
+  if (st && st->pw_done) return;
+  double q[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    q[0] += v[i] * v[i];
+  block_reduce_store<1>(q, partials + (size_t)slot * pstride, pstride, (int)blockIdx.x);
+}
+
+__device__ double sum_fixed(const double *p, int count, double *red) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) s += p[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// Power iteration on A^T A (Section 7): ray = ||A v||^2 for ||v|| = 1,
+// stop when |ray - est| <= tol * ray (after the first step) or A^T A v = 0.
+__global__ void __launch_bounds__(kBlock) power_finalize_kernel(DevState *st,
+                                                                const double *partials,
+                                                                int pstride, int nparts) {
+  if (st->pw_done) return;
+  __shared__ double red[kBlock];
+  const double ray = sum_fixed(partials, nparts, red);
+  const double nw2 = sum_fixed(partials + pstride, nparts, red);
+  if (threadIdx.x != 0) return;
+  const double nw = sqrt(nw2);
+  const int done = (st->pw_iters > 0 && fabs(ray - st->pw_est) <= st->pw_tol * ray);
+  st->pw_est = ray;
+  st->pw_iters += 1;
+  st->pw_nw = nw;
+  if (nw == 0.0 || done || st->pw_iters >= st->pw_max) st->pw_done = 1;
+}
+
+__global__ void power_scale_kernel(double *v, const double *w, int64_t n, const DevState *st) {
+  if (st->pw_done) return;
+  const double nw = st->pw_nw;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = w[i] / nw;
+}
+
+__global__ void norms_finalize_kernel(DevState *st, const double *partials, int pstride,
+                                      int nparts) {
+  __shared__ double red[kBlock];
+  const double b2 = sum_fixed(partials, nparts, red);
+  const double c2 = sum_fixed(partials + pstride, nparts, red);
+  if (threadIdx.x == 0) {
+    st->norm_b = sqrt(b2);
+    st->norm_c = sqrt(c2);
+  }
+}
+
+// -------------------------------------------------------------- utilities
+
+__global__ void gather_kernel(double *out, const double *in, const int32_t *perm, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[perm[i]];
+}
+
+__global__ void scatter_kernel(double *out, const double *in, const int32_t *perm, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[perm[i]] = in[i];
+}
+
+__global__ void fill_kernel(double *p, double val, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = val;
+}
+
+// z <- proj_{X x Y}(z); average and restart point <- z.
+__global__ void project_kernel(DevVecs v, int n, int m) {
+  const int64_t total = (int64_t)n + m;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < n) {
+      const double xv = fmin(fmax(v.x[i], v.lb[i]), v.ub[i]);
+      v.x[i] = xv;
+      v.xbar[i] = xv;
+      v.x0[i] = xv;
+      v.xhat[i] = xv;
+    } else {
+      const int64_t k = i - n;
+      double yv = v.y[k];
+      if (v.row_type[k] == 1) yv = fmax(yv, 0.0);
+      else if (v.row_type[k] == 2) yv = fmin(yv, 0.0);
+      v.y[k] = yv;
+      v.ybar[k] = yv;
+      v.y0[k] = yv;
+    }
+  }
+}
+
+int grid_for(int64_t n, int num_sms) {
+  int64_t g = (n + kBlock - 1) / kBlock;
+  const int64_t cap = (int64_t)num_sms * 8;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+int item_grid(const SellMat &A) {
+  const int64_t items = (int64_t)A.nlong + A.nslices;
+  int64_t g = (items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+int g_num_sms = 0;
+int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 132;
+  }
+  return g_num_sms;
+}
+
+}  // namespace
+
+int check_grid_for(const SellMat &A, int nsm) {
+  const int64_t items = (int64_t)A.nlong + A.nslices;
+  int64_t g = (items + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const int64_t cap = (int64_t)nsm * 4;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+void launch_primal_step(const SellMat &AT, const DevVecs &v, DevState *st, const double *w,
+                        int k, cudaStream_t s) {
+  PrimalEpi epi{v.c, v.lb, v.ub, v.x, v.xhat, v.xbar, 0.0, 0.0};
+  primal_kernel<<<item_grid(AT), kBlock, 0, s>>>(AT, v.y, epi, st, w, k);
+}
+
+void launch_dual_step(const SellMat &A, const DevVecs &v, DevState *st, const double *w, int k,
+                      cudaStream_t s) {
+  DualEpi epi{v.b, v.row_type, v.y, v.ybar, 0.0, 0.0};
+  dual_kernel<<<item_grid(A), kBlock, 0, s>>>(A, v.xhat, epi, st, w, k);
+}
+
+void launch_check(const SellMat &A, const SellMat &AT, const DevVecs &v, DevState *st, double *w,
+                  const CheckScratch &cs, int n, int m, int nsearch, double *trace,
+                  bool decide, cudaStream_t s) {
+  CheckColsEpi ce{};
+  ce.c = v.c; ce.lb = v.lb; ce.ub = v.ub; ce.xbar = v.xbar; ce.x = v.x; ce.x0 = v.x0;
+  ce.ga = GapOut{cs.keys[0], cs.d2[0], cs.g2[0], cs.gd[0]};
+  ce.gc = GapOut{cs.keys[1], cs.d2[1], cs.g2[1], cs.gd[1]};
+  ce.gap_a = 1;  // overridden on device from the scheme unless a radius is given
+  ce.gap_c = 0;
+  CheckRowsEpi re{};
+  re.b = v.b; re.rt = v.row_type; re.ybar = v.ybar; re.y = v.y; re.y0 = v.y0;
+  re.ga = ce.ga;
+  re.gc = ce.gc;
+  re.off = n;
+  re.gap_a = 1;
+  re.gap_c = 0;
+  check_kernel<CheckColsEpi><<<cs.cols_grid, kBlock, 0, s>>>(AT, v.ybar, v.y, ce, st, cs.partials,
+                                                             cs.pstride, 0);
+  check_kernel<CheckRowsEpi><<<cs.rows_grid, kBlock, 0, s>>>(A, v.xbar, v.x, re, st, cs.partials,
+                                                             cs.pstride, cs.cols_grid);
+  check_finalize_kernel<<<1, kBlock, 0, s>>>(st, cs.partials, cs.pstride,
+                                             cs.cols_grid + cs.rows_grid);
+  if (nsearch > 0) {
+    const int64_t N = (int64_t)n + m;
+    for (int p = 0; p < kSearchPasses; ++p) {
+      ls_hist_kernel<<<dim3(cs.hist_grid, nsearch), kHistWarps * kWarp, 0, s>>>(
+          cs.keys[0], cs.d2[0], cs.g2[0], cs.gd[0], cs.keys[1], cs.d2[1], cs.g2[1], cs.gd[1], N,
+          st, p, cs.hpart);
+      ls_select_kernel<<<nsearch, kBuckets, 0, s>>>(st, p, cs.hpart, cs.hist_grid);
+    }
+  }
+  if (decide) {
+    check_decide_kernel<<<1, kBlock, 0, s>>>(st, w, trace);
+    restart_copy_kernel<<<grid_for((int64_t)n + m, num_sms()), kBlock, 0, s>>>(v, st, n, m);
+  }
+}
+
+void launch_advance(DevState *st, double *w, int r, cudaStream_t s) {
+  advance_kernel<<<1, kBlock, 0, s>>>(st, w, r);
+}
+
+void launch_weights(DevState *st, double *w, cudaStream_t s) {
+  weights_kernel<<<1, kBlock, 0, s>>>(st, w);
+}
+
+void launch_spmv(const SellMat &A, const double *v, double *out, cudaStream_t s,
+                 DevState *st_guard) {
+  StoreEpi epi{out};
+  spmv_kernel<<<item_grid(A), kBlock, 0, s>>>(A, v, epi, st_guard);
+}
+
+void launch_power_iteration_step(const SellMat &A, const SellMat &AT, double *v, double *av,
+                                 double *w, DevState *st, double *partials, int pstride,
+                                 int grid, int n, int m, cudaStream_t s) {
+  launch_spmv(A, v, av, s, st);
+  sumsq_kernel<<<grid, kBlock, 0, s>>>(av, m, partials, pstride, 0, st);
+  launch_spmv(AT, av, w, s, st);
+  sumsq_kernel<<<grid, kBlock, 0, s>>>(w, n, partials, pstride, 1, st);
+  power_finalize_kernel<<<1, kBlock, 0, s>>>(st, partials, pstride, grid);
+  power_scale_kernel<<<grid_for(n, num_sms()), kBlock, 0, s>>>(v, w, n, st);
+}
+
+void launch_norms(const DevVecs &v, DevState *st, double *partials, int pstride, int grid, int n,
+                  int m, cudaStream_t s) {
+  sumsq_kernel<<<grid, kBlock, 0, s>>>(v.b, m, partials, pstride, 0, nullptr);
+  sumsq_kernel<<<grid, kBlock, 0, s>>>(v.c, n, partials, pstride, 1, nullptr);
+  norms_finalize_kernel<<<1, kBlock, 0, s>>>(st, partials, pstride, grid);
+}
+
+void launch_gather(double *out, const double *in, const int32_t *perm, int64_t n,
+                   cudaStream_t s) {
+  if (n > 0) gather_kernel<<<grid_for(n, num_sms()), kBlock, 0, s>>>(out, in, perm, n);
+}
+
+void launch_scatter(double *out, const double *in, const int32_t *perm, int64_t n,
+                    cudaStream_t s) {
+  if (n > 0) scatter_kernel<<<grid_for(n, num_sms()), kBlock, 0, s>>>(out, in, perm, n);
+}
+
+void launch_project(const DevVecs &v, int n, int m, cudaStream_t s) {
+  const int64_t total = (int64_t)n + m;
+  if (total > 0) project_kernel<<<grid_for(total, num_sms()), kBlock, 0, s>>>(v, n, m);
+}
+
+void launch_fill(double *p, double val, int64_t n, cudaStream_t s) {
+  if (n > 0) fill_kernel<<<grid_for(n, num_sms()), kBlock, 0, s>>>(p, val, n);
+}
+
+}  // namespace lpg

@@ -1,0 +1,319 @@
+"""Thin ctypes binding of liblp.so (include/lp.h).
+
+Argument marshalling only: every step of the solve runs in the library's
+CUDA kernels.  Functions keep the C names; arrays may be torch tensors
+(CUDA or CPU) or NumPy arrays, passed by pointer.  Streams default to
+torch's current CUDA stream.  There is no CPU fallback: if liblp.so is
+missing or CUDA is unavailable the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+LP_OK, LP_ERR_INVALID_ARG, LP_ERR_CUDA, LP_ERR_OOM, LP_ITER_LIMIT = 0, 1, 2, 3, 4
+LP_ERR_NUMERICAL, LP_ERR_TIMEOUT, LP_ERR_NOT_SOLVED = 5, 6, 7
+LP_ROW_EQ, LP_ROW_GE, LP_ROW_LE = 0, 1, 2
+LP_RESTART_NONE, LP_RESTART_FIXED, LP_RESTART_ADAPTIVE, LP_RESTART_FLEXIBLE = 0, 1, 2, 3
+
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "ITER_LIMIT",
+                5: "NUMERICAL", 6: "TIMEOUT", 7: "NOT_SOLVED"}
+
+
+class lp_options(C.Structure):
+    _fields_ = [("beta", C.c_double), ("check_every", C.c_int32), ("restart_scheme", C.c_int32),
+                ("tau0", C.c_int64), ("fixed_len", C.c_int64), ("omega", C.c_double),
+                ("eta", C.c_double), ("power_iters", C.c_int32), ("power_tol", C.c_double),
+                ("max_iter", C.c_int64), ("long_row_threshold", C.c_int32),
+                ("trace_capacity", C.c_int32), ("reserved", C.c_int32 * 6)]
+
+
+class lp_info(C.Structure):
+    _fields_ = [("iters", C.c_int64), ("restarts", C.c_int64), ("checks", C.c_int64),
+                ("status", C.c_int32), ("returned", C.c_int32),
+                ("kkt_avg", C.c_double * 5), ("kkt_cur", C.c_double * 5),
+                ("eta", C.c_double), ("sigma_max", C.c_double), ("omega", C.c_double),
+                ("tau", C.c_double), ("sigma", C.c_double), ("rho_stored", C.c_double),
+                ("last_rho", C.c_double), ("last_radius", C.c_double),
+                ("nnz_padded", C.c_int64), ("n_long_rows", C.c_int32), ("n_long_cols", C.c_int32)]
+
+
+EXPORTED = ["lp_default_options", "lp_create", "lp_solve", "lp_iterate", "lp_get_solution",
+            "lp_get_state", "lp_set_state", "lp_get_info", "lp_get_trace", "lp_normalized_gap",
+            "lp_profile_kernel", "lp_destroy", "lp_last_error"]
+
+_lib = None
+
+
+class LPError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load liblp.so (building it with nvcc first if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"liblp.so not found at {path}; run paper_2105_12715_gb300.build.build()")
+    lib = C.CDLL(path)
+    P, D, I32, I64 = C.c_void_p, C.c_double, C.c_int32, C.c_int64
+    lib.lp_default_options.argtypes = [C.POINTER(lp_options)]
+    lib.lp_default_options.restype = None
+    lib.lp_create.argtypes = [I32, I32, I64, P, P, P, P, P, P, P, P, C.POINTER(lp_options), P,
+                              C.POINTER(P)]
+    lib.lp_solve.argtypes = [P, D, P]
+    lib.lp_iterate.argtypes = [P, I32, D, P]
+    lib.lp_get_solution.argtypes = [P, P, P, P]
+    lib.lp_get_state.argtypes = [P, P, P, P, P, P, P, P]
+    lib.lp_set_state.argtypes = [P, P, P, P]
+    lib.lp_get_info.argtypes = [P, C.POINTER(lp_info)]
+    lib.lp_get_trace.argtypes = [P, P, I64, C.POINTER(I64)]
+    lib.lp_normalized_gap.argtypes = [P, P, P, D, C.POINTER(D), P]
+    lib.lp_profile_kernel.argtypes = [P, I32, I32, P]
+    lib.lp_destroy.argtypes = [P]
+    lib.lp_destroy.restype = None
+    lib.lp_last_error.argtypes = []
+    lib.lp_last_error.restype = C.c_char_p
+    for name in ["lp_create", "lp_solve", "lp_iterate", "lp_get_solution", "lp_get_state",
+                 "lp_set_state", "lp_get_info", "lp_get_trace", "lp_normalized_gap",
+                 "lp_profile_kernel"]:
+        getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _last_error() -> str:
+    return load().lp_last_error().decode(errors="replace")
+
+
+def _check(status, allow=(LP_OK,)):
+    if status not in allow:
+        raise LPError(status, _last_error())
+    return status
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(getattr(stream, "cuda_stream", stream))
+
+
+def _ptr(a, dtype):
+    """Pointer of a contiguous torch tensor or NumPy array of the given dtype."""
+    if a is None:
+        return None, None
+    try:
+        import torch
+
+        if isinstance(a, torch.Tensor):
+            tdt = {np.float64: torch.float64, np.int32: torch.int32, np.int8: torch.int8}[dtype]
+            if a.dtype != tdt or not a.is_contiguous():
+                a = a.to(tdt).contiguous()
+            return C.c_void_p(a.data_ptr()), a
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return C.c_void_p(arr.ctypes.data), arr
+
+
+def lp_default_options() -> lp_options:
+    o = lp_options()
+    load().lp_default_options(C.byref(o))
+    return o
+
+
+def lp_create(m, n, nnz, row_ptr, col_idx, val, c, b, lb, ub, row_type, opt=None, stream=None):
+    """Returns a handle (C void*).  Arrays: host or device, see include/lp.h."""
+    keep = []
+    ptrs = []
+    for a, dt in [(row_ptr, np.int32), (col_idx, np.int32), (val, np.float64), (c, np.float64),
+                  (b, np.float64), (lb, np.float64), (ub, np.float64), (row_type, np.int8)]:
+        p, k = _ptr(a, dt)
+        ptrs.append(p)
+        keep.append(k)
+    h = C.c_void_p()
+    o = C.byref(opt) if opt is not None else None
+    _check(load().lp_create(int(m), int(n), int(nnz), *ptrs, o, _stream(stream), C.byref(h)))
+    return h
+
+
+def lp_solve(h, tol, stream=None) -> int:
+    return _check(load().lp_solve(h, float(tol), _stream(stream)),
+                  allow=(LP_OK, LP_ITER_LIMIT, LP_ERR_NUMERICAL))
+
+
+def lp_iterate(h, n_checks, tol, stream=None) -> int:
+    return _check(load().lp_iterate(h, int(n_checks), float(tol), _stream(stream)))
+
+
+def lp_get_solution(h, x, y, stream=None):
+    px, _ = _ptr(x, np.float64) if not isinstance(x, np.ndarray) else (C.c_void_p(x.ctypes.data), x)
+    py, _ = _ptr(y, np.float64) if not isinstance(y, np.ndarray) else (C.c_void_p(y.ctypes.data), y)
+    return _check(load().lp_get_solution(h, px, py, _stream(stream)))
+
+
+def _out_ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+        return C.c_void_p(a.ctypes.data)
+    assert a.is_contiguous()
+    return C.c_void_p(a.data_ptr())
+
+
+def lp_get_state(h, x=None, y=None, xbar=None, ybar=None, x0=None, y0=None, stream=None):
+    return _check(load().lp_get_state(h, *[_out_ptr(a) for a in (x, y, xbar, ybar, x0, y0)],
+                                      _stream(stream)))
+
+
+def lp_set_state(h, x=None, y=None, stream=None):
+    px, kx = _ptr(x, np.float64)
+    py, ky = _ptr(y, np.float64)
+    return _check(load().lp_set_state(h, px, py, _stream(stream)))
+
+
+def lp_get_info(h) -> lp_info:
+    info = lp_info()
+    _check(load().lp_get_info(h, C.byref(info)))
+    return info
+
+
+def lp_get_trace(h, capacity=1 << 20) -> np.ndarray:
+    rows = np.empty((capacity, 6))
+    cnt = C.c_int64()
+    _check(load().lp_get_trace(h, C.c_void_p(rows.ctypes.data), capacity, C.byref(cnt)))
+    return rows[:cnt.value].copy()
+
+
+def lp_normalized_gap(h, x, y, r, stream=None) -> float:
+    px, kx = _ptr(x, np.float64)
+    py, ky = _ptr(y, np.float64)
+    out = C.c_double()
+    _check(load().lp_normalized_gap(h, px, py, float(r), C.byref(out), _stream(stream)))
+    return out.value
+
+
+def lp_profile_kernel(h, which, reps, stream=None):
+    return _check(load().lp_profile_kernel(h, int(which), int(reps), _stream(stream)))
+
+
+def lp_destroy(h):
+    if h is not None and h.value:
+        load().lp_destroy(h)
+
+
+# ------------------------------------------------------------ convenience
+
+@dataclass
+class Info:
+    iters: int
+    restarts: int
+    checks: int
+    status: int
+    returned: int
+    kkt_avg: tuple
+    kkt_cur: tuple
+    eta: float
+    sigma_max: float
+    omega: float
+    tau: float
+    sigma: float
+    rho_stored: float
+    last_rho: float
+    last_radius: float
+    nnz_padded: int
+    n_long_rows: int
+    n_long_cols: int
+
+    @property
+    def rel_kkt(self) -> float:
+        return self.kkt_avg[4] if self.returned == 0 else self.kkt_cur[4]
+
+
+class LP:
+    """Owning wrapper of an lp_handle built from an lpgen.LPData-like object."""
+
+    def __init__(self, data, stream=None, **options):
+        opt = lp_default_options()
+        for k, v in options.items():
+            if not hasattr(opt, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(opt, k, v)
+        self.m, self.n = int(data.m), int(data.n)
+        self.stream = stream
+        self.h = lp_create(data.m, data.n, int(data.row_ptr[-1]), data.row_ptr, data.col_idx,
+                           data.val, data.c, data.b, data.lb, data.ub, data.row_type, opt, stream)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            lp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def solve(self, tol=1e-8):
+        return lp_solve(self.h, tol, self.stream)
+
+    def iterate(self, n_checks, tol=1e-8):
+        return lp_iterate(self.h, n_checks, tol, self.stream)
+
+    def solution(self):
+        x, y = np.empty(self.n), np.empty(self.m)
+        lp_get_solution(self.h, x, y, self.stream)
+        return x, y
+
+    def state(self):
+        arrs = [np.empty(self.n), np.empty(self.m), np.empty(self.n), np.empty(self.m),
+                np.empty(self.n), np.empty(self.m)]
+        lp_get_state(self.h, *arrs, stream=self.stream)
+        return dict(zip(["x", "y", "xbar", "ybar", "x0", "y0"], arrs))
+
+    def set_state(self, x=None, y=None):
+        lp_set_state(self.h, x, y, self.stream)
+
+    def info(self) -> Info:
+        i = lp_get_info(self.h)
+        return Info(i.iters, i.restarts, i.checks, i.status, i.returned, tuple(i.kkt_avg),
+                    tuple(i.kkt_cur), i.eta, i.sigma_max, i.omega, i.tau, i.sigma, i.rho_stored,
+                    i.last_rho, i.last_radius, i.nnz_padded, i.n_long_rows, i.n_long_cols)
+
+    def trace(self, capacity=1 << 20):
+        return lp_get_trace(self.h, capacity)
+
+    def gap(self, x, y, r):
+        return lp_normalized_gap(self.h, x, y, r, self.stream)
+
+
+def default_beta() -> float:
+    return math.exp(-1.0)

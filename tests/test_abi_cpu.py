@@ -1,0 +1,79 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds and
+loads, exports every entry point include/lp.h declares, and rejects bad
+arguments before touching the device."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "lp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:lp_status|void|const char \*)\s*(lp_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2105_12715_gb300 import lp
+
+    return lp.load()
+
+
+def test_header_declares_expected_entry_points():
+    names = _declared_functions()
+    for required in ["lp_create", "lp_solve", "lp_get_solution", "lp_get_info", "lp_destroy",
+                     "lp_last_error", "lp_default_options"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2105_12715_gb300 import lp
+
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+        assert name in lp.EXPORTED, name
+
+
+def test_default_options(lib):
+    from paper_2105_12715_gb300 import lp
+
+    o = lp.lp_default_options()
+    assert o.beta == pytest.approx(np.exp(-1))
+    assert o.check_every == 64
+    assert o.restart_scheme == lp.LP_RESTART_ADAPTIVE
+    assert o.omega == 1.0 and o.eta == 0.0
+
+
+def test_create_rejects_bad_sizes_and_options_on_host(lib):
+    from paper_2105_12715_gb300 import lp
+
+    rp = np.array([0, 1], dtype=np.int32)
+    ci = np.array([0], dtype=np.int32)
+    v = np.array([1.0])
+    c = np.array([1.0])
+    b = np.array([1.0])
+    lb, ub = np.array([0.0]), np.array([np.inf])
+    rt = np.zeros(1, dtype=np.int8)
+    with pytest.raises(lp.LPError) as e:
+        lp.lp_create(1, 0, 1, rp, ci, v, c, b, lb, ub, rt, stream=0)
+    assert e.value.status == lp.LP_ERR_INVALID_ARG
+    opt = lp.lp_default_options()
+    opt.beta = 1.5
+    with pytest.raises(lp.LPError) as e:
+        lp.lp_create(1, 1, 1, rp, ci, v, c, b, lb, ub, rt, opt, stream=0)
+    assert e.value.status == lp.LP_ERR_INVALID_ARG
+    assert "beta" in lp._last_error()
+    opt = lp.lp_default_options()
+    opt.check_every = 0
+    with pytest.raises(lp.LPError):
+        lp.lp_create(1, 1, 1, rp, ci, v, c, b, lb, ub, rt, opt, stream=0)
+    h = C.c_void_p()
+    st = lib.lp_create(1, 1, 1, None, None, None, None, None, None, None, None, None, None,
+                       C.byref(h))
+    assert st == lp.LP_ERR_INVALID_ARG
