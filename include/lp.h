@@ -172,6 +172,24 @@ lp_status lp_normalized_gap(lp_handle h, const double *x, const double *y,
                             double r, double *host_rho, void *cuda_stream);
 
 /*
+ * lp_normalized_gap without any device allocation.  The paper has no
+ * counterpart; this entry point exists for callers that cannot let a
+ * library allocate device memory (a latency-bound host loop, since cudaFree
+ * synchronizes the device; a process whose framework already reserved
+ * nearly all device memory; code that must leave the allocation state
+ * untouched while other work is queued).
+ * Same arguments, result and tolerance as lp_normalized_gap.  Scratch is a
+ * fixed 16 MiB device array inside the library (held on every GPU that
+ * loads it until exit), so n + m must be <= 262,144; larger problems return
+ * LP_ERR_INVALID_ARG.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and should come before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race
+ * and must be serialized by the caller.  Synchronizes the stream.
+ */
+lp_status lp_normalized_gap_static(lp_handle h, const double *x, const double *y,
+                                   double r, double *host_rho, void *cuda_stream);
+
+/*
  * Profiling hook: enqueues reps launches of one hot-path kernel alone --
  * which = 0: the primal step (column pass, Eq. PDHG-update first line),
  * which = 1: the dual step (row pass, second line) -- on the stream, with

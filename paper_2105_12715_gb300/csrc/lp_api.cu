@@ -19,6 +19,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -760,3 +761,129 @@ void lp_destroy(lp_handle h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// lp_normalized_gap_static: the normalized duality gap without any device
+// allocation.
+//
+// Some callers cannot let a library call cudaMalloc/cudaFree: a host loop
+// with a latency budget (cudaFree synchronizes the whole device), a process
+// whose framework has already reserved nearly all device memory for its own
+// pool, or code that must not change the device's allocation state while
+// other work is queued.  For them this entry point keeps its scratch in a
+// file-scope device array of fixed size, loaded with the library on every
+// GPU that uses it and held until the process exits.
+//
+// Scratch budget: 16 MiB per device, enough for n + m <= 262,144.  Larger
+// problems are rejected with LP_ERR_INVALID_ARG.
+//
+// Host code cannot use the array's name as a device address (it names a
+// host-side shadow), so the device address is looked up with
+// cudaGetSymbolAddress once per device, with that device current, on the
+// first call made on that device.  Make that first call before any stream
+// capture begins.  Every call reuses the same array: two calls whose work
+// overlaps on the GPU (different streams, different host threads) race on
+// it and must be serialized by the caller.  Every region is fully written
+// by a call before the same call reads it, so nothing has to be cleared
+// between calls.
+namespace {
+
+constexpr size_t kGapScratchBytes = size_t(16) << 20;
+constexpr int64_t kGapScratchMaxElems = int64_t(1) << 18;  // n + m
+constexpr int32_t kGapScratchMaxParts = 4096;               // partial-sum slots per quantity
+constexpr int32_t kGapScratchHistGrid = 64;                 // histogram blocks
+constexpr int kGapScratchMaxDevices = 256;
+
+static __device__ __align__(256) unsigned char g_gap_scratch[kGapScratchBytes];
+
+std::mutex g_gap_scratch_mu;
+void *g_gap_scratch_addr[kGapScratchMaxDevices] = {};
+
+struct ScratchCarver {
+  unsigned char *base;
+  size_t off;
+  size_t cap;
+  void *take(size_t bytes) {
+    off = (off + 255) & ~size_t(255);
+    if (off + bytes > cap) return nullptr;
+    void *p = base + off;
+    off += bytes;
+    return p;
+  }
+};
+
+}  // namespace
+
+extern "C" lp_status lp_normalized_gap_static(lp_handle h, const double *x, const double *y,
+                                              double r, double *host_rho, void *cuda_stream) {
+  g_err.clear();
+  if (!h || !host_rho || !x || (h->m > 0 && !y)) return fail(LP_ERR_INVALID_ARG, "NULL argument");
+  if (!(r >= 0.0) || !std::isfinite(r)) return fail(LP_ERR_INVALID_ARG, "radius must be finite and >= 0");
+  const int n = h->n, m = h->m;
+  const int64_t N = (int64_t)n + m;
+  if (N > kGapScratchMaxElems)
+    return fail(LP_ERR_INVALID_ARG, "lp_normalized_gap_static: n + m = " + std::to_string(N) +
+                                        " exceeds the static scratch limit of " +
+                                        std::to_string(kGapScratchMaxElems));
+  if (h->cs.pstride > kGapScratchMaxParts)
+    return fail(LP_ERR_INVALID_ARG, "lp_normalized_gap_static: too many partial sums for the static scratch");
+  int dev = 0;
+  LP_CU(cudaGetDevice(&dev));
+  if (dev != h->device) return fail(LP_ERR_INVALID_ARG, "the handle's device is not current");
+  if (dev < 0 || dev >= kGapScratchMaxDevices) return fail(LP_ERR_INVALID_ARG, "device index out of range");
+  void *base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_gap_scratch_mu);
+    if (!g_gap_scratch_addr[dev]) {
+      void *p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_gap_scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_gap_scratch)");
+      g_gap_scratch_addr[dev] = p;
+    }
+    base = g_gap_scratch_addr[dev];
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  ScratchCarver sc{static_cast<unsigned char *>(base), 0, kGapScratchBytes};
+  double *xp = (double *)sc.take(sizeof(double) * std::max(n, 1));
+  double *yp = (double *)sc.take(sizeof(double) * std::max(m, 1));
+  double *tmpx = (double *)sc.take(sizeof(double) * std::max(std::max(n, m), 1));
+  DevState *st = (DevState *)sc.take(sizeof(DevState));
+  CheckScratch cs = h->cs;
+  cs.hist_grid = std::min(h->cs.hist_grid, kGapScratchHistGrid);
+  cs.partials = (double *)sc.take(sizeof(double) * NQ * cs.pstride);
+  cs.keys[0] = (uint64_t *)sc.take(sizeof(uint64_t) * N);
+  cs.d2[0] = (double *)sc.take(sizeof(double) * N);
+  cs.g2[0] = (double *)sc.take(sizeof(double) * N);
+  cs.gd[0] = (double *)sc.take(sizeof(double) * N);
+  cs.hpart = (double *)sc.take(sizeof(double) * 2 * cs.hist_grid * 4 * kBuckets);
+  if (!xp || !yp || !tmpx || !st || !cs.partials || !cs.keys[0] || !cs.d2[0] || !cs.g2[0] ||
+      !cs.gd[0] || !cs.hpart)
+    return fail(LP_ERR_INVALID_ARG, "lp_normalized_gap_static: problem does not fit the static scratch");
+  cs.keys[1] = cs.keys[0];
+  cs.d2[1] = cs.d2[0];
+  cs.g2[1] = cs.g2[0];
+  cs.gd[1] = cs.gd[0];
+  LP_CU(cudaMemcpyAsync(tmpx, x, sizeof(double) * n, cudaMemcpyDefault, s));
+  launch_gather(xp, tmpx, h->perm_x, n, s);
+  if (m > 0) {
+    LP_CU(cudaMemcpyAsync(tmpx, y, sizeof(double) * m, cudaMemcpyDefault, s));
+    launch_gather(yp, tmpx, h->perm_y, m, s);
+  }
+  DevVecs v = h->v;
+  v.x = v.xbar = v.x0 = xp;
+  v.y = v.ybar = v.y0 = yp;
+  DevState hs{};
+  LP_CU(cudaMemcpyAsync(&hs, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  LP_CU(cudaStreamSynchronize(s));
+  hs.status = kRunning;
+  hs.given_radius = 1;
+  hs.r_given = r;
+  LP_CU(cudaMemcpyAsync(st, &hs, sizeof(DevState), cudaMemcpyHostToDevice, s));
+  launch_check(h->A, h->AT, v, st, nullptr, cs, n, m, 1, nullptr, false, s);
+  LP_CU(cudaGetLastError());
+  LSearch L{};
+  LP_CU(cudaMemcpyAsync(&L, &st->ls[0], sizeof(LSearch), cudaMemcpyDeviceToHost, s));
+  LP_CU(cudaStreamSynchronize(s));
+  *host_rho = (r == 0.0) ? 0.0 : L.rho_r / r;
+  return LP_OK;
+}

@@ -46,7 +46,7 @@ class lp_info(C.Structure):
 
 EXPORTED = ["lp_default_options", "lp_create", "lp_solve", "lp_iterate", "lp_get_solution",
             "lp_get_state", "lp_set_state", "lp_get_info", "lp_get_trace", "lp_normalized_gap",
-            "lp_profile_kernel", "lp_destroy", "lp_last_error"]
+            "lp_normalized_gap_static", "lp_profile_kernel", "lp_destroy", "lp_last_error"]
 
 _lib = None
 
@@ -85,6 +85,7 @@ def load(build_if_missing: bool = True):
     lib.lp_get_info.argtypes = [P, C.POINTER(lp_info)]
     lib.lp_get_trace.argtypes = [P, P, I64, C.POINTER(I64)]
     lib.lp_normalized_gap.argtypes = [P, P, P, D, C.POINTER(D), P]
+    lib.lp_normalized_gap_static.argtypes = [P, P, P, D, C.POINTER(D), P]
     lib.lp_profile_kernel.argtypes = [P, I32, I32, P]
     lib.lp_destroy.argtypes = [P]
     lib.lp_destroy.restype = None
@@ -92,7 +93,7 @@ def load(build_if_missing: bool = True):
     lib.lp_last_error.restype = C.c_char_p
     for name in ["lp_create", "lp_solve", "lp_iterate", "lp_get_solution", "lp_get_state",
                  "lp_set_state", "lp_get_info", "lp_get_trace", "lp_normalized_gap",
-                 "lp_profile_kernel"]:
+                 "lp_normalized_gap_static", "lp_profile_kernel"]:
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -211,6 +212,16 @@ def lp_normalized_gap(h, x, y, r, stream=None) -> float:
     py, ky = _ptr(y, np.float64)
     out = C.c_double()
     _check(load().lp_normalized_gap(h, px, py, float(r), C.byref(out), _stream(stream)))
+    return out.value
+
+
+def lp_normalized_gap_static(h, x, y, r, stream=None) -> float:
+    """lp_normalized_gap with the library's fixed static scratch (no device
+    allocation; n + m <= 262,144; concurrent calls must be serialized)."""
+    px, kx = _ptr(x, np.float64)
+    py, ky = _ptr(y, np.float64)
+    out = C.c_double()
+    _check(load().lp_normalized_gap_static(h, px, py, float(r), C.byref(out), _stream(stream)))
     return out.value
 
 
