@@ -72,9 +72,15 @@ typedef struct {
   int32_t power_iters;    /* power-iteration cap for sigma_max (default 5000) */
   double power_tol;       /* relative change of the Rayleigh estimate to stop (1e-10) */
   int64_t max_iter;       /* iteration limit of one lp_solve call */
-  int32_t long_row_threshold; /* rows longer than this use the warp-per-row path (512) */
+  int32_t long_row_threshold; /* rows at least this long get a whole warp (32 lanes) (512) */
   int32_t trace_capacity; /* per-check trace rows kept on device (65536) */
-  int32_t reserved[6];
+  int32_t spmv_unroll;    /* gathers in flight per lane, column pass (A^T y): 2, 4, 8; negative
+                             values -2, -4 add a software pipeline over the matrix stream (-2) */
+  int32_t spmv_unroll_rows; /* the same for the row pass (A xhat) (-4) */
+  int32_t lane_steps;     /* rows longer than single_lane_max get the fewest lanes G (power of
+                             two <= 32) with ceil(len / G) <= lane_steps (16) */
+  int32_t single_lane_max; /* rows of at most this many elements get one lane each (64) */
+  int32_t reserved[2];
 } lp_options;
 
 typedef struct {
@@ -90,7 +96,7 @@ typedef struct {
   double last_rho;      /* normalized duality gap at the last check */
   double last_radius;   /* its radius ||zbar - z^{n,0}|| */
   int64_t nnz_padded;   /* stored nonzeros of one copy of A including padding */
-  int32_t n_long_rows, n_long_cols; /* rows/cols on the warp-per-row path */
+  int32_t n_long_rows, n_long_cols; /* rows of A / of A^T handled by a whole warp */
 } lp_info;
 
 /* Defaults: beta = e^-1, K = 64, ADAPTIVE, tau0 = K, omega = 1, eta = 0

@@ -4,8 +4,8 @@
 // Setup (lp_create) builds the library's device layout on the host:
 //   * a CSC copy of A by a stable counting sort (rows ascending per column);
 //   * row and column permutations sorting rows of A and rows of A^T by
-//     length, longest first (stable), so that each SELL-32 slice holds 32
-//     rows of nearly equal length and long rows come first;
+//     length, longest first (stable), so that each slice (one warp) holds
+//     rows of nearly equal length, with 1-32 lanes per row by length;
 //   * both operators relabeled into the permuted index spaces, so every
 //     vector (x, xhat, xbar, x0, c, l, u and y, ybar, y0, b, row sense) is
 //     stored permuted and accessed with unit stride; only the gathered
@@ -50,55 +50,69 @@ lp_status cuda_fail(cudaError_t e, const char *what) {
   } while (0)
 
 struct HostSell {
-  int32_t nrows = 0, ncols = 0, nlong = 0, nslices = 0;
-  std::vector<int64_t> long_ptr, slice_ptr;
-  std::vector<int32_t> long_idx, idx;
-  std::vector<double> long_val, val;
+  int32_t nrows = 0, ncols = 0, nslices = 0, n_warp_rows = 0;
+  std::vector<SliceInfo> info;
+  std::vector<int32_t> idx;
+  std::vector<double> val;
 };
 
-// SELL-32 layout of the operator whose row r (permuted order) is original
-// row perm[r] of the CSR (ptr, ind, v); column indices relabeled by relabel.
+// Lanes per row: rows of at most single_max elements get one lane (no
+// cross-lane sum); longer rows get the fewest lanes G = 2^lg (<= 32) with
+// ceil(len / G) <= lane_steps, so that no lane's chain of dependent
+// gathers is long; rows of at least warp_threshold elements take a warp.
+struct LanePolicy {
+  int32_t warp_threshold, lane_steps, single_max;
+};
+
+int lanes_log2(int64_t len, const LanePolicy &p) {
+  if (len >= p.warp_threshold) return 5;
+  if (len <= p.single_max) return 0;
+  int lg = 0;
+  while (lg < 5 && (int64_t(p.lane_steps) << lg) < len) ++lg;
+  return lg;
+}
+
+// Sliced layout (see SellMat) of the operator whose row r (permuted order)
+// is original row perm[r] of the CSR (ptr, ind, v); column indices
+// relabeled by relabel.  Rows come longest first, so a slice is closed when
+// it is full (32 / G rows) or when the next row wants another G.
 void build_sell(int32_t nrows, int32_t ncols, const std::vector<int64_t> &ptr,
                 const std::vector<int32_t> &ind, const std::vector<double> &v,
                 const std::vector<int32_t> &perm, const std::vector<int32_t> &relabel,
-                int32_t long_threshold, HostSell &S) {
+                const LanePolicy &policy, HostSell &S) {
   S.nrows = nrows;
   S.ncols = ncols;
   auto len = [&](int32_t r) { return ptr[perm[r] + 1] - ptr[perm[r]]; };
-  int32_t nlong = 0;
-  while (nlong < nrows && len(nlong) > long_threshold) ++nlong;
-  S.nlong = nlong;
-  S.long_ptr.assign(nlong + 1, 0);
-  for (int32_t r = 0; r < nlong; ++r) S.long_ptr[r + 1] = S.long_ptr[r] + len(r);
-  S.long_idx.resize(S.long_ptr[nlong]);
-  S.long_val.resize(S.long_ptr[nlong]);
-  for (int32_t r = 0; r < nlong; ++r) {
-    const int64_t src = ptr[perm[r]], dst = S.long_ptr[r];
-    for (int64_t k = 0; k < len(r); ++k) {
-      S.long_idx[dst + k] = relabel[ind[src + k]];
-      S.long_val[dst + k] = v[src + k];
-    }
-  }
-  const int32_t nsell = nrows - nlong;
-  S.nslices = (nsell + kWarp - 1) / kWarp;
-  S.slice_ptr.assign(S.nslices + 1, 0);
-  for (int32_t s = 0; s < S.nslices; ++s) {
+  S.info.clear();
+  int64_t off = 0;
+  int32_t r = 0;
+  while (r < nrows) {
+    const int lg = lanes_log2(len(r), policy);
+    const int cap = kWarp >> lg;
+    int32_t q = r;
     int64_t mx = 0;
-    for (int32_t l = 0; l < kWarp; ++l) {
-      const int32_t r = nlong + s * kWarp + l;
-      if (r < nrows) mx = std::max<int64_t>(mx, len(r));
+    while (q < nrows && q - r < cap && lanes_log2(len(q), policy) == lg) {
+      mx = std::max<int64_t>(mx, len(q));
+      ++q;
     }
-    S.slice_ptr[s + 1] = S.slice_ptr[s] + mx * kWarp;
+    const int64_t steps = (mx + (int64_t(1) << lg) - 1) >> lg;
+    if (lg == 5) S.n_warp_rows += q - r;
+    S.info.push_back(SliceInfo{off, r, (int32_t)((steps << 3) | lg)});
+    off += steps * kWarp;
+    r = q;
   }
-  S.idx.assign(S.slice_ptr[S.nslices], 0);
-  S.val.assign(S.slice_ptr[S.nslices], 0.0);
+  S.nslices = (int32_t)S.info.size();
+  S.info.push_back(SliceInfo{off, nrows, 0});
+  S.idx.assign(off, 0);
+  S.val.assign(off, 0.0);
   for (int32_t s = 0; s < S.nslices; ++s) {
-    for (int32_t l = 0; l < kWarp; ++l) {
-      const int32_t r = nlong + s * kWarp + l;
-      if (r >= nrows) break;
-      const int64_t src = ptr[perm[r]];
-      for (int64_t k = 0; k < len(r); ++k) {
-        const int64_t dst = S.slice_ptr[s] + k * kWarp + l;
+    const SliceInfo &a = S.info[s];
+    const int lg = a.len_g & 7, G = 1 << lg;
+    for (int32_t row = a.row0; row < S.info[s + 1].row0; ++row) {
+      const int64_t src = ptr[perm[row]];
+      const int64_t lane0 = (int64_t)(row - a.row0) * G;
+      for (int64_t k = 0; k < len(row); ++k) {
+        const int64_t dst = a.off + kWarp * (k >> lg) + lane0 + (k & (G - 1));
         S.idx[dst] = relabel[ind[src + k]];
         S.val[dst] = v[src + k];
       }
@@ -168,24 +182,18 @@ struct lp_problem {
   }
 
   lp_status upload_sell(const HostSell &H, SellMat &M) {
-    int64_t *lp = nullptr, *sp = nullptr;
-    int32_t *li = nullptr, *ix = nullptr;
-    double *lv = nullptr, *vv = nullptr;
+    SliceInfo *info = nullptr;
+    int32_t *ix = nullptr;
+    double *vv = nullptr;
     lp_status s;
-    if ((s = upload(&lp, H.long_ptr)) != LP_OK) return s;
-    if ((s = upload(&li, H.long_idx)) != LP_OK) return s;
-    if ((s = upload(&lv, H.long_val)) != LP_OK) return s;
-    if ((s = upload(&sp, H.slice_ptr)) != LP_OK) return s;
+    if ((s = upload(&info, H.info)) != LP_OK) return s;
     if ((s = upload(&ix, H.idx)) != LP_OK) return s;
     if ((s = upload(&vv, H.val)) != LP_OK) return s;
     M.nrows = H.nrows;
     M.ncols = H.ncols;
-    M.nlong = H.nlong;
     M.nslices = H.nslices;
-    M.long_ptr = lp;
-    M.long_idx = li;
-    M.long_val = lv;
-    M.slice_ptr = sp;
+    M.n_warp_rows = H.n_warp_rows;
+    M.info = info;
     M.idx = ix;
     M.val = vv;
     return LP_OK;
@@ -215,6 +223,11 @@ lp_status validate_options(const lp_options &o) {
   if (o.max_iter < 0) return fail(LP_ERR_INVALID_ARG, "max_iter must be >= 0");
   if (o.long_row_threshold < 1) return fail(LP_ERR_INVALID_ARG, "long_row_threshold must be >= 1");
   if (o.trace_capacity < 0) return fail(LP_ERR_INVALID_ARG, "trace_capacity must be >= 0");
+  for (int32_t u : {o.spmv_unroll, o.spmv_unroll_rows})
+    if (u != 2 && u != 4 && u != 8 && u != -2 && u != -4)
+      return fail(LP_ERR_INVALID_ARG, "spmv_unroll(_rows) must be 2, 4, 8, -2 or -4");
+  if (o.lane_steps < 1 || o.lane_steps > 1024) return fail(LP_ERR_INVALID_ARG, "lane_steps must lie in [1, 1024]");
+  if (o.single_lane_max < 0) return fail(LP_ERR_INVALID_ARG, "single_lane_max must be >= 0");
   return LP_OK;
 }
 
@@ -251,8 +264,8 @@ lp_status build_graph(lp_problem *h) {
   cudaStream_t s = h->cap_stream;
   LP_CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   for (int k = 0; k < h->opt.check_every; ++k) {
-    launch_primal_step(h->AT, h->v, h->st, h->w, k, s);
-    launch_dual_step(h->A, h->v, h->st, h->w, k, s);
+    launch_primal_step(h->AT, h->v, h->st, h->w, k, h->opt.spmv_unroll, s);
+    launch_dual_step(h->A, h->v, h->st, h->w, k, h->opt.spmv_unroll_rows, s);
   }
   launch_check(h->A, h->AT, h->v, h->st, h->w, h->cs, h->n, h->m, h->nsearch, h->trace, true, s);
   cudaGraph_t g = nullptr;
@@ -290,6 +303,10 @@ void lp_default_options(lp_options *o) {
   o->max_iter = 10000000;
   o->long_row_threshold = 512;
   o->trace_capacity = 65536;
+  o->spmv_unroll = -2;
+  o->spmv_unroll_rows = -4;
+  o->lane_steps = 16;
+  o->single_lane_max = 64;
 }
 
 const char *lp_last_error(void) { return g_err.c_str(); }
@@ -389,9 +406,10 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
   for (int32_t r = 0; r < m; ++r) inv_y[perm_y[r]] = r;
   for (int32_t r = 0; r < n; ++r) inv_x[perm_x[r]] = r;
   HostSell HA, HAT;
-  build_sell(m, n, rp, hci, hv, perm_y, inv_x, opt.long_row_threshold, HA);
-  build_sell(n, m, cp, ri, cv, perm_x, inv_y, opt.long_row_threshold, HAT);
-  h->nnz_padded = (int64_t)HA.idx.size() + (int64_t)HA.long_idx.size();
+  const LanePolicy policy{opt.long_row_threshold, opt.lane_steps, opt.single_lane_max};
+  build_sell(m, n, rp, hci, hv, perm_y, inv_x, policy, HA);
+  build_sell(n, m, cp, ri, cv, perm_x, inv_y, policy, HAT);
+  h->nnz_padded = (int64_t)HA.idx.size();
 
   // permuted vectors
   std::vector<double> pc(n), pl(n), pu(n), pb(m);
@@ -448,8 +466,9 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
     if ((e = h->alloc(&cs.g2[k], N)) != LP_OK) return e;
     if ((e = h->alloc(&cs.gd[k], N)) != LP_OK) return e;
   }
-  cs.hist_grid = (int)std::min<int64_t>(std::max<int64_t>(1, (N + 4095) / 4096), 2 * h->nsm);
+  cs.hist_grid = (int)std::min<int64_t>(std::max<int64_t>(1, (N + 8191) / 8192), h->nsm);
   if ((e = h->alloc(&cs.hpart, (int64_t)2 * cs.hist_grid * 4 * kBuckets)) != LP_OK) return e;
+  if ((e = h->alloc(&cs.btot, (int64_t)2 * 4 * kBuckets)) != LP_OK) return e;
   LP_CU(cudaMallocHost(&h->h_status, 2 * sizeof(int32_t)));
   LP_CU(cudaEventCreateWithFlags(&h->ev[0], cudaEventDisableTiming));
   LP_CU(cudaEventCreateWithFlags(&h->ev[1], cudaEventDisableTiming));
@@ -580,8 +599,8 @@ lp_status lp_solve(lp_handle h, double tol, void *cuda_stream) {
   if (status == kRunning && remaining > 0) {
     const int r = (int)remaining;
     for (int k = 0; k < r; ++k) {
-      launch_primal_step(h->AT, h->v, h->st, h->w, k, s);
-      launch_dual_step(h->A, h->v, h->st, h->w, k, s);
+      launch_primal_step(h->AT, h->v, h->st, h->w, k, h->opt.spmv_unroll, s);
+      launch_dual_step(h->A, h->v, h->st, h->w, k, h->opt.spmv_unroll_rows, s);
     }
     launch_advance(h->st, h->w, r, s);
     LP_CU(cudaGetLastError());
@@ -659,8 +678,8 @@ lp_status lp_get_info(lp_handle h, lp_info *info) {
   info->last_rho = hs.last_rho;
   info->last_radius = hs.last_r;
   info->nnz_padded = h->nnz_padded;
-  info->n_long_rows = h->A.nlong;
-  info->n_long_cols = h->AT.nlong;
+  info->n_long_rows = h->A.n_warp_rows;
+  info->n_long_cols = h->AT.n_warp_rows;
   return LP_OK;
 }
 
@@ -710,9 +729,10 @@ lp_status lp_normalized_gap(lp_handle h, const double *x, const double *y, doubl
   cs.g2[1] = cs.g2[0];
   cs.gd[1] = cs.gd[0];
   cs.hpart = (double *)get(sizeof(double) * 2 * cs.hist_grid * 4 * kBuckets);
+  cs.btot = (double *)get(sizeof(double) * 2 * 4 * kBuckets);
   double *tmpx = (double *)get(sizeof(double) * std::max(n, m));
   if (!xp || !yp || !st || !cs.partials || !cs.keys[0] || !cs.d2[0] || !cs.g2[0] || !cs.gd[0] ||
-      !cs.hpart || !tmpx) {
+      !cs.hpart || !cs.btot || !tmpx) {
     cudaGetLastError();
     return fail(LP_ERR_OOM, "cudaMalloc of gap scratch failed");
   }
@@ -747,8 +767,8 @@ lp_status lp_profile_kernel(lp_handle h, int32_t which, int32_t reps, void *cuda
   if (which < 0 || which > 1 || reps < 0) return fail(LP_ERR_INVALID_ARG, "which must be 0 or 1, reps >= 0");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   for (int32_t r = 0; r < reps; ++r) {
-    if (which == 0) launch_primal_step(h->AT, h->v, h->st, h->w, 0, s);
-    else launch_dual_step(h->A, h->v, h->st, h->w, 0, s);
+    if (which == 0) launch_primal_step(h->AT, h->v, h->st, h->w, 0, h->opt.spmv_unroll, s);
+    else launch_dual_step(h->A, h->v, h->st, h->w, 0, h->opt.spmv_unroll_rows, s);
   }
   LP_CU(cudaGetLastError());
   return LP_OK;
@@ -856,8 +876,9 @@ extern "C" lp_status lp_normalized_gap_static(lp_handle h, const double *x, cons
   cs.g2[0] = (double *)sc.take(sizeof(double) * N);
   cs.gd[0] = (double *)sc.take(sizeof(double) * N);
   cs.hpart = (double *)sc.take(sizeof(double) * 2 * cs.hist_grid * 4 * kBuckets);
+  cs.btot = (double *)sc.take(sizeof(double) * 2 * 4 * kBuckets);
   if (!xp || !yp || !tmpx || !st || !cs.partials || !cs.keys[0] || !cs.d2[0] || !cs.g2[0] ||
-      !cs.gd[0] || !cs.hpart)
+      !cs.gd[0] || !cs.hpart || !cs.btot)
     return fail(LP_ERR_INVALID_ARG, "lp_normalized_gap_static: problem does not fit the static scratch");
   cs.keys[1] = cs.keys[0];
   cs.d2[1] = cs.d2[0];

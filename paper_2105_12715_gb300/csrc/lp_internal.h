@@ -16,21 +16,28 @@ constexpr int kHistWarps = 4;         // warps per block of the histogram kernel
 constexpr uint64_t kNoKey = ~0ull;    // element that takes no part in the search
 constexpr int32_t kRunning = -1;      // DevState::status while iterating
 
+// Per-slice metadata of the sliced layout (see SellMat).
+struct SliceInfo {
+  int64_t off;    // element offset of the slice (multiple of 32)
+  int32_t row0;   // first row of the slice (permuted order)
+  int32_t len_g;  // (steps << 3) | log2(G): steps of 32 elements, G lanes per row
+};
+
 // One copy of A (or A^T) in the library's device layout.  Rows are in the
-// library's permuted order: rows [0, nlong) are "long" and stored CSR-style
-// (one warp per row); rows [nlong, nrows) are grouped in slices of 32
-// consecutive rows stored column-major inside the slice (SELL-32): element
-// k of the slice's lane l sits at slice_ptr[s] + 32 k + l, padded with
-// zero values up to the slice's longest row.
+// library's permuted order (longest first).  Consecutive rows of similar
+// length form a slice handled by one warp: each row gets G lanes
+// (G = 1, 2, ..., 32, chosen from the row length so that a lane walks about
+// 8-15 elements), so a slice holds 32 / G rows.  Element k of the slice's
+// i-th row sits at off + 32 * (k / G) + i * G + (k % G): every warp-wide
+// load of the matrix stream is 32 consecutive elements.  Rows are padded
+// with zero values up to the slice's longest row (a multiple of G).
+// info has nslices + 1 entries; the last one holds the end offset and nrows.
 struct SellMat {
   int32_t nrows;
   int32_t ncols;
-  int32_t nlong;
   int32_t nslices;
-  const int64_t *long_ptr;   // [nlong + 1]
-  const int32_t *long_idx;
-  const double *long_val;
-  const int64_t *slice_ptr;  // [nslices + 1], element offsets, multiples of 32
+  int32_t n_warp_rows;      // rows with G = 32 (a whole warp per row)
+  const SliceInfo *info;    // [nslices + 1]
   const int32_t *idx;
   const double *val;
 };
@@ -87,6 +94,11 @@ struct DevState {
   int32_t pw_max;
   int32_t pad2;
   double pw_tol;
+  // cross-block reductions (last-block pattern; counters return to 0)
+  double tot[NQ];
+  unsigned int fin_counter;
+  unsigned int sel_counter[2];
+  unsigned int pad3;
 };
 
 // Device arrays of one problem, permuted order.
@@ -105,14 +117,15 @@ struct CheckScratch {
   uint64_t *keys[2];       // [n + m] per candidate
   double *d2[2], *g2[2], *gd[2];
   double *hpart;           // [2][hist_grid][4][kBuckets]
+  double *btot;            // [2][4][kBuckets] bucket totals of the current pass
   int32_t hist_grid;
 };
 
 // ---- launchers (lp_kernels.cu) ----
 void launch_primal_step(const SellMat &AT, const DevVecs &v, DevState *st,
-                        const double *w, int k, cudaStream_t s);
+                        const double *w, int k, int unroll, cudaStream_t s);
 void launch_dual_step(const SellMat &A, const DevVecs &v, DevState *st,
-                      const double *w, int k, cudaStream_t s);
+                      const double *w, int k, int unroll, cudaStream_t s);
 void launch_check(const SellMat &A, const SellMat &AT, const DevVecs &v,
                   DevState *st, double *w, const CheckScratch &cs, int n,
                   int m, int nsearch, double *trace, bool decide,

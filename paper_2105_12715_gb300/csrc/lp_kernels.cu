@@ -27,6 +27,8 @@ namespace lpg {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kUnroll = 8;   // gathers in flight per lane, one vector (plain SpMV)
+constexpr int kUnroll2 = 4;  // gathers in flight per lane and vector, two vectors
 constexpr int kStatusOK = 0;
 constexpr int kStatusNumerical = 5;
 constexpr int kSchemeFixed = 1, kSchemeAdaptive = 2, kSchemeFlexible = 3;
@@ -35,87 +37,99 @@ __device__ __forceinline__ double sq(double v) { return v * v; }
 
 // ------------------------------------------------------------------ SpMV core
 //
-// Row sums of one work item of a SellMat: a long row (whole warp, lanes
-// stride over the row, butterfly reduction) or a slice of 32 rows (one
-// lane per row, sequential in the row's stored order).  NV = 1 or 2
-// gathered vectors.  The epilogue's operands are loaded before the row
-// loop so that their latency overlaps the matrix stream.
-template <int NV, class Epi>
+// Row sums of one slice (one warp).  Each lane walks its row's elements
+// k = g, g + G, g + 2G, ... in stored order, U steps at a time: the U
+// index and value loads of a batch are issued together, then the U
+// gathers, then the FMAs, so a lane has U gathers in flight.  The G lanes of
+// a row are then combined by a butterfly (the same sum in every lane of the
+// group), and the group's first lane runs the epilogue.  The epilogue's
+// operands are loaded before the row loop.  NV = 1 or 2 gathered vectors.
+template <int NV, int U, bool PIPE, class Epi>
 __device__ __forceinline__ void process_item(const SellMat &A,
                                              const double *__restrict__ v0,
                                              const double *__restrict__ v1,
                                              int item, int lane, Epi &epi) {
-  if (item < A.nlong) {
-    const int64_t s = A.long_ptr[item], e = A.long_ptr[item + 1];
-    typename Epi::Pre pre{};
-    if (lane == 0) pre = epi.load(item);
-    double a0 = 0.0, a1 = 0.0;
-    for (int64_t p = s + lane; p < e; p += kWarp) {
-      const int32_t j = __ldcs(A.long_idx + p);
-      const double a = __ldcs(A.long_val + p);
-      a0 = fma(a, __ldg(v0 + j), a0);
-      if (NV == 2) a1 = fma(a, __ldg(v1 + j), a1);
+  const SliceInfo a = A.info[item];
+  const int32_t row_end = A.info[item + 1].row0;
+  const int lg = a.len_g & 7;
+  const int steps = a.len_g >> 3;
+  const int row = a.row0 + (lane >> lg);
+  const bool owner = ((lane & ((1 << lg) - 1)) == 0) && row < row_end;
+  typename Epi::Pre pre{};
+  if (owner) pre = epi.load(row);
+  const int32_t *ip = A.idx + a.off + lane;
+  const double *vp = A.val + a.off + lane;
+  double a0 = 0.0, a1 = 0.0;
+  int32_t j[U];
+  double c[U];
+  if (PIPE) {  // software pipeline: the next batch's index/value loads overlap this batch's gathers
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (u < steps) {
+        j[u] = __ldcs(ip + (size_t)kWarp * u);
+        c[u] = __ldcs(vp + (size_t)kWarp * u);
+      }
+    }
+  }
+  for (int t = 0; t < steps; t += U) {
+    double g[U], h[U];
+    if (!PIPE) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (t + u < steps) {
+          j[u] = __ldcs(ip + (size_t)kWarp * (t + u));
+          c[u] = __ldcs(vp + (size_t)kWarp * (t + u));
+        }
+      }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a0 += __shfl_xor_sync(kFull, a0, o);
-      if (NV == 2) a1 += __shfl_xor_sync(kFull, a1, o);
+    for (int u = 0; u < U; ++u) {
+      if (t + u < steps) {
+        g[u] = __ldg(v0 + j[u]);
+        if (NV == 2) h[u] = __ldg(v1 + j[u]);
+      }
     }
-    if (lane == 0) epi.store(item, a0, a1, pre);
-    return;
-  }
-  const int s = item - A.nlong;
-  const int row = A.nlong + s * kWarp + lane;
-  const bool valid = row < A.nrows;
-  typename Epi::Pre pre{};
-  if (valid) pre = epi.load(row);
-  const int64_t base = A.slice_ptr[s];
-  const int len = (int)((A.slice_ptr[s + 1] - base) >> 5);
-  const int32_t *ip = A.idx + base + lane;
-  const double *vp = A.val + base + lane;
-  double a0 = 0.0, a1 = 0.0;
-  int k = 0;
-  for (; k + 4 <= len; k += 4) {
-    const int32_t j0 = __ldcs(ip), j1 = __ldcs(ip + 32), j2 = __ldcs(ip + 64),
-                  j3 = __ldcs(ip + 96);
-    const double c0 = __ldcs(vp), c1 = __ldcs(vp + 32), c2 = __ldcs(vp + 64),
-                 c3 = __ldcs(vp + 96);
-    const double g0 = __ldg(v0 + j0), g1 = __ldg(v0 + j1), g2 = __ldg(v0 + j2),
-                 g3 = __ldg(v0 + j3);
-    if (NV == 2) {
-      const double h0 = __ldg(v1 + j0), h1 = __ldg(v1 + j1), h2 = __ldg(v1 + j2),
-                   h3 = __ldg(v1 + j3);
-      a1 = fma(c0, h0, a1);
-      a1 = fma(c1, h1, a1);
-      a1 = fma(c2, h2, a1);
-      a1 = fma(c3, h3, a1);
+    int32_t jn[U];
+    double cn[U];
+    if (PIPE) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (t + U + u < steps) {
+          jn[u] = __ldcs(ip + (size_t)kWarp * (t + U + u));
+          cn[u] = __ldcs(vp + (size_t)kWarp * (t + U + u));
+        }
+      }
     }
-    a0 = fma(c0, g0, a0);
-    a0 = fma(c1, g1, a0);
-    a0 = fma(c2, g2, a0);
-    a0 = fma(c3, g3, a0);
-    ip += 4 * kWarp;
-    vp += 4 * kWarp;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (t + u < steps) {
+        a0 = fma(c[u], g[u], a0);
+        if (NV == 2) a1 = fma(c[u], h[u], a1);
+      }
+    }
+    if (PIPE) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        j[u] = jn[u];
+        c[u] = cn[u];
+      }
+    }
   }
-  for (; k < len; ++k) {
-    const int32_t j = __ldcs(ip);
-    const double c = __ldcs(vp);
-    a0 = fma(c, __ldg(v0 + j), a0);
-    if (NV == 2) a1 = fma(c, __ldg(v1 + j), a1);
-    ip += kWarp;
-    vp += kWarp;
+  for (int o = (1 << lg) >> 1; o > 0; o >>= 1) {
+    a0 += __shfl_xor_sync(kFull, a0, o);
+    if (NV == 2) a1 += __shfl_xor_sync(kFull, a1, o);
   }
-  if (valid) epi.store(row, a0, a1, pre);
+  if (owner) epi.store(row, a0, a1, pre);
 }
 
-template <int NV, class Epi>
+template <int NV, int U, bool PIPE = false, class Epi>
 __device__ __forceinline__ void process_all(const SellMat &A, const double *v0,
                                             const double *v1, Epi &epi) {
   const int lane = threadIdx.x & (kWarp - 1);
   const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nwarps = (int)(gridDim.x * blockDim.x) >> 5;
-  const int items = A.nlong + A.nslices;
-  for (int it = warp; it < items; it += nwarps) process_item<NV>(A, v0, v1, it, lane, epi);
+  for (int it = warp; it < A.nslices; it += nwarps)
+    process_item<NV, U, PIPE>(A, v0, v1, it, lane, epi);
 }
 
 // Fixed-order block reduction of NV2 per-thread values; thread q < NV2 of
@@ -320,28 +334,30 @@ struct CheckRowsEpi {
 
 // ------------------------------------------------------------ iteration
 
+template <int U, bool PIPE>
 __global__ void __launch_bounds__(kBlock) primal_kernel(SellMat AT, const double *__restrict__ y,
                                                         PrimalEpi epi, const DevState *st,
                                                         const double *__restrict__ w, int k) {
   if (st->status != kRunning) return;
   epi.tau = st->tau;
   epi.w = w[k];
-  process_all<1>(AT, y, nullptr, epi);
+  process_all<1, U, PIPE>(AT, y, nullptr, epi);
 }
 
+template <int U, bool PIPE>
 __global__ void __launch_bounds__(kBlock) dual_kernel(SellMat A, const double *__restrict__ xhat,
                                                       DualEpi epi, const DevState *st,
                                                       const double *__restrict__ w, int k) {
   if (st->status != kRunning) return;
   epi.sigma = st->sigma;
   epi.w = w[k];
-  process_all<1>(A, xhat, nullptr, epi);
+  process_all<1, U, PIPE>(A, xhat, nullptr, epi);
 }
 
 __global__ void __launch_bounds__(kBlock) spmv_kernel(SellMat A, const double *__restrict__ v,
                                                       StoreEpi epi, const DevState *st) {
   if (st && (st->status != kRunning || st->pw_done)) return;
-  process_all<1>(A, v, nullptr, epi);
+  process_all<1, kUnroll>(A, v, nullptr, epi);
 }
 
 // ---------------------------------------------------------------- check
@@ -361,7 +377,7 @@ __global__ void __launch_bounds__(kBlock) check_kernel(SellMat A, const double *
   epi.isw = 1.0 / epi.sw;
 #pragma unroll
   for (int i = 0; i < NQ; ++i) epi.q[i] = 0.0;
-  process_all<2>(A, v0, v1, epi);
+  process_all<2, kUnroll2>(A, v0, v1, epi);
   block_reduce_store<NQ>(epi.q, partials, pstride, poff + (int)blockIdx.x);
 }
 
@@ -392,25 +408,39 @@ __device__ void kkt_from(const double *t, int qp, int qd, int qpo, int qdo, doub
   out[0] = rp; out[1] = rd; out[2] = p; out[3] = d; out[4] = rel;
 }
 
+// Reduction of the check's partial sums: block q sums quantity q over the
+// partial blocks in a fixed order (strided per thread, then a fixed tree);
+// the last block to finish (threadfence + counter; no waiting) applies the
+// termination test and prepares the multiplier search.  Spreading the FP64
+// additions over NQ blocks keeps them off a single SM's FP64 pipe.
 __global__ void __launch_bounds__(kBlock) check_finalize_kernel(DevState *st,
                                                                 const double *partials,
                                                                 int pstride, int nparts) {
   if (st->status != kRunning) return;
-  __shared__ double tot[NQ];
   __shared__ double red[kBlock];
-  for (int qi = 0; qi < NQ; ++qi) {
-    double s = 0.0;
-    for (int p = threadIdx.x; p < nparts; p += kBlock) s += partials[(size_t)qi * pstride + p];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = kBlock / 2; o > 0; o >>= 1) {
-      if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) tot[qi] = red[0];
+  __shared__ bool last;
+  const int q = blockIdx.x;
+  double acc = 0.0;
+  for (int p = threadIdx.x; p < nparts; p += kBlock) acc += partials[(size_t)q * pstride + p];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = kBlock / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
+  if (threadIdx.x == 0) {
+    st->tot[q] = red[0];
+    __threadfence();
+    last = (atomicAdd(&st->fin_counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
   if (threadIdx.x != 0) return;
+  __threadfence();
+  st->fin_counter = 0u;
+  double tot[NQ];
+  const volatile double *vt = st->tot;
+  for (int i = 0; i < NQ; ++i) tot[i] = vt[i];
   const double om = st->omega;
   if (st->given_radius) {  // standalone gap evaluation
     init_search(st->ls[0], st->r_given, tot[Q_D2_A], tot[Q_GD_A], tot[Q_G2INF_A]);
@@ -505,27 +535,64 @@ __global__ void __launch_bounds__(kHistWarps *kWarp) ls_hist_kernel(
       }
     }
     if (__ballot_sync(kFull, act) == 0u) continue;
+    double vd = 0.0, vg = 0.0, ve = 0.0;
     if (act) {
-      stage[warp][lane][0] = d2[e];
-      stage[warp][lane][1] = g2[e];
-      stage[warp][lane][2] = gd[e];
+      vd = d2[e];
+      vg = g2[e];
+      ve = gd[e];
     }
-    __syncwarp();
     const unsigned grp = __match_any_sync(kFull, bk);
-    if (act && (grp & ((1u << lane) - 1u)) == 0u) {
-      double sd = 0.0, sg = 0.0, se = 0.0;
-      unsigned gm = grp;
-      while (gm) {
-        const int l = __ffs(gm) - 1;
-        gm &= gm - 1u;
-        sd += stage[warp][l][0];
-        sg += stage[warp][l][1];
-        se += stage[warp][l][2];
+    const bool leader = act && (grp & ((1u << lane) - 1u)) == 0u;
+    const unsigned leaders = __ballot_sync(kFull, leader);
+    const int ndist = __popc(leaders);
+    const int maxg = (int)__reduce_max_sync(kFull, act ? (unsigned)__popc(grp) : 0u);
+    if (15 * ndist < 3 * maxg) {
+      // few distinct buckets: one warp-wide butterfly sum per bucket
+      unsigned rem = leaders;
+      while (rem) {
+        const int l = __ffs(rem) - 1;
+        rem &= rem - 1u;
+        const int b = __shfl_sync(kFull, bk, l);
+        const bool mine = act && bk == b;
+        const unsigned mm = __ballot_sync(kFull, mine);
+        double sd = mine ? vd : 0.0, sg = mine ? vg : 0.0, se = mine ? ve : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          sd += __shfl_xor_sync(kFull, sd, o);
+          sg += __shfl_xor_sync(kFull, sg, o);
+          se += __shfl_xor_sync(kFull, se, o);
+        }
+        if (lane == 0) {
+          hist[warp][b][0] += sd;
+          hist[warp][b][1] += sg;
+          hist[warp][b][2] += se;
+          cnt[warp][b] += (unsigned)__popc(mm);
+        }
+        __syncwarp();
       }
-      hist[warp][bk][0] += sd;
-      hist[warp][bk][1] += sg;
-      hist[warp][bk][2] += se;
-      cnt[warp][bk] += (unsigned)__popc(grp);
+    } else {
+      // many distinct buckets: each group's lowest lane sums its group in lane order
+      if (act) {
+        stage[warp][lane][0] = vd;
+        stage[warp][lane][1] = vg;
+        stage[warp][lane][2] = ve;
+      }
+      __syncwarp();
+      if (leader) {
+        double sd = 0.0, sg = 0.0, se = 0.0;
+        unsigned gm = grp;
+        while (gm) {
+          const int l = __ffs(gm) - 1;
+          gm &= gm - 1u;
+          sd += stage[warp][l][0];
+          sg += stage[warp][l][1];
+          se += stage[warp][l][2];
+        }
+        hist[warp][bk][0] += sd;
+        hist[warp][bk][1] += sg;
+        hist[warp][bk][2] += se;
+        cnt[warp][bk] += (unsigned)__popc(grp);
+      }
     }
     __syncwarp();
   }
@@ -546,55 +613,114 @@ __global__ void __launch_bounds__(kHistWarps *kWarp) ls_hist_kernel(
   }
 }
 
+// Fixed-order inclusive scan of 256 values held one per thread of the
+// first 256 threads (8 warps): shuffle scan inside each warp, then the warp
+// totals.  Returns the inclusive prefix for thread b.
+__device__ __forceinline__ double scan256(double v, double *warp_tot) {
+  const int b = threadIdx.x, lane = b & 31, w = b >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double u = __shfl_up_sync(kFull, v, o);
+    if (lane >= o) v += u;
+  }
+  if (lane == 31) warp_tot[w] = v;
+  __syncwarp();
+  return v;
+}
+
+// Block (b, search) sums bucket b's four values over the histogram blocks
+// in a fixed order; the last block to finish (threadfence + counter) picks
+// the bracket.  The FP64 additions are spread over 256 blocks.
 __global__ void __launch_bounds__(kBuckets) ls_select_kernel(DevState *st, int pass,
-                                                             const double *hpart, int hist_grid) {
-  LSearch &L = st->ls[blockIdx.x];
+                                                             const double *hpart, double *btot,
+                                                             int hist_grid) {
+  const int sidx = blockIdx.y;
+  LSearch &L = st->ls[sidx];
   if (L.done) return;
-  const int b = threadIdx.x;
+  const int tid = threadIdx.x, bucket = blockIdx.x;
+  __shared__ double red[4][kBuckets];
+  __shared__ bool last;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const double *base = hpart + (size_t)sidx * hist_grid * 4 * kBuckets;
+  for (int blk = tid; blk < hist_grid; blk += kBuckets) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] += base[((size_t)blk * 4 + q) * kBuckets + bucket];
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) red[q][tid] = acc[q];
+  __syncthreads();
+  for (int o = kBuckets / 2; o > 0; o >>= 1) {
+    if (tid < o) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) red[q][tid] += red[q][tid + o];
+    }
+    __syncthreads();
+  }
+  double *bt = btot + (size_t)sidx * 4 * kBuckets;
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) bt[q * kBuckets + bucket] = red[q][0];
+    __threadfence();
+    last = (atomicAdd(&st->sel_counter[sidx], 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int b = tid;
   __shared__ double cnt[kBuckets], sd[kBuckets], sg[kBuckets], se[kBuckets];
   __shared__ double cum_d[kBuckets + 1], cum_e[kBuckets + 1], tail_g[kBuckets + 1];
+  __shared__ double wt[3][8];
   __shared__ int kstar;
-  double c = 0.0, d = 0.0, g = 0.0, e = 0.0;
-  for (int blk = 0; blk < hist_grid; ++blk) {
-    const double *p = hpart + ((size_t)blockIdx.x * hist_grid + blk) * 4 * kBuckets;
-    c += p[b];
-    d += p[kBuckets + b];
-    g += p[2 * kBuckets + b];
-    e += p[3 * kBuckets + b];
-  }
-  cnt[b] = c;
-  sd[b] = d;
-  sg[b] = g;
-  se[b] = e;
-  if (b == 0) kstar = -1;
-  __syncthreads();
-  // exclusive prefix sums of d^2 and d g, inclusive suffix sums of g^2
-  if (b == 0) {
-    double s = 0.0;
-    for (int k = 0; k < kBuckets; ++k) { cum_d[k] = s; s += sd[k]; }
-    cum_d[kBuckets] = s;
-  } else if (b == 32) {
-    double s = 0.0;
-    for (int k = 0; k < kBuckets; ++k) { cum_e[k] = s; s += se[k]; }
-    cum_e[kBuckets] = s;
-  } else if (b == 64) {
-    double s = 0.0;
-    tail_g[kBuckets] = 0.0;
-    for (int k = kBuckets - 1; k >= 0; --k) { s += sg[k]; tail_g[k] = s; }
+  const volatile double *vb = bt;
+  cnt[b] = vb[b];
+  sd[b] = vb[kBuckets + b];
+  sg[b] = vb[2 * kBuckets + b];
+  se[b] = vb[3 * kBuckets + b];
+  if (tid == 0) {
+    kstar = -1;
+    st->sel_counter[sidx] = 0u;
   }
   __syncthreads();
-  const int shift = 56 - 8 * pass;
-  const uint64_t edge_bits = L.prefix | ((uint64_t)b << shift);
-  const double edge = __longlong_as_double((long long)edge_bits);
-  bool ok = false;
-  if ((edge_bits >> 63) == 0ull && isfinite(edge)) {  // edges are nonnegative finite doubles
-    const double f = L.f_lo + cum_d[b] + edge * edge * (L.f_hi + tail_g[b]);
-    ok = f <= L.r2;
+  // exclusive prefix sums of d^2 and d g, suffix sums of g^2 (fixed order)
+  double pd = 0.0, pe = 0.0, pg = 0.0;
+  if (tid < kBuckets) {  // warps 0..7, whole warps
+    pd = scan256(sd[b], wt[0]);
+    pe = scan256(se[b], wt[1]);
+    pg = scan256(sg[kBuckets - 1 - b], wt[2]);  // reversed order: suffix sums
   }
-  if (ok) atomicMax(&kstar, b);
   __syncthreads();
-  if (b != 0) return;
+  if (tid < kBuckets) {
+    double od = 0.0, oe = 0.0, og = 0.0;
+    for (int w = 0; w < (b >> 5); ++w) {
+      od += wt[0][w];
+      oe += wt[1][w];
+      og += wt[2][w];
+    }
+    cum_d[b + 1] = od + pd;
+    cum_e[b + 1] = oe + pe;
+    tail_g[kBuckets - 1 - b] = og + pg;
+    if (b == 0) {
+      cum_d[0] = 0.0;
+      cum_e[0] = 0.0;
+      tail_g[kBuckets] = 0.0;
+    }
+  }
+  __syncthreads();
+  if (tid < kBuckets) {
+    const int shift = 56 - 8 * pass;
+    const uint64_t edge_bits = L.prefix | ((uint64_t)b << shift);
+    const double edge = __longlong_as_double((long long)edge_bits);
+    bool ok = false;
+    if ((edge_bits >> 63) == 0ull && isfinite(edge)) {  // edges are nonnegative finite doubles
+      const double f = L.f_lo + cum_d[b] + edge * edge * (L.f_hi + tail_g[b]);
+      ok = f <= L.r2;
+    }
+    if (ok) atomicMax(&kstar, b);
+  }
+  __syncthreads();
+  if (tid != 0) return;
   const int k = kstar < 0 ? 0 : kstar;
+  const int shift = 56 - 8 * pass;
   L.f_lo += cum_d[k];
   L.e_lo += cum_e[k];
   L.f_hi += tail_g[k + 1];
@@ -840,7 +966,7 @@ int grid_for(int64_t n, int num_sms) {
 }
 
 int item_grid(const SellMat &A) {
-  const int64_t items = (int64_t)A.nlong + A.nslices;
+  const int64_t items = A.nslices;
   int64_t g = (items + kWarpsPerBlock - 1) / kWarpsPerBlock;
   if (g < 1) g = 1;
   return (int)g;
@@ -860,7 +986,7 @@ int num_sms() {
 }  // namespace
 
 int check_grid_for(const SellMat &A, int nsm) {
-  const int64_t items = (int64_t)A.nlong + A.nslices;
+  const int64_t items = A.nslices;
   int64_t g = (items + kWarpsPerBlock - 1) / kWarpsPerBlock;
   const int64_t cap = (int64_t)nsm * 4;
   if (g > cap) g = cap;
@@ -869,15 +995,29 @@ int check_grid_for(const SellMat &A, int nsm) {
 }
 
 void launch_primal_step(const SellMat &AT, const DevVecs &v, DevState *st, const double *w,
-                        int k, cudaStream_t s) {
+                        int k, int unroll, cudaStream_t s) {
   PrimalEpi epi{v.c, v.lb, v.ub, v.x, v.xhat, v.xbar, 0.0, 0.0};
-  primal_kernel<<<item_grid(AT), kBlock, 0, s>>>(AT, v.y, epi, st, w, k);
+  const int g = item_grid(AT);
+  switch (unroll) {
+    case 2: primal_kernel<2, false><<<g, kBlock, 0, s>>>(AT, v.y, epi, st, w, k); break;
+    case 8: primal_kernel<8, false><<<g, kBlock, 0, s>>>(AT, v.y, epi, st, w, k); break;
+    case -2: primal_kernel<2, true><<<g, kBlock, 0, s>>>(AT, v.y, epi, st, w, k); break;
+    case -4: primal_kernel<4, true><<<g, kBlock, 0, s>>>(AT, v.y, epi, st, w, k); break;
+    default: primal_kernel<4, false><<<g, kBlock, 0, s>>>(AT, v.y, epi, st, w, k); break;
+  }
 }
 
 void launch_dual_step(const SellMat &A, const DevVecs &v, DevState *st, const double *w, int k,
-                      cudaStream_t s) {
+                      int unroll, cudaStream_t s) {
   DualEpi epi{v.b, v.row_type, v.y, v.ybar, 0.0, 0.0};
-  dual_kernel<<<item_grid(A), kBlock, 0, s>>>(A, v.xhat, epi, st, w, k);
+  const int g = item_grid(A);
+  switch (unroll) {
+    case 2: dual_kernel<2, false><<<g, kBlock, 0, s>>>(A, v.xhat, epi, st, w, k); break;
+    case 8: dual_kernel<8, false><<<g, kBlock, 0, s>>>(A, v.xhat, epi, st, w, k); break;
+    case -2: dual_kernel<2, true><<<g, kBlock, 0, s>>>(A, v.xhat, epi, st, w, k); break;
+    case -4: dual_kernel<4, true><<<g, kBlock, 0, s>>>(A, v.xhat, epi, st, w, k); break;
+    default: dual_kernel<4, false><<<g, kBlock, 0, s>>>(A, v.xhat, epi, st, w, k); break;
+  }
 }
 
 void launch_check(const SellMat &A, const SellMat &AT, const DevVecs &v, DevState *st, double *w,
@@ -900,7 +1040,7 @@ void launch_check(const SellMat &A, const SellMat &AT, const DevVecs &v, DevStat
                                                              cs.pstride, 0);
   check_kernel<CheckRowsEpi><<<cs.rows_grid, kBlock, 0, s>>>(A, v.xbar, v.x, re, st, cs.partials,
                                                              cs.pstride, cs.cols_grid);
-  check_finalize_kernel<<<1, kBlock, 0, s>>>(st, cs.partials, cs.pstride,
+  check_finalize_kernel<<<NQ, kBlock, 0, s>>>(st, cs.partials, cs.pstride,
                                              cs.cols_grid + cs.rows_grid);
   if (nsearch > 0) {
     const int64_t N = (int64_t)n + m;
@@ -908,7 +1048,8 @@ void launch_check(const SellMat &A, const SellMat &AT, const DevVecs &v, DevStat
       ls_hist_kernel<<<dim3(cs.hist_grid, nsearch), kHistWarps * kWarp, 0, s>>>(
           cs.keys[0], cs.d2[0], cs.g2[0], cs.gd[0], cs.keys[1], cs.d2[1], cs.g2[1], cs.gd[1], N,
           st, p, cs.hpart);
-      ls_select_kernel<<<nsearch, kBuckets, 0, s>>>(st, p, cs.hpart, cs.hist_grid);
+      ls_select_kernel<<<dim3(kBuckets, nsearch), kBuckets, 0, s>>>(st, p, cs.hpart, cs.btot,
+                                                                 cs.hist_grid);
     }
   }
   if (decide) {

@@ -31,7 +31,9 @@ class lp_options(C.Structure):
                 ("tau0", C.c_int64), ("fixed_len", C.c_int64), ("omega", C.c_double),
                 ("eta", C.c_double), ("power_iters", C.c_int32), ("power_tol", C.c_double),
                 ("max_iter", C.c_int64), ("long_row_threshold", C.c_int32),
-                ("trace_capacity", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("trace_capacity", C.c_int32), ("spmv_unroll", C.c_int32),
+                ("spmv_unroll_rows", C.c_int32), ("lane_steps", C.c_int32),
+                ("single_lane_max", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class lp_info(C.Structure):

@@ -37,9 +37,10 @@ def close(gpu, ref, tol=TOL, what=""):
 
 
 def run_both(lpm, oracle_mod, data, iters, eta, K=64, omega=1.0, scheme=2, long_thr=512,
-             x_init=None, y_init=None):
+             x_init=None, y_init=None, unroll=4):
     with lpm.LP(data, eta=eta, omega=omega, check_every=K, restart_scheme=scheme,
-                max_iter=iters, long_row_threshold=long_thr) as g:
+                max_iter=iters, long_row_threshold=long_thr, spmv_unroll=unroll,
+                spmv_unroll_rows=unroll) as g:
         if x_init is not None:
             g.set_state(x_init, y_init)
         status = g.solve(1e-300)
@@ -101,11 +102,12 @@ def test_mixed_bounds_rows_and_long_rows(lpm, oracle_mod, omega):
     np.testing.assert_array_equal(tr[:, 2], ref.trace[:, 2])
 
 
-def test_ragged_multi_slice_power_law(lpm, oracle_mod):
+@pytest.mark.parametrize("unroll", [2, 4, 8, -2, -4])
+def test_ragged_multi_slice_power_law(lpm, oracle_mod, unroll):
     """Several hundred slices with a ragged last slice, power-law columns."""
     data = lpgen.large_mixed(11, m=3001, n=15007)
     eta = eta_of(oracle_mod, data)
-    status, st, info, tr, ref = run_both(lpm, oracle_mod, data, 130, eta, K=64)
+    status, st, info, tr, ref = run_both(lpm, oracle_mod, data, 130, eta, K=64, unroll=unroll)
     compare_states(st, ref)
     assert info.restarts == ref.restarts
 
