@@ -80,7 +80,10 @@ typedef struct {
   int32_t lane_steps;     /* rows longer than single_lane_max get the fewest lanes G (power of
                              two <= 32) with ceil(len / G) <= lane_steps (16) */
   int32_t single_lane_max; /* rows of at most this many elements get one lane each (64) */
-  int32_t reserved[2];
+  int32_t spmv_mode;      /* iteration kernels: 0 = one warp per slice with register batches,
+                             1 = persistent warps with a TMA-staged (cp.async.bulk) matrix
+                             stream (0) */
+  int32_t reserved[1];
 } lp_options;
 
 typedef struct {

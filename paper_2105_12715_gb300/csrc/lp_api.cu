@@ -120,6 +120,39 @@ void build_sell(int32_t nrows, int32_t ncols, const std::vector<int64_t> &ptr,
   }
 }
 
+// Segments of at most kSegSteps steps, and a split of them over nwarps
+// persistent warps: contiguous ranges, cut only where a slice starts,
+// balanced by cost = elements + 64 per slice (the epilogue).
+void build_plan(const HostSell &S, int32_t nwarps, std::vector<WorkSeg> &segs,
+                std::vector<int32_t> &warp_begin) {
+  segs.clear();
+  std::vector<int64_t> cost;
+  for (int32_t s = 0; s < S.nslices; ++s) {
+    const SliceInfo &a = S.info[s];
+    const int32_t steps = a.len_g >> 3;
+    int32_t t0 = 0;
+    do {
+      const int32_t ns = std::min(kSegSteps, steps - t0);
+      const int first = (t0 == 0), last = (t0 + ns >= steps);
+      segs.push_back(WorkSeg{a.off + (int64_t)kWarp * t0, s, (ns << 2) | (first << 1) | last});
+      cost.push_back((int64_t)kWarp * ns + (last ? 64 : 0));
+      t0 += ns;
+    } while (t0 < steps);
+  }
+  const int64_t nseg = (int64_t)segs.size();
+  int64_t total = 0;
+  for (int64_t c : cost) total += c;
+  warp_begin.assign(nwarps + 1, (int32_t)nseg);
+  warp_begin[0] = 0;
+  int64_t acc = 0;
+  int32_t w = 1;
+  for (int64_t i = 0; i < nseg && w < nwarps; ++i) {
+    // a cut before segment i is allowed only at a slice start
+    while (w < nwarps && (segs[i].steps_fl & 2) && acc >= (total * w) / nwarps) warp_begin[w++] = (int32_t)i;
+    acc += cost[i];
+  }
+}
+
 double now_seconds() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
       .count();
@@ -135,6 +168,7 @@ struct lp_problem {
   int nsm = 0;
   std::vector<void *> allocs;
   SellMat A{}, AT{};
+  StreamPlan PA{}, PAT{};  // staged-kernel plans of A (row pass) and A^T (column pass)
   DevVecs v{};
   DevState *st = nullptr;
   double *w = nullptr;
@@ -178,6 +212,22 @@ struct lp_problem {
     lp_status s = alloc(p, (int64_t)h.size());
     if (s != LP_OK) return s;
     if (!h.empty()) LP_CU(cudaMemcpy(*p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+    return LP_OK;
+  }
+
+  lp_status upload_plan(const HostSell &H, int32_t nwarps, StreamPlan &P) {
+    std::vector<WorkSeg> segs;
+    std::vector<int32_t> wb;
+    build_plan(H, nwarps, segs, wb);
+    WorkSeg *ds = nullptr;
+    int32_t *dw = nullptr;
+    lp_status s;
+    if ((s = upload(&ds, segs)) != LP_OK) return s;
+    if ((s = upload(&dw, wb)) != LP_OK) return s;
+    P.segs = ds;
+    P.warp_begin = dw;
+    P.nwarps = nwarps;
+    P.nseg = (int32_t)segs.size();
     return LP_OK;
   }
 
@@ -228,6 +278,7 @@ lp_status validate_options(const lp_options &o) {
       return fail(LP_ERR_INVALID_ARG, "spmv_unroll(_rows) must be 2, 4, 8, -2 or -4");
   if (o.lane_steps < 1 || o.lane_steps > 1024) return fail(LP_ERR_INVALID_ARG, "lane_steps must lie in [1, 1024]");
   if (o.single_lane_max < 0) return fail(LP_ERR_INVALID_ARG, "single_lane_max must be >= 0");
+  if (o.spmv_mode != 0 && o.spmv_mode != 1) return fail(LP_ERR_INVALID_ARG, "spmv_mode must be 0 or 1");
   return LP_OK;
 }
 
@@ -259,14 +310,21 @@ lp_status reset_state(lp_problem *h, cudaStream_t s) {
   return LP_OK;
 }
 
+void launch_iteration(lp_problem *h, int k, cudaStream_t s) {
+  if (h->opt.spmv_mode == 1) {
+    launch_primal_stream(h->AT, h->PAT, h->v, h->st, h->w, k, s);
+    launch_dual_stream(h->A, h->PA, h->v, h->st, h->w, k, s);
+  } else {
+    launch_primal_step(h->AT, h->v, h->st, h->w, k, h->opt.spmv_unroll, s);
+    launch_dual_step(h->A, h->v, h->st, h->w, k, h->opt.spmv_unroll_rows, s);
+  }
+}
+
 lp_status build_graph(lp_problem *h) {
   if (h->exec) return LP_OK;
   cudaStream_t s = h->cap_stream;
   LP_CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  for (int k = 0; k < h->opt.check_every; ++k) {
-    launch_primal_step(h->AT, h->v, h->st, h->w, k, h->opt.spmv_unroll, s);
-    launch_dual_step(h->A, h->v, h->st, h->w, k, h->opt.spmv_unroll_rows, s);
-  }
+  for (int k = 0; k < h->opt.check_every; ++k) launch_iteration(h, k, s);
   launch_check(h->A, h->AT, h->v, h->st, h->w, h->cs, h->n, h->m, h->nsearch, h->trace, true, s);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(s, &g);
@@ -307,6 +365,7 @@ void lp_default_options(lp_options *o) {
   o->spmv_unroll_rows = -4;
   o->lane_steps = 16;
   o->single_lane_max = 64;
+  o->spmv_mode = 0;
 }
 
 const char *lp_last_error(void) { return g_err.c_str(); }
@@ -428,6 +487,12 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
   lp_status e;
   if ((e = h->upload_sell(HA, h->A)) != LP_OK) return e;
   if ((e = h->upload_sell(HAT, h->AT)) != LP_OK) return e;
+  if (opt.spmv_mode == 1) {
+    const int32_t nwarps = h->nsm * kStreamWarpsPerSM;
+    if ((e = h->upload_plan(HA, nwarps, h->PA)) != LP_OK) return e;
+    if ((e = h->upload_plan(HAT, nwarps, h->PAT)) != LP_OK) return e;
+    LP_CU(prepare_stream_kernels());
+  }
   if ((e = h->upload(&h->v.c, pc)) != LP_OK) return e;
   if ((e = h->upload(&h->v.lb, pl)) != LP_OK) return e;
   if ((e = h->upload(&h->v.ub, pu)) != LP_OK) return e;
@@ -598,10 +663,7 @@ lp_status lp_solve(lp_handle h, double tol, void *cuda_stream) {
   LP_CU(cudaStreamSynchronize(s));
   if (status == kRunning && remaining > 0) {
     const int r = (int)remaining;
-    for (int k = 0; k < r; ++k) {
-      launch_primal_step(h->AT, h->v, h->st, h->w, k, h->opt.spmv_unroll, s);
-      launch_dual_step(h->A, h->v, h->st, h->w, k, h->opt.spmv_unroll_rows, s);
-    }
+    for (int k = 0; k < r; ++k) launch_iteration(h, k, s);
     launch_advance(h->st, h->w, r, s);
     LP_CU(cudaGetLastError());
   }
@@ -767,8 +829,13 @@ lp_status lp_profile_kernel(lp_handle h, int32_t which, int32_t reps, void *cuda
   if (which < 0 || which > 1 || reps < 0) return fail(LP_ERR_INVALID_ARG, "which must be 0 or 1, reps >= 0");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   for (int32_t r = 0; r < reps; ++r) {
-    if (which == 0) launch_primal_step(h->AT, h->v, h->st, h->w, 0, h->opt.spmv_unroll, s);
-    else launch_dual_step(h->A, h->v, h->st, h->w, 0, h->opt.spmv_unroll_rows, s);
+    if (h->opt.spmv_mode == 1) {
+      if (which == 0) launch_primal_stream(h->AT, h->PAT, h->v, h->st, h->w, 0, s);
+      else launch_dual_stream(h->A, h->PA, h->v, h->st, h->w, 0, s);
+    } else {
+      if (which == 0) launch_primal_step(h->AT, h->v, h->st, h->w, 0, h->opt.spmv_unroll, s);
+      else launch_dual_step(h->A, h->v, h->st, h->w, 0, h->opt.spmv_unroll_rows, s);
+    }
   }
   LP_CU(cudaGetLastError());
   return LP_OK;

@@ -33,7 +33,8 @@ class lp_options(C.Structure):
                 ("max_iter", C.c_int64), ("long_row_threshold", C.c_int32),
                 ("trace_capacity", C.c_int32), ("spmv_unroll", C.c_int32),
                 ("spmv_unroll_rows", C.c_int32), ("lane_steps", C.c_int32),
-                ("single_lane_max", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("single_lane_max", C.c_int32), ("spmv_mode", C.c_int32),
+                ("reserved", C.c_int32 * 1)]
 
 
 class lp_info(C.Structure):
