@@ -531,7 +531,7 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
     if ((e = h->alloc(&cs.g2[k], N)) != LP_OK) return e;
     if ((e = h->alloc(&cs.gd[k], N)) != LP_OK) return e;
   }
-  cs.hist_grid = (int)std::min<int64_t>(std::max<int64_t>(1, (N + 8191) / 8192), h->nsm);
+  cs.hist_grid = (int)std::min<int64_t>(std::max<int64_t>(1, (N + 2047) / 2048), 4 * h->nsm);
   if ((e = h->alloc(&cs.hpart, (int64_t)2 * cs.hist_grid * 4 * kBuckets)) != LP_OK) return e;
   if ((e = h->alloc(&cs.btot, (int64_t)2 * 4 * kBuckets)) != LP_OK) return e;
   LP_CU(cudaMallocHost(&h->h_status, 2 * sizeof(int32_t)));
