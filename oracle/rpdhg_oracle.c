@@ -406,8 +406,9 @@ typedef struct {
  * smaller relative KKT error at the last check.
  *
  * Every check_every iterations (Section 7: 30) the relative KKT error is
- * evaluated at the average and at the current iterate (Table 3 caption:
- * "either for the average or last iterate"; the average wins ties), and the
+ * evaluated at the average and at the current iterate (Table 3 counts a
+ * run as solved when either candidate meets the tolerance; here the
+ * average wins ties), and the
  * restart rule runs:
  *   ADAPTIVE, Eq. (adaptive-restart-scheme): restart when
  *     rho_{||zbar - z^{n,0}||}(zbar) <= beta * rho_{||z^{n,0} - z^{n-1,0}||}(z^{n,0})
