@@ -75,7 +75,9 @@ typedef struct {
   int32_t long_row_threshold; /* rows at least this long get a whole warp (32 lanes) (512) */
   int32_t trace_capacity; /* per-check trace rows kept on device (65536) */
   int32_t spmv_unroll;    /* gathers in flight per lane, column pass (A^T y): 2, 4, 8; negative
-                             values -2, -4 add a software pipeline over the matrix stream (-2) */
+                             values -2, -4 add a software pipeline over the matrix stream;
+                             adding 100 (or -100 for negative values) caps the registers for
+                             higher occupancy (-2) */
   int32_t spmv_unroll_rows; /* the same for the row pass (A xhat) (-4) */
   int32_t lane_steps;     /* rows longer than single_lane_max get the fewest lanes G (power of
                              two <= 32) with ceil(len / G) <= lane_steps (16) */

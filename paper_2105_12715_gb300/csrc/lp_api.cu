@@ -185,6 +185,7 @@ struct lp_problem {
   cudaEvent_t ev[2] = {nullptr, nullptr};
   bool solved = false;
   int nsearch = 1;
+  int grid_cap = 0;  // blocks of the per-slice iteration kernels (0: one warp per slice)
 
   ~lp_problem() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -273,9 +274,12 @@ lp_status validate_options(const lp_options &o) {
   if (o.max_iter < 0) return fail(LP_ERR_INVALID_ARG, "max_iter must be >= 0");
   if (o.long_row_threshold < 1) return fail(LP_ERR_INVALID_ARG, "long_row_threshold must be >= 1");
   if (o.trace_capacity < 0) return fail(LP_ERR_INVALID_ARG, "trace_capacity must be >= 0");
-  for (int32_t u : {o.spmv_unroll, o.spmv_unroll_rows})
-    if (u != 2 && u != 4 && u != 8 && u != -2 && u != -4)
-      return fail(LP_ERR_INVALID_ARG, "spmv_unroll(_rows) must be 2, 4, 8, -2 or -4");
+  for (int32_t u : {o.spmv_unroll, o.spmv_unroll_rows}) {
+    const int32_t b = u % 100;
+    if (u / 100 < -1 || u / 100 > 1 || (b != 2 && b != 4 && b != 8 && b != -2 && b != -4))
+      return fail(LP_ERR_INVALID_ARG,
+                  "spmv_unroll(_rows) must be 2, 4, 8, -2 or -4, or that +-100 (capped registers)");
+  }
   if (o.lane_steps < 1 || o.lane_steps > 1024) return fail(LP_ERR_INVALID_ARG, "lane_steps must lie in [1, 1024]");
   if (o.single_lane_max < 0) return fail(LP_ERR_INVALID_ARG, "single_lane_max must be >= 0");
   if (o.spmv_mode != 0 && o.spmv_mode != 1) return fail(LP_ERR_INVALID_ARG, "spmv_mode must be 0 or 1");
@@ -315,8 +319,8 @@ void launch_iteration(lp_problem *h, int k, cudaStream_t s) {
     launch_primal_stream(h->AT, h->PAT, h->v, h->st, h->w, k, s);
     launch_dual_stream(h->A, h->PA, h->v, h->st, h->w, k, s);
   } else {
-    launch_primal_step(h->AT, h->v, h->st, h->w, k, h->opt.spmv_unroll, s);
-    launch_dual_step(h->A, h->v, h->st, h->w, k, h->opt.spmv_unroll_rows, s);
+    launch_primal_step(h->AT, h->v, h->st, h->w, k, h->opt.spmv_unroll, h->grid_cap, s);
+    launch_dual_step(h->A, h->v, h->st, h->w, k, h->opt.spmv_unroll_rows, h->grid_cap, s);
   }
 }
 
@@ -436,6 +440,7 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
   h->opt = opt;
   LP_CU(cudaGetDevice(&h->device));
   LP_CU(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device));
+  h->grid_cap = opt.reserved[0] > 0 ? opt.reserved[0] * h->nsm : 0;
   h->nsearch = (opt.restart_scheme == LP_RESTART_ADAPTIVE) ? 1
                : (opt.restart_scheme == LP_RESTART_FLEXIBLE) ? 2 : 0;
 
@@ -496,6 +501,20 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
   if ((e = h->upload(&h->v.c, pc)) != LP_OK) return e;
   if ((e = h->upload(&h->v.lb, pl)) != LP_OK) return e;
   if ((e = h->upload(&h->v.ub, pu)) != LP_OK) return e;
+  {
+    // order keys of the bounds: the bit pattern, with all bits but the sign
+    // flipped for negative values (monotone as signed 64-bit integers)
+    std::vector<long long> lk(n), uk(n);
+    for (int32_t r = 0; r < n; ++r) {
+      long long bl, bu;
+      std::memcpy(&bl, &pl[r], 8);
+      std::memcpy(&bu, &pu[r], 8);
+      lk[r] = bl < 0 ? (bl ^ 0x7fffffffffffffffll) : bl;
+      uk[r] = bu < 0 ? (bu ^ 0x7fffffffffffffffll) : bu;
+    }
+    if ((e = h->upload(&h->v.lbk, lk)) != LP_OK) return e;
+    if ((e = h->upload(&h->v.ubk, uk)) != LP_OK) return e;
+  }
   if ((e = h->upload(&h->v.b, pb)) != LP_OK) return e;
   if ((e = h->upload(&h->v.row_type, prt)) != LP_OK) return e;
   if ((e = h->upload(&h->perm_x, perm_x)) != LP_OK) return e;
@@ -833,8 +852,8 @@ lp_status lp_profile_kernel(lp_handle h, int32_t which, int32_t reps, void *cuda
       if (which == 0) launch_primal_stream(h->AT, h->PAT, h->v, h->st, h->w, 0, s);
       else launch_dual_stream(h->A, h->PA, h->v, h->st, h->w, 0, s);
     } else {
-      if (which == 0) launch_primal_step(h->AT, h->v, h->st, h->w, 0, h->opt.spmv_unroll, s);
-      else launch_dual_step(h->A, h->v, h->st, h->w, 0, h->opt.spmv_unroll_rows, s);
+      if (which == 0) launch_primal_step(h->AT, h->v, h->st, h->w, 0, h->opt.spmv_unroll, h->grid_cap, s);
+      else launch_dual_step(h->A, h->v, h->st, h->w, 0, h->opt.spmv_unroll_rows, h->grid_cap, s);
     }
   }
   LP_CU(cudaGetLastError());

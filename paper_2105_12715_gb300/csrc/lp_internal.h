@@ -123,6 +123,7 @@ struct DevState {
 // Device arrays of one problem, permuted order.
 struct DevVecs {
   double *c, *lb, *ub, *b;
+  long long *lbk, *ubk;  // order keys of lb, ub (integer-pipe clamps)
   int8_t *row_type;
   double *x, *xhat, *xbar, *x0;
   double *y, *ybar, *y0;
@@ -142,9 +143,9 @@ struct CheckScratch {
 
 // ---- launchers (lp_kernels.cu) ----
 void launch_primal_step(const SellMat &AT, const DevVecs &v, DevState *st,
-                        const double *w, int k, int unroll, cudaStream_t s);
+                        const double *w, int k, int unroll, int grid_cap, cudaStream_t s);
 void launch_dual_step(const SellMat &A, const DevVecs &v, DevState *st,
-                      const double *w, int k, int unroll, cudaStream_t s);
+                      const double *w, int k, int unroll, int grid_cap, cudaStream_t s);
 void launch_primal_stream(const SellMat &AT, const StreamPlan &P, const DevVecs &v,
                           DevState *st, const double *w, int k, cudaStream_t s);
 void launch_dual_stream(const SellMat &A, const StreamPlan &P, const DevVecs &v,

@@ -18,6 +18,7 @@
 //   restart_copy: z^{n+1,0} <- zbar and z <- zbar on restart.
 // All reductions run in a fixed order, so results are bitwise reproducible
 // for a given problem and launch configuration.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -59,7 +60,7 @@ __device__ __forceinline__ void process_item(const SellMat &A,
   if (owner) pre = epi.load(row);
   const int32_t *ip = A.idx + a.off + lane;
   const double *vp = A.val + a.off + lane;
-  double a0 = 0.0, a1 = 0.0;
+  double a0 = owner ? epi.init(pre) : 0.0, a1 = 0.0;
   int32_t j[U];
   double c[U];
   if (PIPE) {  // software pipeline: the next batch's index/value loads overlap this batch's gathers
@@ -156,25 +157,42 @@ __device__ __forceinline__ void block_reduce_store(const double (&q)[NV2], doubl
 
 // -------------------------------------------------------------- epilogues
 
-// Eq. (PDHG-update), primal half, and Algorithm 1's running average.
+// Order-preserving map of a double's bit pattern to a signed integer
+// (negative values: all bits but the sign flipped); it is its own inverse.
+// Clamps and sign projections compare these keys on the integer pipe
+// instead of issuing FP64 min/max (GB300 runs 2 FP64 operations per cycle
+// per SM).
+__device__ __forceinline__ long long ord_key(long long b) {
+  return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+
+// Eq. (PDHG-update), primal half, and Algorithm 1's running average.  The
+// row sum starts at -c_j, so it ends as (A^T y)_j - c_j = -g_j.  lbk/ubk are
+// the bounds' order keys.
 struct PrimalEpi {
   const double *__restrict__ c;
-  const double *__restrict__ lb;
-  const double *__restrict__ ub;
+  const long long *__restrict__ lbk;
+  const long long *__restrict__ ubk;
   double *x, *xhat, *xbar;
   double tau, w;
-  struct Pre { double c, lb, ub, x, xb; };
-  __device__ __forceinline__ Pre load(int j) const { return {c[j], lb[j], ub[j], x[j], xbar[j]}; }
-  __device__ __forceinline__ void store(int j, double aty, double, const Pre &p) const {
-    const double g = p.c - aty;
-    const double xn = fmin(fmax(fma(-tau, g, p.x), p.lb), p.ub);
+  struct Pre { double c, x, xb; long long lk, uk; };
+  __device__ __forceinline__ Pre load(int j) const { return {c[j], x[j], xbar[j], lbk[j], ubk[j]}; }
+  __device__ __forceinline__ double init(const Pre &p) const { return -p.c; }
+  __device__ __forceinline__ void store(int j, double neg_g, double, const Pre &p) const {
+    const double v = fma(tau, neg_g, p.x);  // x - tau (c - A^T y)
+    long long k = ord_key(__double_as_longlong(v));
+    k = k < p.lk ? p.lk : k;
+    k = k > p.uk ? p.uk : k;
+    const double xn = __longlong_as_double(ord_key(k));
     x[j] = xn;
     xhat[j] = fma(2.0, xn, -p.x);
     xbar[j] = fma(w, xn - p.xb, p.xb);
   }
 };
 
-// Eq. (PDHG-update), dual half: projection onto Y_i by row sense.
+// Eq. (PDHG-update), dual half: projection onto Y_i by row sense (on the
+// integer pipe: a negative double has a negative bit pattern).  The row sum
+// starts at -b_i, so it ends as (A xhat)_i - b_i.
 struct DualEpi {
   const double *__restrict__ b;
   const int8_t *__restrict__ rt;
@@ -182,10 +200,12 @@ struct DualEpi {
   double sigma, w;
   struct Pre { double b, y, yb; int t; };
   __device__ __forceinline__ Pre load(int i) const { return {b[i], y[i], ybar[i], (int)rt[i]}; }
-  __device__ __forceinline__ void store(int i, double ax, double, const Pre &p) const {
-    double yn = fma(sigma, p.b - ax, p.y);
-    if (p.t == 1) yn = fmax(yn, 0.0);
-    else if (p.t == 2) yn = fmin(yn, 0.0);
+  __device__ __forceinline__ double init(const Pre &p) const { return -p.b; }
+  __device__ __forceinline__ void store(int i, double r, double, const Pre &p) const {
+    long long bits = __double_as_longlong(fma(-sigma, r, p.y));  // y + sigma (b - A xhat)
+    if (p.t == 1 && bits < 0) bits = 0;       // GE: [0, inf)
+    else if (p.t == 2 && bits > 0) bits = 0;  // LE: (-inf, 0]
+    const double yn = __longlong_as_double(bits);
     y[i] = yn;
     ybar[i] = fma(w, yn - p.yb, p.yb);
   }
@@ -195,6 +215,7 @@ struct StoreEpi {
   double *out;
   struct Pre {};
   __device__ __forceinline__ Pre load(int) const { return {}; }
+  __device__ __forceinline__ double init(const Pre &) const { return 0.0; }
   __device__ __forceinline__ void store(int r, double a, double, const Pre &) const { out[r] = a; }
 };
 
@@ -252,6 +273,7 @@ struct CheckColsEpi {
   __device__ __forceinline__ Pre load(int j) const {
     return {c[j], lb[j], ub[j], xbar[j], x[j], x0[j]};
   }
+  __device__ __forceinline__ double init(const Pre &) const { return 0.0; }
   __device__ __forceinline__ void store(int j, double aty_a, double aty_c, const Pre &p) {
     const bool lf = p.lb > -INFINITY, uf = p.ub < INFINITY;
     // Lambda_j: {0} free, [0,inf) only l finite, (-inf,0] only u finite, R both
@@ -302,6 +324,7 @@ struct CheckRowsEpi {
   double q[NQ];
   struct Pre { double b, yb, y, y0; int t; };
   __device__ __forceinline__ Pre load(int i) const { return {b[i], ybar[i], y[i], y0[i], (int)rt[i]}; }
+  __device__ __forceinline__ double init(const Pre &) const { return 0.0; }
   __device__ __forceinline__ void store(int i, double ax_a, double ax_c, const Pre &p) {
     double va = ax_a - p.b, vc = ax_c - p.b;
     if (p.t == 1) { va = fmin(va, 0.0); vc = fmin(vc, 0.0); }
@@ -334,8 +357,8 @@ struct CheckRowsEpi {
 
 // ------------------------------------------------------------ iteration
 
-template <int U, bool PIPE>
-__global__ void __launch_bounds__(kBlock) primal_kernel(SellMat AT, const double *__restrict__ y,
+template <int U, bool PIPE, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) primal_kernel(SellMat AT, const double *__restrict__ y,
                                                         PrimalEpi epi, const DevState *st,
                                                         const double *__restrict__ w, int k) {
   if (st->status != kRunning) return;
@@ -344,8 +367,8 @@ __global__ void __launch_bounds__(kBlock) primal_kernel(SellMat AT, const double
   process_all<1, U, PIPE>(AT, y, nullptr, epi);
 }
 
-template <int U, bool PIPE>
-__global__ void __launch_bounds__(kBlock) dual_kernel(SellMat A, const double *__restrict__ xhat,
+template <int U, bool PIPE, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) dual_kernel(SellMat A, const double *__restrict__ xhat,
                                                       DualEpi epi, const DevState *st,
                                                       const double *__restrict__ w, int k) {
   if (st->status != kRunning) return;
@@ -465,7 +488,7 @@ __device__ __forceinline__ void stream_warp(const SellMat &A, const StreamPlan &
       row = a.row0 + (lane >> lg);
       owner = ((lane & ((1 << lg) - 1)) == 0) && row < row_end;
       if (owner) pre = epi.load(row);
-      a0 = 0.0;
+      a0 = owner ? epi.init(pre) : 0.0;
     }
     if (ns > 0) {
       const uint32_t parity = (b ? uses1 : uses0) & 1u;
@@ -1147,35 +1170,54 @@ int check_grid_for(const SellMat &A, int nsm) {
   return (int)g;
 }
 
+// unroll: 2, 4, 8 = register batches; -2, -4 = software-pipelined batches.
+// |unroll| >= 100 (e.g. 102, -104): the same with registers capped for 5
+// (column pass) or 4 (row pass) resident blocks of 256 threads.
+template <int U, bool PIPE>
+void primal_launch(int occ, int g, cudaStream_t s, const SellMat &AT, const double *y,
+                   const PrimalEpi &epi, DevState *st, const double *w, int k) {
+  if (occ) primal_kernel<U, PIPE, 5><<<g, kBlock, 0, s>>>(AT, y, epi, st, w, k);
+  else primal_kernel<U, PIPE, 1><<<g, kBlock, 0, s>>>(AT, y, epi, st, w, k);
+}
+
+template <int U, bool PIPE>
+void dual_launch(int occ, int g, cudaStream_t s, const SellMat &A, const double *xhat,
+                 const DualEpi &epi, DevState *st, const double *w, int k) {
+  if (occ) dual_kernel<U, PIPE, 4><<<g, kBlock, 0, s>>>(A, xhat, epi, st, w, k);
+  else dual_kernel<U, PIPE, 1><<<g, kBlock, 0, s>>>(A, xhat, epi, st, w, k);
+}
+
 void launch_primal_step(const SellMat &AT, const DevVecs &v, DevState *st, const double *w,
-                        int k, int unroll, cudaStream_t s) {
-  PrimalEpi epi{v.c, v.lb, v.ub, v.x, v.xhat, v.xbar, 0.0, 0.0};
-  const int g = item_grid(AT);
-  switch (unroll) {
-    case 2: primal_kernel<2, false><<<g, kBlock, 0, s>>>(AT, v.y, epi, st, w, k); break;
-    case 8: primal_kernel<8, false><<<g, kBlock, 0, s>>>(AT, v.y, epi, st, w, k); break;
-    case -2: primal_kernel<2, true><<<g, kBlock, 0, s>>>(AT, v.y, epi, st, w, k); break;
-    case -4: primal_kernel<4, true><<<g, kBlock, 0, s>>>(AT, v.y, epi, st, w, k); break;
-    default: primal_kernel<4, false><<<g, kBlock, 0, s>>>(AT, v.y, epi, st, w, k); break;
+                        int k, int unroll, int grid_cap, cudaStream_t s) {
+  PrimalEpi epi{v.c, v.lbk, v.ubk, v.x, v.xhat, v.xbar, 0.0, 0.0};
+  const int g = grid_cap > 0 ? std::min(item_grid(AT), grid_cap) : item_grid(AT);
+  const int occ = (unroll >= 100 || unroll <= -100) ? 1 : 0;
+  switch (unroll % 100) {
+    case 2: primal_launch<2, false>(occ, g, s, AT, v.y, epi, st, w, k); break;
+    case 8: primal_launch<8, false>(occ, g, s, AT, v.y, epi, st, w, k); break;
+    case -2: primal_launch<2, true>(occ, g, s, AT, v.y, epi, st, w, k); break;
+    case -4: primal_launch<4, true>(occ, g, s, AT, v.y, epi, st, w, k); break;
+    default: primal_launch<4, false>(occ, g, s, AT, v.y, epi, st, w, k); break;
   }
 }
 
 void launch_dual_step(const SellMat &A, const DevVecs &v, DevState *st, const double *w, int k,
-                      int unroll, cudaStream_t s) {
+                      int unroll, int grid_cap, cudaStream_t s) {
   DualEpi epi{v.b, v.row_type, v.y, v.ybar, 0.0, 0.0};
-  const int g = item_grid(A);
-  switch (unroll) {
-    case 2: dual_kernel<2, false><<<g, kBlock, 0, s>>>(A, v.xhat, epi, st, w, k); break;
-    case 8: dual_kernel<8, false><<<g, kBlock, 0, s>>>(A, v.xhat, epi, st, w, k); break;
-    case -2: dual_kernel<2, true><<<g, kBlock, 0, s>>>(A, v.xhat, epi, st, w, k); break;
-    case -4: dual_kernel<4, true><<<g, kBlock, 0, s>>>(A, v.xhat, epi, st, w, k); break;
-    default: dual_kernel<4, false><<<g, kBlock, 0, s>>>(A, v.xhat, epi, st, w, k); break;
+  const int g = grid_cap > 0 ? std::min(item_grid(A), grid_cap) : item_grid(A);
+  const int occ = (unroll >= 100 || unroll <= -100) ? 1 : 0;
+  switch (unroll % 100) {
+    case 2: dual_launch<2, false>(occ, g, s, A, v.xhat, epi, st, w, k); break;
+    case 8: dual_launch<8, false>(occ, g, s, A, v.xhat, epi, st, w, k); break;
+    case -2: dual_launch<2, true>(occ, g, s, A, v.xhat, epi, st, w, k); break;
+    case -4: dual_launch<4, true>(occ, g, s, A, v.xhat, epi, st, w, k); break;
+    default: dual_launch<4, false>(occ, g, s, A, v.xhat, epi, st, w, k); break;
   }
 }
 
 void launch_primal_stream(const SellMat &AT, const StreamPlan &P, const DevVecs &v, DevState *st,
                           const double *w, int k, cudaStream_t s) {
-  PrimalEpi epi{v.c, v.lb, v.ub, v.x, v.xhat, v.xbar, 0.0, 0.0};
+  PrimalEpi epi{v.c, v.lbk, v.ubk, v.x, v.xhat, v.xbar, 0.0, 0.0};
   const int grid = (P.nwarps + kStreamWarps - 1) / kStreamWarps;
   primal_stream_kernel<<<grid, kStreamWarps * kWarp, kStreamSmem, s>>>(AT, P, v.y, epi, st, w, k);
 }
