@@ -51,6 +51,16 @@ typedef enum {
 
 enum { LP_ROW_EQ = 0, LP_ROW_GE = 1, LP_ROW_LE = 2 };
 
+/* Arithmetic of the iterations.  FP64: everything in double.  MIXED: the
+ * PDHG iterations run in FP32 (FP32 matrix values, iterates, FP32
+ * accumulation) on a scaled correction dz = s (z - z^{n,0}) around the
+ * restart point of Algorithm 1; the running average, the KKT and
+ * normalized-gap checks, the restart point and the correction data
+ * (residuals formed at every restart) stay in FP64.  Re-forming the
+ * correction at each restart is a residual-correction refinement, so the
+ * solution reaches FP64 accuracy. */
+enum { LP_PRECISION_FP64 = 0, LP_PRECISION_MIXED = 1 };
+
 /* Restart schemes of Section 4 (fixed frequency, Eq. define:t-star;
  * adaptive, Eq. adaptive-restart-scheme) and Section 7 (no restarts; the
  * flexible scheme of Remark "Flexible restarts"). */
@@ -85,7 +95,7 @@ typedef struct {
   int32_t spmv_mode;      /* iteration kernels: 0 = one warp per slice with register batches,
                              1 = persistent warps with a TMA-staged (cp.async.bulk) matrix
                              stream (0) */
-  int32_t reserved[1];
+  int32_t precision;      /* LP_PRECISION_FP64 (default) or LP_PRECISION_MIXED */
 } lp_options;
 
 typedef struct {

@@ -170,6 +170,8 @@ struct lp_problem {
   SellMat A{}, AT{};
   StreamPlan PA{}, PAT{};  // staged-kernel plans of A (row pass) and A^T (column pass)
   DevVecs v{};
+  MixVecs mv{};
+  bool mixed = false;
   DevState *st = nullptr;
   double *w = nullptr;
   CheckScratch cs{};
@@ -232,14 +234,21 @@ struct lp_problem {
     return LP_OK;
   }
 
-  lp_status upload_sell(const HostSell &H, SellMat &M) {
+  lp_status upload_sell(const HostSell &H, SellMat &M, bool with_f32) {
     SliceInfo *info = nullptr;
     int32_t *ix = nullptr;
     double *vv = nullptr;
+    float *vf = nullptr;
     lp_status s;
     if ((s = upload(&info, H.info)) != LP_OK) return s;
     if ((s = upload(&ix, H.idx)) != LP_OK) return s;
     if ((s = upload(&vv, H.val)) != LP_OK) return s;
+    if (with_f32) {
+      std::vector<float> hf(H.val.size());
+      for (size_t i = 0; i < hf.size(); ++i) hf[i] = (float)H.val[i];
+      if ((s = upload(&vf, hf)) != LP_OK) return s;
+    }
+    M.valf = vf;
     M.nrows = H.nrows;
     M.ncols = H.ncols;
     M.nslices = H.nslices;
@@ -283,6 +292,8 @@ lp_status validate_options(const lp_options &o) {
   if (o.lane_steps < 1 || o.lane_steps > 1024) return fail(LP_ERR_INVALID_ARG, "lane_steps must lie in [1, 1024]");
   if (o.single_lane_max < 0) return fail(LP_ERR_INVALID_ARG, "single_lane_max must be >= 0");
   if (o.spmv_mode != 0 && o.spmv_mode != 1) return fail(LP_ERR_INVALID_ARG, "spmv_mode must be 0 or 1");
+  if (o.precision != LP_PRECISION_FP64 && o.precision != LP_PRECISION_MIXED)
+    return fail(LP_ERR_INVALID_ARG, "precision must be LP_PRECISION_FP64 or LP_PRECISION_MIXED");
   return LP_OK;
 }
 
@@ -307,15 +318,23 @@ lp_status reset_state(lp_problem *h, cudaStream_t s) {
   hs.ls[0].done = hs.ls[1].done = 1;
   hs.trace_count = 0;
   hs.given_radius = 0;
+  hs.mix_s = 1.0;
   LP_CU(cudaMemcpyAsync(h->st, &hs, sizeof(DevState), cudaMemcpyHostToDevice, s));
   LP_CU(cudaStreamSynchronize(s));
   launch_weights(h->st, h->w, s);
+  if (h->mixed) {  // correction data at the starting point, dz = 0
+    launch_residuals(h->A, h->AT, h->v, h->mv, h->n, h->m, s);
+    launch_recenter(h->v, h->mv, h->st, h->n, h->m, 1, s);
+  }
   LP_CU(cudaGetLastError());
   return LP_OK;
 }
 
 void launch_iteration(lp_problem *h, int k, cudaStream_t s) {
-  if (h->opt.spmv_mode == 1) {
+  if (h->mixed) {
+    launch_primal_mix(h->AT, h->mv, h->st, h->w, k, s);
+    launch_dual_mix(h->A, h->mv, h->v, h->st, h->w, k, s);
+  } else if (h->opt.spmv_mode == 1) {
     launch_primal_stream(h->AT, h->PAT, h->v, h->st, h->w, k, s);
     launch_dual_stream(h->A, h->PA, h->v, h->st, h->w, k, s);
   } else {
@@ -329,7 +348,8 @@ lp_status build_graph(lp_problem *h) {
   cudaStream_t s = h->cap_stream;
   LP_CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   for (int k = 0; k < h->opt.check_every; ++k) launch_iteration(h, k, s);
-  launch_check(h->A, h->AT, h->v, h->st, h->w, h->cs, h->n, h->m, h->nsearch, h->trace, true, s);
+  launch_check(h->A, h->AT, h->v, h->st, h->w, h->cs, h->n, h->m, h->nsearch, h->trace, true, s,
+               h->mixed ? &h->mv : nullptr);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(s, &g);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
@@ -440,7 +460,6 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
   h->opt = opt;
   LP_CU(cudaGetDevice(&h->device));
   LP_CU(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device));
-  h->grid_cap = opt.reserved[0] > 0 ? opt.reserved[0] * h->nsm : 0;
   h->nsearch = (opt.restart_scheme == LP_RESTART_ADAPTIVE) ? 1
                : (opt.restart_scheme == LP_RESTART_FLEXIBLE) ? 2 : 0;
 
@@ -490,8 +509,9 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
 
   // ---- device buffers
   lp_status e;
-  if ((e = h->upload_sell(HA, h->A)) != LP_OK) return e;
-  if ((e = h->upload_sell(HAT, h->AT)) != LP_OK) return e;
+  h->mixed = (opt.precision == LP_PRECISION_MIXED);
+  if ((e = h->upload_sell(HA, h->A, h->mixed)) != LP_OK) return e;
+  if ((e = h->upload_sell(HAT, h->AT, h->mixed)) != LP_OK) return e;
   if (opt.spmv_mode == 1) {
     const int32_t nwarps = h->nsm * kStreamWarpsPerSM;
     if ((e = h->upload_plan(HA, nwarps, h->PA)) != LP_OK) return e;
@@ -526,6 +546,21 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
   for (double **p : ys)
     if ((e = h->alloc(p, m)) != LP_OK) return e;
   if ((e = h->alloc(&h->tmp, std::max(n, m))) != LP_OK) return e;
+  if (h->mixed) {
+    MixVecs &mv = h->mv;
+    float **fn[] = {&mv.cf, &mv.lf, &mv.uf, &mv.dx, &mv.dxhat};
+    for (float **p : fn)
+      if ((e = h->alloc(p, n)) != LP_OK) return e;
+    float **fm[] = {&mv.bf, &mv.ylo, &mv.yhi, &mv.dy};
+    for (float **p : fm)
+      if ((e = h->alloc(p, m)) != LP_OK) return e;
+    double **dn[] = {&mv.dxbar, &mv.lam[0], &mv.lam[1]};
+    for (double **p : dn)
+      if ((e = h->alloc(p, n)) != LP_OK) return e;
+    double **dm[] = {&mv.dybar, &mv.gy[0], &mv.gy[1]};
+    for (double **p : dm)
+      if ((e = h->alloc(p, m)) != LP_OK) return e;
+  }
   if ((e = h->alloc(&h->st, 1)) != LP_OK) return e;
   if ((e = h->alloc(&h->w, opt.check_every)) != LP_OK) return e;
   if ((e = h->alloc(&h->trace, (int64_t)6 * std::max(1, opt.trace_capacity))) != LP_OK) return e;
@@ -571,6 +606,8 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
   hs.trace_cap = opt.trace_capacity;
   hs.pw_tol = opt.power_tol;
   hs.pw_max = opt.power_iters;
+  hs.mixed = h->mixed ? 1 : 0;
+  hs.mix_s = 1.0;
   LP_CU(cudaMemcpy(h->st, &hs, sizeof(DevState), cudaMemcpyHostToDevice));
   const int rgrid = std::min(std::max(1, (int)((std::max(n, m) + kBlock - 1) / kBlock)), 8 * h->nsm);
   launch_norms(h->v, h->st, cs.partials, cs.pstride, rgrid, n, m, s);
@@ -699,6 +736,7 @@ lp_status lp_get_solution(lp_handle h, double *x, double *y, void *cuda_stream) 
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   if (!h->solved) return fail(LP_ERR_NOT_SOLVED, "no solve has run on this handle");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (h->mixed) launch_combine(h->v, h->mv, h->st, h->n, h->m, 1, s);
   int32_t returned = 0;
   LP_CU(cudaMemcpyAsync(&returned, &h->st->returned, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   LP_CU(cudaStreamSynchronize(s));
@@ -721,6 +759,7 @@ lp_status lp_get_state(lp_handle h, double *x, double *y, double *xbar, double *
   g_err.clear();
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (h->mixed) launch_combine(h->v, h->mv, h->st, h->n, h->m, 1, s);
   struct Item { double *dst; const double *src; const int32_t *perm; int32_t len; };
   const Item items[] = {{x, h->v.x, h->perm_x, h->n},       {y, h->v.y, h->perm_y, h->m},
                         {xbar, h->v.xbar, h->perm_x, h->n}, {ybar, h->v.ybar, h->perm_y, h->m},
@@ -848,7 +887,10 @@ lp_status lp_profile_kernel(lp_handle h, int32_t which, int32_t reps, void *cuda
   if (which < 0 || which > 1 || reps < 0) return fail(LP_ERR_INVALID_ARG, "which must be 0 or 1, reps >= 0");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   for (int32_t r = 0; r < reps; ++r) {
-    if (h->opt.spmv_mode == 1) {
+    if (h->mixed) {
+      if (which == 0) launch_primal_mix(h->AT, h->mv, h->st, h->w, 0, s);
+      else launch_dual_mix(h->A, h->mv, h->v, h->st, h->w, 0, s);
+    } else if (h->opt.spmv_mode == 1) {
       if (which == 0) launch_primal_stream(h->AT, h->PAT, h->v, h->st, h->w, 0, s);
       else launch_dual_stream(h->A, h->PA, h->v, h->st, h->w, 0, s);
     } else {

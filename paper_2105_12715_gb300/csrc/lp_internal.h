@@ -40,6 +40,7 @@ struct SellMat {
   const SliceInfo *info;    // [nslices + 1]
   const int32_t *idx;
   const double *val;
+  const float *valf;        // FP32 copy of val (mixed precision), or null
 };
 
 // Work plan of the staged (TMA) SpMV kernels.  A segment is at most
@@ -117,7 +118,8 @@ struct DevState {
   double tot[NQ];
   unsigned int fin_counter;
   unsigned int sel_counter[2];
-  unsigned int pad3;
+  int32_t mixed;        // 1: mixed-precision iterations (MixVecs)
+  double mix_s;         // scale of the current correction
 };
 
 // Device arrays of one problem, permuted order.
@@ -127,6 +129,22 @@ struct DevVecs {
   int8_t *row_type;
   double *x, *xhat, *xbar, *x0;
   double *y, *ybar, *y0;
+};
+
+// Mixed-precision state (FP32 iterations on scaled corrections).  Within an
+// outer loop of Algorithm 1 the iterate is z = z^{n,0} + dz / s, where
+// z^{n,0} (x0, y0, FP64) is the restart point and s the scale chosen at the
+// restart; dz runs PDHG in FP32 on the correction data below, which is
+// re-formed in FP64 at every restart (residual correction).
+struct MixVecs {
+  float *cf, *lf, *uf;     // [n] s (c - A^T y0), s (l - x0), s (u - x0)
+  float *dx, *dxhat;       // [n]
+  double *dxbar;           // [n] FP64 average of dx
+  float *bf, *ylo, *yhi;   // [m] s (b - A x0), s (Y_lo - y0), s (Y_hi - y0)
+  float *dy;               // [m]
+  double *dybar;           // [m]
+  double *lam[2];          // [n] c - A^T y of the average / current candidate (from the check)
+  double *gy[2];           // [m] A x - b of the average / current candidate
 };
 
 // Scratch of the check and of the multiplier search.
@@ -154,7 +172,7 @@ cudaError_t prepare_stream_kernels();
 void launch_check(const SellMat &A, const SellMat &AT, const DevVecs &v,
                   DevState *st, double *w, const CheckScratch &cs, int n,
                   int m, int nsearch, double *trace, bool decide,
-                  cudaStream_t s);
+                  cudaStream_t s, const MixVecs *mv = nullptr);
 void launch_advance(DevState *st, double *w, int r, cudaStream_t s);
 void launch_spmv(const SellMat &A, const double *v, double *out, cudaStream_t s,
                  DevState *st_guard);
@@ -172,5 +190,15 @@ void launch_weights(DevState *st, double *w, cudaStream_t s);
 void launch_norms(const DevVecs &v, DevState *st, double *partials, int pstride,
                   int grid, int n, int m, cudaStream_t s);
 int check_grid_for(const SellMat &A, int num_sms);
+void launch_primal_mix(const SellMat &AT, const MixVecs &mv, DevState *st, const double *w,
+                       int k, cudaStream_t s);
+void launch_dual_mix(const SellMat &A, const MixVecs &mv, const DevVecs &v, DevState *st,
+                     const double *w, int k, cudaStream_t s);
+void launch_combine(const DevVecs &v, const MixVecs &mv, DevState *st, int n, int m, int force,
+                    cudaStream_t s);
+void launch_recenter(const DevVecs &v, const MixVecs &mv, DevState *st, int n, int m, int force,
+                     cudaStream_t s);
+void launch_residuals(const SellMat &A, const SellMat &AT, const DevVecs &v, const MixVecs &mv,
+                      int n, int m, cudaStream_t s);
 
 }  // namespace lpg

@@ -45,11 +45,17 @@ __device__ __forceinline__ double sq(double v) { return v * v; }
 // a row are then combined by a butterfly (the same sum in every lane of the
 // group), and the group's first lane runs the epilogue.  The epilogue's
 // operands are loaded before the row loop.  NV = 1 or 2 gathered vectors.
-template <int NV, int U, bool PIPE, class Epi>
-__device__ __forceinline__ void process_item(const SellMat &A,
-                                             const double *__restrict__ v0,
-                                             const double *__restrict__ v1,
-                                             int item, int lane, Epi &epi) {
+// T is the value type of the matrix copy, of the gathered vectors and of
+// the accumulators (double for the FP64 path, float for the mixed path).
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ const double *vals_of(const SellMat &A, double) { return A.val; }
+__device__ __forceinline__ const float *vals_of(const SellMat &A, float) { return A.valf; }
+
+template <int NV, int U, bool PIPE, typename T, class Epi>
+__device__ __forceinline__ void process_item(const SellMat &A, const T *__restrict__ v0,
+                                             const T *__restrict__ v1, int item, int lane,
+                                             Epi &epi) {
   const SliceInfo a = A.info[item];
   const int32_t row_end = A.info[item + 1].row0;
   const int lg = a.len_g & 7;
@@ -59,10 +65,10 @@ __device__ __forceinline__ void process_item(const SellMat &A,
   typename Epi::Pre pre{};
   if (owner) pre = epi.load(row);
   const int32_t *ip = A.idx + a.off + lane;
-  const double *vp = A.val + a.off + lane;
-  double a0 = owner ? epi.init(pre) : 0.0, a1 = 0.0;
+  const T *vp = vals_of(A, T(0)) + a.off + lane;
+  T a0 = owner ? epi.init(pre) : T(0), a1 = T(0);
   int32_t j[U];
-  double c[U];
+  T c[U];
   if (PIPE) {  // software pipeline: the next batch's index/value loads overlap this batch's gathers
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -73,7 +79,7 @@ __device__ __forceinline__ void process_item(const SellMat &A,
     }
   }
   for (int t = 0; t < steps; t += U) {
-    double g[U], h[U];
+    T g[U], h[U];
     if (!PIPE) {
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -91,7 +97,7 @@ __device__ __forceinline__ void process_item(const SellMat &A,
       }
     }
     int32_t jn[U];
-    double cn[U];
+    T cn[U];
     if (PIPE) {
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -104,8 +110,8 @@ __device__ __forceinline__ void process_item(const SellMat &A,
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (t + u < steps) {
-        a0 = fma(c[u], g[u], a0);
-        if (NV == 2) a1 = fma(c[u], h[u], a1);
+        a0 = fma_t(c[u], g[u], a0);
+        if (NV == 2) a1 = fma_t(c[u], h[u], a1);
       }
     }
     if (PIPE) {
@@ -123,9 +129,9 @@ __device__ __forceinline__ void process_item(const SellMat &A,
   if (owner) epi.store(row, a0, a1, pre);
 }
 
-template <int NV, int U, bool PIPE = false, class Epi>
-__device__ __forceinline__ void process_all(const SellMat &A, const double *v0,
-                                            const double *v1, Epi &epi) {
+template <int NV, int U, bool PIPE = false, typename T, class Epi>
+__device__ __forceinline__ void process_all(const SellMat &A, const T *v0, const T *v1,
+                                            Epi &epi) {
   const int lane = threadIdx.x & (kWarp - 1);
   const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nwarps = (int)(gridDim.x * blockDim.x) >> 5;
@@ -266,6 +272,7 @@ struct CheckColsEpi {
   const double *__restrict__ x;
   const double *__restrict__ x0;
   GapOut ga, gc;
+  double *lam_out0, *lam_out1;  // mixed precision: c - A^T y of both candidates, or null
   double sw, isw;
   int gap_a, gap_c;
   double q[NQ];
@@ -280,6 +287,10 @@ struct CheckColsEpi {
     const double lo = uf ? -INFINITY : 0.0;
     const double hi = lf ? INFINITY : 0.0;
     const double lam_a = p.c - aty_a, lam_c = p.c - aty_c;
+    if (lam_out0) {
+      lam_out0[j] = lam_a;
+      lam_out1[j] = lam_c;
+    }
     const double lt_a = fmin(fmax(lam_a, lo), hi), lt_c = fmin(fmax(lam_c, lo), hi);
     q[Q_RD2_A] += sq(lam_a - lt_a);
     q[Q_RD2_C] += sq(lam_c - lt_c);
@@ -318,6 +329,7 @@ struct CheckRowsEpi {
   const double *__restrict__ y;
   const double *__restrict__ y0;
   GapOut ga, gc;
+  double *gy_out0, *gy_out1;  // mixed precision: A x - b of both candidates, or null
   double sw, isw;
   int64_t off;  // element offset of the y-part in the search arrays (= n)
   int gap_a, gap_c;
@@ -327,6 +339,10 @@ struct CheckRowsEpi {
   __device__ __forceinline__ double init(const Pre &) const { return 0.0; }
   __device__ __forceinline__ void store(int i, double ax_a, double ax_c, const Pre &p) {
     double va = ax_a - p.b, vc = ax_c - p.b;
+    if (gy_out0) {
+      gy_out0[i] = va;
+      gy_out1[i] = vc;
+    }
     if (p.t == 1) { va = fmin(va, 0.0); vc = fmin(vc, 0.0); }
     if (p.t == 2) { va = fmax(va, 0.0); vc = fmax(vc, 0.0); }
     q[Q_RP2_A] += va * va;
@@ -364,7 +380,7 @@ __global__ void __launch_bounds__(kBlock, MINB) primal_kernel(SellMat AT, const 
   if (st->status != kRunning) return;
   epi.tau = st->tau;
   epi.w = w[k];
-  process_all<1, U, PIPE>(AT, y, nullptr, epi);
+  process_all<1, U, PIPE>(AT, y, (const double *)nullptr, epi);
 }
 
 template <int U, bool PIPE, int MINB>
@@ -374,13 +390,13 @@ __global__ void __launch_bounds__(kBlock, MINB) dual_kernel(SellMat A, const dou
   if (st->status != kRunning) return;
   epi.sigma = st->sigma;
   epi.w = w[k];
-  process_all<1, U, PIPE>(A, xhat, nullptr, epi);
+  process_all<1, U, PIPE>(A, xhat, (const double *)nullptr, epi);
 }
 
 __global__ void __launch_bounds__(kBlock) spmv_kernel(SellMat A, const double *__restrict__ v,
                                                       StoreEpi epi, const DevState *st) {
   if (st && (st->status != kRunning || st->pw_done)) return;
-  process_all<1, kUnroll>(A, v, nullptr, epi);
+  process_all<1, kUnroll>(A, v, (const double *)nullptr, epi);
 }
 
 // ------------------------------------------------ staged (TMA) iteration
@@ -534,6 +550,158 @@ __global__ void __launch_bounds__(kStreamWarps *kWarp) dual_stream_kernel(
   epi.sigma = st->sigma;
   epi.w = w[k];
   stream_warp(A, P, xhat, epi, st);
+}
+
+// --------------------------------------------------- mixed precision
+//
+// FP32 PDHG step on the correction dz = s (z - z^{n,0}): the same update as
+// Eq. (PDHG-update) with the correction's data (cf, bf, bounds lf/uf,
+// ylo/yhi), FP32 matrix values and FP32 accumulation; the running average
+// of the correction stays in FP64.
+struct PrimalMixEpi {
+  const float *__restrict__ cf;
+  const float *__restrict__ lf;
+  const float *__restrict__ uf;
+  float *dx, *dxhat;
+  double *dxbar;
+  float tau;
+  double w;
+  struct Pre { float c, l, u, x; double xb; };
+  __device__ __forceinline__ Pre load(int j) const { return {cf[j], lf[j], uf[j], dx[j], dxbar[j]}; }
+  __device__ __forceinline__ float init(const Pre &p) const { return -p.c; }
+  __device__ __forceinline__ void store(int j, float neg_g, float, const Pre &p) const {
+    const float xn = fminf(fmaxf(fmaf(tau, neg_g, p.x), p.l), p.u);
+    dx[j] = xn;
+    dxhat[j] = fmaf(2.0f, xn, -p.x);
+    dxbar[j] = fma(w, (double)xn - p.xb, p.xb);
+  }
+};
+
+struct DualMixEpi {
+  const float *__restrict__ bf;
+  const float *__restrict__ lo;
+  const float *__restrict__ hi;
+  float *dy;
+  double *dybar;
+  float sigma;
+  double w;
+  struct Pre { float b, l, h, y; double yb; };
+  __device__ __forceinline__ Pre load(int i) const { return {bf[i], lo[i], hi[i], dy[i], dybar[i]}; }
+  __device__ __forceinline__ float init(const Pre &p) const { return -p.b; }
+  __device__ __forceinline__ void store(int i, float r, float, const Pre &p) const {
+    const float yn = fminf(fmaxf(fmaf(-sigma, r, p.y), p.l), p.h);
+    dy[i] = yn;
+    dybar[i] = fma(w, (double)yn - p.yb, p.yb);
+  }
+};
+
+template <int U, bool PIPE>
+__global__ void __launch_bounds__(kBlock) primal_mix_kernel(SellMat AT, const float *__restrict__ dy,
+                                                            PrimalMixEpi epi, const DevState *st,
+                                                            const double *__restrict__ w, int k) {
+  if (st->status != kRunning) return;
+  epi.tau = (float)st->tau;
+  epi.w = w[k];
+  process_all<1, U, PIPE>(AT, dy, (const float *)nullptr, epi);
+}
+
+template <int U, bool PIPE>
+__global__ void __launch_bounds__(kBlock) dual_mix_kernel(SellMat A, const float *__restrict__ dxhat,
+                                                          DualMixEpi epi, const DevState *st,
+                                                          const double *__restrict__ w, int k) {
+  if (st->status != kRunning) return;
+  epi.sigma = (float)st->sigma;
+  epi.w = w[k];
+  process_all<1, U, PIPE>(A, dxhat, (const float *)nullptr, epi);
+}
+
+__device__ __forceinline__ double clampd(double v, double lo, double hi) {
+  return fmin(fmax(v, lo), hi);
+}
+
+// FP64 iterate and average in original coordinates, z = z^{n,0} + dz / s,
+// projected onto X x Y (removes the FP32 rounding of the bounds).
+__global__ void combine_kernel(DevVecs v, MixVecs mv, const DevState *st, int n, int m,
+                               int force) {
+  if (!force && st->status != kRunning) return;
+  const double inv = 1.0 / st->mix_s;
+  const int64_t total = (int64_t)n + m;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < n) {
+      const double x0 = v.x0[i], l = v.lb[i], u = v.ub[i];
+      v.x[i] = clampd(fma((double)mv.dx[i], inv, x0), l, u);
+      v.xbar[i] = clampd(fma(mv.dxbar[i], inv, x0), l, u);
+    } else {
+      const int64_t r = i - n;
+      const int t = v.row_type[r];
+      const double lo = (t == 1) ? 0.0 : -INFINITY, hi = (t == 2) ? 0.0 : INFINITY;
+      const double y0 = v.y0[r];
+      v.y[r] = clampd(fma((double)mv.dy[r], inv, y0), lo, hi);
+      v.ybar[r] = clampd(fma(mv.dybar[r], inv, y0), lo, hi);
+    }
+  }
+}
+
+// Re-forms the correction at a restart (or when forced, at set-up): with the
+// new restart point z^{n,0} and scale s (set by the restart decision), the
+// correction data are s times the FP64 residuals of the chosen candidate,
+// and dz starts at 0.  Without a restart, the flexible scheme's
+// replacement of the average by the current iterate is applied to dz.
+__global__ void recenter_kernel(DevVecs v, MixVecs mv, const DevState *st, int n, int m,
+                                int force) {
+  if (!force && st->status != kRunning) return;
+  const int rs = force ? 1 : st->restart_now, uc = force ? 0 : st->use_cur;
+  if (!rs && !uc) return;
+  const double s = st->mix_s;
+  const double *lam = mv.lam[uc], *gy = mv.gy[uc];
+  const int64_t total = (int64_t)n + m;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < n) {
+      if (rs) {
+        const double x0 = v.x0[i];
+        mv.cf[i] = (float)(s * lam[i]);
+        mv.lf[i] = (float)(s * (v.lb[i] - x0));
+        mv.uf[i] = (float)(s * (v.ub[i] - x0));
+        mv.dx[i] = 0.0f;
+        mv.dxhat[i] = 0.0f;
+        mv.dxbar[i] = 0.0;
+      } else {
+        mv.dxbar[i] = (double)mv.dx[i];
+      }
+    } else {
+      const int64_t r = i - n;
+      if (rs) {
+        const int t = v.row_type[r];
+        const double lo = (t == 1) ? 0.0 : -INFINITY, hi = (t == 2) ? 0.0 : INFINITY;
+        const double y0 = v.y0[r];
+        mv.bf[r] = (float)(-s * gy[r]);
+        mv.ylo[r] = (float)(s * (lo - y0));
+        mv.yhi[r] = (float)(s * (hi - y0));
+        mv.dy[r] = 0.0f;
+        mv.dybar[r] = 0.0;
+      } else {
+        mv.dybar[r] = (double)mv.dy[r];
+      }
+    }
+  }
+}
+
+// Residuals of the restart point at set-up: lam = c - A^T y0, gy = A x0 - b
+// (aty and ax hold A^T y0 and A x0).
+__global__ void residuals_kernel(DevVecs v, MixVecs mv, const double *aty, const double *ax,
+                                 int n, int m) {
+  const int64_t total = (int64_t)n + m;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < n) {
+      mv.lam[0][i] = v.c[i] - aty[i];
+    } else {
+      const int64_t r = i - n;
+      mv.gy[0][r] = ax[r] - v.b[r];
+    }
+  }
 }
 
 // ---------------------------------------------------------------- check
@@ -968,6 +1136,8 @@ __global__ void __launch_bounds__(kBlock) check_decide_kernel(DevState *st, doub
         st->rho_stored = rho;
         st->restarts += 1;
         st->t0 = 0;
+        // mixed precision: the next correction is scaled by the distance moved
+        if (st->mixed && r > 0.0 && isfinite(r)) st->mix_s = fmin(1.0 / r, 1e12);
       } else {
         st->t0 = t;
       }
@@ -1239,8 +1409,13 @@ cudaError_t prepare_stream_kernels() {
 
 void launch_check(const SellMat &A, const SellMat &AT, const DevVecs &v, DevState *st, double *w,
                   const CheckScratch &cs, int n, int m, int nsearch, double *trace,
-                  bool decide, cudaStream_t s) {
+                  bool decide, cudaStream_t s, const MixVecs *mv) {
+  if (mv) launch_combine(v, *mv, st, n, m, 0, s);
   CheckColsEpi ce{};
+  if (mv) {
+    ce.lam_out0 = mv->lam[0];
+    ce.lam_out1 = mv->lam[1];
+  }
   ce.c = v.c; ce.lb = v.lb; ce.ub = v.ub; ce.xbar = v.xbar; ce.x = v.x; ce.x0 = v.x0;
   ce.ga = GapOut{cs.keys[0], cs.d2[0], cs.g2[0], cs.gd[0]};
   ce.gc = GapOut{cs.keys[1], cs.d2[1], cs.g2[1], cs.gd[1]};
@@ -1253,6 +1428,10 @@ void launch_check(const SellMat &A, const SellMat &AT, const DevVecs &v, DevStat
   re.off = n;
   re.gap_a = 1;
   re.gap_c = 0;
+  if (mv) {
+    re.gy_out0 = mv->gy[0];
+    re.gy_out1 = mv->gy[1];
+  }
   check_kernel<CheckColsEpi><<<cs.cols_grid, kBlock, 0, s>>>(AT, v.ybar, v.y, ce, st, cs.partials,
                                                              cs.pstride, 0);
   check_kernel<CheckRowsEpi><<<cs.rows_grid, kBlock, 0, s>>>(A, v.xbar, v.x, re, st, cs.partials,
@@ -1272,7 +1451,39 @@ void launch_check(const SellMat &A, const SellMat &AT, const DevVecs &v, DevStat
   if (decide) {
     check_decide_kernel<<<1, kBlock, 0, s>>>(st, w, trace);
     restart_copy_kernel<<<grid_for((int64_t)n + m, num_sms()), kBlock, 0, s>>>(v, st, n, m);
+    if (mv) launch_recenter(v, *mv, st, n, m, 0, s);
   }
+}
+
+void launch_primal_mix(const SellMat &AT, const MixVecs &mv, DevState *st, const double *w,
+                       int k, cudaStream_t s) {
+  PrimalMixEpi epi{mv.cf, mv.lf, mv.uf, mv.dx, mv.dxhat, mv.dxbar, 0.0f, 0.0};
+  primal_mix_kernel<2, true><<<item_grid(AT), kBlock, 0, s>>>(AT, mv.dy, epi, st, w, k);
+}
+
+void launch_dual_mix(const SellMat &A, const MixVecs &mv, const DevVecs &, DevState *st,
+                     const double *w, int k, cudaStream_t s) {
+  DualMixEpi epi{mv.bf, mv.ylo, mv.yhi, mv.dy, mv.dybar, 0.0f, 0.0};
+  dual_mix_kernel<4, true><<<item_grid(A), kBlock, 0, s>>>(A, mv.dxhat, epi, st, w, k);
+}
+
+void launch_combine(const DevVecs &v, const MixVecs &mv, DevState *st, int n, int m, int force,
+                    cudaStream_t s) {
+  combine_kernel<<<grid_for((int64_t)n + m, num_sms()), kBlock, 0, s>>>(v, mv, st, n, m, force);
+}
+
+void launch_recenter(const DevVecs &v, const MixVecs &mv, DevState *st, int n, int m, int force,
+                     cudaStream_t s) {
+  recenter_kernel<<<grid_for((int64_t)n + m, num_sms()), kBlock, 0, s>>>(v, mv, st, n, m, force);
+}
+
+void launch_residuals(const SellMat &A, const SellMat &AT, const DevVecs &v, const MixVecs &mv,
+                      int n, int m, cudaStream_t s) {
+  // A^T y0 into lam[1], A x0 into gy[1] (scratch), then the residuals
+  launch_spmv(AT, v.y0, mv.lam[1], s, nullptr);
+  launch_spmv(A, v.x0, mv.gy[1], s, nullptr);
+  residuals_kernel<<<grid_for((int64_t)n + m, num_sms()), kBlock, 0, s>>>(v, mv, mv.lam[1],
+                                                                          mv.gy[1], n, m);
 }
 
 void launch_advance(DevState *st, double *w, int r, cudaStream_t s) {

@@ -21,6 +21,7 @@ LP_OK, LP_ERR_INVALID_ARG, LP_ERR_CUDA, LP_ERR_OOM, LP_ITER_LIMIT = 0, 1, 2, 3, 
 LP_ERR_NUMERICAL, LP_ERR_TIMEOUT, LP_ERR_NOT_SOLVED = 5, 6, 7
 LP_ROW_EQ, LP_ROW_GE, LP_ROW_LE = 0, 1, 2
 LP_RESTART_NONE, LP_RESTART_FIXED, LP_RESTART_ADAPTIVE, LP_RESTART_FLEXIBLE = 0, 1, 2, 3
+LP_PRECISION_FP64, LP_PRECISION_MIXED = 0, 1
 
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "ITER_LIMIT",
                 5: "NUMERICAL", 6: "TIMEOUT", 7: "NOT_SOLVED"}
@@ -34,7 +35,7 @@ class lp_options(C.Structure):
                 ("trace_capacity", C.c_int32), ("spmv_unroll", C.c_int32),
                 ("spmv_unroll_rows", C.c_int32), ("lane_steps", C.c_int32),
                 ("single_lane_max", C.c_int32), ("spmv_mode", C.c_int32),
-                ("reserved", C.c_int32 * 1)]
+                ("precision", C.c_int32)]
 
 
 class lp_info(C.Structure):
