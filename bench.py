@@ -50,6 +50,9 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--e2e-iters", type=int, default=6400)
     p.add_argument("--cpu-iters", type=int, default=64)
+    p.add_argument("--no-mixed", action="store_true")
+    p.add_argument("--no-ttk", action="store_true")
+    p.add_argument("--ttk-tol", type=float, default=1e-6)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--kernel-reps", type=int, default=50)  # >= 1
     return p.parse_args()
@@ -78,10 +81,39 @@ def config_of(args, data):
 
 
 def algorithmic_bytes(m, n, nnz):
-    """Bytes one PDHG iteration must move (each array once, gathers once)."""
+    """Bytes one FP64 PDHG iteration must move (each array once, gathers once)."""
     primal = 12 * nnz + 64 * n + 8 * m  # A^T values+indices; c,l,u,x,xbar in; x,xhat,xbar out; y gathered
     dual = 12 * nnz + 41 * m + 8 * n    # A values+indices; b,y,ybar,rowtype in; y,ybar out; xhat gathered
     return primal, dual
+
+
+def algorithmic_bytes_mixed(m, n, nnz):
+    """The same for the mixed path: FP32 values, iterates and correction data, FP64 averages."""
+    primal = 8 * nnz + 40 * n + 4 * m  # cf,lf,uf,dx (f32) + dxbar in; dx,dxhat (f32) + dxbar out; dy gathered
+    dual = 8 * nnz + 36 * m + 4 * n    # bf,ylo,yhi,dy (f32) + dybar in; dy (f32) + dybar out; dxhat gathered
+    return primal, dual
+
+
+def time_steps(lp, g, stream, steps):
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.iterate(steps, 1e-300)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def time_kernel(lp, g, which, reps, stream):
+    import torch
+
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    lp.lp_profile_kernel(g.h, which, reps, stream)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    return k0.elapsed_time(k1) / reps
 
 
 def peaks():
@@ -281,6 +313,44 @@ def run_ours(args):
            "d2h_bytes_per_step": d2h,
            "what": f"lp_create(host arrays)+lp_solve({args.e2e_iters} iters)+lp_get_solution(host)"}
 
+    # mixed precision on the same workload (same step, same timing rules)
+    mixed = None
+    if not args.no_mixed:
+        gm = lp.LP(data, stream=stream, check_every=K_CHECK, eta=info0.eta,
+                   precision=lp.LP_PRECISION_MIXED)
+        gm.iterate(args.warmup, 1e-300)
+        barrier()
+        msm = time_steps(lp, gm, stream, args.steps)
+        mp, md = algorithmic_bytes_mixed(data.m, data.n, data.nnz)
+        mp_ms = time_kernel(lp, gm, 0, args.kernel_reps, stream)
+        md_ms = time_kernel(lp, gm, 1, args.kernel_reps, stream)
+        gm.close()
+        mixed = {"value": ws * args.steps * K_CHECK / (msm / 1000.0), "unit": "iters/s",
+                 "ms_per_step": msm / args.steps, "dtype": "f32 iterations, f64 averages/checks",
+                 "bytes_per_iter_algorithmic": mp + md,
+                 "primal_kernel_ms": mp_ms, "dual_kernel_ms": md_ms,
+                 "primal_achieved_gbs": mp / (mp_ms / 1000.0) / 1e9}
+
+    # time to relative KKT on a medium LP that reaches the tolerance in seconds
+    ttk = None
+    if not args.no_ttk:
+        from paper_2105_12715_gb300 import lpgen
+
+        med = lpgen.large_mixed(5, m=20_000, n=100_000)
+        ttk = {"lp": f"large_mixed m={med.m} n={med.n} nnz={med.nnz} seed 5", "tol": args.ttk_tol}
+        for name, prec in (("fp64", lp.LP_PRECISION_FP64), ("mixed", lp.LP_PRECISION_MIXED)):
+            barrier()
+            t0 = time.perf_counter()
+            gt = lp.LP(med, stream=stream, check_every=K_CHECK, max_iter=2_000_000, precision=prec)
+            st = gt.solve(args.ttk_tol)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            it = gt.info()
+            gt.close()
+            ttk[name] = {"seconds": dt, "iters": it.iters, "restarts": it.restarts,
+                         "status": lp.STATUS_NAMES.get(st, st),
+                         "rel_kkt": min(it.kkt_avg[4], it.kkt_cur[4])}
+
     out = None
     if rank == 0:
         out = {"metric": "PDHG iterations/s (fp64 restarted PDHG, large mixed LP)", "value": value,
@@ -298,13 +368,23 @@ def run_ours(args):
                             "peak_kind": peak_kind, "traffic": PRIMAL_TRAFFIC_BYTES,
                             "algorithmic_bytes": primal_b, "avg_launch_ms": primal_ms,
                             "dual_kernel_ms": dual_ms, "dual_algorithmic_bytes": dual_b},
-               "clocks": clocks, "e2e": e2e,
+               "clocks": clocks, "e2e": e2e, "mixed": mixed, "time_to_kkt": ttk,
                "solver": {"eta": info0.eta, "sigma_max": info0.sigma_max,
                           "iters_done": info.iters, "restarts": info.restarts,
                           "rel_kkt_avg": info.kkt_avg[4], "rel_kkt_cur": info.kkt_cur[4],
                           "nnz_padded": info.nnz_padded}}
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args, data)
+            if ttk is not None:
+                import oracle
+
+                t0 = time.perf_counter()
+                r = oracle.solve(med, 0.9 / 11.0, tol=1e-300, max_iter=256, check_every=K_CHECK)
+                rate = r.iters / (time.perf_counter() - t0)
+                ttk["oracle_iters_per_s"] = rate
+                ttk["oracle_extrapolated_seconds"] = ttk["fp64"]["iters"] / rate
+                ttk["oracle_note"] = ("oracle time = GPU FP64 iteration count / oracle iterations/s "
+                                      "measured over 256 iterations (extrapolation)")
         print(json.dumps(out))
     if ws > 1:
         torch.distributed.barrier()

@@ -96,6 +96,9 @@ typedef struct {
                              1 = persistent warps with a TMA-staged (cp.async.bulk) matrix
                              stream (0) */
   int32_t precision;      /* LP_PRECISION_FP64 (default) or LP_PRECISION_MIXED */
+  int32_t lane_auto;      /* > 0: per matrix, halve single_lane_max and lane_steps until the
+                             layout has at least lane_auto x (SM count) slices (warps); 0: use
+                             the given lane policy as is (32) */
 } lp_options;
 
 typedef struct {

@@ -72,6 +72,38 @@ int lanes_log2(int64_t len, const LanePolicy &p) {
   return lg;
 }
 
+// Number of slices the layout of rows perm[0..) (longest first) would have.
+int64_t count_slices(const std::vector<int64_t> &ptr, const std::vector<int32_t> &perm,
+                     const LanePolicy &p) {
+  const int32_t nrows = (int32_t)perm.size();
+  int64_t ns = 0;
+  int32_t r = 0;
+  while (r < nrows) {
+    const int lg = lanes_log2(ptr[perm[r] + 1] - ptr[perm[r]], p);
+    const int cap = kWarp >> lg;
+    int32_t q = r;
+    while (q < nrows && q - r < cap && lanes_log2(ptr[perm[q] + 1] - ptr[perm[q]], p) == lg) ++q;
+    ++ns;
+    r = q;
+  }
+  return ns;
+}
+
+// Launch-shape tuning by a model: a pass runs one warp per slice, and
+// fewer slices than `target` warps leave SMs idle while each warp walks a
+// long chain of dependent gathers.  Starting from the given policy, give
+// rows more lanes (halving single_max and lane_steps) until the layout
+// has at least `target` slices or rows get one element per lane.
+LanePolicy choose_policy(const std::vector<int64_t> &ptr, const std::vector<int32_t> &perm,
+                         LanePolicy p, int64_t target) {
+  if (target <= 0) return p;
+  while (count_slices(ptr, perm, p) < target && (p.single_max > 1 || p.lane_steps > 1)) {
+    p.single_max = p.single_max / 2;
+    p.lane_steps = std::max(1, p.lane_steps / 2);
+  }
+  return p;
+}
+
 // Sliced layout (see SellMat) of the operator whose row r (permuted order)
 // is original row perm[r] of the CSR (ptr, ind, v); column indices
 // relabeled by relabel.  Rows come longest first, so a slice is closed when
@@ -292,6 +324,7 @@ lp_status validate_options(const lp_options &o) {
   if (o.lane_steps < 1 || o.lane_steps > 1024) return fail(LP_ERR_INVALID_ARG, "lane_steps must lie in [1, 1024]");
   if (o.single_lane_max < 0) return fail(LP_ERR_INVALID_ARG, "single_lane_max must be >= 0");
   if (o.spmv_mode != 0 && o.spmv_mode != 1) return fail(LP_ERR_INVALID_ARG, "spmv_mode must be 0 or 1");
+  if (o.lane_auto < 0) return fail(LP_ERR_INVALID_ARG, "lane_auto must be >= 0");
   if (o.precision != LP_PRECISION_FP64 && o.precision != LP_PRECISION_MIXED)
     return fail(LP_ERR_INVALID_ARG, "precision must be LP_PRECISION_FP64 or LP_PRECISION_MIXED");
   return LP_OK;
@@ -390,6 +423,7 @@ void lp_default_options(lp_options *o) {
   o->lane_steps = 16;
   o->single_lane_max = 64;
   o->spmv_mode = 0;
+  o->lane_auto = 32;
 }
 
 const char *lp_last_error(void) { return g_err.c_str(); }
@@ -490,8 +524,11 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
   for (int32_t r = 0; r < n; ++r) inv_x[perm_x[r]] = r;
   HostSell HA, HAT;
   const LanePolicy policy{opt.long_row_threshold, opt.lane_steps, opt.single_lane_max};
-  build_sell(m, n, rp, hci, hv, perm_y, inv_x, policy, HA);
-  build_sell(n, m, cp, ri, cv, perm_x, inv_y, policy, HAT);
+  const int64_t target = (int64_t)opt.lane_auto * h->nsm;
+  const LanePolicy pa = choose_policy(rp, perm_y, policy, target);
+  const LanePolicy pat = choose_policy(cp, perm_x, policy, target);
+  build_sell(m, n, rp, hci, hv, perm_y, inv_x, pa, HA);
+  build_sell(n, m, cp, ri, cv, perm_x, inv_y, pat, HAT);
   h->nnz_padded = (int64_t)HA.idx.size();
 
   // permuted vectors

@@ -35,7 +35,7 @@ class lp_options(C.Structure):
                 ("trace_capacity", C.c_int32), ("spmv_unroll", C.c_int32),
                 ("spmv_unroll_rows", C.c_int32), ("lane_steps", C.c_int32),
                 ("single_lane_max", C.c_int32), ("spmv_mode", C.c_int32),
-                ("precision", C.c_int32)]
+                ("precision", C.c_int32), ("lane_auto", C.c_int32)]
 
 
 class lp_info(C.Structure):
