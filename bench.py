@@ -33,8 +33,8 @@ sys.path.insert(0, ROOT)
 K_CHECK = 64
 FALLBACK_HBM_GBS = 6800.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one primal_kernel launch on
-# this workload with warm L2 (the benchmark's steady state), from
-# profiles/primal_kernel_large_mixed.md; set to None when the kernel changes.
+# this workload with warm L2 (the benchmark's steady state), from a one-pass
+# ncu capture; set to None when the kernel changes.
 PRIMAL_TRAFFIC_BYTES = 127.6e6
 
 
