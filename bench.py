@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--cpu-iters", type=int, default=64)
     p.add_argument("--no-mixed", action="store_true")
     p.add_argument("--no-ttk", action="store_true")
+    p.add_argument("--no-mcf", action="store_true")
     p.add_argument("--ttk-tol", type=float, default=1e-6)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--kernel-reps", type=int, default=50)  # >= 1
@@ -351,6 +352,25 @@ def run_ours(args):
                          "status": lp.STATUS_NAMES.get(st, st),
                          "rel_kkt": min(it.kkt_avg[4], it.kkt_cur[4])}
 
+    # multicommodity flow LP (300 x 300 grid, 8 commodities): FP64 vs mixed throughput
+    mcf = None
+    if not args.no_mcf:
+        from paper_2105_12715_gb300 import lpgen
+
+        mc = lpgen.multicommodity_grid(4)
+        mcf = {"lp": f"multicommodity grid 300x300, 8 commodities: m={mc.m} n={mc.n} nnz={mc.nnz}"}
+        mp, md = algorithmic_bytes(mc.m, mc.n, mc.nnz)
+        for name, prec in (("fp64", lp.LP_PRECISION_FP64), ("mixed", lp.LP_PRECISION_MIXED)):
+            gmc = lp.LP(mc, stream=stream, check_every=K_CHECK, precision=prec)
+            gmc.iterate(args.warmup, 1e-300)
+            barrier()
+            msm = time_steps(lp, gmc, stream, args.steps)
+            mcf[name] = {"iters_per_s": args.steps * K_CHECK / (msm / 1000.0),
+                         "ms_per_step": msm / args.steps}
+            if prec == lp.LP_PRECISION_FP64:
+                mcf[name]["achieved_gbs_per_iter"] = (mp + md) * mcf[name]["iters_per_s"] / 1e9
+            gmc.close()
+
     out = None
     if rank == 0:
         out = {"metric": "PDHG iterations/s (fp64 restarted PDHG, large mixed LP)", "value": value,
@@ -369,6 +389,7 @@ def run_ours(args):
                             "algorithmic_bytes": primal_b, "avg_launch_ms": primal_ms,
                             "dual_kernel_ms": dual_ms, "dual_algorithmic_bytes": dual_b},
                "clocks": clocks, "e2e": e2e, "mixed": mixed, "time_to_kkt": ttk,
+               "multicommodity": mcf,
                "solver": {"eta": info0.eta, "sigma_max": info0.sigma_max,
                           "iters_done": info.iters, "restarts": info.restarts,
                           "rel_kkt_avg": info.kkt_avg[4], "rel_kkt_cur": info.kkt_cur[4],

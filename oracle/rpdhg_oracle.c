@@ -111,9 +111,22 @@ void orc_pdhg_step(const orc_lp *lp, double tau, double sigma, const double *x,
 
 /* ------------------------------------------------ power iteration (Sec. 7) */
 
+/* SplitMix64 output function (Steele, Lea, Flood 2014; the form in Vigna's
+ * public-domain splitmix64.c), used as a counter-based generator: the j-th
+ * value is the mix of (j + 1) * golden gamma. */
+static uint64_t splitmix64_at(uint64_t j) {
+  uint64_t z = (j + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
 /*
  * Largest singular value of A by power iteration on A^T A (Section 7 names
- * power iteration without details).  Start at the all-ones vector / sqrt(n);
+ * power iteration without details).  Start at v_j = 0.5 + u_j, u_j uniform
+ * in [0, 1) from SplitMix64 at counter j (a start orthogonal to the top
+ * singular vector, as the all-ones vector is for symmetric network
+ * matrices, would converge to a smaller value), normalized;
  * v <- A^T A v / ||A^T A v||; stop when the Rayleigh estimate
  * ||A v||^2 changes by less than tol relative, or after max_iter steps.
  */
@@ -121,7 +134,13 @@ double orc_sigma_max(const orc_lp *lp, int32_t max_iter, double tol) {
   int32_t n = lp->n, m = lp->m;
   double *v = malloc(sizeof(double) * n), *w = malloc(sizeof(double) * n);
   double *av = malloc(sizeof(double) * (m > 0 ? m : 1));
-  for (int32_t j = 0; j < n; ++j) v[j] = 1.0 / sqrt((double)n);
+  double nv = 0.0;
+  for (int32_t j = 0; j < n; ++j) {
+    v[j] = 0.5 + (double)(splitmix64_at((uint64_t)j) >> 11) * 0x1.0p-53;
+    nv += v[j] * v[j];
+  }
+  nv = sqrt(nv);
+  for (int32_t j = 0; j < n; ++j) v[j] /= nv;
   double est = 0.0;
   for (int32_t it = 0; it < max_iter; ++it) {
     orc_matvec(lp, v, av);

@@ -654,7 +654,24 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
   } else {
     // Section 7: eta = 0.9 / sigma_max(A), sigma_max by power iteration
     double *pv = h->v.x, *pav = h->v.y, *pw = h->v.xhat;
-    launch_fill(pv, 1.0 / std::sqrt((double)n), n, s);
+    {
+      // start vector v_j = 0.5 + u_j (u_j in [0,1) from SplitMix64 at counter j, the
+      // original column index), normalized; the all-ones vector can be orthogonal
+      // to the top singular vector (symmetric network matrices)
+      std::vector<double> v0(n);
+      double nv = 0.0;
+      for (int32_t r = 0; r < n; ++r) {
+        uint64_t z = ((uint64_t)perm_x[r] + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        v0[r] = 0.5 + (double)(z >> 11) * 0x1.0p-53;
+        nv += v0[r] * v0[r];
+      }
+      nv = std::sqrt(nv);
+      for (int32_t r = 0; r < n; ++r) v0[r] /= nv;
+      LP_CU(cudaMemcpy(pv, v0.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    }
     const int chunk = 25;
     for (int it = 0; it < opt.power_iters; it += chunk) {
       for (int k = 0; k < chunk; ++k)

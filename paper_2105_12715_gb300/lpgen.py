@@ -333,3 +333,50 @@ CONFIGS = {
     "tiny": lambda seed=0: tiny_standard_form(seed),
     "large": lambda seed=1: large_mixed(seed),
 }
+
+
+def multicommodity_grid(seed: int = 4, side: int = 300, commodities: int = 8) -> LPData:
+    """Multicommodity min-cost flow on a side x side directed grid.
+
+    Arcs join 4-neighbours in both directions (2 * 2 * side * (side - 1)
+    arcs); cost U(1,10) and capacity U(5,50) per arc; each commodity has one
+    random source != sink with demand U(1,20).  Variables f[k, a] >= 0
+    (column k * arcs + a).  Rows: node balance (out - in = demand at the
+    source, -demand at the sink, 0 elsewhere; EQ), one per commodity and
+    node, then one capacity row per arc (sum_k f[k, a] <= cap_a; LE).  Every
+    value is +-1.  No planted optimum: the optimum is certified by KKT and
+    an LP solver.
+    """
+    rng = np.random.default_rng(seed)
+    V = side * side
+    idx = np.arange(V).reshape(side, side)
+    tails = [idx[:, :-1].ravel(), idx[:, 1:].ravel(), idx[:-1, :].ravel(), idx[1:, :].ravel()]
+    heads = [idx[:, 1:].ravel(), idx[:, :-1].ravel(), idx[1:, :].ravel(), idx[:-1, :].ravel()]
+    tail = np.concatenate(tails).astype(np.int64)
+    head = np.concatenate(heads).astype(np.int64)
+    n_arcs = tail.shape[0]
+    cost = rng.uniform(1.0, 10.0, n_arcs)
+    cap = rng.uniform(5.0, 50.0, n_arcs)
+    K = commodities
+    m = K * V + n_arcs
+    n = K * n_arcs
+    rows, cols, vals = [], [], []
+    b = np.zeros(m)
+    for k in range(K):
+        col = k * n_arcs + np.arange(n_arcs)
+        rows += [k * V + tail, k * V + head, K * V + np.arange(n_arcs)]
+        cols += [col, col, col]
+        vals += [np.ones(n_arcs), -np.ones(n_arcs), np.ones(n_arcs)]
+        s, t = rng.choice(V, size=2, replace=False)
+        d = rng.uniform(1.0, 20.0)
+        b[k * V + s] += d
+        b[k * V + t] -= d
+    b[K * V:] = cap
+    row_type = np.zeros(m, dtype=np.int8)
+    row_type[K * V:] = ROW_LE
+    row_ptr, col_idx, val = _coo_to_csr(m, np.concatenate(rows), np.concatenate(cols),
+                                        np.concatenate(vals))
+    c = np.tile(cost, K)
+    return LPData(m, n, row_ptr, col_idx, val, c, b, np.zeros(n), np.full(n, np.inf), row_type,
+                  None, None, name=f"multicommodity_grid(side={side},K={K},seed={seed})",
+                  meta={"arcs": n_arcs, "nodes": V})

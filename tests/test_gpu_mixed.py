@@ -80,3 +80,31 @@ def test_mixed_warm_start_and_bounds(lpm, oracle_mod):
     for k in ("x", "y", "xbar", "ybar"):
         assert rel_err(st[k], getattr(ref, k)) <= MIX_TOL, k
     assert np.all(st["x"] >= data.lb) and np.all(st["x"] <= data.ub)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_multicommodity_solve_matches_highs(lpm, oracle_mod, precision):
+    """Multicommodity grid LP (all values +-1, no planted optimum): FP64 and
+    mixed GPU solves reach relative KKT 1e-8 (oracle's KKT) and HiGHS's
+    optimal objective; the first 128 FP64 iterations match the oracle."""
+    linprog = pytest.importorskip("scipy.optimize").linprog
+    d = lpgen.multicommodity_grid(2, side=8, commodities=3)
+    A = d.dense()
+    eq, le = d.row_type == 0, d.row_type == 2
+    res = linprog(d.c, A_ub=A[le], b_ub=d.b[le], A_eq=A[eq], b_eq=d.b[eq], bounds=(0, None),
+                  method="highs")
+    with lpm.LP(d, check_every=64, max_iter=400000, precision=precision) as g:
+        assert g.info().sigma_max == pytest.approx(np.linalg.norm(A, 2), rel=1e-6)
+        assert g.solve(1e-8) == lpm.LP_OK
+        x, y = g.solution()
+    k = oracle_mod.kkt(d, x, y)
+    assert k["rel"] <= 1e-8
+    assert k["pobj"] == pytest.approx(res.fun, rel=1e-7)
+    if precision == 0:
+        eta = 0.9 / oracle_mod.sigma_max(d)
+        with lpm.LP(d, eta=eta, check_every=64, max_iter=128) as g:
+            g.solve(1e-300)
+            st = g.state()
+        ref = oracle_mod.solve(d, eta, tol=1e-300, max_iter=128, check_every=64)
+        for key in ("x", "y", "xbar", "ybar"):
+            assert rel_err(st[key], getattr(ref, key)) <= 1e-9, key

@@ -423,3 +423,24 @@ def test_figure1_restarted_average_beats_plain(oracle_mod):
     d_rest = np.hypot(rest.x0[0], rest.y0[0])  # z^{2,0}: average restarted twice
     assert rest.restarts == 2
     assert d_rest < d_last and d_rest < d_avg
+
+
+def test_multicommodity_oracle_matches_highs(oracle_mod):
+    """Multicommodity grid LPs (no planted optimum): the oracle's solve reaches
+    relative KKT 1e-8 and HiGHS's optimal objective; power iteration finds
+    sigma_max although the top singular vector is orthogonal to the all-ones
+    vector on these symmetric network matrices."""
+    linprog = pytest.importorskip("scipy.optimize").linprog
+    for side, K, seed in [(5, 2, 4), (6, 2, 1)]:
+        d = lpgen.multicommodity_grid(seed, side=side, commodities=K)
+        A = d.dense()
+        assert oracle_mod.sigma_max(d) == pytest.approx(np.linalg.norm(A, 2), rel=1e-6)
+        eq, le = d.row_type == 0, d.row_type == 2
+        res = linprog(d.c, A_ub=A[le], b_ub=d.b[le], A_eq=A[eq], b_eq=d.b[eq], bounds=(0, None),
+                      method="highs")
+        r = oracle_mod.solve(d, 0.9 / oracle_mod.sigma_max(d), tol=1e-8, max_iter=200000,
+                             check_every=64)
+        assert r.status == 0
+        k = oracle_mod.kkt(d, r.x_sol, r.y_sol)
+        assert k["rel"] <= 1e-8
+        assert k["pobj"] == pytest.approx(res.fun, rel=1e-7)
