@@ -223,6 +223,20 @@ lp_status lp_normalized_gap_static(lp_handle h, const double *x, const double *y
  */
 lp_status lp_profile_kernel(lp_handle h, int32_t which, int32_t reps, void *cuda_stream);
 
+/*
+ * Primal-weight selection of Section 7: for each omega in host_omegas[count]
+ * (each > 0), restart from the projection of zero onto X x Y and run
+ * `iters` iterations of PDHG without restarts (iters >= K; checks every K),
+ * with tau = eta/omega, sigma = eta*omega; host_kkt[k] receives the smaller
+ * relative KKT error of the average and the current iterate at the last
+ * check.  Then the handle takes the omega with the smallest value (first on
+ * ties; *host_best receives it), its restart scheme is restored, and its
+ * state is reset to the projection of zero.  Synchronizes the stream.
+ */
+lp_status lp_select_omega(lp_handle h, const double *host_omegas, int32_t count,
+                          int64_t iters, double *host_kkt, double *host_best,
+                          void *cuda_stream);
+
 /* Releases every resource of the handle (NULL is a no-op). */
 void lp_destroy(lp_handle h);
 

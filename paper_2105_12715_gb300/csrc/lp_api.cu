@@ -935,6 +935,53 @@ lp_status lp_normalized_gap(lp_handle h, const double *x, const double *y, doubl
   return LP_OK;
 }
 
+lp_status lp_select_omega(lp_handle h, const double *omegas, int32_t count, int64_t iters,
+                          double *kkt_out, double *best_out, void *cuda_stream) {
+  g_err.clear();
+  if (!h || !omegas || !kkt_out || count < 1) return fail(LP_ERR_INVALID_ARG, "bad arguments");
+  if (iters < h->opt.check_every) return fail(LP_ERR_INVALID_ARG, "iters must be >= check_every");
+  for (int32_t k = 0; k < count; ++k)
+    if (!(omegas[k] > 0.0) || !std::isfinite(omegas[k]))
+      return fail(LP_ERR_INVALID_ARG, "every omega must be finite and > 0");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  lp_status e = build_graph(h);
+  if (e != LP_OK) return e;
+  const int32_t scheme = h->opt.restart_scheme;
+  const int K = h->opt.check_every;
+  auto set_weight = [&](double om, int32_t sch) -> lp_status {
+    const double tau = h->eta / om, sigma = h->eta * om;
+    LP_CU(cudaMemcpyAsync(&h->st->omega, &om, sizeof(double), cudaMemcpyHostToDevice, s));
+    LP_CU(cudaMemcpyAsync(&h->st->tau, &tau, sizeof(double), cudaMemcpyHostToDevice, s));
+    LP_CU(cudaMemcpyAsync(&h->st->sigma, &sigma, sizeof(double), cudaMemcpyHostToDevice, s));
+    LP_CU(cudaMemcpyAsync(&h->st->scheme, &sch, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    LP_CU(cudaStreamSynchronize(s));
+    return LP_OK;
+  };
+  int32_t best = 0;
+  for (int32_t k = 0; k < count; ++k) {
+    if ((e = set_weight(omegas[k], LP_RESTART_NONE)) != LP_OK) return e;
+    if ((e = lp_set_state(h, nullptr, nullptr, cuda_stream)) != LP_OK) return e;
+    if ((e = set_run_params(h, 1e-300, s)) != LP_OK) return e;
+    const int64_t blocks = iters / K, rem = iters % K;
+    for (int64_t b = 0; b < blocks; ++b) LP_CU(cudaGraphLaunch(h->exec, s));
+    for (int64_t r = 0; r < rem; ++r) launch_iteration(h, (int)r, s);
+    if (rem) launch_advance(h->st, h->w, (int)rem, s);
+    LP_CU(cudaGetLastError());
+    DevState hs{};
+    LP_CU(cudaMemcpyAsync(&hs, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    LP_CU(cudaStreamSynchronize(s));
+    double v = std::fmin(hs.kkt_a[4], hs.kkt_c[4]);
+    if (!std::isfinite(v)) v = INFINITY;
+    kkt_out[k] = v;
+    if (v < kkt_out[best]) best = k;
+  }
+  h->opt.omega = omegas[best];
+  if ((e = set_weight(omegas[best], scheme)) != LP_OK) return e;
+  if (best_out) *best_out = omegas[best];
+  h->solved = false;
+  return lp_set_state(h, nullptr, nullptr, cuda_stream);
+}
+
 lp_status lp_profile_kernel(lp_handle h, int32_t which, int32_t reps, void *cuda_stream) {
   g_err.clear();
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");

@@ -50,7 +50,8 @@ class lp_info(C.Structure):
 
 EXPORTED = ["lp_default_options", "lp_create", "lp_solve", "lp_iterate", "lp_get_solution",
             "lp_get_state", "lp_set_state", "lp_get_info", "lp_get_trace", "lp_normalized_gap",
-            "lp_normalized_gap_static", "lp_profile_kernel", "lp_destroy", "lp_last_error"]
+            "lp_normalized_gap_static", "lp_select_omega", "lp_profile_kernel", "lp_destroy",
+            "lp_last_error"]
 
 _lib = None
 
@@ -91,13 +92,14 @@ def load(build_if_missing: bool = True):
     lib.lp_normalized_gap.argtypes = [P, P, P, D, C.POINTER(D), P]
     lib.lp_normalized_gap_static.argtypes = [P, P, P, D, C.POINTER(D), P]
     lib.lp_profile_kernel.argtypes = [P, I32, I32, P]
+    lib.lp_select_omega.argtypes = [P, P, I32, I64, P, P, P]
     lib.lp_destroy.argtypes = [P]
     lib.lp_destroy.restype = None
     lib.lp_last_error.argtypes = []
     lib.lp_last_error.restype = C.c_char_p
     for name in ["lp_create", "lp_solve", "lp_iterate", "lp_get_solution", "lp_get_state",
                  "lp_set_state", "lp_get_info", "lp_get_trace", "lp_normalized_gap",
-                 "lp_normalized_gap_static", "lp_profile_kernel"]:
+                 "lp_normalized_gap_static", "lp_profile_kernel", "lp_select_omega"]:
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -229,6 +231,16 @@ def lp_normalized_gap_static(h, x, y, r, stream=None) -> float:
     return out.value
 
 
+def lp_select_omega(h, omegas, iters=5000, stream=None):
+    """Section 7's primal-weight search; returns (best omega, relative KKT per omega)."""
+    om = np.ascontiguousarray(omegas, dtype=np.float64)
+    kkt = np.empty(om.shape[0])
+    best = C.c_double()
+    _check(load().lp_select_omega(h, C.c_void_p(om.ctypes.data), om.shape[0], int(iters),
+                                  C.c_void_p(kkt.ctypes.data), C.byref(best), _stream(stream)))
+    return best.value, kkt
+
+
 def lp_profile_kernel(h, which, reps, stream=None):
     return _check(load().lp_profile_kernel(h, int(which), int(reps), _stream(stream)))
 
@@ -328,6 +340,12 @@ class LP:
 
     def gap(self, x, y, r):
         return lp_normalized_gap(self.h, x, y, r, self.stream)
+
+    def select_omega(self, omegas=None, iters=5000):
+        """Primal weight by the grid of Section 7 (4^-5 .. 4^5 by default)."""
+        if omegas is None:
+            omegas = 4.0 ** np.arange(-5, 6)
+        return lp_select_omega(self.h, omegas, iters, self.stream)
 
 
 def default_beta() -> float:

@@ -255,3 +255,22 @@ def test_reproducible_bitwise(lpm):
             outs.append(g.state())
     for k in outs[0]:
         np.testing.assert_array_equal(outs[0][k], outs[1][k])
+
+
+def test_select_omega_matches_oracle_runs(lpm, oracle_mod):
+    """Section 7's primal-weight grid: per-omega relative KKT after a fixed
+    number of non-restarted iterations, against the oracle's runs."""
+    data = lpgen.tiny_standard_form(3)
+    eta = eta_of(oracle_mod, data)
+    omegas = [0.25, 1.0, 4.0]
+    with lpm.LP(data, eta=eta, check_every=64) as g:
+        best, kkt = g.select_omega(omegas, iters=640)
+        info = g.info()
+        assert info.iters == 0 and info.omega == best
+    want = []
+    for om in omegas:
+        r = oracle_mod.solve(data, eta, omega=om, tol=1e-300, max_iter=640, check_every=64,
+                             restart_scheme=oracle_mod.RESTART_NONE)
+        want.append(min(r.kkt_avg[4], r.kkt_cur[4]))
+    np.testing.assert_allclose(kkt, want, rtol=1e-7)
+    assert best == omegas[int(np.argmin(want))]
