@@ -237,6 +237,31 @@ lp_status lp_select_omega(lp_handle h, const double *host_omegas, int32_t count,
                           int64_t iters, double *host_kkt, double *host_best,
                           void *cuda_stream);
 
+/*
+ * Unrolled forward for differentiation (spec extension; the paper
+ * has no gradients): runs exactly `iters` iterations of Algorithm 1 from the
+ * current state (iters a multiple of K; FP64; adaptive, fixed or no
+ * restarts; no termination test), keeping a checkpoint of (x, y, xbar, ybar)
+ * and the inner iteration count at the start of every block of K
+ * iterations and the restart decision of every check.  The unrolled map's
+ * output is the running average (xbar, ybar) after the last check.
+ */
+lp_status lp_solve_recorded(lp_handle h, int64_t iters, void *cuda_stream);
+
+/*
+ * Adjoint of the recorded unrolled map (c, b) -> (xbar, ybar): given
+ * dl_dx[n] = dL/dxbar and dl_dy[m] = dL/dybar (NULL = 0), writes
+ * dl_dc[n] = dL/dc and dl_db[m] = dL/db (host or device pointers, caller's
+ * order).  Restart decisions and the clamp / projection masks of every step
+ * are those of the recorded solve (the map is differentiated where they do
+ * not change); blocks are recomputed from their checkpoints in reverse
+ * order, each adjoint step running the transposed products of the forward
+ * step.  Leaves the state of the recorded solve.  LP_ERR_NOT_SOLVED without
+ * a recording.  Synchronizes the stream.
+ */
+lp_status lp_backward(lp_handle h, const double *dl_dx, const double *dl_dy,
+                      double *dl_dc, double *dl_db, void *cuda_stream);
+
 /* Releases every resource of the handle (NULL is a no-op). */
 void lp_destroy(lp_handle h);
 

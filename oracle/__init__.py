@@ -27,7 +27,7 @@ _SRC = os.path.join(_HERE, "rpdhg_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 
-RESTART_NONE, RESTART_FIXED, RESTART_ADAPTIVE, RESTART_FLEXIBLE = 0, 1, 2, 3
+RESTART_NONE, RESTART_FIXED, RESTART_ADAPTIVE, RESTART_FLEXIBLE, RESTART_SCHEDULE = 0, 1, 2, 3, 4
 STATUS_OK, STATUS_ITER_LIMIT, STATUS_NUMERICAL = 0, 4, 5
 
 
@@ -54,7 +54,8 @@ class _LP(C.Structure):
 class _Options(C.Structure):
     _fields_ = [("eta", C.c_double), ("omega", C.c_double), ("beta", C.c_double),
                 ("tol", C.c_double), ("max_iter", C.c_int64), ("check_every", C.c_int32),
-                ("restart_scheme", C.c_int32), ("tau0", C.c_int64), ("fixed_len", C.c_int64)]
+                ("restart_scheme", C.c_int32), ("tau0", C.c_int64), ("fixed_len", C.c_int64),
+                ("schedule", C.c_void_p), ("nschedule", C.c_int64)]
 
 
 class _Info(C.Structure):
@@ -221,15 +222,19 @@ class SolveResult:
 
 def solve(lp, eta, omega=1.0, beta=float(np.exp(-1.0)), tol=1e-8, max_iter=100000,
           check_every=64, restart_scheme=RESTART_ADAPTIVE, tau0=None, fixed_len=0,
-          x_init=None, y_init=None, trace_cap=100000) -> SolveResult:
-    """Algorithm 1 (restarted PDHG) from z^{0,0} = (x_init, y_init) (zeros by default)."""
+          x_init=None, y_init=None, trace_cap=100000, schedule=None) -> SolveResult:
+    """Algorithm 1 (restarted PDHG) from z^{0,0} = (x_init, y_init) (zeros by default).
+
+    schedule (RESTART_SCHEDULE): one flag per check, restart where nonzero."""
     lp = _olp(lp)
     x = np.zeros(lp.n) if x_init is None else _f64(x_init).copy()
     y = np.zeros(lp.m) if y_init is None else _f64(y_init).copy()
     xbar, ybar = np.empty(lp.n), np.empty(lp.m)
     x0, y0 = np.empty(lp.n), np.empty(lp.m)
+    sched = np.ascontiguousarray([] if schedule is None else schedule, dtype=np.int8)
     opt = _Options(eta, omega, beta, tol, int(max_iter), int(check_every), int(restart_scheme),
-                   int(check_every if tau0 is None else tau0), int(fixed_len))
+                   int(check_every if tau0 is None else tau0), int(fixed_len),
+                   sched.ctypes.data if sched.size else None, int(sched.size))
     info = _Info()
     cap = max(1, min(trace_cap, max_iter // max(1, check_every) + 1))
     trace = np.full((cap, 6), np.nan)

@@ -36,7 +36,7 @@
 
 enum { ORC_ROW_EQ = 0, ORC_ROW_GE = 1, ORC_ROW_LE = 2 };
 enum { ORC_RESTART_NONE = 0, ORC_RESTART_FIXED = 1, ORC_RESTART_ADAPTIVE = 2,
-       ORC_RESTART_FLEXIBLE = 3 };
+       ORC_RESTART_FLEXIBLE = 3, ORC_RESTART_SCHEDULE = 4 };
 enum { ORC_OK = 0, ORC_ITER_LIMIT = 4, ORC_NUMERICAL = 5 };
 
 typedef struct {
@@ -401,6 +401,8 @@ typedef struct {
   int32_t restart_scheme; /* ORC_RESTART_* */
   int64_t tau0;           /* first restart length (n = 0 branch) */
   int64_t fixed_len;      /* restart length of the fixed-frequency scheme */
+  const int8_t *schedule; /* SCHEDULE: restart at check c iff schedule[c - 1] != 0 */
+  int64_t nschedule;
 } orc_options;
 
 typedef struct {
@@ -438,6 +440,8 @@ typedef struct {
  *   replaced by the current iterate when the latter has the smaller gap.
  *   FIXED, Eq. (define:t-star): restart when t >= fixed_len.
  *   NONE: never restart.
+ *   SCHEDULE: restart at the checks the caller flags (decisions held
+ *   fixed, so that the unrolled map is a fixed composition of steps).
  * On restart z^{n+1,0} <- zbar and the iteration continues from zbar.
  *
  * trace (optional, may be NULL): per check 6 doubles
@@ -502,6 +506,10 @@ int32_t orc_solve(const orc_lp *lp, const orc_options *opt, double *x,
       restart = (restarts == 0) ? (t >= opt->tau0) : (rho <= opt->beta * rho_stored);
     } else if (opt->restart_scheme == ORC_RESTART_FIXED) {
       restart = (t >= opt->fixed_len);
+    } else if (opt->restart_scheme == ORC_RESTART_SCHEDULE) {
+      /* restart decisions given from outside (the unrolled map with its
+         decisions held fixed, for finite differences of the adjoint) */
+      restart = (checks <= opt->nschedule) && opt->schedule[checks - 1] != 0;
     }
     if (trace && checks <= trace_cap) {
       double *row = trace + 6 * (checks - 1);

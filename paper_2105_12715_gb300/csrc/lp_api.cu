@@ -204,6 +204,13 @@ struct lp_problem {
   DevVecs v{};
   MixVecs mv{};
   bool mixed = false;
+  // unrolled-forward recording for lp_backward
+  double *ckpt = nullptr;              // [blocks][2n + 2m]: x, y, xbar, ybar at block start
+  std::vector<int64_t> ckpt_t0;        // inner iteration count at each block start
+  std::vector<int8_t> ckpt_restart;    // restart decision of each block's check
+  int64_t rec_blocks = 0;
+  AdjVecs adj{};
+  uint8_t *mask_x = nullptr, *mask_y = nullptr;  // [K][n], [K][m]
   DevState *st = nullptr;
   double *w = nullptr;
   CheckScratch cs{};
@@ -222,6 +229,7 @@ struct lp_problem {
   int grid_cap = 0;  // blocks of the per-slice iteration kernels (0: one warp per slice)
 
   ~lp_problem() {
+    if (ckpt) cudaFree(ckpt);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     for (auto &e : ev)
@@ -980,6 +988,141 @@ lp_status lp_select_omega(lp_handle h, const double *omegas, int32_t count, int6
   if (best_out) *best_out = omegas[best];
   h->solved = false;
   return lp_set_state(h, nullptr, nullptr, cuda_stream);
+}
+
+lp_status lp_solve_recorded(lp_handle h, int64_t iters, void *cuda_stream) {
+  g_err.clear();
+  if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
+  const int K = h->opt.check_every;
+  if (iters < K || iters % K != 0) return fail(LP_ERR_INVALID_ARG, "iters must be a positive multiple of check_every");
+  if (h->mixed) return fail(LP_ERR_INVALID_ARG, "recording needs LP_PRECISION_FP64");
+  if (h->opt.restart_scheme == LP_RESTART_FLEXIBLE)
+    return fail(LP_ERR_INVALID_ARG, "recording supports the adaptive, fixed and no-restart schemes");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  lp_status e = build_graph(h);
+  if (e != LP_OK) return e;
+  const int n = h->n, m = h->m;
+  const int64_t blocks = iters / K, slot = 2 * (int64_t)n + 2 * (int64_t)m;
+  if (h->ckpt) {
+    cudaFree(h->ckpt);
+    h->ckpt = nullptr;
+  }
+  LP_CU(cudaMalloc(&h->ckpt, sizeof(double) * std::max<int64_t>(1, blocks * slot)));
+  if (!h->mask_x) {  // masks and adjoint vectors, allocated once per handle
+    if ((e = h->alloc(&h->mask_x, (int64_t)K * n)) != LP_OK) return e;
+    if ((e = h->alloc(&h->mask_y, (int64_t)K * std::max(m, 1))) != LP_OK) return e;
+    double **xs[] = {&h->adj.ax, &h->adj.axb, &h->adj.ac, &h->adj.v};
+    for (double **p : xs)
+      if ((e = h->alloc(p, n)) != LP_OK) return e;
+    double **ys[] = {&h->adj.ay, &h->adj.ayb, &h->adj.ab, &h->adj.u};
+    for (double **p : ys)
+      if ((e = h->alloc(p, m)) != LP_OK) return e;
+  }
+  h->ckpt_t0.assign(blocks, 0);
+  h->ckpt_restart.assign(blocks, 0);
+  h->rec_blocks = 0;
+  if ((e = set_run_params(h, 1e-300, s)) != LP_OK) return e;
+  for (int64_t b = 0; b < blocks; ++b) {
+    double *c = h->ckpt + b * slot;
+    LP_CU(cudaMemcpyAsync(c, h->v.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    LP_CU(cudaMemcpyAsync(c + n, h->v.y, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    LP_CU(cudaMemcpyAsync(c + n + m, h->v.xbar, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    LP_CU(cudaMemcpyAsync(c + 2 * n + m, h->v.ybar, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    DevState hs{};
+    LP_CU(cudaMemcpyAsync(&hs, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    LP_CU(cudaStreamSynchronize(s));
+    if (hs.status != kRunning) return fail(LP_ERR_NUMERICAL, "solve stopped during recording");
+    h->ckpt_t0[b] = hs.t0;
+    const int64_t restarts_before = hs.restarts;
+    LP_CU(cudaGraphLaunch(h->exec, s));
+    LP_CU(cudaMemcpyAsync(&hs, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    LP_CU(cudaStreamSynchronize(s));
+    h->ckpt_restart[b] = (hs.restarts > restarts_before) ? 1 : 0;
+  }
+  h->rec_blocks = blocks;
+  h->solved = true;
+  return LP_OK;
+}
+
+lp_status lp_backward(lp_handle h, const double *dl_dx, const double *dl_dy, double *dl_dc,
+                      double *dl_db, void *cuda_stream) {
+  g_err.clear();
+  if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
+  if (h->rec_blocks == 0) return fail(LP_ERR_NOT_SOLVED, "no recorded solve (lp_solve_recorded)");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const int n = h->n, m = h->m, K = h->opt.check_every;
+  const int64_t slot = 2 * (int64_t)n + 2 * (int64_t)m;
+  DevState hs{};
+  LP_CU(cudaMemcpyAsync(&hs, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  LP_CU(cudaStreamSynchronize(s));
+  const double tau = hs.tau, sigma = hs.sigma;
+  // adjoint seeds: gradients of the loss with respect to the final averages
+  launch_fill(h->adj.ax, 0.0, n, s);
+  launch_fill(h->adj.ac, 0.0, n, s);
+  launch_fill(h->adj.ay, 0.0, m, s);
+  launch_fill(h->adj.ab, 0.0, m, s);
+  if (dl_dx) {
+    LP_CU(cudaMemcpyAsync(h->tmp, dl_dx, sizeof(double) * n, cudaMemcpyDefault, s));
+    launch_gather(h->adj.axb, h->tmp, h->perm_x, n, s);
+  } else {
+    launch_fill(h->adj.axb, 0.0, n, s);
+  }
+  if (dl_dy && m > 0) {
+    LP_CU(cudaMemcpyAsync(h->tmp, dl_dy, sizeof(double) * m, cudaMemcpyDefault, s));
+    launch_gather(h->adj.ayb, h->tmp, h->perm_y, m, s);
+  } else {
+    launch_fill(h->adj.ayb, 0.0, m, s);
+  }
+  for (int64_t b = h->rec_blocks - 1; b >= 0; --b) {
+    // recompute the block's forward steps with their masks
+    const double *c = h->ckpt + b * slot;
+    LP_CU(cudaMemcpyAsync(h->v.x, c, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    LP_CU(cudaMemcpyAsync(h->v.y, c + n, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    LP_CU(cudaMemcpyAsync(h->v.xbar, c + n + m, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    LP_CU(cudaMemcpyAsync(h->v.ybar, c + 2 * n + m, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    const int64_t t0 = h->ckpt_t0[b];
+    auto wk = [&](int k) { return 1.0 / (double)(t0 + k + 1); };
+    for (int k = 0; k < K; ++k)
+      launch_forward_masked(h->A, h->AT, h->v, tau, sigma, wk(k), h->mask_x + (int64_t)k * n,
+                            h->mask_y + (int64_t)k * m, s);
+    // reverse through the block
+    launch_adjoint_block_start(h->adj, h->mask_y + (int64_t)(K - 1) * m, h->ckpt_restart[b],
+                               sigma, wk(K - 1), n, m, s);
+    for (int k = K - 1; k >= 0; --k)
+      launch_adjoint_step(h->A, h->AT, h->adj, h->mask_x + (int64_t)k * n,
+                          k > 0 ? h->mask_y + (int64_t)(k - 1) * m : nullptr, tau, sigma, wk(k),
+                          k > 0 ? wk(k - 1) : 0.0, k > 0 ? 1 : 0, s);
+    LP_CU(cudaGetLastError());
+  }
+  // restore the final state of the recorded solve: replay the last block
+  {
+    const int64_t b = h->rec_blocks - 1;
+    const double *c = h->ckpt + b * slot;
+    LP_CU(cudaMemcpyAsync(h->v.x, c, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    LP_CU(cudaMemcpyAsync(h->v.y, c + n, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    LP_CU(cudaMemcpyAsync(h->v.xbar, c + n + m, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    LP_CU(cudaMemcpyAsync(h->v.ybar, c + 2 * n + m, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    const int64_t t0 = h->ckpt_t0[b];
+    for (int k = 0; k < K; ++k)
+      launch_forward_masked(h->A, h->AT, h->v, tau, sigma, 1.0 / (double)(t0 + k + 1),
+                            h->mask_x + (int64_t)k * n, h->mask_y + (int64_t)k * m, s);
+    if (h->ckpt_restart[b]) {  // the recorded check restarted: z <- zbar
+      LP_CU(cudaMemcpyAsync(h->v.x, h->v.xbar, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      LP_CU(cudaMemcpyAsync(h->v.y, h->v.ybar, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  if (dl_dc) {
+    launch_scatter(h->tmp, h->adj.ac, h->perm_x, n, s);
+    LP_CU(cudaMemcpyAsync(dl_dc, h->tmp, sizeof(double) * n, cudaMemcpyDefault, s));
+    LP_CU(cudaStreamSynchronize(s));
+  }
+  if (dl_db && m > 0) {
+    launch_scatter(h->tmp, h->adj.ab, h->perm_y, m, s);
+    LP_CU(cudaMemcpyAsync(dl_db, h->tmp, sizeof(double) * m, cudaMemcpyDefault, s));
+  }
+  LP_CU(cudaGetLastError());
+  LP_CU(cudaStreamSynchronize(s));
+  return LP_OK;
 }
 
 lp_status lp_profile_kernel(lp_handle h, int32_t which, int32_t reps, void *cuda_stream) {

@@ -147,6 +147,12 @@ struct MixVecs {
   double *gy[2];           // [m] A x - b of the average / current candidate
 };
 
+// Adjoint state of the unrolled iteration (FP64).
+struct AdjVecs {
+  double *ax, *axb, *ac, *v;  // [n]
+  double *ay, *ayb, *ab, *u;  // [m]
+};
+
 // Scratch of the check and of the multiplier search.
 struct CheckScratch {
   double *partials;        // [NQ][pstride]
@@ -200,5 +206,12 @@ void launch_recenter(const DevVecs &v, const MixVecs &mv, DevState *st, int n, i
                      cudaStream_t s);
 void launch_residuals(const SellMat &A, const SellMat &AT, const DevVecs &v, const MixVecs &mv,
                       int n, int m, cudaStream_t s);
+void launch_forward_masked(const SellMat &A, const SellMat &AT, const DevVecs &v, double tau,
+                           double sigma, double w, uint8_t *mx, uint8_t *my, cudaStream_t s);
+void launch_adjoint_step(const SellMat &A, const SellMat &AT, const AdjVecs &a,
+                         const uint8_t *mx, const uint8_t *my_prev, double tau, double sigma,
+                         double w, double w_prev, int has_prev, cudaStream_t s);
+void launch_adjoint_block_start(const AdjVecs &a, const uint8_t *my_last, int restarted,
+                                double sigma, double w, int n, int m, cudaStream_t s);
 
 }  // namespace lpg

@@ -181,12 +181,14 @@ struct PrimalEpi {
   const long long *__restrict__ ubk;
   double *x, *xhat, *xbar;
   double tau, w;
+  uint8_t *mask;  // adjoint recording: 1 where the clamp is inactive, or null
   struct Pre { double c, x, xb; long long lk, uk; };
   __device__ __forceinline__ Pre load(int j) const { return {c[j], x[j], xbar[j], lbk[j], ubk[j]}; }
   __device__ __forceinline__ double init(const Pre &p) const { return -p.c; }
   __device__ __forceinline__ void store(int j, double neg_g, double, const Pre &p) const {
     const double v = fma(tau, neg_g, p.x);  // x - tau (c - A^T y)
     long long k = ord_key(__double_as_longlong(v));
+    if (mask) mask[j] = (k > p.lk && k < p.uk) ? 1 : 0;
     k = k < p.lk ? p.lk : k;
     k = k > p.uk ? p.uk : k;
     const double xn = __longlong_as_double(ord_key(k));
@@ -204,11 +206,13 @@ struct DualEpi {
   const int8_t *__restrict__ rt;
   double *y, *ybar;
   double sigma, w;
+  uint8_t *mask;  // adjoint recording: 1 where the projection is inactive, or null
   struct Pre { double b, y, yb; int t; };
   __device__ __forceinline__ Pre load(int i) const { return {b[i], y[i], ybar[i], (int)rt[i]}; }
   __device__ __forceinline__ double init(const Pre &p) const { return -p.b; }
   __device__ __forceinline__ void store(int i, double r, double, const Pre &p) const {
     long long bits = __double_as_longlong(fma(-sigma, r, p.y));  // y + sigma (b - A xhat)
+    if (mask) mask[i] = (p.t == 0 || (p.t == 1 && bits > 0) || (p.t == 2 && bits < 0)) ? 1 : 0;
     if (p.t == 1 && bits < 0) bits = 0;       // GE: [0, inf)
     else if (p.t == 2 && bits > 0) bits = 0;  // LE: (-inf, 0]
     const double yn = __longlong_as_double(bits);
@@ -700,6 +704,114 @@ __global__ void residuals_kernel(DevVecs v, MixVecs mv, const double *aty, const
     } else {
       const int64_t r = i - n;
       mv.gy[0][r] = ax[r] - v.b[r];
+    }
+  }
+}
+
+// ------------------------------------------------------------ adjoint
+//
+// Reverse mode of the unrolled iteration with the clamp/projection masks of
+// a recomputed forward block and the restart decisions held fixed.  With
+// adjoints (ax, ay, axb, ayb) of the outputs (x, y, xbar, ybar) of step k:
+//   u   = D_y (ay + w ayb),  grad_b += sigma u,  ayb <- (1 - w) ayb
+//   v   = D_x (ax + w axb - 2 sigma A^T u),       grad_c -= tau v
+//   ax <- v + sigma A^T u,   axb <- (1 - w) axb,  ay <- u + tau A v
+// (dual half of Eq. PDHG-update, then the extrapolation 2x+ - x, then the
+// primal half; the running average of Algorithm 1 is linear).  A restart
+// (x <- xbar) moves ax into axb.
+
+// Forward step with masks, for the recomputation of one block.
+__global__ void __launch_bounds__(kBlock) primal_mask_kernel(SellMat AT,
+                                                             const double *__restrict__ y,
+                                                             PrimalEpi epi, double tau, double w) {
+  epi.tau = tau;
+  epi.w = w;
+  process_all<1, 2, true>(AT, y, (const double *)nullptr, epi);
+}
+
+__global__ void __launch_bounds__(kBlock) dual_mask_kernel(SellMat A,
+                                                           const double *__restrict__ xhat,
+                                                           DualEpi epi, double sigma, double w) {
+  epi.sigma = sigma;
+  epi.w = w;
+  process_all<1, 4, true>(A, xhat, (const double *)nullptr, epi);
+}
+
+struct AdjColsEpi {
+  double *ax, *axb, *ac, *v;
+  const uint8_t *__restrict__ mx;
+  double tau, sigma, w;
+  struct Pre { double ax, axb, ac; int m; };
+  __device__ __forceinline__ Pre load(int j) const { return {ax[j], axb[j], ac[j], (int)mx[j]}; }
+  __device__ __forceinline__ double init(const Pre &) const { return 0.0; }
+  __device__ __forceinline__ void store(int j, double atu, double, const Pre &p) const {
+    const double adj_xhat = -sigma * atu;
+    const double adj_xp = fma(2.0, adj_xhat, fma(w, p.axb, p.ax));
+    const double vv = p.m ? adj_xp : 0.0;
+    ax[j] = vv - adj_xhat;
+    ac[j] = fma(-tau, vv, p.ac);
+    axb[j] = (1.0 - w) * p.axb;
+    v[j] = vv;
+  }
+};
+
+struct AdjRowsEpi {
+  double *ay, *ayb, *ab, *u;
+  const uint8_t *__restrict__ my_prev;
+  double tau, sigma, w_prev;
+  int has_prev;
+  struct Pre { double u, ayb, ab; int mp; };
+  __device__ __forceinline__ Pre load(int i) const {
+    return {u[i], ayb[i], ab[i], has_prev ? (int)my_prev[i] : 0};
+  }
+  __device__ __forceinline__ double init(const Pre &) const { return 0.0; }
+  __device__ __forceinline__ void store(int i, double av, double, const Pre &p) const {
+    const double ayk = fma(tau, av, p.u);
+    ay[i] = ayk;
+    if (has_prev) {
+      const double up = p.mp ? fma(w_prev, p.ayb, ayk) : 0.0;
+      ab[i] = fma(sigma, up, p.ab);
+      ayb[i] = (1.0 - w_prev) * p.ayb;
+      u[i] = up;
+    }
+  }
+};
+
+__global__ void __launch_bounds__(kBlock) adj_cols_kernel(SellMat AT, const double *__restrict__ u,
+                                                          AdjColsEpi epi) {
+  process_all<1, 2, true>(AT, u, (const double *)nullptr, epi);
+}
+
+__global__ void __launch_bounds__(kBlock) adj_rows_kernel(SellMat A, const double *__restrict__ v,
+                                                          AdjRowsEpi epi) {
+  process_all<1, 4, true>(A, v, (const double *)nullptr, epi);
+}
+
+// Start of a reverse block: the restart after the block (if any), then u of
+// the block's last step.
+__global__ void adj_block_start_kernel(double *ax, double *axb, double *ay, double *ayb, double *u,
+                                       double *ab, const uint8_t *my_last, int restarted,
+                                       double sigma, double w, int n, int m) {
+  const int64_t total = (int64_t)n + m;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < n) {
+      if (restarted) {
+        axb[i] += ax[i];
+        ax[i] = 0.0;
+      }
+    } else {
+      const int64_t r = i - n;
+      double a = ay[r], yb = ayb[r];
+      if (restarted) {
+        yb += a;
+        a = 0.0;
+        ay[r] = 0.0;
+      }
+      const double up = my_last[r] ? fma(w, yb, a) : 0.0;
+      ab[r] = fma(sigma, up, ab[r]);
+      ayb[r] = (1.0 - w) * yb;
+      u[r] = up;
     }
   }
 }
@@ -1359,7 +1471,7 @@ void dual_launch(int occ, int g, cudaStream_t s, const SellMat &A, const double 
 
 void launch_primal_step(const SellMat &AT, const DevVecs &v, DevState *st, const double *w,
                         int k, int unroll, int grid_cap, cudaStream_t s) {
-  PrimalEpi epi{v.c, v.lbk, v.ubk, v.x, v.xhat, v.xbar, 0.0, 0.0};
+  PrimalEpi epi{v.c, v.lbk, v.ubk, v.x, v.xhat, v.xbar, 0.0, 0.0, nullptr};
   const int g = grid_cap > 0 ? std::min(item_grid(AT), grid_cap) : item_grid(AT);
   const int occ = (unroll >= 100 || unroll <= -100) ? 1 : 0;
   switch (unroll % 100) {
@@ -1373,7 +1485,7 @@ void launch_primal_step(const SellMat &AT, const DevVecs &v, DevState *st, const
 
 void launch_dual_step(const SellMat &A, const DevVecs &v, DevState *st, const double *w, int k,
                       int unroll, int grid_cap, cudaStream_t s) {
-  DualEpi epi{v.b, v.row_type, v.y, v.ybar, 0.0, 0.0};
+  DualEpi epi{v.b, v.row_type, v.y, v.ybar, 0.0, 0.0, nullptr};
   const int g = grid_cap > 0 ? std::min(item_grid(A), grid_cap) : item_grid(A);
   const int occ = (unroll >= 100 || unroll <= -100) ? 1 : 0;
   switch (unroll % 100) {
@@ -1387,14 +1499,14 @@ void launch_dual_step(const SellMat &A, const DevVecs &v, DevState *st, const do
 
 void launch_primal_stream(const SellMat &AT, const StreamPlan &P, const DevVecs &v, DevState *st,
                           const double *w, int k, cudaStream_t s) {
-  PrimalEpi epi{v.c, v.lbk, v.ubk, v.x, v.xhat, v.xbar, 0.0, 0.0};
+  PrimalEpi epi{v.c, v.lbk, v.ubk, v.x, v.xhat, v.xbar, 0.0, 0.0, nullptr};
   const int grid = (P.nwarps + kStreamWarps - 1) / kStreamWarps;
   primal_stream_kernel<<<grid, kStreamWarps * kWarp, kStreamSmem, s>>>(AT, P, v.y, epi, st, w, k);
 }
 
 void launch_dual_stream(const SellMat &A, const StreamPlan &P, const DevVecs &v, DevState *st,
                         const double *w, int k, cudaStream_t s) {
-  DualEpi epi{v.b, v.row_type, v.y, v.ybar, 0.0, 0.0};
+  DualEpi epi{v.b, v.row_type, v.y, v.ybar, 0.0, 0.0, nullptr};
   const int grid = (P.nwarps + kStreamWarps - 1) / kStreamWarps;
   dual_stream_kernel<<<grid, kStreamWarps * kWarp, kStreamSmem, s>>>(A, P, v.xhat, epi, st, w, k);
 }
@@ -1484,6 +1596,29 @@ void launch_residuals(const SellMat &A, const SellMat &AT, const DevVecs &v, con
   launch_spmv(A, v.x0, mv.gy[1], s, nullptr);
   residuals_kernel<<<grid_for((int64_t)n + m, num_sms()), kBlock, 0, s>>>(v, mv, mv.lam[1],
                                                                           mv.gy[1], n, m);
+}
+
+void launch_forward_masked(const SellMat &A, const SellMat &AT, const DevVecs &v, double tau,
+                           double sigma, double w, uint8_t *mx, uint8_t *my, cudaStream_t s) {
+  PrimalEpi pe{v.c, v.lbk, v.ubk, v.x, v.xhat, v.xbar, 0.0, 0.0, mx};
+  primal_mask_kernel<<<item_grid(AT), kBlock, 0, s>>>(AT, v.y, pe, tau, w);
+  DualEpi de{v.b, v.row_type, v.y, v.ybar, 0.0, 0.0, my};
+  dual_mask_kernel<<<item_grid(A), kBlock, 0, s>>>(A, v.xhat, de, sigma, w);
+}
+
+void launch_adjoint_step(const SellMat &A, const SellMat &AT, const AdjVecs &a,
+                         const uint8_t *mx, const uint8_t *my_prev, double tau, double sigma,
+                         double w, double w_prev, int has_prev, cudaStream_t s) {
+  AdjColsEpi ce{a.ax, a.axb, a.ac, a.v, mx, tau, sigma, w};
+  adj_cols_kernel<<<item_grid(AT), kBlock, 0, s>>>(AT, a.u, ce);
+  AdjRowsEpi re{a.ay, a.ayb, a.ab, a.u, my_prev, tau, sigma, w_prev, has_prev};
+  adj_rows_kernel<<<item_grid(A), kBlock, 0, s>>>(A, a.v, re);
+}
+
+void launch_adjoint_block_start(const AdjVecs &a, const uint8_t *my_last, int restarted,
+                                double sigma, double w, int n, int m, cudaStream_t s) {
+  adj_block_start_kernel<<<grid_for((int64_t)n + m, num_sms()), kBlock, 0, s>>>(
+      a.ax, a.axb, a.ay, a.ayb, a.u, a.ab, my_last, restarted, sigma, w, n, m);
 }
 
 void launch_advance(DevState *st, double *w, int r, cudaStream_t s) {

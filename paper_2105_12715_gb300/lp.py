@@ -50,8 +50,8 @@ class lp_info(C.Structure):
 
 EXPORTED = ["lp_default_options", "lp_create", "lp_solve", "lp_iterate", "lp_get_solution",
             "lp_get_state", "lp_set_state", "lp_get_info", "lp_get_trace", "lp_normalized_gap",
-            "lp_normalized_gap_static", "lp_select_omega", "lp_profile_kernel", "lp_destroy",
-            "lp_last_error"]
+            "lp_normalized_gap_static", "lp_select_omega", "lp_solve_recorded", "lp_backward",
+            "lp_profile_kernel", "lp_destroy", "lp_last_error"]
 
 _lib = None
 
@@ -93,13 +93,16 @@ def load(build_if_missing: bool = True):
     lib.lp_normalized_gap_static.argtypes = [P, P, P, D, C.POINTER(D), P]
     lib.lp_profile_kernel.argtypes = [P, I32, I32, P]
     lib.lp_select_omega.argtypes = [P, P, I32, I64, P, P, P]
+    lib.lp_solve_recorded.argtypes = [P, I64, P]
+    lib.lp_backward.argtypes = [P, P, P, P, P, P]
     lib.lp_destroy.argtypes = [P]
     lib.lp_destroy.restype = None
     lib.lp_last_error.argtypes = []
     lib.lp_last_error.restype = C.c_char_p
     for name in ["lp_create", "lp_solve", "lp_iterate", "lp_get_solution", "lp_get_state",
                  "lp_set_state", "lp_get_info", "lp_get_trace", "lp_normalized_gap",
-                 "lp_normalized_gap_static", "lp_profile_kernel", "lp_select_omega"]:
+                 "lp_normalized_gap_static", "lp_profile_kernel", "lp_select_omega",
+                 "lp_solve_recorded", "lp_backward"]:
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -239,6 +242,16 @@ def lp_select_omega(h, omegas, iters=5000, stream=None):
     _check(load().lp_select_omega(h, C.c_void_p(om.ctypes.data), om.shape[0], int(iters),
                                   C.c_void_p(kkt.ctypes.data), C.byref(best), _stream(stream)))
     return best.value, kkt
+
+
+def lp_solve_recorded(h, iters, stream=None):
+    return _check(load().lp_solve_recorded(h, int(iters), _stream(stream)))
+
+
+def lp_backward(h, dl_dx, dl_dy, dl_dc, dl_db, stream=None):
+    px, kx = _ptr(dl_dx, np.float64)
+    py, ky = _ptr(dl_dy, np.float64)
+    return _check(load().lp_backward(h, px, py, _out_ptr(dl_dc), _out_ptr(dl_db), _stream(stream)))
 
 
 def lp_profile_kernel(h, which, reps, stream=None):
