@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--no-mixed", action="store_true")
     p.add_argument("--no-ttk", action="store_true")
     p.add_argument("--no-mcf", action="store_true")
+    p.add_argument("--no-adjoint", action="store_true")
+    p.add_argument("--adjoint-lps", type=int, default=4)
     p.add_argument("--ttk-tol", type=float, default=1e-6)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--kernel-reps", type=int, default=50)  # >= 1
@@ -371,6 +373,34 @@ def run_ours(args):
                 mcf[name]["achieved_gbs_per_iter"] = (mp + md) * mcf[name]["iters_per_s"] / 1e9
             gmc.close()
 
+    # adjoint of the unrolled map on differentiable-LP-shaped instances
+    # (m=2000, n=5000, nnz=50k, box [0,1]; 2000 iterations, checkpoint every 100)
+    adjoint = None
+    if not args.no_adjoint:
+        from paper_2105_12715_gb300 import lpgen
+
+        fw, bw = [], []
+        for sd in range(args.adjoint_lps):
+            d3 = lpgen.box_standard_form(100 + sd)
+            g3 = lp.LP(d3, stream=stream, check_every=100)
+            wv = np.random.default_rng(sd).standard_normal(d3.n)
+            dc, db = np.empty(d3.n), np.empty(d3.m)
+            barrier()
+            t0 = time.perf_counter()
+            lp.lp_solve_recorded(g3.h, 2000, stream)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            lp.lp_backward(g3.h, wv, None, dc, db, stream)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            fw.append(t1 - t0)
+            bw.append(t2 - t1)
+            g3.close()
+        adjoint = {"lp": "box_standard_form m=2000 n=5000 nnz=50000 (4 seeds), K=100, 2000 iterations",
+                   "forward_recorded_ms": 1000 * float(np.median(fw)),
+                   "backward_ms": 1000 * float(np.median(bw)),
+                   "backward_over_forward": float(np.median(bw) / np.median(fw))}
+
     out = None
     if rank == 0:
         out = {"metric": "PDHG iterations/s (fp64 restarted PDHG, large mixed LP)", "value": value,
@@ -389,7 +419,7 @@ def run_ours(args):
                             "algorithmic_bytes": primal_b, "avg_launch_ms": primal_ms,
                             "dual_kernel_ms": dual_ms, "dual_algorithmic_bytes": dual_b},
                "clocks": clocks, "e2e": e2e, "mixed": mixed, "time_to_kkt": ttk,
-               "multicommodity": mcf,
+               "multicommodity": mcf, "adjoint": adjoint,
                "solver": {"eta": info0.eta, "sigma_max": info0.sigma_max,
                           "iters_done": info.iters, "restarts": info.restarts,
                           "rel_kkt_avg": info.kkt_avg[4], "rel_kkt_cur": info.kkt_cur[4],

@@ -380,3 +380,14 @@ def multicommodity_grid(seed: int = 4, side: int = 300, commodities: int = 8) ->
     return LPData(m, n, row_ptr, col_idx, val, c, b, np.zeros(n), np.full(n, np.inf), row_type,
                   None, None, name=f"multicommodity_grid(side={side},K={K},seed={seed})",
                   meta={"arcs": n_arcs, "nodes": V})
+
+
+def box_standard_form(seed: int = 3, m: int = 2000, n: int = 5000, per_col: int = 10) -> LPData:
+    """Standard-form LP with box bounds [0, 1] and a planted optimum (x* zero
+    on half the columns with s > 0, U(0,1) interior elsewhere with s = 0),
+    the shape of the differentiable-LP workload (m = 2000, n = 5000,
+    nnz = 50k)."""
+    d = tiny_standard_form(seed, m=m, n=n, per_col=per_col)
+    d.ub = np.ones(n)
+    d.name = f"box_standard_form(m={m},n={n},seed={seed})"
+    return d
