@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblp.so")
 SOURCES = ["lp_api.cu", "lp_kernels.cu"]
-HEADERS = [os.path.join(CSRC, "lp_internal.h"), os.path.join(ROOT, "include", "lp.h")]
+HEADERS = [os.path.join(CSRC, h) for h in ("lp_internal.h", "lp_host.h", "spmv_core.cuh")] + [
+    os.path.join(ROOT, "include", "lp.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

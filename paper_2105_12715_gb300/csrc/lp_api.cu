@@ -25,132 +25,11 @@
 
 #include "../../include/lp.h"
 #include "lp_internal.h"
+#include "lp_host.h"
 
 using namespace lpg;
 
 namespace {
-
-thread_local std::string g_err;
-
-lp_status fail(lp_status s, const std::string &msg) {
-  g_err = msg;
-  return s;
-}
-
-lp_status cuda_fail(cudaError_t e, const char *what) {
-  cudaGetLastError();
-  return fail(e == cudaErrorMemoryAllocation ? LP_ERR_OOM : LP_ERR_CUDA,
-              std::string(what) + ": " + cudaGetErrorString(e));
-}
-
-#define LP_CU(call)                                   \
-  do {                                                \
-    cudaError_t e_ = (call);                          \
-    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
-  } while (0)
-
-struct HostSell {
-  int32_t nrows = 0, ncols = 0, nslices = 0, n_warp_rows = 0;
-  std::vector<SliceInfo> info;
-  std::vector<int32_t> idx;
-  std::vector<double> val;
-};
-
-// Lanes per row: rows of at most single_max elements get one lane (no
-// cross-lane sum); longer rows get the fewest lanes G = 2^lg (<= 32) with
-// ceil(len / G) <= lane_steps, so that no lane's chain of dependent
-// gathers is long; rows of at least warp_threshold elements take a warp.
-struct LanePolicy {
-  int32_t warp_threshold, lane_steps, single_max;
-};
-
-int lanes_log2(int64_t len, const LanePolicy &p) {
-  if (len >= p.warp_threshold) return 5;
-  if (len <= p.single_max) return 0;
-  int lg = 0;
-  while (lg < 5 && (int64_t(p.lane_steps) << lg) < len) ++lg;
-  return lg;
-}
-
-// Number of slices the layout of rows perm[0..) (longest first) would have.
-int64_t count_slices(const std::vector<int64_t> &ptr, const std::vector<int32_t> &perm,
-                     const LanePolicy &p) {
-  const int32_t nrows = (int32_t)perm.size();
-  int64_t ns = 0;
-  int32_t r = 0;
-  while (r < nrows) {
-    const int lg = lanes_log2(ptr[perm[r] + 1] - ptr[perm[r]], p);
-    const int cap = kWarp >> lg;
-    int32_t q = r;
-    while (q < nrows && q - r < cap && lanes_log2(ptr[perm[q] + 1] - ptr[perm[q]], p) == lg) ++q;
-    ++ns;
-    r = q;
-  }
-  return ns;
-}
-
-// Launch-shape tuning by a model: a pass runs one warp per slice, and
-// fewer slices than `target` warps leave SMs idle while each warp walks a
-// long chain of dependent gathers.  Starting from the given policy, give
-// rows more lanes (halving single_max and lane_steps) until the layout
-// has at least `target` slices or rows get one element per lane.
-LanePolicy choose_policy(const std::vector<int64_t> &ptr, const std::vector<int32_t> &perm,
-                         LanePolicy p, int64_t target) {
-  if (target <= 0) return p;
-  while (count_slices(ptr, perm, p) < target && (p.single_max > 1 || p.lane_steps > 1)) {
-    p.single_max = p.single_max / 2;
-    p.lane_steps = std::max(1, p.lane_steps / 2);
-  }
-  return p;
-}
-
-// Sliced layout (see SellMat) of the operator whose row r (permuted order)
-// is original row perm[r] of the CSR (ptr, ind, v); column indices
-// relabeled by relabel.  Rows come longest first, so a slice is closed when
-// it is full (32 / G rows) or when the next row wants another G.
-void build_sell(int32_t nrows, int32_t ncols, const std::vector<int64_t> &ptr,
-                const std::vector<int32_t> &ind, const std::vector<double> &v,
-                const std::vector<int32_t> &perm, const std::vector<int32_t> &relabel,
-                const LanePolicy &policy, HostSell &S) {
-  S.nrows = nrows;
-  S.ncols = ncols;
-  auto len = [&](int32_t r) { return ptr[perm[r] + 1] - ptr[perm[r]]; };
-  S.info.clear();
-  int64_t off = 0;
-  int32_t r = 0;
-  while (r < nrows) {
-    const int lg = lanes_log2(len(r), policy);
-    const int cap = kWarp >> lg;
-    int32_t q = r;
-    int64_t mx = 0;
-    while (q < nrows && q - r < cap && lanes_log2(len(q), policy) == lg) {
-      mx = std::max<int64_t>(mx, len(q));
-      ++q;
-    }
-    const int64_t steps = (mx + (int64_t(1) << lg) - 1) >> lg;
-    if (lg == 5) S.n_warp_rows += q - r;
-    S.info.push_back(SliceInfo{off, r, (int32_t)((steps << 3) | lg)});
-    off += steps * kWarp;
-    r = q;
-  }
-  S.nslices = (int32_t)S.info.size();
-  S.info.push_back(SliceInfo{off, nrows, 0});
-  S.idx.assign(off, 0);
-  S.val.assign(off, 0.0);
-  for (int32_t s = 0; s < S.nslices; ++s) {
-    const SliceInfo &a = S.info[s];
-    const int lg = a.len_g & 7, G = 1 << lg;
-    for (int32_t row = a.row0; row < S.info[s + 1].row0; ++row) {
-      const int64_t src = ptr[perm[row]];
-      const int64_t lane0 = (int64_t)(row - a.row0) * G;
-      for (int64_t k = 0; k < len(row); ++k) {
-        const int64_t dst = a.off + kWarp * (k >> lg) + lane0 + (k & (G - 1));
-        S.idx[dst] = relabel[ind[src + k]];
-        S.val[dst] = v[src + k];
-      }
-    }
-  }
-}
 
 // Segments of at most kSegSteps steps, and a split of them over nwarps
 // persistent warps: contiguous ranges, cut only where a slice starts,
@@ -302,42 +181,6 @@ struct lp_problem {
 
 namespace {
 
-template <class T>
-bool copy_in(std::vector<T> &dst, const T *src, int64_t count) {
-  dst.resize(count);
-  if (count == 0) return true;
-  return cudaMemcpy(dst.data(), src, sizeof(T) * count, cudaMemcpyDefault) == cudaSuccess;
-}
-
-lp_status validate_options(const lp_options &o) {
-  if (!(o.beta > 0.0 && o.beta < 1.0)) return fail(LP_ERR_INVALID_ARG, "beta must lie in (0, 1)");
-  if (o.check_every < 1 || o.check_every > 65536)
-    return fail(LP_ERR_INVALID_ARG, "check_every must lie in [1, 65536]");
-  if (o.restart_scheme < LP_RESTART_NONE || o.restart_scheme > LP_RESTART_FLEXIBLE)
-    return fail(LP_ERR_INVALID_ARG, "unknown restart_scheme");
-  if (o.tau0 < 0 || o.fixed_len < 0) return fail(LP_ERR_INVALID_ARG, "tau0 and fixed_len must be >= 0");
-  if (!(o.omega > 0.0) || !std::isfinite(o.omega)) return fail(LP_ERR_INVALID_ARG, "omega must be finite and > 0");
-  if (!(o.eta >= 0.0) || !std::isfinite(o.eta)) return fail(LP_ERR_INVALID_ARG, "eta must be finite and >= 0");
-  if (o.power_iters < 1) return fail(LP_ERR_INVALID_ARG, "power_iters must be >= 1");
-  if (!(o.power_tol >= 0.0)) return fail(LP_ERR_INVALID_ARG, "power_tol must be >= 0");
-  if (o.max_iter < 0) return fail(LP_ERR_INVALID_ARG, "max_iter must be >= 0");
-  if (o.long_row_threshold < 1) return fail(LP_ERR_INVALID_ARG, "long_row_threshold must be >= 1");
-  if (o.trace_capacity < 0) return fail(LP_ERR_INVALID_ARG, "trace_capacity must be >= 0");
-  for (int32_t u : {o.spmv_unroll, o.spmv_unroll_rows}) {
-    const int32_t b = u % 100;
-    if (u / 100 < -1 || u / 100 > 1 || (b != 2 && b != 4 && b != 8 && b != -2 && b != -4))
-      return fail(LP_ERR_INVALID_ARG,
-                  "spmv_unroll(_rows) must be 2, 4, 8, -2 or -4, or that +-100 (capped registers)");
-  }
-  if (o.lane_steps < 1 || o.lane_steps > 1024) return fail(LP_ERR_INVALID_ARG, "lane_steps must lie in [1, 1024]");
-  if (o.single_lane_max < 0) return fail(LP_ERR_INVALID_ARG, "single_lane_max must be >= 0");
-  if (o.spmv_mode != 0 && o.spmv_mode != 1) return fail(LP_ERR_INVALID_ARG, "spmv_mode must be 0 or 1");
-  if (o.lane_auto < 0) return fail(LP_ERR_INVALID_ARG, "lane_auto must be >= 0");
-  if (o.precision != LP_PRECISION_FP64 && o.precision != LP_PRECISION_MIXED)
-    return fail(LP_ERR_INVALID_ARG, "precision must be LP_PRECISION_FP64 or LP_PRECISION_MIXED");
-  return LP_OK;
-}
-
 // Resets Algorithm 1's counters on the device (status running).
 lp_status reset_state(lp_problem *h, cudaStream_t s) {
   DevState hs{};
@@ -434,13 +277,13 @@ void lp_default_options(lp_options *o) {
   o->lane_auto = 32;
 }
 
-const char *lp_last_error(void) { return g_err.c_str(); }
+const char *lp_last_error(void) { return err_msg().c_str(); }
 
 lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
                     const int32_t *col_idx, const double *val, const double *c, const double *b,
                     const double *lb, const double *ub, const int8_t *row_type,
                     const lp_options *opt_in, void *cuda_stream, lp_handle *out) {
-  g_err.clear();
+  err_msg().clear();
   if (!out) return fail(LP_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (m < 0 || n < 1) return fail(LP_ERR_INVALID_ARG, "need m >= 0 and n >= 1");
@@ -714,7 +557,7 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
 }
 
 lp_status lp_set_state(lp_handle h, const double *x, const double *y, void *cuda_stream) {
-  g_err.clear();
+  err_msg().clear();
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   if (x) {
@@ -736,7 +579,7 @@ lp_status lp_set_state(lp_handle h, const double *x, const double *y, void *cuda
 }
 
 lp_status lp_iterate(lp_handle h, int32_t n_checks, double tol, void *cuda_stream) {
-  g_err.clear();
+  err_msg().clear();
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   if (!(tol > 0.0)) return fail(LP_ERR_INVALID_ARG, "tol must be > 0");
   if (n_checks < 0) return fail(LP_ERR_INVALID_ARG, "n_checks must be >= 0");
@@ -750,7 +593,7 @@ lp_status lp_iterate(lp_handle h, int32_t n_checks, double tol, void *cuda_strea
 }
 
 lp_status lp_solve(lp_handle h, double tol, void *cuda_stream) {
-  g_err.clear();
+  err_msg().clear();
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   if (!(tol > 0.0)) return fail(LP_ERR_INVALID_ARG, "tol must be > 0");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -794,7 +637,7 @@ lp_status lp_solve(lp_handle h, double tol, void *cuda_stream) {
 }
 
 lp_status lp_get_solution(lp_handle h, double *x, double *y, void *cuda_stream) {
-  g_err.clear();
+  err_msg().clear();
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   if (!h->solved) return fail(LP_ERR_NOT_SOLVED, "no solve has run on this handle");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -818,7 +661,7 @@ lp_status lp_get_solution(lp_handle h, double *x, double *y, void *cuda_stream) 
 
 lp_status lp_get_state(lp_handle h, double *x, double *y, double *xbar, double *ybar, double *x0,
                        double *y0, void *cuda_stream) {
-  g_err.clear();
+  err_msg().clear();
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   if (h->mixed) launch_combine(h->v, h->mv, h->st, h->n, h->m, 1, s);
@@ -837,7 +680,7 @@ lp_status lp_get_state(lp_handle h, double *x, double *y, double *xbar, double *
 }
 
 lp_status lp_get_info(lp_handle h, lp_info *info) {
-  g_err.clear();
+  err_msg().clear();
   if (!h || !info) return fail(LP_ERR_INVALID_ARG, "NULL argument");
   DevState hs{};
   LP_CU(cudaMemcpy(&hs, h->st, sizeof(DevState), cudaMemcpyDeviceToHost));
@@ -866,7 +709,7 @@ lp_status lp_get_info(lp_handle h, lp_info *info) {
 }
 
 lp_status lp_get_trace(lp_handle h, double *rows, int64_t capacity, int64_t *count) {
-  g_err.clear();
+  err_msg().clear();
   if (!h || !count || (capacity > 0 && !rows)) return fail(LP_ERR_INVALID_ARG, "NULL argument");
   int64_t tc = 0;
   LP_CU(cudaMemcpy(&tc, &h->st->trace_count, sizeof(int64_t), cudaMemcpyDeviceToHost));
@@ -879,7 +722,7 @@ lp_status lp_get_trace(lp_handle h, double *rows, int64_t capacity, int64_t *cou
 
 lp_status lp_normalized_gap(lp_handle h, const double *x, const double *y, double r,
                             double *host_rho, void *cuda_stream) {
-  g_err.clear();
+  err_msg().clear();
   if (!h || !host_rho || !x || (h->m > 0 && !y)) return fail(LP_ERR_INVALID_ARG, "NULL argument");
   if (!(r >= 0.0) || !std::isfinite(r)) return fail(LP_ERR_INVALID_ARG, "radius must be finite and >= 0");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -945,7 +788,7 @@ lp_status lp_normalized_gap(lp_handle h, const double *x, const double *y, doubl
 
 lp_status lp_select_omega(lp_handle h, const double *omegas, int32_t count, int64_t iters,
                           double *kkt_out, double *best_out, void *cuda_stream) {
-  g_err.clear();
+  err_msg().clear();
   if (!h || !omegas || !kkt_out || count < 1) return fail(LP_ERR_INVALID_ARG, "bad arguments");
   if (iters < h->opt.check_every) return fail(LP_ERR_INVALID_ARG, "iters must be >= check_every");
   for (int32_t k = 0; k < count; ++k)
@@ -991,7 +834,7 @@ lp_status lp_select_omega(lp_handle h, const double *omegas, int32_t count, int6
 }
 
 lp_status lp_solve_recorded(lp_handle h, int64_t iters, void *cuda_stream) {
-  g_err.clear();
+  err_msg().clear();
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   const int K = h->opt.check_every;
   if (iters < K || iters % K != 0) return fail(LP_ERR_INVALID_ARG, "iters must be a positive multiple of check_every");
@@ -1046,7 +889,7 @@ lp_status lp_solve_recorded(lp_handle h, int64_t iters, void *cuda_stream) {
 
 lp_status lp_backward(lp_handle h, const double *dl_dx, const double *dl_dy, double *dl_dc,
                       double *dl_db, void *cuda_stream) {
-  g_err.clear();
+  err_msg().clear();
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   if (h->rec_blocks == 0) return fail(LP_ERR_NOT_SOLVED, "no recorded solve (lp_solve_recorded)");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -1126,7 +969,7 @@ lp_status lp_backward(lp_handle h, const double *dl_dx, const double *dl_dy, dou
 }
 
 lp_status lp_profile_kernel(lp_handle h, int32_t which, int32_t reps, void *cuda_stream) {
-  g_err.clear();
+  err_msg().clear();
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   if (which < 0 || which > 1 || reps < 0) return fail(LP_ERR_INVALID_ARG, "which must be 0 or 1, reps >= 0");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -1208,7 +1051,7 @@ struct ScratchCarver {
 
 extern "C" lp_status lp_normalized_gap_static(lp_handle h, const double *x, const double *y,
                                               double r, double *host_rho, void *cuda_stream) {
-  g_err.clear();
+  err_msg().clear();
   if (!h || !host_rho || !x || (h->m > 0 && !y)) return fail(LP_ERR_INVALID_ARG, "NULL argument");
   if (!(r >= 0.0) || !std::isfinite(r)) return fail(LP_ERR_INVALID_ARG, "radius must be finite and >= 0");
   const int n = h->n, m = h->m;

@@ -1,0 +1,362 @@
+// SpMV core of the sliced layout and the fused epilogues of the PDHG step
+// and of the check, shared by the single-problem kernels (lp_kernels.cu)
+// and the batched kernels (lp_batch.cu).  Header-only device code.
+#pragma once
+
+#include <cmath>
+#include <cstdint>
+
+#include "lp_internal.h"
+
+namespace lpg {
+namespace {
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kUnroll = 8;   // gathers in flight per lane, one vector (plain SpMV)
+constexpr int kUnroll2 = 4;  // gathers in flight per lane and vector, two vectors
+constexpr int kStatusOK = 0;
+constexpr int kStatusNumerical = 5;
+constexpr int kSchemeFixed = 1, kSchemeAdaptive = 2, kSchemeFlexible = 3;
+
+__device__ __forceinline__ double sq(double v) { return v * v; }
+
+// ------------------------------------------------------------------ SpMV core
+//
+// Row sums of one slice (one warp).  Each lane walks its row's elements
+// k = g, g + G, g + 2G, ... in stored order, U steps at a time: the U
+// index and value loads of a batch are issued together, then the U
+// gathers, then the FMAs, so a lane has U gathers in flight.  The G lanes of
+// a row are then combined by a butterfly (the same sum in every lane of the
+// group), and the group's first lane runs the epilogue.  The epilogue's
+// operands are loaded before the row loop.  NV = 1 or 2 gathered vectors.
+// T is the value type of the matrix copy, of the gathered vectors and of
+// the accumulators (double for the FP64 path, float for the mixed path).
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ const double *vals_of(const SellMat &A, double) { return A.val; }
+__device__ __forceinline__ const float *vals_of(const SellMat &A, float) { return A.valf; }
+
+template <int NV, int U, bool PIPE, typename T, class Epi>
+__device__ __forceinline__ void process_item(const SellMat &A, const T *__restrict__ v0,
+                                             const T *__restrict__ v1, int item, int lane,
+                                             Epi &epi) {
+  const SliceInfo a = A.info[item];
+  const int32_t row_end = A.info[item + 1].row0;
+  const int lg = a.len_g & 7;
+  const int steps = a.len_g >> 3;
+  const int row = a.row0 + (lane >> lg);
+  const bool owner = ((lane & ((1 << lg) - 1)) == 0) && row < row_end;
+  typename Epi::Pre pre{};
+  if (owner) pre = epi.load(row);
+  const int32_t *ip = A.idx + a.off + lane;
+  const T *vp = vals_of(A, T(0)) + a.off + lane;
+  T a0 = owner ? epi.init(pre) : T(0), a1 = T(0);
+  int32_t j[U];
+  T c[U];
+  if (PIPE) {  // software pipeline: the next batch's index/value loads overlap this batch's gathers
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (u < steps) {
+        j[u] = __ldcs(ip + (size_t)kWarp * u);
+        c[u] = __ldcs(vp + (size_t)kWarp * u);
+      }
+    }
+  }
+  for (int t = 0; t < steps; t += U) {
+    T g[U], h[U];
+    if (!PIPE) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (t + u < steps) {
+          j[u] = __ldcs(ip + (size_t)kWarp * (t + u));
+          c[u] = __ldcs(vp + (size_t)kWarp * (t + u));
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (t + u < steps) {
+        g[u] = __ldg(v0 + j[u]);
+        if (NV == 2) h[u] = __ldg(v1 + j[u]);
+      }
+    }
+    int32_t jn[U];
+    T cn[U];
+    if (PIPE) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (t + U + u < steps) {
+          jn[u] = __ldcs(ip + (size_t)kWarp * (t + U + u));
+          cn[u] = __ldcs(vp + (size_t)kWarp * (t + U + u));
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (t + u < steps) {
+        a0 = fma_t(c[u], g[u], a0);
+        if (NV == 2) a1 = fma_t(c[u], h[u], a1);
+      }
+    }
+    if (PIPE) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        j[u] = jn[u];
+        c[u] = cn[u];
+      }
+    }
+  }
+  for (int o = (1 << lg) >> 1; o > 0; o >>= 1) {
+    a0 += __shfl_xor_sync(kFull, a0, o);
+    if (NV == 2) a1 += __shfl_xor_sync(kFull, a1, o);
+  }
+  if (owner) epi.store(row, a0, a1, pre);
+}
+
+template <int NV, int U, bool PIPE = false, typename T, class Epi>
+__device__ __forceinline__ void process_all(const SellMat &A, const T *v0, const T *v1,
+                                            Epi &epi) {
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)(gridDim.x * blockDim.x) >> 5;
+  for (int it = warp; it < A.nslices; it += nwarps)
+    process_item<NV, U, PIPE>(A, v0, v1, it, lane, epi);
+}
+
+// Fixed-order block reduction of NV2 per-thread values; thread q < NV2 of
+// the block writes the block's value q to partials[q * pstride + col].
+template <int NV2>
+__device__ __forceinline__ void block_reduce_store(const double (&q)[NV2], double *partials,
+                                                   int pstride, int col) {
+  __shared__ double sh[kBlock / kWarp][NV2];
+  const int lane = threadIdx.x & (kWarp - 1), warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV2; ++i) {
+    double v = q[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    if (lane == 0) sh[warp][i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV2) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w][threadIdx.x];
+    partials[(size_t)threadIdx.x * pstride + col] = s;
+  }
+}
+
+// -------------------------------------------------------------- epilogues
+
+// Order-preserving map of a double's bit pattern to a signed integer
+// (negative values: all bits but the sign flipped); it is its own inverse.
+// Clamps and sign projections compare these keys on the integer pipe
+// instead of issuing FP64 min/max (GB300 runs 2 FP64 operations per cycle
+// per SM).
+__device__ __forceinline__ long long ord_key(long long b) {
+  return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+
+// Eq. (PDHG-update), primal half, and Algorithm 1's running average.  The
+// row sum starts at -c_j, so it ends as (A^T y)_j - c_j = -g_j.  lbk/ubk are
+// the bounds' order keys.
+struct PrimalEpi {
+  const double *__restrict__ c;
+  const long long *__restrict__ lbk;
+  const long long *__restrict__ ubk;
+  double *x, *xhat, *xbar;
+  double tau, w;
+  uint8_t *mask;  // adjoint recording: 1 where the clamp is inactive, or null
+  struct Pre { double c, x, xb; long long lk, uk; };
+  __device__ __forceinline__ Pre load(int j) const { return {c[j], x[j], xbar[j], lbk[j], ubk[j]}; }
+  __device__ __forceinline__ double init(const Pre &p) const { return -p.c; }
+  __device__ __forceinline__ void store(int j, double neg_g, double, const Pre &p) const {
+    const double v = fma(tau, neg_g, p.x);  // x - tau (c - A^T y)
+    long long k = ord_key(__double_as_longlong(v));
+    if (mask) mask[j] = (k > p.lk && k < p.uk) ? 1 : 0;
+    k = k < p.lk ? p.lk : k;
+    k = k > p.uk ? p.uk : k;
+    const double xn = __longlong_as_double(ord_key(k));
+    x[j] = xn;
+    xhat[j] = fma(2.0, xn, -p.x);
+    xbar[j] = fma(w, xn - p.xb, p.xb);
+  }
+};
+
+// Eq. (PDHG-update), dual half: projection onto Y_i by row sense (on the
+// integer pipe: a negative double has a negative bit pattern).  The row sum
+// starts at -b_i, so it ends as (A xhat)_i - b_i.
+struct DualEpi {
+  const double *__restrict__ b;
+  const int8_t *__restrict__ rt;
+  double *y, *ybar;
+  double sigma, w;
+  uint8_t *mask;  // adjoint recording: 1 where the projection is inactive, or null
+  struct Pre { double b, y, yb; int t; };
+  __device__ __forceinline__ Pre load(int i) const { return {b[i], y[i], ybar[i], (int)rt[i]}; }
+  __device__ __forceinline__ double init(const Pre &p) const { return -p.b; }
+  __device__ __forceinline__ void store(int i, double r, double, const Pre &p) const {
+    long long bits = __double_as_longlong(fma(-sigma, r, p.y));  // y + sigma (b - A xhat)
+    if (mask) mask[i] = (p.t == 0 || (p.t == 1 && bits > 0) || (p.t == 2 && bits < 0)) ? 1 : 0;
+    if (p.t == 1 && bits < 0) bits = 0;       // GE: [0, inf)
+    else if (p.t == 2 && bits > 0) bits = 0;  // LE: (-inf, 0]
+    const double yn = __longlong_as_double(bits);
+    y[i] = yn;
+    ybar[i] = fma(w, yn - p.yb, p.yb);
+  }
+};
+
+struct StoreEpi {
+  double *out;
+  struct Pre {};
+  __device__ __forceinline__ Pre load(int) const { return {}; }
+  __device__ __forceinline__ double init(const Pre &) const { return 0.0; }
+  __device__ __forceinline__ void store(int r, double a, double, const Pre &) const { out[r] = a; }
+};
+
+// One coordinate of the linear trust region of Section 6.3 in the
+// omega-rescaled space: objective component G, distance dist >= 0 to the
+// bound it moves toward (INFINITY if none), scales sd (distance) and sg
+// (objective).  Breakpoint lambda_hat = d / g; its bit pattern is the key.
+struct GapOut {
+  uint64_t *keys;
+  double *d2, *g2, *gd;
+};
+
+__device__ __forceinline__ void gap_elem(double G, double dist, double sd, double sg, int64_t e,
+                                         const GapOut &o, double &sum_d2, double &sum_gd,
+                                         double &sum_g2inf) {
+  uint64_t key = kNoKey;
+  if (G != 0.0) {
+    const double g = fabs(G) * sg;
+    if (isinf(dist)) {
+      sum_g2inf += g * g;
+    } else {
+      const double d = dist * sd;
+      const double lam = d / g;
+      if (isinf(lam)) {
+        sum_g2inf += g * g;
+      } else {
+        key = (uint64_t)__double_as_longlong(lam);
+        const double vd2 = d * d, vg2 = g * g, vgd = d * g;
+        sum_d2 += vd2;
+        sum_gd += vgd;
+        o.d2[e] = vd2;
+        o.g2[e] = vg2;
+        o.gd[e] = vgd;
+      }
+    }
+  }
+  o.keys[e] = key;
+}
+
+// Check epilogue over columns (x-space): reduced costs lam = c - A^T y for
+// both candidates, dual residual, dual-objective bound terms, primal
+// objective, and the x-part of the trust region with F_x = lam.
+struct CheckColsEpi {
+  const double *__restrict__ c;
+  const double *__restrict__ lb;
+  const double *__restrict__ ub;
+  const double *__restrict__ xbar;
+  const double *__restrict__ x;
+  const double *__restrict__ x0;
+  GapOut ga, gc;
+  double *lam_out0, *lam_out1;  // mixed precision: c - A^T y of both candidates, or null
+  double sw, isw;
+  int gap_a, gap_c;
+  double q[NQ];
+  struct Pre { double c, lb, ub, xb, x, x0; };
+  __device__ __forceinline__ Pre load(int j) const {
+    return {c[j], lb[j], ub[j], xbar[j], x[j], x0[j]};
+  }
+  __device__ __forceinline__ double init(const Pre &) const { return 0.0; }
+  __device__ __forceinline__ void store(int j, double aty_a, double aty_c, const Pre &p) {
+    const bool lf = p.lb > -INFINITY, uf = p.ub < INFINITY;
+    // Lambda_j: {0} free, [0,inf) only l finite, (-inf,0] only u finite, R both
+    const double lo = uf ? -INFINITY : 0.0;
+    const double hi = lf ? INFINITY : 0.0;
+    const double lam_a = p.c - aty_a, lam_c = p.c - aty_c;
+    if (lam_out0) {
+      lam_out0[j] = lam_a;
+      lam_out1[j] = lam_c;
+    }
+    const double lt_a = fmin(fmax(lam_a, lo), hi), lt_c = fmin(fmax(lam_c, lo), hi);
+    q[Q_RD2_A] += sq(lam_a - lt_a);
+    q[Q_RD2_C] += sq(lam_c - lt_c);
+    if (lf && lt_a > 0.0) q[Q_DOBJ_A] += p.lb * lt_a;
+    if (uf && lt_a < 0.0) q[Q_DOBJ_A] += p.ub * lt_a;
+    if (lf && lt_c > 0.0) q[Q_DOBJ_C] += p.lb * lt_c;
+    if (uf && lt_c < 0.0) q[Q_DOBJ_C] += p.ub * lt_c;
+    q[Q_POBJ_A] += p.c * p.xb;
+    q[Q_POBJ_C] += p.c * p.x;
+    if (!(isfinite(lam_a) && isfinite(lam_c) && isfinite(p.xb) && isfinite(p.x))) q[Q_BAD] += 1.0;
+    if (gap_a) {
+      const double dx = p.xb - p.x0;
+      q[Q_RRX_A] += dx * dx;
+      double dist = INFINITY;
+      if (lam_a > 0.0 && lf) dist = fmax(p.xb - p.lb, 0.0);
+      if (lam_a < 0.0 && uf) dist = fmax(p.ub - p.xb, 0.0);
+      gap_elem(lam_a, dist, sw, isw, j, ga, q[Q_D2_A], q[Q_GD_A], q[Q_G2INF_A]);
+    }
+    if (gap_c) {
+      const double dx = p.x - p.x0;
+      q[Q_RRX_C] += dx * dx;
+      double dist = INFINITY;
+      if (lam_c > 0.0 && lf) dist = fmax(p.x - p.lb, 0.0);
+      if (lam_c < 0.0 && uf) dist = fmax(p.ub - p.x, 0.0);
+      gap_elem(lam_c, dist, sw, isw, j, gc, q[Q_D2_C], q[Q_GD_C], q[Q_G2INF_C]);
+    }
+  }
+};
+
+// Check epilogue over rows (y-space): primal residual by row sense, b^T y,
+// and the y-part of the trust region with F_y = A x - b.
+struct CheckRowsEpi {
+  const double *__restrict__ b;
+  const int8_t *__restrict__ rt;
+  const double *__restrict__ ybar;
+  const double *__restrict__ y;
+  const double *__restrict__ y0;
+  GapOut ga, gc;
+  double *gy_out0, *gy_out1;  // mixed precision: A x - b of both candidates, or null
+  double sw, isw;
+  int64_t off;  // element offset of the y-part in the search arrays (= n)
+  int gap_a, gap_c;
+  double q[NQ];
+  struct Pre { double b, yb, y, y0; int t; };
+  __device__ __forceinline__ Pre load(int i) const { return {b[i], ybar[i], y[i], y0[i], (int)rt[i]}; }
+  __device__ __forceinline__ double init(const Pre &) const { return 0.0; }
+  __device__ __forceinline__ void store(int i, double ax_a, double ax_c, const Pre &p) {
+    double va = ax_a - p.b, vc = ax_c - p.b;
+    if (gy_out0) {
+      gy_out0[i] = va;
+      gy_out1[i] = vc;
+    }
+    if (p.t == 1) { va = fmin(va, 0.0); vc = fmin(vc, 0.0); }
+    if (p.t == 2) { va = fmax(va, 0.0); vc = fmax(vc, 0.0); }
+    q[Q_RP2_A] += va * va;
+    q[Q_RP2_C] += vc * vc;
+    q[Q_DOBJ_A] += p.b * p.yb;
+    q[Q_DOBJ_C] += p.b * p.y;
+    if (!(isfinite(ax_a) && isfinite(ax_c) && isfinite(p.yb) && isfinite(p.y))) q[Q_BAD] += 1.0;
+    if (gap_a) {
+      const double G = ax_a - p.b;
+      const double dy = p.yb - p.y0;
+      q[Q_RRY_A] += dy * dy;
+      double dist = INFINITY;
+      if (G > 0.0 && p.t == 1) dist = fmax(p.yb, 0.0);
+      if (G < 0.0 && p.t == 2) dist = fmax(-p.yb, 0.0);
+      gap_elem(G, dist, isw, sw, off + i, ga, q[Q_D2_A], q[Q_GD_A], q[Q_G2INF_A]);
+    }
+    if (gap_c) {
+      const double G = ax_c - p.b;
+      const double dy = p.y - p.y0;
+      q[Q_RRY_C] += dy * dy;
+      double dist = INFINITY;
+      if (G > 0.0 && p.t == 1) dist = fmax(p.y, 0.0);
+      if (G < 0.0 && p.t == 2) dist = fmax(-p.y, 0.0);
+      gap_elem(G, dist, isw, sw, off + i, gc, q[Q_D2_C], q[Q_GD_C], q[Q_G2INF_C]);
+    }
+  }
+};
+
+}  // namespace
+}  // namespace lpg
