@@ -1,6 +1,6 @@
 """Builds liblp.so (the C-ABI library of include/lp.h) for sm_103a with nvcc.
 
-The two translation units compile in parallel, then link into
+The translation units compile in parallel, then link into
 paper_2105_12715_gb300/_build/liblp.so.  Rebuilds only when a source or
 header is newer than the library (or when force=True).
 """
@@ -15,9 +15,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblp.so")
-SOURCES = ["lp_api.cu", "lp_kernels.cu"]
+SOURCES = ["lp_api.cu", "lp_kernels.cu", "lp_batch.cu"]
 HEADERS = [os.path.join(CSRC, h) for h in ("lp_internal.h", "lp_host.h", "spmv_core.cuh")] + [
-    os.path.join(ROOT, "include", "lp.h")]
+    os.path.join(ROOT, "include", h) for h in ("lp.h", "lp_batch.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

@@ -1,0 +1,1378 @@
+// Batched restarted PDHG (include/lp_batch.h): many independent LPs of
+// uneven sizes on one GPU, each running Algorithm 1 with its own step
+// sizes, restart state and termination test.
+//
+// Layout.  The batch is stored as one block-diagonal LP in the sliced
+// layout of the single-problem solver, with rows (and columns) permuted by
+// length WITHIN each problem, so every problem keeps a contiguous range of
+// rows, columns and slices, and no slice spans two problems.  A slice knows
+// its problem (sinst), a problem knows its ranges (BInst).
+//
+// Per block of K_base iterations (one CUDA graph):
+//   b_primal / b_dual (x K_base): one warp per slice of the running
+//       problems' work list, with that problem's tau or sigma and averaging
+//       weight 1 / (t + k + 1) -- the fused step and average of the
+//       single-problem kernels;
+//   b_pre_check: counters; a problem is due for its check every K_k
+//       iterations (K_k a multiple of K_base);
+//   b_check (columns, rows): the check epilogues on the due problems'
+//       slices, one fixed-order partial sum per slice and quantity;
+//   b_finalize: one block per due problem: its sums, relative KKT,
+//       termination, radius, search setup;
+//   b_search: one block per due problem: the whole multiplier search of
+//       Section 6.3 (8 radix passes over the breakpoints' bit patterns,
+//       shared-memory histograms per warp, bracket selection in-block);
+//   b_decide: restart rule, counters, next averaging weights, running count;
+//   b_restart_copy: z^{n+1,0} <- zbar, z <- zbar for restarting problems;
+//   b_worklist: the next block's slice lists (running problems only).
+// All reductions run in a fixed order: results are bitwise reproducible
+// for a given batch and launch configuration.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <vector>
+
+#include "../../include/lp_batch.h"
+#include "lp_host.h"
+#include "lp_internal.h"
+#include "spmv_core.cuh"
+
+namespace lpg {
+namespace {
+
+constexpr int kMaxClasses = 8;
+constexpr int kStatusIterLimit = 4;
+constexpr int kListThreads = 1024;
+constexpr int kSearchWarps = 8;
+constexpr int kSearchThreads = kSearchWarps * kWarp;  // one thread per bucket
+static_assert(kSearchThreads == kBuckets, "bracket selection uses one thread per bucket");
+constexpr size_t kSearchHistBytes = sizeof(double) * kSearchWarps * kBuckets * 3;
+constexpr size_t kSearchCntBytes = sizeof(unsigned) * kSearchWarps * kBuckets;
+constexpr size_t kSearchSmem = kSearchHistBytes + kSearchCntBytes + sizeof(double) * kSearchWarps * kWarp * 3;
+
+// Per-problem state (device, one per problem).
+struct BInst {
+  int32_t col0, ncol, row0, nrow;  // ranges in the permuted index spaces
+  int32_t cs0, cs1, rs0, rs1;      // slice ranges in A^T and A
+  int32_t K;                       // check period (multiple of K_base)
+  int32_t status;                  // kRunning or a final lp_status
+  int32_t returned, restart_now, use_cur, due;
+  int32_t pw_done, pw_iters;
+  int64_t t0;                      // inner iterations since the restart, at block start
+  int64_t iters, checks, restarts;
+  int64_t since;                   // iterations since the last check
+  int64_t iter_cap;                // stop (iteration limit) once iters reaches it
+  int64_t tau0, fixed_len;
+  double tau, sigma, omega;
+  double norm_b, norm_c;
+  double rho_stored, last_rho, last_r;
+  double kkt_a[5], kkt_c[5];
+  double pw_est, pw_nw;
+  LSearch ls[2];
+};
+
+// Batch-wide parameters and counters (device).
+struct BGlobal {
+  double tol, beta, pw_tol;
+  int32_t count, Kb, scheme, pw_max;
+  int32_t running;     // problems still iterating after the last check
+  int32_t pw_running;  // problems still in the power iteration after the last step
+  int32_t wl_n[2];     // work-list lengths: [0] column slices, [1] row slices
+};
+
+struct SearchArrays {
+  uint64_t *keys[2];
+  double *d2[2], *g2[2], *gd[2];
+};
+
+// ---------------------------------------------------------------- iteration
+
+template <int U, bool PIPE>
+__global__ void __launch_bounds__(kBlock) b_primal_kernel(SellMat AT, const double *__restrict__ y,
+                                                          PrimalEpi epi,
+                                                          const BInst *__restrict__ I,
+                                                          const int32_t *__restrict__ sinst,
+                                                          const int32_t *__restrict__ wl,
+                                                          const BGlobal *G,
+                                                          const double *__restrict__ wtab, int k) {
+  const int nwl = G->wl_n[0], Kb = G->Kb;
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int nwarps = (int)(gridDim.x * blockDim.x) >> 5;
+  for (int it = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); it < nwl; it += nwarps) {
+    const int s = wl[it];
+    const int i = sinst[s];
+    epi.tau = I[i].tau;
+    epi.w = wtab[(size_t)i * Kb + k];
+    process_item<1, U, PIPE>(AT, y, (const double *)nullptr, s, lane, epi);
+  }
+}
+
+template <int U, bool PIPE>
+__global__ void __launch_bounds__(kBlock) b_dual_kernel(SellMat A, const double *__restrict__ xhat,
+                                                        DualEpi epi, const BInst *__restrict__ I,
+                                                        const int32_t *__restrict__ sinst,
+                                                        const int32_t *__restrict__ wl,
+                                                        const BGlobal *G,
+                                                        const double *__restrict__ wtab, int k) {
+  const int nwl = G->wl_n[1], Kb = G->Kb;
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int nwarps = (int)(gridDim.x * blockDim.x) >> 5;
+  for (int it = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); it < nwl; it += nwarps) {
+    const int s = wl[it];
+    const int i = sinst[s];
+    epi.sigma = I[i].sigma;
+    epi.w = wtab[(size_t)i * Kb + k];
+    process_item<1, U, PIPE>(A, xhat, (const double *)nullptr, s, lane, epi);
+  }
+}
+
+// ------------------------------------------------------------------- check
+
+__global__ void b_pre_check_kernel(BInst *I, const BGlobal *G) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= G->count) return;
+  BInst &B = I[i];
+  B.due = 0;
+  if (B.status != kRunning) return;
+  B.iters += G->Kb;
+  B.since += G->Kb;
+  B.due = (B.since >= B.K) ? 1 : 0;
+}
+
+// Check epilogue over the due problems' slices; one partial sum per slice
+// and quantity (warp butterfly, fixed order) at spart[q * pstride + poff + s].
+template <class Epi>
+__global__ void __launch_bounds__(kBlock) b_check_kernel(SellMat A, const double *__restrict__ v0,
+                                                         const double *__restrict__ v1, Epi epi,
+                                                         const BInst *__restrict__ I,
+                                                         const int32_t *__restrict__ sinst,
+                                                         const BGlobal *G, double *spart,
+                                                         int64_t pstride, int poff) {
+  const int scheme = G->scheme;
+  epi.gap_a = (scheme == kSchemeAdaptive || scheme == kSchemeFlexible);
+  epi.gap_c = (scheme == kSchemeFlexible);
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int nwarps = (int)(gridDim.x * blockDim.x) >> 5;
+  for (int s = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); s < A.nslices; s += nwarps) {
+    const int i = sinst[s];
+    if (!I[i].due) continue;
+    epi.sw = sqrt(I[i].omega);
+    epi.isw = 1.0 / epi.sw;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) epi.q[q] = 0.0;
+    process_item<2, kUnroll2, false>(A, v0, v1, s, lane, epi);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double v = epi.q[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+      if (lane == 0) spart[(size_t)q * pstride + poff + s] = v;
+    }
+  }
+}
+
+// One block per problem: the due problem's check sums (warp q sums quantity
+// q over its slices in order), relative KKT, termination, search setup.
+__global__ void __launch_bounds__(kBlock) b_finalize_kernel(BInst *I, const BGlobal *G,
+                                                            const double *__restrict__ spart,
+                                                            int64_t pstride, int ncs) {
+  BInst &B = I[blockIdx.x];
+  if (!B.due) return;
+  __shared__ double tot[NQ];
+  const int lane = threadIdx.x & (kWarp - 1), warp = threadIdx.x >> 5;
+  for (int q = warp; q < NQ; q += kBlock / kWarp) {
+    const double *p = spart + (size_t)q * pstride;
+    double acc = 0.0;
+    for (int s = B.cs0 + lane; s < B.cs1; s += kWarp) acc += p[s];
+    for (int s = B.rs0 + lane; s < B.rs1; s += kWarp) acc += p[ncs + s];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    if (lane == 0) tot[q] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const int scheme = G->scheme;
+  const double om = B.omega, tol = G->tol;
+  B.checks += 1;
+  kkt_from(tot, Q_RP2_A, Q_RD2_A, Q_POBJ_A, Q_DOBJ_A, B.norm_b, B.norm_c, B.kkt_a);
+  kkt_from(tot, Q_RP2_C, Q_RD2_C, Q_POBJ_C, Q_DOBJ_C, B.norm_b, B.norm_c, B.kkt_c);
+  const double ra = B.kkt_a[4], rc = B.kkt_c[4];
+  B.ls[0].done = 1;
+  B.ls[1].done = 1;
+  if (tot[Q_BAD] > 0.0 || !isfinite(ra) || !isfinite(rc)) {
+    B.status = kStatusNumerical;
+    return;
+  }
+  if (ra <= tol) {
+    B.status = kStatusOK;
+    B.returned = 0;
+    return;
+  }
+  if (rc <= tol) {
+    B.status = kStatusOK;
+    B.returned = 1;
+    return;
+  }
+  B.returned = (ra <= rc) ? 0 : 1;
+  if (scheme == kSchemeAdaptive || scheme == kSchemeFlexible) {
+    const double r = sqrt(om * tot[Q_RRX_A] + tot[Q_RRY_A] / om);
+    init_search(B.ls[0], r, tot[Q_D2_A], tot[Q_GD_A], tot[Q_G2INF_A]);
+    B.last_r = r;
+  }
+  if (scheme == kSchemeFlexible) {
+    const double r = sqrt(om * tot[Q_RRX_C] + tot[Q_RRY_C] / om);
+    init_search(B.ls[1], r, tot[Q_D2_C], tot[Q_GD_C], tot[Q_G2INF_C]);
+  }
+}
+
+// One block per (due problem, candidate): the multiplier search of
+// Section 6.3 over the problem's breakpoints -- the search of the
+// single-problem solver (8-bit radix passes over the bit patterns of the
+// breakpoints, exact f at bucket edges, closed form on the final bracket),
+// with every pass's histogram and bracket selection inside the block.  Warp
+// w owns elements w*32 + 256 t + lane; within a warp, equal buckets are
+// summed by their lowest lane in lane order; warps are combined in order.
+__global__ void __launch_bounds__(kSearchThreads) b_search_kernel(BInst *I, int64_t nx_total,
+                                                                  SearchArrays sa) {
+  BInst &B = I[blockIdx.x];
+  const int sidx = blockIdx.y;
+  __shared__ LSearch L;
+  __shared__ double bc[kBuckets], bsd[kBuckets], bsg[kBuckets], bse[kBuckets];
+  __shared__ double cum_d[kBuckets + 1], cum_e[kBuckets + 1], tail_g[kBuckets + 1];
+  __shared__ double wt[3][8];
+  __shared__ int kstar;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  double(*hist)[kBuckets][3] = reinterpret_cast<double(*)[kBuckets][3]>(dsm);
+  unsigned(*cnt)[kBuckets] = reinterpret_cast<unsigned(*)[kBuckets]>(dsm + kSearchHistBytes);
+  double(*stage)[kWarp][3] =
+      reinterpret_cast<double(*)[kWarp][3]>(dsm + kSearchHistBytes + kSearchCntBytes);
+  const int tid = threadIdx.x;
+  if (tid == 0) L = B.ls[sidx];
+  __syncthreads();
+  if (!B.due || B.status != kRunning || L.done) return;  // uniform over the block
+  const uint64_t *__restrict__ keys = sidx ? sa.keys[1] : sa.keys[0];
+  const double *__restrict__ d2 = sidx ? sa.d2[1] : sa.d2[0];
+  const double *__restrict__ g2 = sidx ? sa.g2[1] : sa.g2[0];
+  const double *__restrict__ gd = sidx ? sa.gd[1] : sa.gd[0];
+  const int64_t nx = B.ncol, N = nx + B.nrow;
+  const int64_t xbase = B.col0, ybase = nx_total + B.row0 - nx;
+  const int lane = tid & (kWarp - 1), warp = tid >> 5;
+  for (int pass = 0; pass < kSearchPasses; ++pass) {
+    const int shift = 56 - 8 * pass;
+    const uint64_t pre = L.prefix;
+    for (int i = tid; i < kSearchWarps * kBuckets; i += kSearchThreads) {
+      double *h = &hist[0][0][0] + 3 * i;
+      h[0] = 0.0;
+      h[1] = 0.0;
+      h[2] = 0.0;
+      (&cnt[0][0])[i] = 0u;
+    }
+    __syncthreads();
+    for (int64_t base = (int64_t)warp * kWarp; base < N; base += kSearchThreads) {
+      const int64_t v = base + lane;
+      bool act = false;
+      int bk = -1;
+      int64_t e = 0;
+      if (v < N) {
+        e = v < nx ? xbase + v : ybase + v;
+        const uint64_t k = keys[e];
+        if (k != kNoKey && (pass == 0 || (k >> (shift + 8)) == (pre >> (shift + 8)))) {
+          act = true;
+          bk = (int)((k >> shift) & 255u);
+        }
+      }
+      if (__ballot_sync(kFull, act) == 0u) continue;
+      double vd = 0.0, vg = 0.0, ve = 0.0;
+      if (act) {
+        vd = d2[e];
+        vg = g2[e];
+        ve = gd[e];
+      }
+      const unsigned grp = __match_any_sync(kFull, bk);
+      const bool leader = act && (grp & ((1u << lane) - 1u)) == 0u;
+      if (act) {
+        stage[warp][lane][0] = vd;
+        stage[warp][lane][1] = vg;
+        stage[warp][lane][2] = ve;
+      }
+      __syncwarp();
+      if (leader) {
+        double sd = 0.0, sg = 0.0, se = 0.0;
+        unsigned gm = grp;
+        while (gm) {
+          const int l = __ffs(gm) - 1;
+          gm &= gm - 1u;
+          sd += stage[warp][l][0];
+          sg += stage[warp][l][1];
+          se += stage[warp][l][2];
+        }
+        hist[warp][bk][0] += sd;
+        hist[warp][bk][1] += sg;
+        hist[warp][bk][2] += se;
+        cnt[warp][bk] += (unsigned)__popc(grp);
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    {
+      const int b = tid;
+      double c = 0.0, sd = 0.0, sg = 0.0, se = 0.0;
+      for (int w = 0; w < kSearchWarps; ++w) {
+        c += (double)cnt[w][b];
+        sd += hist[w][b][0];
+        sg += hist[w][b][1];
+        se += hist[w][b][2];
+      }
+      bc[b] = c;
+      bsd[b] = sd;
+      bsg[b] = sg;
+      bse[b] = se;
+      if (b == 0) kstar = -1;
+    }
+    __syncthreads();
+    const int b = tid;
+    const double pd = scan256(bsd[b], wt[0]);
+    const double pe = scan256(bse[b], wt[1]);
+    const double pg = scan256(bsg[kBuckets - 1 - b], wt[2]);  // reversed: suffix sums
+    __syncthreads();
+    {
+      double od = 0.0, oe = 0.0, og = 0.0;
+      for (int w = 0; w < (b >> 5); ++w) {
+        od += wt[0][w];
+        oe += wt[1][w];
+        og += wt[2][w];
+      }
+      cum_d[b + 1] = od + pd;
+      cum_e[b + 1] = oe + pe;
+      tail_g[kBuckets - 1 - b] = og + pg;
+      if (b == 0) {
+        cum_d[0] = 0.0;
+        cum_e[0] = 0.0;
+        tail_g[kBuckets] = 0.0;
+      }
+    }
+    __syncthreads();
+    {
+      const uint64_t edge_bits = L.prefix | ((uint64_t)b << shift);
+      const double edge = __longlong_as_double((long long)edge_bits);
+      bool ok = false;
+      if ((edge_bits >> 63) == 0ull && isfinite(edge)) {  // nonnegative finite edges only
+        const double f = L.f_lo + cum_d[b] + edge * edge * (L.f_hi + tail_g[b]);
+        ok = f <= L.r2;
+      }
+      if (ok) atomicMax(&kstar, b);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const int k = kstar < 0 ? 0 : kstar;
+      L.f_lo += cum_d[k];
+      L.e_lo += cum_e[k];
+      L.f_hi += tail_g[k + 1];
+      L.prefix = L.prefix | ((uint64_t)k << shift);
+      if (bc[k] == 0.0 || pass == kSearchPasses - 1) {
+        if (bc[k] != 0.0) {  // last pass: breakpoints equal to the edge are clamped
+          L.f_lo += bsd[k];
+          L.e_lo += bse[k];
+        }
+        if (L.f_hi > 0.0) {
+          L.lambda = sqrt(fmax(L.r2 - L.f_lo, 0.0) / L.f_hi);
+          L.rho_r = L.e_lo + L.lambda * L.f_hi;
+        } else {
+          L.lambda = INFINITY;
+          L.rho_r = L.e_lo;
+        }
+        L.done = 1;
+      }
+    }
+    __syncthreads();
+    if (L.done) break;
+  }
+  if (tid == 0) B.ls[sidx] = L;
+}
+
+// Restart rule per due problem (Eq. adaptive-restart-scheme, flexible,
+// fixed), counters and iteration limits, the next block's averaging weights
+// w[i][k] = 1 / (t0_i + k + 1), and the running count.
+__global__ void __launch_bounds__(kListThreads) b_decide_kernel(BInst *I, BGlobal *G,
+                                                                double *wtab) {
+  __shared__ int running;
+  if (threadIdx.x == 0) running = 0;
+  __syncthreads();
+  const int count = G->count, Kb = G->Kb, scheme = G->scheme;
+  const double beta = G->beta;
+  int mine = 0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    BInst &B = I[i];
+    B.restart_now = 0;
+    B.use_cur = 0;
+    if (B.status != kRunning) continue;
+    if (B.due) {
+      double rho = NAN, r = B.last_r;
+      int use_cur = 0;
+      if (scheme == kSchemeAdaptive || scheme == kSchemeFlexible) {
+        const LSearch &La = B.ls[0];
+        r = sqrt(La.r2);
+        rho = (La.r2 > 0.0) ? La.rho_r / r : 0.0;
+        if (scheme == kSchemeFlexible) {
+          const LSearch &Lc = B.ls[1];
+          const double rc = sqrt(Lc.r2);
+          const double rho_c = (Lc.r2 > 0.0) ? Lc.rho_r / rc : 0.0;
+          if (rho_c < rho) {
+            use_cur = 1;
+            rho = rho_c;
+            r = rc;
+          }
+        }
+      }
+      const int64_t t = B.t0 + Kb;
+      int restart = 0;
+      if (scheme == kSchemeAdaptive || scheme == kSchemeFlexible)
+        restart = (B.restarts == 0) ? (t >= B.tau0) : (rho <= beta * B.rho_stored);
+      else if (scheme == kSchemeFixed)
+        restart = (t >= B.fixed_len);
+      B.last_rho = rho;
+      B.last_r = r;
+      B.use_cur = use_cur;
+      B.restart_now = restart;
+      if (restart) {
+        B.rho_stored = rho;
+        B.restarts += 1;
+        B.t0 = 0;
+      } else {
+        B.t0 = t;
+      }
+      B.since = 0;
+    } else {
+      B.t0 += Kb;
+    }
+    if (B.iters >= B.iter_cap) {  // the check's restart (if any) still takes place
+      B.status = kStatusIterLimit;
+      continue;
+    }
+    ++mine;
+  }
+  if (mine) atomicAdd(&running, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) G->running = running;
+  for (int64_t e = threadIdx.x; e < (int64_t)count * Kb; e += blockDim.x) {
+    const int i = (int)(e / Kb), k = (int)(e - (int64_t)i * Kb);
+    wtab[e] = 1.0 / (double)(I[i].t0 + k + 1);
+  }
+}
+
+// Restart of Algorithm 1 for the problems whose check decided one (the
+// flags are cleared for every problem at each check).
+__global__ void __launch_bounds__(kBlock) b_restart_copy_kernel(DevVecs v, const BInst *I) {
+  const BInst &B = I[blockIdx.x];
+  const int rs = B.restart_now, uc = B.use_cur;
+  if (!rs && !uc) return;
+  for (int j = B.col0 + threadIdx.x; j < B.col0 + B.ncol; j += blockDim.x) {
+    const double s = uc ? v.x[j] : v.xbar[j];
+    if (rs) {
+      v.x0[j] = s;
+      v.x[j] = s;
+    }
+    v.xbar[j] = s;
+  }
+  for (int i = B.row0 + threadIdx.x; i < B.row0 + B.nrow; i += blockDim.x) {
+    const double s = uc ? v.y[i] : v.ybar[i];
+    if (rs) {
+      v.y0[i] = s;
+      v.y[i] = s;
+    }
+    v.ybar[i] = s;
+  }
+}
+
+// Block-wide exclusive scan of one int per thread (kListThreads threads);
+// returns the exclusive prefix, *total receives the block total.
+__device__ __forceinline__ int block_exscan(int v, int *warp_tot, int *total) {
+  const int lane = threadIdx.x & (kWarp - 1), warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < kWarp; o <<= 1) {
+    const int u = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += u;
+  }
+  if (lane == kWarp - 1) warp_tot[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int t = warp_tot[lane];
+#pragma unroll
+    for (int o = 1; o < kWarp; o <<= 1) {
+      const int u = __shfl_up_sync(kFull, t, o);
+      if (lane >= o) t += u;
+    }
+    warp_tot[lane] = t;  // inclusive over warps
+  }
+  __syncthreads();
+  const int before = (warp == 0 ? 0 : warp_tot[warp - 1]) + x - v;
+  *total = warp_tot[kWarp - 1];
+  __syncthreads();
+  return before;
+}
+
+// Work lists of the next block: slices of the running problems, in order.
+__global__ void __launch_bounds__(kListThreads) b_worklist_kernel(const BInst *I, BGlobal *G,
+                                                                  int32_t *wl_c, int32_t *wl_r) {
+  __shared__ int wt[kWarp];
+  const int count = G->count;
+  int carry_c = 0, carry_r = 0;
+  for (int base = 0; base < count; base += kListThreads) {
+    const int i = base + (int)threadIdx.x;
+    int nc = 0, nr = 0, c0 = 0, r0 = 0;
+    if (i < count && I[i].status == kRunning) {
+      c0 = I[i].cs0;
+      r0 = I[i].rs0;
+      nc = I[i].cs1 - c0;
+      nr = I[i].rs1 - r0;
+    }
+    int tc = 0, tr = 0;
+    const int oc = carry_c + block_exscan(nc, wt, &tc);
+    const int orr = carry_r + block_exscan(nr, wt, &tr);
+    for (int t = 0; t < nc; ++t) wl_c[oc + t] = c0 + t;
+    for (int t = 0; t < nr; ++t) wl_r[orr + t] = r0 + t;
+    carry_c += tc;
+    carry_r += tr;
+  }
+  if (threadIdx.x == 0) {
+    G->wl_n[0] = carry_c;
+    G->wl_n[1] = carry_r;
+  }
+}
+
+// --------------------------------------------------------- setup kernels
+
+__device__ double block_sum_sq(const double *p, int64_t begin, int64_t end, double *red) {
+  double s = 0.0;
+  for (int64_t j = begin + threadIdx.x; j < end; j += blockDim.x) s += p[j] * p[j];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// One power-iteration step per problem (Section 7: sigma_max(A_k)^2 as the
+// Rayleigh quotient of A_k^T A_k), after av = A v and w = A^T av over the
+// whole batch: ray = ||A v||^2 (||v|| = 1), stop when |ray - est| <= tol ray
+// after the first step, or A^T A v = 0, or at the step cap; otherwise
+// v <- w / ||w||.
+__global__ void __launch_bounds__(kBlock) b_power_kernel(BInst *I, BGlobal *G, double *v,
+                                                         const double *av, const double *w) {
+  BInst &B = I[blockIdx.x];
+  if (B.pw_done) return;
+  __shared__ double red[kBlock];
+  __shared__ int stop;
+  const double ray = block_sum_sq(av, B.row0, (int64_t)B.row0 + B.nrow, red);
+  const double nw2 = block_sum_sq(w, B.col0, (int64_t)B.col0 + B.ncol, red);
+  const double nw = sqrt(nw2);
+  if (threadIdx.x == 0) {
+    const int done = (B.pw_iters > 0 && fabs(ray - B.pw_est) <= G->pw_tol * ray);
+    B.pw_est = ray;
+    B.pw_iters += 1;
+    B.pw_nw = nw;
+    stop = (nw == 0.0 || done || B.pw_iters >= G->pw_max) ? 1 : 0;
+    if (stop) B.pw_done = 1;
+    else atomicAdd(&G->pw_running, 1);
+  }
+  __syncthreads();
+  if (stop) return;
+  for (int j = B.col0 + threadIdx.x; j < B.col0 + B.ncol; j += blockDim.x) v[j] = w[j] / nw;
+}
+
+__global__ void __launch_bounds__(kBlock) b_norms_kernel(BInst *I, const double *b,
+                                                         const double *c) {
+  BInst &B = I[blockIdx.x];
+  __shared__ double red[kBlock];
+  const double b2 = block_sum_sq(b, B.row0, (int64_t)B.row0 + B.nrow, red);
+  const double c2 = block_sum_sq(c, B.col0, (int64_t)B.col0 + B.ncol, red);
+  if (threadIdx.x == 0) {
+    B.norm_b = sqrt(b2);
+    B.norm_c = sqrt(c2);
+  }
+}
+
+// Each problem's solution candidate (average or current iterate).
+__global__ void __launch_bounds__(kBlock) b_select_kernel(const BInst *I, const double *cur,
+                                                          const double *avg, double *out,
+                                                          int rows) {
+  const BInst &B = I[blockIdx.x];
+  const int lo = rows ? B.row0 : B.col0, len = rows ? B.nrow : B.ncol;
+  const double *src = B.returned ? cur : avg;
+  for (int j = lo + threadIdx.x; j < lo + len; j += blockDim.x) out[j] = src[j];
+}
+
+// ------------------------------------------------------------- launchers
+
+int blocks_for_slices(int nslices) { return std::max(1, (nslices + kWarpsPerBlock - 1) / kWarpsPerBlock); }
+
+template <int U, bool PIPE>
+void b_primal_launch(int g, cudaStream_t s, const SellMat &AT, const double *y, const PrimalEpi &epi,
+                     const BInst *I, const int32_t *sinst, const int32_t *wl, const BGlobal *G,
+                     const double *wtab, int k) {
+  b_primal_kernel<U, PIPE><<<g, kBlock, 0, s>>>(AT, y, epi, I, sinst, wl, G, wtab, k);
+}
+
+template <int U, bool PIPE>
+void b_dual_launch(int g, cudaStream_t s, const SellMat &A, const double *xhat, const DualEpi &epi,
+                   const BInst *I, const int32_t *sinst, const int32_t *wl, const BGlobal *G,
+                   const double *wtab, int k) {
+  b_dual_kernel<U, PIPE><<<g, kBlock, 0, s>>>(A, xhat, epi, I, sinst, wl, G, wtab, k);
+}
+
+}  // namespace
+}  // namespace lpg
+
+using namespace lpg;
+
+struct lp_batch {
+  int32_t count = 0, m = 0, n = 0;
+  int64_t nnz = 0;
+  lp_options opt{};
+  lp_batch_tuning tune{};
+  int device = 0, nsm = 0;
+  std::vector<void *> allocs;
+  SellMat A{}, AT{};
+  int32_t *sinst_a = nullptr, *sinst_at = nullptr;
+  DevVecs v{};
+  BInst *I = nullptr;
+  BGlobal *G = nullptr;
+  double *wtab = nullptr;
+  double *spart = nullptr;
+  int64_t pstride = 0;
+  SearchArrays sa{};
+  int nsearch = 0;
+  int32_t *wl[2] = {nullptr, nullptr};
+  int32_t *perm_x = nullptr, *perm_y = nullptr;
+  double *tmp = nullptr, *tmp2 = nullptr;
+  std::vector<int32_t> row_start, col_start;
+  std::vector<int32_t> size_class;
+  int32_t class_k[kMaxClasses] = {0};
+  int32_t unroll_cols = -2, unroll_rows = -4;
+  int grid_cols = 1, grid_rows = 1;
+  double tune_ms = 0.0, setup_ms = 0.0;
+  std::vector<double> eta, sigma_max;
+  int64_t blocks = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int32_t *h_running = nullptr;  // pinned [2]
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  bool solved = false;
+
+  ~lp_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (auto &e : ev)
+      if (e) cudaEventDestroy(e);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (h_running) cudaFreeHost(h_running);
+    for (void *p : allocs) cudaFree(p);
+  }
+
+  template <class T>
+  lp_status alloc(T **p, int64_t count_) {
+    void *q = nullptr;
+    const size_t bytes = std::max<size_t>(16, sizeof(T) * (size_t)std::max<int64_t>(count_, 1));
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    allocs.push_back(q);
+    *p = static_cast<T *>(q);
+    return LP_OK;
+  }
+
+  template <class T>
+  lp_status upload(T **p, const std::vector<T> &h) {
+    lp_status s = alloc(p, (int64_t)h.size());
+    if (s != LP_OK) return s;
+    if (!h.empty()) LP_CU(cudaMemcpy(*p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+    return LP_OK;
+  }
+
+  lp_status upload_sell(const HostSell &H, SellMat &M) {
+    SliceInfo *info = nullptr;
+    int32_t *ix = nullptr;
+    double *vv = nullptr;
+    lp_status s;
+    if ((s = upload(&info, H.info)) != LP_OK) return s;
+    if ((s = upload(&ix, H.idx)) != LP_OK) return s;
+    if ((s = upload(&vv, H.val)) != LP_OK) return s;
+    M.nrows = H.nrows;
+    M.ncols = H.ncols;
+    M.nslices = H.nslices;
+    M.n_warp_rows = H.n_warp_rows;
+    M.info = info;
+    M.idx = ix;
+    M.val = vv;
+    M.valf = nullptr;
+    return LP_OK;
+  }
+
+  void launch_primal(int k, cudaStream_t s) {
+    PrimalEpi epi{v.c, v.lbk, v.ubk, v.x, v.xhat, v.xbar, 0.0, 0.0, nullptr};
+    const int g = grid_cols;
+    switch (unroll_cols) {
+      case 2: b_primal_launch<2, false>(g, s, AT, v.y, epi, I, sinst_at, wl[0], G, wtab, k); break;
+      case 4: b_primal_launch<4, false>(g, s, AT, v.y, epi, I, sinst_at, wl[0], G, wtab, k); break;
+      case -4: b_primal_launch<4, true>(g, s, AT, v.y, epi, I, sinst_at, wl[0], G, wtab, k); break;
+      default: b_primal_launch<2, true>(g, s, AT, v.y, epi, I, sinst_at, wl[0], G, wtab, k); break;
+    }
+  }
+
+  void launch_dual(int k, cudaStream_t s) {
+    DualEpi epi{v.b, v.row_type, v.y, v.ybar, 0.0, 0.0, nullptr};
+    const int g = grid_rows;
+    switch (unroll_rows) {
+      case 2: b_dual_launch<2, false>(g, s, A, v.xhat, epi, I, sinst_a, wl[1], G, wtab, k); break;
+      case 4: b_dual_launch<4, false>(g, s, A, v.xhat, epi, I, sinst_a, wl[1], G, wtab, k); break;
+      case -2: b_dual_launch<2, true>(g, s, A, v.xhat, epi, I, sinst_a, wl[1], G, wtab, k); break;
+      default: b_dual_launch<4, true>(g, s, A, v.xhat, epi, I, sinst_a, wl[1], G, wtab, k); break;
+    }
+  }
+
+  void launch_worklist(cudaStream_t s) {
+    b_worklist_kernel<<<1, kListThreads, 0, s>>>(I, G, wl[0], wl[1]);
+  }
+
+  void launch_check(cudaStream_t s) {
+    b_pre_check_kernel<<<(count + kBlock - 1) / kBlock, kBlock, 0, s>>>(I, G);
+    CheckColsEpi ce{};
+    ce.c = v.c; ce.lb = v.lb; ce.ub = v.ub; ce.xbar = v.xbar; ce.x = v.x; ce.x0 = v.x0;
+    ce.ga = GapOut{sa.keys[0], sa.d2[0], sa.g2[0], sa.gd[0]};
+    ce.gc = GapOut{sa.keys[1], sa.d2[1], sa.g2[1], sa.gd[1]};
+    CheckRowsEpi re{};
+    re.b = v.b; re.rt = v.row_type; re.ybar = v.ybar; re.y = v.y; re.y0 = v.y0;
+    re.ga = ce.ga;
+    re.gc = ce.gc;
+    re.off = n;
+    b_check_kernel<CheckColsEpi><<<blocks_for_slices(AT.nslices), kBlock, 0, s>>>(
+        AT, v.ybar, v.y, ce, I, sinst_at, G, spart, pstride, 0);
+    b_check_kernel<CheckRowsEpi><<<blocks_for_slices(A.nslices), kBlock, 0, s>>>(
+        A, v.xbar, v.x, re, I, sinst_a, G, spart, pstride, AT.nslices);
+    b_finalize_kernel<<<count, kBlock, 0, s>>>(I, G, spart, pstride, AT.nslices);
+    if (nsearch > 0)
+      b_search_kernel<<<dim3(count, nsearch), kSearchThreads, kSearchSmem, s>>>(I, n, sa);
+    b_decide_kernel<<<1, kListThreads, 0, s>>>(I, G, wtab);
+    b_restart_copy_kernel<<<count, kBlock, 0, s>>>(v, I);
+    launch_worklist(s);
+  }
+};
+
+namespace {
+
+lp_status batch_build_graph(lp_batch *h) {
+  if (h->exec) return LP_OK;
+  cudaStream_t s = h->cap_stream;
+  LP_CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < h->opt.check_every; ++k) {
+    h->launch_primal(k, s);
+    h->launch_dual(k, s);
+  }
+  h->launch_check(s);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  h->graph = g;
+  LP_CU(cudaGraphInstantiate(&h->exec, g, 0));
+  return LP_OK;
+}
+
+// Resets every problem's Algorithm-1 state to z^{0,0} = proj(0) (status
+// running, counters zero), the averaging weights and the work lists.
+lp_status batch_reset(lp_batch *h, cudaStream_t s) {
+  std::vector<BInst> hi(h->count);
+  LP_CU(cudaMemcpyAsync(hi.data(), h->I, sizeof(BInst) * h->count, cudaMemcpyDeviceToHost, s));
+  LP_CU(cudaStreamSynchronize(s));
+  for (BInst &B : hi) {
+    B.status = kRunning;
+    B.returned = B.restart_now = B.use_cur = B.due = 0;
+    B.t0 = B.iters = B.checks = B.restarts = B.since = 0;
+    B.iter_cap = h->opt.max_iter;
+    B.tau0 = h->opt.tau0 > 0 ? h->opt.tau0 : B.K;
+    B.fixed_len = h->opt.fixed_len;
+    B.rho_stored = B.last_rho = B.last_r = NAN;
+    for (int q = 0; q < 5; ++q) B.kkt_a[q] = B.kkt_c[q] = NAN;
+    B.kkt_a[4] = B.kkt_c[4] = INFINITY;
+    B.ls[0].done = B.ls[1].done = 1;
+  }
+  LP_CU(cudaMemcpyAsync(h->I, hi.data(), sizeof(BInst) * h->count, cudaMemcpyHostToDevice, s));
+  const int Kb = h->opt.check_every;
+  std::vector<double> w((size_t)h->count * Kb);
+  for (int32_t i = 0; i < h->count; ++i)
+    for (int k = 0; k < Kb; ++k) w[(size_t)i * Kb + k] = 1.0 / (double)(k + 1);
+  LP_CU(cudaMemcpyAsync(h->wtab, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice, s));
+  launch_fill(h->v.x, 0.0, h->n, s);
+  launch_fill(h->v.y, 0.0, h->m, s);
+  launch_project(h->v, h->n, h->m, s);
+  h->launch_worklist(s);
+  LP_CU(cudaGetLastError());
+  LP_CU(cudaStreamSynchronize(s));
+  h->blocks = 0;
+  h->solved = false;
+  return LP_OK;
+}
+
+// Status <- running for every problem that has not failed; iteration cap
+// <- iters + max_iter; tol.  Then the work lists.
+lp_status batch_start(lp_batch *h, double tol, cudaStream_t s) {
+  std::vector<BInst> hi(h->count);
+  LP_CU(cudaMemcpyAsync(hi.data(), h->I, sizeof(BInst) * h->count, cudaMemcpyDeviceToHost, s));
+  LP_CU(cudaStreamSynchronize(s));
+  for (BInst &B : hi) {
+    if (B.status == kStatusNumerical) continue;
+    B.status = kRunning;
+    B.iter_cap = B.iters + h->opt.max_iter;
+  }
+  LP_CU(cudaMemcpyAsync(h->I, hi.data(), sizeof(BInst) * h->count, cudaMemcpyHostToDevice, s));
+  LP_CU(cudaMemcpyAsync(&h->G->tol, &tol, sizeof(double), cudaMemcpyHostToDevice, s));
+  h->launch_worklist(s);
+  LP_CU(cudaGetLastError());
+  return LP_OK;
+}
+
+double ms_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+int class_of(int64_t nnz) {
+  int c = 0;
+  int64_t lim = 256;  // 64 * 4
+  while (c < kMaxClasses - 1 && nnz >= lim) {
+    ++c;
+    lim *= 4;
+  }
+  return c;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lp_batch_default_tuning(lp_batch_tuning *t) {
+  if (!t) return;
+  t->autotune = 1;
+  t->max_k_shift = 2;
+  t->check_budget = 0.05;
+}
+
+lp_status lp_batch_create(int32_t count, const int32_t *host_row_start,
+                          const int32_t *host_col_start, int64_t nnz, const int32_t *row_ptr,
+                          const int32_t *col_idx, const double *val, const double *c,
+                          const double *b, const double *lb, const double *ub,
+                          const int8_t *row_type, const lp_options *opt_in,
+                          const lp_batch_tuning *tuning, void *cuda_stream,
+                          lp_batch_handle *out) {
+  err_msg().clear();
+  const auto t_start = std::chrono::steady_clock::now();
+  if (!out) return fail(LP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (count < 1) return fail(LP_ERR_INVALID_ARG, "count must be >= 1");
+  if (!host_row_start || !host_col_start) return fail(LP_ERR_INVALID_ARG, "NULL problem boundaries");
+  std::vector<int32_t> rs(host_row_start, host_row_start + count + 1);
+  std::vector<int32_t> cs(host_col_start, host_col_start + count + 1);
+  if (rs[0] != 0 || cs[0] != 0) return fail(LP_ERR_INVALID_ARG, "problem boundaries must start at 0");
+  for (int32_t k = 0; k < count; ++k) {
+    if (rs[k + 1] < rs[k]) return fail(LP_ERR_INVALID_ARG, "host_row_start must be nondecreasing");
+    if (cs[k + 1] <= cs[k]) return fail(LP_ERR_INVALID_ARG, "every problem needs at least one column");
+  }
+  const int32_t m = rs[count], n = cs[count];
+  if (nnz < 0 || nnz >= (int64_t(1) << 31)) return fail(LP_ERR_INVALID_ARG, "nnz must lie in [0, 2^31)");
+  if (!row_ptr || !c || !lb || !ub || (m > 0 && (!b || !row_type)) ||
+      (nnz > 0 && (!col_idx || !val)))
+    return fail(LP_ERR_INVALID_ARG, "NULL array argument");
+  lp_options opt;
+  if (opt_in) opt = *opt_in;
+  else lp_default_options(&opt);
+  lp_status st = validate_options(opt);
+  if (st != LP_OK) return st;
+  if (opt.precision != LP_PRECISION_FP64)
+    return fail(LP_ERR_INVALID_ARG, "the batched solver runs in FP64 (precision must be LP_PRECISION_FP64)");
+  if (opt.spmv_mode != 0) return fail(LP_ERR_INVALID_ARG, "the batched solver has spmv_mode 0 only");
+  lp_batch_tuning tune{};
+  tune.autotune = 0;
+  tune.max_k_shift = 0;
+  tune.check_budget = 0.05;
+  if (tuning) tune = *tuning;
+  if (tune.max_k_shift < 0 || tune.max_k_shift > 8) return fail(LP_ERR_INVALID_ARG, "max_k_shift must lie in [0, 8]");
+  if (!(tune.check_budget > 0.0)) return fail(LP_ERR_INVALID_ARG, "check_budget must be > 0");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+
+  // ---- copy in and validate
+  std::vector<int32_t> hrp32, hci;
+  std::vector<double> hv, hc, hb, hl, hu;
+  std::vector<int8_t> hrt;
+  LP_CU(cudaStreamSynchronize(s));
+  if (!copy_in(hrp32, row_ptr, (int64_t)m + 1) || !copy_in(hci, col_idx, nnz) ||
+      !copy_in(hv, val, nnz) || !copy_in(hc, c, n) || !copy_in(hb, b, m) || !copy_in(hl, lb, n) ||
+      !copy_in(hu, ub, n) || !copy_in(hrt, row_type, m)) {
+    cudaGetLastError();
+    return fail(LP_ERR_INVALID_ARG, "could not read an input array (bad pointer?)");
+  }
+  if (hrp32[0] != 0) return fail(LP_ERR_INVALID_ARG, "row_ptr[0] must be 0");
+  for (int32_t i = 0; i < m; ++i)
+    if (hrp32[i + 1] < hrp32[i]) return fail(LP_ERR_INVALID_ARG, "row_ptr must be nondecreasing");
+  if (hrp32[m] != nnz) return fail(LP_ERR_INVALID_ARG, "row_ptr[m] must equal nnz");
+  {
+    std::vector<int32_t> mark(n, -1);
+    for (int32_t k = 0; k < count; ++k) {
+      for (int32_t i = rs[k]; i < rs[k + 1]; ++i) {
+        for (int64_t p = hrp32[i]; p < hrp32[i + 1]; ++p) {
+          const int32_t j = hci[p];
+          if (j < cs[k] || j >= cs[k + 1])
+            return fail(LP_ERR_INVALID_ARG, "col_idx outside its problem's columns");
+          if (mark[j] == i) return fail(LP_ERR_INVALID_ARG, "duplicate column in a row");
+          mark[j] = i;
+          if (!std::isfinite(hv[p])) return fail(LP_ERR_INVALID_ARG, "non-finite matrix value");
+        }
+      }
+    }
+  }
+  for (int32_t j = 0; j < n; ++j) {
+    if (!std::isfinite(hc[j])) return fail(LP_ERR_INVALID_ARG, "non-finite objective c");
+    if (std::isnan(hl[j]) || std::isnan(hu[j]) || hl[j] > hu[j] || hl[j] == INFINITY ||
+        hu[j] == -INFINITY)
+      return fail(LP_ERR_INVALID_ARG, "invalid bounds (need lb <= ub, lb < inf, ub > -inf)");
+  }
+  for (int32_t i = 0; i < m; ++i) {
+    if (!std::isfinite(hb[i])) return fail(LP_ERR_INVALID_ARG, "non-finite right-hand side b");
+    if (hrt[i] < LP_ROW_EQ || hrt[i] > LP_ROW_LE) return fail(LP_ERR_INVALID_ARG, "row_type must be 0, 1 or 2");
+  }
+
+  std::unique_ptr<lp_batch> h(new lp_batch());
+  h->count = count;
+  h->m = m;
+  h->n = n;
+  h->nnz = nnz;
+  h->opt = opt;
+  h->tune = tune;
+  h->row_start = rs;
+  h->col_start = cs;
+  LP_CU(cudaGetDevice(&h->device));
+  LP_CU(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device));
+  h->nsearch = (opt.restart_scheme == LP_RESTART_ADAPTIVE) ? 1
+               : (opt.restart_scheme == LP_RESTART_FLEXIBLE) ? 2 : 0;
+  h->unroll_cols = opt.spmv_unroll % 100;
+  h->unroll_rows = opt.spmv_unroll_rows % 100;
+
+  // ---- CSC, per-problem permutations by length, sliced layouts
+  std::vector<int64_t> rp(m + 1), cp(n + 1, 0);
+  for (int32_t i = 0; i <= m; ++i) rp[i] = hrp32[i];
+  for (int64_t p = 0; p < nnz; ++p) cp[hci[p] + 1]++;
+  for (int32_t j = 0; j < n; ++j) cp[j + 1] += cp[j];
+  std::vector<int32_t> ri(nnz);
+  std::vector<double> cv(nnz);
+  {
+    std::vector<int64_t> pos(cp.begin(), cp.end() - 1);
+    for (int32_t i = 0; i < m; ++i)
+      for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+        const int64_t q = pos[hci[p]]++;
+        ri[q] = i;
+        cv[q] = hv[p];
+      }
+  }
+  std::vector<int32_t> perm_y(m), perm_x(n), inv_y(m), inv_x(n);
+  std::iota(perm_y.begin(), perm_y.end(), 0);
+  std::iota(perm_x.begin(), perm_x.end(), 0);
+  for (int32_t k = 0; k < count; ++k) {
+    std::stable_sort(perm_y.begin() + rs[k], perm_y.begin() + rs[k + 1], [&](int32_t a, int32_t bb) {
+      return rp[a + 1] - rp[a] > rp[bb + 1] - rp[bb];
+    });
+    std::stable_sort(perm_x.begin() + cs[k], perm_x.begin() + cs[k + 1], [&](int32_t a, int32_t bb) {
+      return cp[a + 1] - cp[a] > cp[bb + 1] - cp[bb];
+    });
+  }
+  for (int32_t r = 0; r < m; ++r) inv_y[perm_y[r]] = r;
+  for (int32_t r = 0; r < n; ++r) inv_x[perm_x[r]] = r;
+  const std::vector<int32_t> brk_rows(rs.begin() + 1, rs.end() - 1);
+  const std::vector<int32_t> brk_cols(cs.begin() + 1, cs.end() - 1);
+  HostSell HA, HAT;
+  const LanePolicy policy{opt.long_row_threshold, opt.lane_steps, opt.single_lane_max};
+  const int64_t target = (int64_t)opt.lane_auto * h->nsm;
+  const LanePolicy pa = choose_policy(rp, perm_y, policy, target, brk_rows);
+  const LanePolicy pat = choose_policy(cp, perm_x, policy, target, brk_cols);
+  build_sell(m, n, rp, hci, hv, perm_y, inv_x, pa, HA, brk_rows);
+  build_sell(n, m, cp, ri, cv, perm_x, inv_y, pat, HAT, brk_cols);
+
+  // slice -> problem, problem -> slice ranges
+  std::vector<BInst> hi(count);
+  std::vector<int32_t> sa_host(HA.nslices), sat_host(HAT.nslices);
+  {
+    int32_t k = 0;
+    for (int32_t sl = 0; sl < HA.nslices; ++sl) {
+      while (HA.info[sl].row0 >= rs[k + 1]) ++k;
+      sa_host[sl] = k;
+    }
+    k = 0;
+    for (int32_t sl = 0; sl < HAT.nslices; ++sl) {
+      while (HAT.info[sl].row0 >= cs[k + 1]) ++k;
+      sat_host[sl] = k;
+    }
+    for (int32_t q = 0; q < count; ++q) {
+      hi[q].rs0 = hi[q].rs1 = -1;
+      hi[q].cs0 = hi[q].cs1 = -1;
+    }
+    for (int32_t sl = 0; sl < HA.nslices; ++sl) {
+      BInst &B = hi[sa_host[sl]];
+      if (B.rs0 < 0) B.rs0 = sl;
+      B.rs1 = sl + 1;
+    }
+    for (int32_t sl = 0; sl < HAT.nslices; ++sl) {
+      BInst &B = hi[sat_host[sl]];
+      if (B.cs0 < 0) B.cs0 = sl;
+      B.cs1 = sl + 1;
+    }
+    h->size_class.resize(count);
+    for (int32_t q = 0; q < count; ++q) {
+      BInst &B = hi[q];
+      if (B.rs0 < 0) B.rs0 = B.rs1 = 0;
+      if (B.cs0 < 0) B.cs0 = B.cs1 = 0;
+      B.col0 = cs[q];
+      B.ncol = cs[q + 1] - cs[q];
+      B.row0 = rs[q];
+      B.nrow = rs[q + 1] - rs[q];
+      B.K = opt.check_every;
+      B.omega = opt.omega;
+      B.status = kRunning;
+      h->size_class[q] = class_of(rp[rs[q + 1]] - rp[rs[q]]);
+    }
+  }
+
+  // permuted vectors
+  std::vector<double> pc(n), pl(n), pu(n), pb(m);
+  std::vector<int8_t> prt(m);
+  std::vector<long long> lk(n), uk(n);
+  for (int32_t r = 0; r < n; ++r) {
+    pc[r] = hc[perm_x[r]];
+    pl[r] = hl[perm_x[r]];
+    pu[r] = hu[perm_x[r]];
+    long long bl, bu;
+    std::memcpy(&bl, &pl[r], 8);
+    std::memcpy(&bu, &pu[r], 8);
+    lk[r] = bl < 0 ? (bl ^ 0x7fffffffffffffffll) : bl;
+    uk[r] = bu < 0 ? (bu ^ 0x7fffffffffffffffll) : bu;
+  }
+  for (int32_t r = 0; r < m; ++r) {
+    pb[r] = hb[perm_y[r]];
+    prt[r] = hrt[perm_y[r]];
+  }
+
+  // ---- device buffers
+  lp_status e;
+  if ((e = h->upload_sell(HA, h->A)) != LP_OK) return e;
+  if ((e = h->upload_sell(HAT, h->AT)) != LP_OK) return e;
+  if ((e = h->upload(&h->sinst_a, sa_host)) != LP_OK) return e;
+  if ((e = h->upload(&h->sinst_at, sat_host)) != LP_OK) return e;
+  if ((e = h->upload(&h->v.c, pc)) != LP_OK) return e;
+  if ((e = h->upload(&h->v.lb, pl)) != LP_OK) return e;
+  if ((e = h->upload(&h->v.ub, pu)) != LP_OK) return e;
+  if ((e = h->upload(&h->v.lbk, lk)) != LP_OK) return e;
+  if ((e = h->upload(&h->v.ubk, uk)) != LP_OK) return e;
+  if ((e = h->upload(&h->v.b, pb)) != LP_OK) return e;
+  if ((e = h->upload(&h->v.row_type, prt)) != LP_OK) return e;
+  if ((e = h->upload(&h->perm_x, perm_x)) != LP_OK) return e;
+  if ((e = h->upload(&h->perm_y, perm_y)) != LP_OK) return e;
+  double **xs[] = {&h->v.x, &h->v.xhat, &h->v.xbar, &h->v.x0};
+  for (double **p : xs)
+    if ((e = h->alloc(p, n)) != LP_OK) return e;
+  double **ys[] = {&h->v.y, &h->v.ybar, &h->v.y0};
+  for (double **p : ys)
+    if ((e = h->alloc(p, m)) != LP_OK) return e;
+  if ((e = h->alloc(&h->tmp, std::max(n, m))) != LP_OK) return e;
+  if ((e = h->alloc(&h->tmp2, std::max(n, m))) != LP_OK) return e;
+  if ((e = h->alloc(&h->I, count)) != LP_OK) return e;
+  if ((e = h->alloc(&h->G, 1)) != LP_OK) return e;
+  if ((e = h->alloc(&h->wtab, (int64_t)count * opt.check_every)) != LP_OK) return e;
+  h->pstride = (int64_t)HA.nslices + HAT.nslices;
+  if ((e = h->alloc(&h->spart, (int64_t)NQ * h->pstride)) != LP_OK) return e;
+  if ((e = h->alloc(&h->wl[0], HAT.nslices)) != LP_OK) return e;
+  if ((e = h->alloc(&h->wl[1], HA.nslices)) != LP_OK) return e;
+  const int64_t N = (int64_t)n + m;
+  for (int k = 0; k < 2; ++k) {
+    if (k == 1 && h->nsearch < 2) {
+      h->sa.keys[1] = h->sa.keys[0];
+      h->sa.d2[1] = h->sa.d2[0];
+      h->sa.g2[1] = h->sa.g2[0];
+      h->sa.gd[1] = h->sa.gd[0];
+      break;
+    }
+    if ((e = h->alloc(&h->sa.keys[k], N)) != LP_OK) return e;
+    if ((e = h->alloc(&h->sa.d2[k], N)) != LP_OK) return e;
+    if ((e = h->alloc(&h->sa.g2[k], N)) != LP_OK) return e;
+    if ((e = h->alloc(&h->sa.gd[k], N)) != LP_OK) return e;
+  }
+  LP_CU(cudaFuncSetAttribute(b_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSearchSmem));
+  LP_CU(cudaMallocHost(&h->h_running, 2 * sizeof(int32_t)));
+  LP_CU(cudaEventCreateWithFlags(&h->ev[0], cudaEventDisableTiming));
+  LP_CU(cudaEventCreateWithFlags(&h->ev[1], cudaEventDisableTiming));
+  LP_CU(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  h->grid_cols = blocks_for_slices(HAT.nslices);
+  h->grid_rows = blocks_for_slices(HA.nslices);
+
+  BGlobal hg{};
+  hg.tol = 1e-8;
+  hg.beta = opt.beta;
+  hg.pw_tol = opt.power_tol;
+  hg.count = count;
+  hg.Kb = opt.check_every;
+  hg.scheme = opt.restart_scheme;
+  hg.pw_max = opt.power_iters;
+  hg.running = count;
+  LP_CU(cudaMemcpy(h->G, &hg, sizeof(BGlobal), cudaMemcpyHostToDevice));
+  LP_CU(cudaMemcpy(h->I, hi.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice));
+  b_norms_kernel<<<count, kBlock, 0, s>>>(h->I, h->v.b, h->v.c);
+  LP_CU(cudaGetLastError());
+
+  // ---- step sizes (Section 7): eta_k = 0.9 / sigma_max(A_k) per problem
+  h->eta.assign(count, opt.eta);
+  h->sigma_max.assign(count, NAN);
+  if (!(opt.eta > 0.0)) {
+    // start vector per problem: v_j = 0.5 + u_j, u_j from SplitMix64 at the
+    // problem-local original column index j, normalized per problem
+    std::vector<double> v0(n);
+    std::vector<double> nv(count, 0.0);
+    int32_t k = 0;
+    for (int32_t r = 0; r < n; ++r) {
+      while (r >= cs[k + 1]) ++k;
+      const uint64_t j = (uint64_t)(perm_x[r] - cs[k]);
+      uint64_t z = (j + 1) * 0x9E3779B97F4A7C15ull;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      v0[r] = 0.5 + (double)(z >> 11) * 0x1.0p-53;
+      nv[k] += v0[r] * v0[r];
+    }
+    k = 0;
+    for (int32_t r = 0; r < n; ++r) {
+      while (r >= cs[k + 1]) ++k;
+      v0[r] /= std::sqrt(nv[k]);
+    }
+    double *pv = h->v.x, *pav = h->v.y, *pw = h->v.xhat;
+    LP_CU(cudaMemcpy(pv, v0.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    const int chunk = 25;
+    for (int it = 0; it < opt.power_iters; it += chunk) {
+      for (int q = 0; q < chunk; ++q) {
+        LP_CU(cudaMemsetAsync(&h->G->pw_running, 0, sizeof(int32_t), s));
+        launch_spmv(h->A, pv, pav, s, nullptr);
+        launch_spmv(h->AT, pav, pw, s, nullptr);
+        b_power_kernel<<<count, kBlock, 0, s>>>(h->I, h->G, pv, pav, pw);
+      }
+      LP_CU(cudaGetLastError());
+      int32_t left = 0;
+      LP_CU(cudaMemcpyAsync(&left, &h->G->pw_running, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      LP_CU(cudaStreamSynchronize(s));
+      if (left == 0) break;
+    }
+    LP_CU(cudaStreamSynchronize(s));
+    LP_CU(cudaMemcpy(hi.data(), h->I, sizeof(BInst) * count, cudaMemcpyDeviceToHost));
+    for (int32_t q = 0; q < count; ++q) {
+      h->sigma_max[q] = std::sqrt(hi[q].pw_est);
+      if (!(h->sigma_max[q] > 0.0) || !std::isfinite(h->sigma_max[q]))
+        return fail(LP_ERR_NUMERICAL, "sigma_max of problem " + std::to_string(q) +
+                                          " is zero or not finite; pass eta explicitly");
+      h->eta[q] = 0.9 / h->sigma_max[q];
+    }
+  } else {
+    LP_CU(cudaStreamSynchronize(s));
+    LP_CU(cudaMemcpy(hi.data(), h->I, sizeof(BInst) * count, cudaMemcpyDeviceToHost));
+  }
+  for (int32_t q = 0; q < count; ++q) {
+    hi[q].tau = h->eta[q] / opt.omega;
+    hi[q].sigma = h->eta[q] * opt.omega;
+  }
+  LP_CU(cudaMemcpy(h->I, hi.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice));
+  for (int q = 0; q < kMaxClasses; ++q) h->class_k[q] = 0;
+  for (int32_t q = 0; q < count; ++q) h->class_k[h->size_class[q]] = opt.check_every;
+  if ((e = batch_reset(h.get(), s)) != LP_OK) return e;
+  h->setup_ms = ms_since(t_start);
+  *out = h.release();
+  return LP_OK;
+}
+
+lp_status lp_batch_set_check_every(lp_batch_handle h, const int32_t *host_k, void *cuda_stream) {
+  err_msg().clear();
+  if (!h || !host_k) return fail(LP_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const int Kb = h->opt.check_every;
+  for (int32_t q = 0; q < h->count; ++q)
+    if (host_k[q] < Kb || host_k[q] % Kb != 0)
+      return fail(LP_ERR_INVALID_ARG, "check periods must be positive multiples of check_every");
+  std::vector<BInst> hi(h->count);
+  LP_CU(cudaMemcpyAsync(hi.data(), h->I, sizeof(BInst) * h->count, cudaMemcpyDeviceToHost, s));
+  LP_CU(cudaStreamSynchronize(s));
+  for (int32_t q = 0; q < h->count; ++q) hi[q].K = host_k[q];
+  LP_CU(cudaMemcpyAsync(h->I, hi.data(), sizeof(BInst) * h->count, cudaMemcpyHostToDevice, s));
+  for (int q = 0; q < kMaxClasses; ++q) h->class_k[q] = 0;
+  for (int32_t q = 0; q < h->count; ++q)
+    h->class_k[h->size_class[q]] = std::max(h->class_k[h->size_class[q]], host_k[q]);
+  return batch_reset(h, s);
+}
+
+lp_status lp_batch_iterate(lp_batch_handle h, int32_t n_blocks, double tol, void *cuda_stream) {
+  err_msg().clear();
+  if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
+  if (!(tol > 0.0)) return fail(LP_ERR_INVALID_ARG, "tol must be > 0");
+  if (n_blocks < 0) return fail(LP_ERR_INVALID_ARG, "n_blocks must be >= 0");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  lp_status e = batch_build_graph(h);
+  if (e != LP_OK) return e;
+  if ((e = batch_start(h, tol, s)) != LP_OK) return e;
+  for (int32_t i = 0; i < n_blocks; ++i) LP_CU(cudaGraphLaunch(h->exec, s));
+  h->blocks += n_blocks;
+  h->solved = true;
+  return LP_OK;
+}
+
+lp_status lp_batch_solve(lp_batch_handle h, double tol, void *cuda_stream) {
+  err_msg().clear();
+  if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
+  if (!(tol > 0.0)) return fail(LP_ERR_INVALID_ARG, "tol must be > 0");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  lp_status e = batch_build_graph(h);
+  if (e != LP_OK) return e;
+  if ((e = batch_start(h, tol, s)) != LP_OK) return e;
+  const int Kb = h->opt.check_every;
+  // every problem stops within max_iter iterations (+ one block): bound the loop
+  int64_t remaining = h->opt.max_iter / Kb + 2;
+  int32_t running = 1;
+  int inflight = 0, head = 0;  // ring of two (event, running-count slot)
+  while (true) {
+    while (inflight < 2 && remaining > 0) {
+      const int slot = (head + inflight) & 1;
+      LP_CU(cudaGraphLaunch(h->exec, s));
+      LP_CU(cudaMemcpyAsync(&h->h_running[slot], &h->G->running, sizeof(int32_t),
+                            cudaMemcpyDeviceToHost, s));
+      LP_CU(cudaEventRecord(h->ev[slot], s));
+      --remaining;
+      ++h->blocks;
+      ++inflight;
+    }
+    if (inflight == 0) break;
+    LP_CU(cudaEventSynchronize(h->ev[head]));
+    running = h->h_running[head];
+    head ^= 1;
+    --inflight;
+    if (running == 0) break;
+  }
+  LP_CU(cudaStreamSynchronize(s));
+  h->solved = true;
+  std::vector<BInst> hi(h->count);
+  LP_CU(cudaMemcpy(hi.data(), h->I, sizeof(BInst) * h->count, cudaMemcpyDeviceToHost));
+  bool numerical = false, limit = false;
+  for (const BInst &B : hi) {
+    if (B.status == kStatusNumerical) numerical = true;
+    else if (B.status != kStatusOK) limit = true;
+  }
+  if (numerical) return fail(LP_ERR_NUMERICAL, "NaN or Inf in a problem's iterates or residuals");
+  if (limit) return fail(LP_ITER_LIMIT, "iteration limit reached by some problem");
+  return LP_OK;
+}
+
+lp_status lp_batch_get_solution(lp_batch_handle h, double *x, double *y, void *cuda_stream) {
+  err_msg().clear();
+  if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
+  if (!h->solved) return fail(LP_ERR_NOT_SOLVED, "no solve has run on this batch");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (x) {
+    b_select_kernel<<<h->count, kBlock, 0, s>>>(h->I, h->v.x, h->v.xbar, h->tmp2, 0);
+    launch_scatter(h->tmp, h->tmp2, h->perm_x, h->n, s);
+    LP_CU(cudaMemcpyAsync(x, h->tmp, sizeof(double) * h->n, cudaMemcpyDefault, s));
+    LP_CU(cudaStreamSynchronize(s));
+  }
+  if (y && h->m > 0) {
+    b_select_kernel<<<h->count, kBlock, 0, s>>>(h->I, h->v.y, h->v.ybar, h->tmp2, 1);
+    launch_scatter(h->tmp, h->tmp2, h->perm_y, h->m, s);
+    LP_CU(cudaMemcpyAsync(y, h->tmp, sizeof(double) * h->m, cudaMemcpyDefault, s));
+    LP_CU(cudaStreamSynchronize(s));
+  }
+  LP_CU(cudaGetLastError());
+  return LP_OK;
+}
+
+lp_status lp_batch_get_state(lp_batch_handle h, double *x, double *y, double *xbar, double *ybar,
+                             double *x0, double *y0, void *cuda_stream) {
+  err_msg().clear();
+  if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  struct Item { double *dst; const double *src; const int32_t *perm; int32_t len; };
+  const Item items[] = {{x, h->v.x, h->perm_x, h->n},       {y, h->v.y, h->perm_y, h->m},
+                        {xbar, h->v.xbar, h->perm_x, h->n}, {ybar, h->v.ybar, h->perm_y, h->m},
+                        {x0, h->v.x0, h->perm_x, h->n},     {y0, h->v.y0, h->perm_y, h->m}};
+  for (const Item &it : items) {
+    if (!it.dst || it.len == 0) continue;
+    launch_scatter(h->tmp, it.src, it.perm, it.len, s);
+    LP_CU(cudaMemcpyAsync(it.dst, h->tmp, sizeof(double) * it.len, cudaMemcpyDefault, s));
+    LP_CU(cudaStreamSynchronize(s));
+  }
+  LP_CU(cudaGetLastError());
+  return LP_OK;
+}
+
+lp_status lp_batch_get_info(lp_batch_handle h, lp_batch_info *info,
+                            lp_batch_problem_info *probs, int32_t capacity) {
+  err_msg().clear();
+  if (!h || !info) return fail(LP_ERR_INVALID_ARG, "NULL argument");
+  if (probs && capacity < 0) return fail(LP_ERR_INVALID_ARG, "capacity must be >= 0");
+  std::vector<BInst> hi(h->count);
+  BGlobal hg{};
+  LP_CU(cudaMemcpy(hi.data(), h->I, sizeof(BInst) * h->count, cudaMemcpyDeviceToHost));
+  LP_CU(cudaMemcpy(&hg, h->G, sizeof(BGlobal), cudaMemcpyDeviceToHost));
+  std::memset(info, 0, sizeof(*info));
+  info->count = h->count;
+  int32_t running = 0;
+  for (const BInst &B : hi) running += (B.status == kRunning);
+  info->running = h->solved ? running : h->count;
+  info->m = h->m;
+  info->n = h->n;
+  info->nnz = h->nnz;
+  info->blocks = h->blocks;
+  info->k_base = h->opt.check_every;
+  info->spmv_unroll = h->unroll_cols;
+  info->spmv_unroll_rows = h->unroll_rows;
+  int nc = 0;
+  for (int q = 0; q < kMaxClasses; ++q) {
+    info->class_k[q] = h->class_k[q];
+    nc += h->class_k[q] > 0;
+  }
+  info->n_classes = nc;
+  info->tune_ms = h->tune_ms;
+  info->setup_ms = h->setup_ms;
+  if (probs) {
+    const int32_t k = std::min(capacity, h->count);
+    for (int32_t q = 0; q < k; ++q) {
+      const BInst &B = hi[q];
+      lp_batch_problem_info &P = probs[q];
+      std::memset(&P, 0, sizeof(P));
+      P.iters = B.iters;
+      P.restarts = B.restarts;
+      P.checks = B.checks;
+      P.status = (B.status == kRunning) ? (h->solved ? LP_ITER_LIMIT : LP_ERR_NOT_SOLVED) : B.status;
+      P.returned = B.returned;
+      P.check_every = B.K;
+      P.size_class = h->size_class[q];
+      for (int i = 0; i < 5; ++i) {
+        P.kkt_avg[i] = B.kkt_a[i];
+        P.kkt_cur[i] = B.kkt_c[i];
+      }
+      P.eta = h->eta[q];
+      P.sigma_max = h->sigma_max[q];
+      P.tau = B.tau;
+      P.sigma = B.sigma;
+      P.rho_stored = B.rho_stored;
+      P.last_rho = B.last_rho;
+    }
+  }
+  return LP_OK;
+}
+
+void lp_batch_destroy(lp_batch_handle h) { delete h; }
+
+}  // extern "C"

@@ -358,5 +358,50 @@ struct CheckRowsEpi {
   }
 };
 
+// ------------------------------------------------------ check helpers
+
+__device__ __forceinline__ void init_search(LSearch &L, double r, double d2, double gd, double g2inf) {
+  L.r2 = r * r;
+  L.f_lo = 0.0;
+  L.e_lo = 0.0;
+  L.f_hi = g2inf;
+  L.prefix = 0ull;
+  L.lambda = 0.0;
+  L.rho_r = 0.0;
+  L.done = 0;
+  if (r == 0.0) {
+    L.done = 1;  // zero radius: rho := 0 (Section 6.1)
+  } else if (g2inf == 0.0 && d2 <= L.r2) {
+    L.done = 1;  // the full clamp is inside the ball (Algorithm 2, first test)
+    L.lambda = INFINITY;
+    L.rho_r = gd;
+  }
+}
+
+__device__ __forceinline__ void kkt_from(const double *t, int qp, int qd, int qpo, int qdo, double nb, double nc,
+                         double *out) {
+  const double rp = sqrt(t[qp]), rd = sqrt(t[qd]);
+  const double p = t[qpo], d = t[qdo];
+  double rel = fmax(rp / (1.0 + nb), rd / (1.0 + nc));
+  rel = fmax(rel, fabs(p - d) / (1.0 + fabs(p) + fabs(d)));
+  out[0] = rp; out[1] = rd; out[2] = p; out[3] = d; out[4] = rel;
+}
+
+// Fixed-order inclusive scan of 256 values held one per thread of the
+// first 256 threads (8 warps): shuffle scan inside each warp, then the warp
+// totals.  Returns the inclusive prefix for thread b.
+__device__ __forceinline__ double scan256(double v, double *warp_tot) {
+  const int b = threadIdx.x, lane = b & 31, w = b >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double u = __shfl_up_sync(kFull, v, o);
+    if (lane >= o) v += u;
+  }
+  if (lane == 31) warp_tot[w] = v;
+  __syncwarp();
+  return v;
+}
+
+
 }  // namespace
 }  // namespace lpg

@@ -48,10 +48,35 @@ class lp_info(C.Structure):
                 ("nnz_padded", C.c_int64), ("n_long_rows", C.c_int32), ("n_long_cols", C.c_int32)]
 
 
+class lp_batch_tuning(C.Structure):
+    _fields_ = [("autotune", C.c_int32), ("max_k_shift", C.c_int32), ("check_budget", C.c_double)]
+
+
+class lp_batch_problem_info(C.Structure):
+    _fields_ = [("iters", C.c_int64), ("restarts", C.c_int64), ("checks", C.c_int64),
+                ("status", C.c_int32), ("returned", C.c_int32), ("check_every", C.c_int32),
+                ("size_class", C.c_int32), ("kkt_avg", C.c_double * 5),
+                ("kkt_cur", C.c_double * 5), ("eta", C.c_double), ("sigma_max", C.c_double),
+                ("tau", C.c_double), ("sigma", C.c_double), ("rho_stored", C.c_double),
+                ("last_rho", C.c_double)]
+
+
+class lp_batch_info(C.Structure):
+    _fields_ = [("count", C.c_int32), ("running", C.c_int32), ("m", C.c_int32), ("n", C.c_int32),
+                ("nnz", C.c_int64), ("blocks", C.c_int64), ("k_base", C.c_int32),
+                ("spmv_unroll", C.c_int32), ("spmv_unroll_rows", C.c_int32),
+                ("n_classes", C.c_int32), ("class_k", C.c_int32 * 8), ("tune_ms", C.c_double),
+                ("setup_ms", C.c_double)]
+
+
 EXPORTED = ["lp_default_options", "lp_create", "lp_solve", "lp_iterate", "lp_get_solution",
             "lp_get_state", "lp_set_state", "lp_get_info", "lp_get_trace", "lp_normalized_gap",
             "lp_normalized_gap_static", "lp_select_omega", "lp_solve_recorded", "lp_backward",
-            "lp_profile_kernel", "lp_destroy", "lp_last_error"]
+            "lp_profile_kernel", "lp_destroy", "lp_last_error",
+            # include/lp_batch.h
+            "lp_batch_default_tuning", "lp_batch_create", "lp_batch_set_check_every",
+            "lp_batch_solve", "lp_batch_iterate", "lp_batch_get_solution", "lp_batch_get_state",
+            "lp_batch_get_info", "lp_batch_destroy"]
 
 _lib = None
 
@@ -99,10 +124,25 @@ def load(build_if_missing: bool = True):
     lib.lp_destroy.restype = None
     lib.lp_last_error.argtypes = []
     lib.lp_last_error.restype = C.c_char_p
+    lib.lp_batch_default_tuning.argtypes = [C.POINTER(lp_batch_tuning)]
+    lib.lp_batch_default_tuning.restype = None
+    lib.lp_batch_create.argtypes = [I32, P, P, I64, P, P, P, P, P, P, P, P,
+                                    C.POINTER(lp_options), C.POINTER(lp_batch_tuning), P,
+                                    C.POINTER(P)]
+    lib.lp_batch_set_check_every.argtypes = [P, P, P]
+    lib.lp_batch_solve.argtypes = [P, D, P]
+    lib.lp_batch_iterate.argtypes = [P, I32, D, P]
+    lib.lp_batch_get_solution.argtypes = [P, P, P, P]
+    lib.lp_batch_get_state.argtypes = [P, P, P, P, P, P, P, P]
+    lib.lp_batch_get_info.argtypes = [P, C.POINTER(lp_batch_info), P, I32]
+    lib.lp_batch_destroy.argtypes = [P]
+    lib.lp_batch_destroy.restype = None
     for name in ["lp_create", "lp_solve", "lp_iterate", "lp_get_solution", "lp_get_state",
                  "lp_set_state", "lp_get_info", "lp_get_trace", "lp_normalized_gap",
                  "lp_normalized_gap_static", "lp_profile_kernel", "lp_select_omega",
-                 "lp_solve_recorded", "lp_backward"]:
+                 "lp_solve_recorded", "lp_backward", "lp_batch_create",
+                 "lp_batch_set_check_every", "lp_batch_solve", "lp_batch_iterate",
+                 "lp_batch_get_solution", "lp_batch_get_state", "lp_batch_get_info"]:
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -363,3 +403,162 @@ class LP:
 
 def default_beta() -> float:
     return math.exp(-1.0)
+
+
+# ------------------------------------------------------------ batched solver
+
+def lp_batch_default_tuning() -> lp_batch_tuning:
+    t = lp_batch_tuning()
+    load().lp_batch_default_tuning(C.byref(t))
+    return t
+
+
+def lp_batch_create(row_start, col_start, nnz, row_ptr, col_idx, val, c, b, lb, ub, row_type,
+                    opt=None, tuning=None, stream=None):
+    """Returns a batch handle (C void*); see include/lp_batch.h.  row_start and
+    col_start are host arrays of count + 1 problem boundaries."""
+    rs = np.ascontiguousarray(row_start, dtype=np.int32)
+    cs = np.ascontiguousarray(col_start, dtype=np.int32)
+    keep, ptrs = [rs, cs], []
+    for a, dt in [(row_ptr, np.int32), (col_idx, np.int32), (val, np.float64), (c, np.float64),
+                  (b, np.float64), (lb, np.float64), (ub, np.float64), (row_type, np.int8)]:
+        p, k = _ptr(a, dt)
+        ptrs.append(p)
+        keep.append(k)
+    h = C.c_void_p()
+    o = C.byref(opt) if opt is not None else None
+    t = C.byref(tuning) if tuning is not None else None
+    _check(load().lp_batch_create(rs.shape[0] - 1, C.c_void_p(rs.ctypes.data),
+                                  C.c_void_p(cs.ctypes.data), int(nnz), *ptrs, o, t,
+                                  _stream(stream), C.byref(h)))
+    return h
+
+
+def lp_batch_set_check_every(h, ks, stream=None):
+    k = np.ascontiguousarray(ks, dtype=np.int32)
+    return _check(load().lp_batch_set_check_every(h, C.c_void_p(k.ctypes.data), _stream(stream)))
+
+
+def lp_batch_solve(h, tol, stream=None) -> int:
+    return _check(load().lp_batch_solve(h, float(tol), _stream(stream)),
+                  allow=(LP_OK, LP_ITER_LIMIT, LP_ERR_NUMERICAL))
+
+
+def lp_batch_iterate(h, n_blocks, tol, stream=None) -> int:
+    return _check(load().lp_batch_iterate(h, int(n_blocks), float(tol), _stream(stream)))
+
+
+def lp_batch_get_solution(h, x, y, stream=None):
+    return _check(load().lp_batch_get_solution(h, _out_ptr(x), _out_ptr(y), _stream(stream)))
+
+
+def lp_batch_get_state(h, x=None, y=None, xbar=None, ybar=None, x0=None, y0=None, stream=None):
+    return _check(load().lp_batch_get_state(h, *[_out_ptr(a) for a in (x, y, xbar, ybar, x0, y0)],
+                                            _stream(stream)))
+
+
+def lp_batch_get_info(h, count):
+    info = lp_batch_info()
+    probs = (lp_batch_problem_info * max(1, count))()
+    _check(load().lp_batch_get_info(h, C.byref(info), C.cast(probs, C.c_void_p), int(count)))
+    return info, probs
+
+
+def lp_batch_destroy(h):
+    if h is not None and h.value:
+        load().lp_batch_destroy(h)
+
+
+class LPBatch:
+    """Owning wrapper of an lp_batch_handle built from a list of lpgen.LPData-like
+    problems (concatenated into the block-diagonal batch here, on the host)."""
+
+    def __init__(self, problems, stream=None, tuning=None, **options):
+        opt = lp_default_options()
+        for k, v in options.items():
+            if not hasattr(opt, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(opt, k, v)
+        self.stream = stream
+        self.count = len(problems)
+        ms = [int(p.m) for p in problems]
+        ns = [int(p.n) for p in problems]
+        self.row_start = np.concatenate([[0], np.cumsum(ms)]).astype(np.int64)
+        self.col_start = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+        self.m, self.n = int(self.row_start[-1]), int(self.col_start[-1])
+        rp = [np.zeros(1, np.int64)]
+        off = 0
+        for p in problems:
+            rp.append(np.asarray(p.row_ptr[1:], np.int64) + off)
+            off += int(p.row_ptr[-1])
+        row_ptr = np.concatenate(rp)
+        col_idx = np.concatenate([np.asarray(p.col_idx, np.int64) + int(cs)
+                                  for p, cs in zip(problems, self.col_start[:-1])])
+        cat = lambda f, dt: np.concatenate([np.asarray(getattr(p, f), dt) for p in problems])
+        if isinstance(tuning, dict):
+            t = lp_batch_default_tuning()
+            for k, v in tuning.items():
+                setattr(t, k, v)
+            tuning = t
+        self.h = lp_batch_create(self.row_start, self.col_start, int(row_ptr[-1]), row_ptr,
+                                 col_idx, cat("val", np.float64), cat("c", np.float64),
+                                 cat("b", np.float64), cat("lb", np.float64),
+                                 cat("ub", np.float64), cat("row_type", np.int8), opt, tuning,
+                                 stream)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            lp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def solve(self, tol=1e-8):
+        return lp_batch_solve(self.h, tol, self.stream)
+
+    def iterate(self, n_blocks, tol=1e-8):
+        return lp_batch_iterate(self.h, n_blocks, tol, self.stream)
+
+    def set_check_every(self, ks):
+        lp_batch_set_check_every(self.h, ks, self.stream)
+
+    def split(self, vec, rows=False):
+        st = self.row_start if rows else self.col_start
+        return [vec[st[k]:st[k + 1]] for k in range(self.count)]
+
+    def solution(self):
+        x, y = np.empty(self.n), np.empty(self.m)
+        lp_batch_get_solution(self.h, x, y, self.stream)
+        return x, y
+
+    def state(self):
+        arrs = [np.empty(self.n), np.empty(self.m), np.empty(self.n), np.empty(self.m),
+                np.empty(self.n), np.empty(self.m)]
+        lp_batch_get_state(self.h, *arrs, stream=self.stream)
+        return dict(zip(["x", "y", "xbar", "ybar", "x0", "y0"], arrs))
+
+    def info(self):
+        """(batch summary, list of per-problem dicts)."""
+        info, probs = lp_batch_get_info(self.h, self.count)
+        per = []
+        for k in range(self.count):
+            p = probs[k]
+            per.append(dict(iters=p.iters, restarts=p.restarts, checks=p.checks, status=p.status,
+                            returned=p.returned, check_every=p.check_every,
+                            size_class=p.size_class, kkt_avg=tuple(p.kkt_avg),
+                            kkt_cur=tuple(p.kkt_cur), eta=p.eta, sigma_max=p.sigma_max,
+                            tau=p.tau, sigma=p.sigma, rho_stored=p.rho_stored,
+                            last_rho=p.last_rho))
+        summary = {f: getattr(info, f) for f, _ in lp_batch_info._fields_}
+        summary["class_k"] = list(info.class_k)
+        return summary, per

@@ -25,6 +25,8 @@ these seeded instances stand in for them):
 * ``large_mixed``: 70% equality / 30% >= rows, bounds 40% [0,inf),
   40% [0,U(1,10)], 20% free, power-law column degree on 2..200 (exponent
   1.82, mean ~10), uniform rows, N(0,1) values.
+* ``batch_standard_form``: batches of uneven standard-form LPs (m log-uniform,
+  n = 2m, 3-12 rows per column) for the batched solver.
 * ``adversarial``: small LPs with empty rows/columns, one dense row, one
   dense column, LE rows and every bound kind, for edge-case coverage.
 """
@@ -143,6 +145,38 @@ def tiny_standard_form(seed: int = 0, m: int = 200, n: int = 400, per_col: int =
     return LPData(m, n, row_ptr, col_idx, val, c, b,
                   np.zeros(n), np.full(n, np.inf), np.zeros(m, dtype=np.int8),
                   x_star, y_star, name=f"tiny_standard_form(m={m},n={n},seed={seed})")
+
+
+def batch_standard_form(seed: int = 2, count: int = 512, m_lo: int = 50, m_hi: int = 20000,
+                        k_lo: int = 3, k_hi: int = 12) -> list:
+    """A batch of uneven standard-form LPs (Ax = b, x >= 0), each with a planted optimum.
+
+    Problem k has m_k rows with log(m_k) ~ U(log m_lo, log m_hi), n_k = 2 m_k
+    columns, U{k_lo..k_hi} distinct uniform rows per column, N(0,1) values,
+    and the planted pair of ``tiny_standard_form``.  Problem k is drawn from
+    its own stream (seed, k), so a prefix of a batch is the smaller batch.
+    """
+    out = []
+    for k in range(count):
+        rng = np.random.default_rng([seed, k])
+        m = int(round(float(np.exp(rng.uniform(np.log(m_lo), np.log(m_hi))))))
+        n = 2 * m
+        degree = rng.integers(min(k_lo, m), min(k_hi, m) + 1, size=n).astype(np.int64)
+        rows, cols = _distinct_rows_per_column(rng, m, degree)
+        vals = rng.standard_normal(rows.shape[0])
+        x_star = np.zeros(n)
+        pos = rng.permutation(n)[: n // 2]
+        x_star[pos] = rng.random(pos.shape[0])
+        y_star = rng.standard_normal(m)
+        sv = rng.random(n)
+        sv[pos] = 0.0
+        b = _matvec(m, rows, cols, vals, x_star)
+        c = _rmatvec(n, rows, cols, vals, y_star) + sv
+        row_ptr, col_idx, val = _coo_to_csr(m, rows, cols, vals)
+        out.append(LPData(m, n, row_ptr, col_idx, val, c, b, np.zeros(n), np.full(n, np.inf),
+                          np.zeros(m, dtype=np.int8), x_star, y_star,
+                          name=f"batch_standard_form(seed={seed},k={k},m={m})"))
+    return out
 
 
 def power_law_degrees(rng, n: int, kmin: int = 2, kmax: int = 200, exponent: float = 1.82):

@@ -12,9 +12,14 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared_functions():
-    src = open(os.path.join(ROOT, "include", "lp.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:lp_status|void|const char \*)\s*(lp_\w+)\s*\(", src, flags=re.M)
+    names = []
+    for hdr in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not hdr.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", hdr)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:lp_status|void|const char \*)\s*(lp_\w+)\s*\(", src,
+                            flags=re.M)
     return sorted(set(names))
 
 
@@ -28,7 +33,8 @@ def lib():
 def test_header_declares_expected_entry_points():
     names = _declared_functions()
     for required in ["lp_create", "lp_solve", "lp_get_solution", "lp_get_info", "lp_destroy",
-                     "lp_last_error", "lp_default_options"]:
+                     "lp_last_error", "lp_default_options", "lp_batch_create", "lp_batch_solve",
+                     "lp_batch_get_solution", "lp_batch_get_info", "lp_batch_destroy"]:
         assert required in names
 
 
@@ -77,3 +83,30 @@ def test_create_rejects_bad_sizes_and_options_on_host(lib):
     st = lib.lp_create(1, 1, 1, None, None, None, None, None, None, None, None, None, None,
                        C.byref(h))
     assert st == lp.LP_ERR_INVALID_ARG
+
+
+def test_batch_create_rejects_bad_boundaries_on_host(lib):
+    from paper_2105_12715_gb300 import lp
+
+    rp = np.array([0, 1, 2], dtype=np.int32)
+    ci = np.array([0, 1], dtype=np.int32)
+    v = np.array([1.0, 1.0])
+    ones, zeros = np.ones(2), np.zeros(2)
+    rt = np.zeros(2, dtype=np.int8)
+    cases = [([0], [0], "count"),                      # no problems
+             ([1, 2], [0, 1, 2], "start at 0"),         # row boundaries not from 0
+             ([0, 2, 1], [0, 1, 2], "nondecreasing"),   # decreasing row boundaries
+             ([0, 1, 2], [0, 0, 2], "column")]          # a problem without columns
+    for rs, cs, what in cases:
+        rs_a, cs_a = np.array(rs, np.int32), np.array(cs, np.int32)
+        h = C.c_void_p()
+        st = lib.lp_batch_create(max(0, len(rs) - 1), C.c_void_p(rs_a.ctypes.data),
+                                 C.c_void_p(cs_a.ctypes.data), 2, C.c_void_p(rp.ctypes.data),
+                                 C.c_void_p(ci.ctypes.data), C.c_void_p(v.ctypes.data),
+                                 C.c_void_p(ones.ctypes.data), C.c_void_p(ones.ctypes.data),
+                                 C.c_void_p(zeros.ctypes.data), C.c_void_p(ones.ctypes.data),
+                                 C.c_void_p(rt.ctypes.data), None, None, None, C.byref(h))
+        assert st == lp.LP_ERR_INVALID_ARG, what
+        assert what in lp._last_error(), (what, lp._last_error())
+    t = lp.lp_batch_default_tuning()
+    assert t.autotune == 1 and t.max_k_shift == 2 and t.check_budget == pytest.approx(0.05)

@@ -1,0 +1,212 @@
+"""Parity of the batched solver (include/lp_batch.h, through the C ABI)
+against the CPU oracle run on each problem alone.
+
+Every problem of a batch must follow the single-problem iteration exactly:
+same step sizes, same checks every K_k iterations, same restart decisions,
+iterates equal to rounding (1e-9 relative, as for the single-problem
+solver).  Batches mix problem sizes so that problems span one to many
+slices with ragged last slices, and mix row senses and bound kinds.
+"""
+import numpy as np
+import pytest
+
+from paper_2105_12715_gb300 import lpgen
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def lpm():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2105_12715_gb300 import lp
+
+    lp.load()
+    return lp
+
+
+def close(gpu, ref, tol=TOL, what=""):
+    gpu, ref = np.asarray(gpu), np.asarray(ref)
+    assert gpu.shape == ref.shape, what
+    if ref.size == 0:
+        return
+    scale = max(1.0, float(np.abs(ref).max()))
+    err = float(np.abs(gpu - ref).max())
+    assert err <= tol * scale, f"{what}: max abs err {err:.3e} (scale {scale:.3e})"
+
+
+def mixed_batch():
+    """Uneven problems: 1 to ~40 slices per operator, every row sense and
+    bound kind, empty rows and columns, a dense row and column."""
+    return [lpgen.tiny_standard_form(0, m=37, n=61, per_col=3),
+            lpgen.adversarial(7),
+            lpgen.tiny_standard_form(1),
+            lpgen.large_mixed(11, m=301, n=1507),
+            lpgen.tiny_standard_form(2, m=5, n=9, per_col=2),
+            lpgen.tiny_standard_form(3, m=700, n=1300, per_col=6)]
+
+
+def norm_bound(d):
+    """sqrt(||A||_1 ||A||_inf) >= sigma_max(A): a step size valid for every problem."""
+    a = np.abs(d.val)
+    rows = np.add.reduceat(a, d.row_ptr[:-1]) if d.nnz else np.zeros(1)
+    rows[np.diff(d.row_ptr) == 0] = 0.0
+    cols = np.bincount(d.col_idx, weights=a, minlength=d.n)
+    return float(np.sqrt(rows.max() * cols.max()))
+
+
+def common_eta(oracle_mod, probs):
+    return 0.9 / max(oracle_mod.sigma_max(d) for d in probs)
+
+
+def states_of(g, probs):
+    st = g.state()
+    out = []
+    for k, d in enumerate(probs):
+        xs, ys = slice(g.col_start[k], g.col_start[k + 1]), slice(g.row_start[k], g.row_start[k + 1])
+        out.append({key: st[key][xs if key[0] == "x" else ys] for key in st})
+    return out
+
+
+def compare(stk, ref, tol=TOL, what=""):
+    for key in ["x", "y", "xbar", "ybar", "x0", "y0"]:
+        close(stk[key], getattr(ref, key), tol, f"{what} {key}")
+
+
+@pytest.mark.parametrize("K", [50, 16])
+def test_batch_iterates_match_oracle_per_problem(lpm, oracle_mod, K):
+    """The first 100 (K = 50) or 480 (K = 16, 30 checks) iterations."""
+    probs = mixed_batch()
+    iters = 100 if K == 50 else 480
+    eta = common_eta(oracle_mod, probs)
+    with lpm.LPBatch(probs, eta=eta, check_every=K, max_iter=iters) as g:
+        status = g.solve(1e-300)
+        summary, per = g.info()
+        sts = states_of(g, probs)
+    assert status == lpm.LP_ITER_LIMIT
+    assert summary["running"] == 0
+    for k, d in enumerate(probs):
+        ref = oracle_mod.solve(d, eta, tol=1e-300, max_iter=iters, check_every=K)
+        assert per[k]["iters"] == ref.iters == iters
+        assert per[k]["restarts"] == ref.restarts, k
+        assert per[k]["checks"] == iters // K
+        compare(sts[k], ref, TOL if K == 50 else 1e-8, f"problem {k}")
+
+
+def test_batch_per_problem_check_periods(lpm, oracle_mod):
+    """K_k = 16, 32 or 64 within one batch (K_base = 16): each problem checks
+    and restarts on its own schedule."""
+    probs = mixed_batch()
+    ks = [16, 32, 64, 16, 48, 32]
+    eta = common_eta(oracle_mod, probs)
+    with lpm.LPBatch(probs, eta=eta, check_every=16, max_iter=384) as g:
+        g.set_check_every(ks)
+        g.solve(1e-300)
+        summary, per = g.info()
+        sts = states_of(g, probs)
+    for k, d in enumerate(probs):
+        ref = oracle_mod.solve(d, eta, tol=1e-300, max_iter=384, check_every=ks[k])
+        assert per[k]["check_every"] == ks[k]
+        assert per[k]["checks"] == 384 // ks[k]
+        assert per[k]["restarts"] == ref.restarts, k
+        compare(sts[k], ref, 1e-8, f"problem {k}")
+
+
+def test_batch_flexible_and_fixed_schemes(lpm, oracle_mod):
+    probs = mixed_batch()[:4]
+    eta = common_eta(oracle_mod, probs)
+    for scheme, extra in [(3, {}), (1, {"fixed_len": 96}), (0, {})]:
+        with lpm.LPBatch(probs, eta=eta, check_every=32, max_iter=320, restart_scheme=scheme,
+                         **extra) as g:
+            g.solve(1e-300)
+            summary, per = g.info()
+            sts = states_of(g, probs)
+        for k, d in enumerate(probs):
+            ref = oracle_mod.solve(d, eta, tol=1e-300, max_iter=320, check_every=32,
+                                   restart_scheme=scheme, fixed_len=extra.get("fixed_len", 0))
+            assert per[k]["restarts"] == ref.restarts, (scheme, k)
+            compare(sts[k], ref, 1e-8, f"scheme {scheme} problem {k}")
+
+
+def test_batch_sigma_max_per_problem(lpm, oracle_mod):
+    """Power iteration per problem (Section 7) against the oracle's."""
+    probs = mixed_batch()
+    with lpm.LPBatch(probs) as g:
+        summary, per = g.info()
+    for k, d in enumerate(probs):
+        s_ref = oracle_mod.sigma_max(d)
+        assert per[k]["sigma_max"] == pytest.approx(s_ref, rel=1e-8), k
+        assert per[k]["eta"] == pytest.approx(0.9 / s_ref, rel=1e-8)
+        assert per[k]["tau"] == pytest.approx(per[k]["eta"], rel=1e-15)
+
+
+def test_batch_full_solve_to_1e8(lpm, oracle_mod):
+    """Every problem reaches relative KKT <= 1e-8 (checked by the oracle on
+    the returned solution), objective within 1e-7 of the planted optimum,
+    with the oracle's iteration count."""
+    probs = [lpgen.tiny_standard_form(s, m=m, n=2 * m, per_col=5)
+             for s, m in [(0, 200), (5, 60), (6, 350), (7, 120)]]
+    eta = common_eta(oracle_mod, probs)
+    with lpm.LPBatch(probs, eta=eta, check_every=64, max_iter=200000) as g:
+        status = g.solve(1e-8)
+        summary, per = g.info()
+        x, y = g.solution()
+    assert status == lpm.LP_OK
+    xs, ys = g.split(x), g.split(y, rows=True)
+    for k, d in enumerate(probs):
+        assert per[k]["status"] == lpm.LP_OK
+        kk = oracle_mod.kkt(d, xs[k], ys[k])
+        assert kk["rel"] <= 1e-8 * (1 + 1e-6), k
+        assert kk["pobj"] == pytest.approx(d.obj_star, rel=1e-7, abs=1e-7)
+        ref = oracle_mod.solve(d, eta, tol=1e-8, max_iter=200000, check_every=64)
+        assert ref.status == 0
+        assert per[k]["iters"] == ref.iters, k
+        assert per[k]["returned"] == ref.returned
+
+
+def test_batch_problem_without_rows_and_single_problem(lpm, oracle_mod):
+    """Edge cases: a problem with no rows (min c^T x over a box) inside a
+    batch, and a batch of one problem."""
+    n = 7
+    box = lpgen.LPData(0, n, np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0),
+                       np.linspace(-1.0, 1.0, n), np.zeros(0), np.full(n, -2.0), np.full(n, 3.0),
+                       np.zeros(0, np.int8))
+    probs = [lpgen.tiny_standard_form(0, m=37, n=61, per_col=3), box]
+    eta = 0.1
+    with lpm.LPBatch(probs, eta=eta, check_every=16, max_iter=64) as g:
+        g.solve(1e-300)
+        sts = states_of(g, probs)
+    for k, d in enumerate(probs):
+        ref = oracle_mod.solve(d, eta, tol=1e-300, max_iter=64, check_every=16)
+        compare(sts[k], ref, TOL, f"problem {k}")
+    one = [lpgen.adversarial(7)]
+    with lpm.LPBatch(one, eta=eta, check_every=16, max_iter=64) as g:
+        g.solve(1e-300)
+        sts = states_of(g, one)
+    compare(sts[0], oracle_mod.solve(one[0], eta, tol=1e-300, max_iter=64, check_every=16))
+
+
+def test_batch_rejects_cross_problem_columns(lpm):
+    a, b = lpgen.tiny_standard_form(0, m=5, n=9, per_col=2), lpgen.tiny_standard_form(1, m=5, n=9, per_col=2)
+    bad_col = np.concatenate([a.col_idx, b.col_idx])  # problem 1 indexes problem 0's columns
+    rp = np.concatenate([a.row_ptr, b.row_ptr[1:] + a.nnz]).astype(np.int32)
+    cat = lambda f: np.concatenate([getattr(a, f), getattr(b, f)])
+    with pytest.raises(lpm.LPError) as e:
+        lpm.lp_batch_create([0, 5, 10], [0, 9, 18], a.nnz + b.nnz, rp, bad_col, cat("val"),
+                            cat("c"), cat("b"), cat("lb"), cat("ub"), cat("row_type"))
+    assert e.value.status == lpm.LP_ERR_INVALID_ARG
+    assert "outside its problem" in str(e.value)
+
+
+def test_batch_is_bitwise_reproducible(lpm):
+    probs = mixed_batch()
+    outs = []
+    for _ in range(2):
+        with lpm.LPBatch(probs, check_every=32, max_iter=640) as g:
+            g.solve(1e-300)
+            outs.append(g.state())
+    for key in outs[0]:
+        np.testing.assert_array_equal(outs[0][key], outs[1][key])
