@@ -58,6 +58,16 @@ def norm_bound(d):
     return float(np.sqrt(rows.max() * cols.max()))
 
 
+def start(d):
+    """z^{0,0} = proj_{X x Y}(0), the library's starting point."""
+    return np.clip(np.zeros(d.n), d.lb, d.ub), np.zeros(d.m)
+
+
+def osolve(oracle_mod, d, eta, **kw):
+    x0, y0 = start(d)
+    return oracle_mod.solve(d, eta, x_init=x0, y_init=y0, **kw)
+
+
 def common_eta(oracle_mod, probs):
     return 0.9 / max(oracle_mod.sigma_max(d) for d in probs)
 
@@ -89,7 +99,7 @@ def test_batch_iterates_match_oracle_per_problem(lpm, oracle_mod, K):
     assert status == lpm.LP_ITER_LIMIT
     assert summary["running"] == 0
     for k, d in enumerate(probs):
-        ref = oracle_mod.solve(d, eta, tol=1e-300, max_iter=iters, check_every=K)
+        ref = osolve(oracle_mod, d, eta, tol=1e-300, max_iter=iters, check_every=K)
         assert per[k]["iters"] == ref.iters == iters
         assert per[k]["restarts"] == ref.restarts, k
         assert per[k]["checks"] == iters // K
@@ -108,7 +118,7 @@ def test_batch_per_problem_check_periods(lpm, oracle_mod):
         summary, per = g.info()
         sts = states_of(g, probs)
     for k, d in enumerate(probs):
-        ref = oracle_mod.solve(d, eta, tol=1e-300, max_iter=384, check_every=ks[k])
+        ref = osolve(oracle_mod, d, eta, tol=1e-300, max_iter=384, check_every=ks[k])
         assert per[k]["check_every"] == ks[k]
         assert per[k]["checks"] == 384 // ks[k]
         assert per[k]["restarts"] == ref.restarts, k
@@ -125,8 +135,8 @@ def test_batch_flexible_and_fixed_schemes(lpm, oracle_mod):
             summary, per = g.info()
             sts = states_of(g, probs)
         for k, d in enumerate(probs):
-            ref = oracle_mod.solve(d, eta, tol=1e-300, max_iter=320, check_every=32,
-                                   restart_scheme=scheme, fixed_len=extra.get("fixed_len", 0))
+            ref = osolve(oracle_mod, d, eta, tol=1e-300, max_iter=320, check_every=32,
+                         restart_scheme=scheme, fixed_len=extra.get("fixed_len", 0))
             assert per[k]["restarts"] == ref.restarts, (scheme, k)
             compare(sts[k], ref, 1e-8, f"scheme {scheme} problem {k}")
 
@@ -148,9 +158,9 @@ def test_batch_full_solve_to_1e8(lpm, oracle_mod):
     the returned solution), objective within 1e-7 of the planted optimum,
     with the oracle's iteration count."""
     probs = [lpgen.tiny_standard_form(s, m=m, n=2 * m, per_col=5)
-             for s, m in [(0, 200), (5, 60), (6, 350), (7, 120)]]
+             for s, m in [(0, 40), (1, 80), (2, 150), (9, 60), (4, 100)]]
     eta = common_eta(oracle_mod, probs)
-    with lpm.LPBatch(probs, eta=eta, check_every=64, max_iter=200000) as g:
+    with lpm.LPBatch(probs, eta=eta, check_every=64, max_iter=150000) as g:
         status = g.solve(1e-8)
         summary, per = g.info()
         x, y = g.solution()
@@ -161,7 +171,7 @@ def test_batch_full_solve_to_1e8(lpm, oracle_mod):
         kk = oracle_mod.kkt(d, xs[k], ys[k])
         assert kk["rel"] <= 1e-8 * (1 + 1e-6), k
         assert kk["pobj"] == pytest.approx(d.obj_star, rel=1e-7, abs=1e-7)
-        ref = oracle_mod.solve(d, eta, tol=1e-8, max_iter=200000, check_every=64)
+        ref = osolve(oracle_mod, d, eta, tol=1e-8, max_iter=150000, check_every=64)
         assert ref.status == 0
         assert per[k]["iters"] == ref.iters, k
         assert per[k]["returned"] == ref.returned
@@ -180,13 +190,13 @@ def test_batch_problem_without_rows_and_single_problem(lpm, oracle_mod):
         g.solve(1e-300)
         sts = states_of(g, probs)
     for k, d in enumerate(probs):
-        ref = oracle_mod.solve(d, eta, tol=1e-300, max_iter=64, check_every=16)
+        ref = osolve(oracle_mod, d, eta, tol=1e-300, max_iter=64, check_every=16)
         compare(sts[k], ref, TOL, f"problem {k}")
     one = [lpgen.adversarial(7)]
     with lpm.LPBatch(one, eta=eta, check_every=16, max_iter=64) as g:
         g.solve(1e-300)
         sts = states_of(g, one)
-    compare(sts[0], oracle_mod.solve(one[0], eta, tol=1e-300, max_iter=64, check_every=16))
+    compare(sts[0], osolve(oracle_mod, one[0], eta, tol=1e-300, max_iter=64, check_every=16))
 
 
 def test_batch_rejects_cross_problem_columns(lpm):
