@@ -56,6 +56,10 @@ def parse():
     p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--adjoint-lps", type=int, default=4)
     p.add_argument("--ttk-tol", type=float, default=1e-6)
+    p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--batch-count", type=int, default=512)
+    p.add_argument("--batch-cap", type=int, default=100_000)
+    p.add_argument("--batch-loop-sample", type=int, default=16)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--kernel-reps", type=int, default=50)  # >= 1
     return p.parse_args()
@@ -224,6 +228,95 @@ def run_reference(args):
             "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def run_batched(args, lp, stream, barrier):
+    """Batched solver on 512 uneven standard-form LPs (m log-uniform in
+    [50, 20000], n = 2m, 3-12 nonzeros per column): tuned create, aggregate
+    throughput (device-timed blocks of 64 iterations), and time to relative
+    KKT 1e-8 (per-problem cap batch_cap iterations) against solving the same
+    problems one at a time with the plain FP64 path (lp_create + lp_solve on
+    a seeded sample, scaled to the whole batch)."""
+    import torch
+
+    from paper_2105_12715_gb300 import lpgen
+
+    probs = lpgen.batch_standard_form(2, args.batch_count)
+    M = sum(d.m for d in probs)
+    N = sum(d.n for d in probs)
+    Z = sum(d.nnz for d in probs)
+    res = {"workload": f"batch_standard_form seed 2: {len(probs)} LPs, m log-uniform [50,20000], "
+                       f"n=2m, 3-12 nnz/col, x>=0, EQ rows; total m={M} n={N} nnz={Z}",
+           "check_every_base": K_CHECK}
+    barrier()
+    t0 = time.perf_counter()
+    g = lp.LPBatch(probs, stream=stream, check_every=K_CHECK, max_iter=args.batch_cap,
+                   tuning={"autotune": 1})
+    torch.cuda.synchronize()
+    res["create_s"] = time.perf_counter() - t0
+    summary, per = g.info()
+    res["tuner"] = {"spmv_unroll": summary["spmv_unroll"],
+                    "spmv_unroll_rows": summary["spmv_unroll_rows"],
+                    "class_k": summary["class_k"],
+                    "class_iter_ms": [round(v, 4) for v in summary["class_iter_ms"]],
+                    "class_check_ms": [round(v, 4) for v in summary["class_check_ms"]],
+                    "tune_ms": summary["tune_ms"]}
+    g.iterate(2, 1e-300)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nb = 8
+    e0.record(stream)
+    g.iterate(nb, 1e-300)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_block = e0.elapsed_time(e1) / nb
+    pb, db = algorithmic_bytes(M, N, Z)
+    res["iter_us"] = 1000.0 * ms_block / K_CHECK
+    res["problem_iters_per_s"] = len(probs) * K_CHECK / (ms_block / 1000.0)
+    res["achieved_gbs_per_iter"] = (pb + db) / (ms_block / K_CHECK / 1000.0) / 1e9
+    res["bytes_per_iter_algorithmic"] = pb + db
+    g.close()
+    # time to 1e-8 (fresh batch; setup = create incl. power iterations and tuning)
+    barrier()
+    t0 = time.perf_counter()
+    g = lp.LPBatch(probs, stream=stream, check_every=K_CHECK, max_iter=args.batch_cap,
+                   tuning={"autotune": 1})
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    g.solve(1e-8)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    summary, per = g.info()
+    its = np.array([p["iters"] for p in per])
+    conv = np.array([p["status"] == lp.LP_OK for p in per])
+    g.close()
+    res["solve"] = {"tol": 1e-8, "cap_iters": args.batch_cap, "seconds": t_batch,
+                    "seconds_with_setup": t_batch + t_setup,
+                    "converged": int(conv.sum()), "problems": len(probs),
+                    "iters_median": float(np.median(its)), "iters_sum": int(its.sum())}
+    # the plain FP64 path, one problem at a time, on a seeded sample
+    rng = np.random.default_rng(0)
+    idx = rng.choice(len(probs), size=min(args.batch_loop_sample, len(probs)), replace=False)
+    t_loop, same, conv_loop = 0.0, 0, 0
+    for k in idx:
+        barrier()
+        t0 = time.perf_counter()
+        h = lp.LP(probs[k], stream=stream, check_every=K_CHECK, max_iter=args.batch_cap)
+        st = h.solve(1e-8)
+        torch.cuda.synchronize()
+        t_loop += time.perf_counter() - t0
+        conv_loop += int(st == lp.LP_OK)
+        same += int(abs(h.info().iters - int(its[k])) <= K_CHECK)
+        h.close()
+    est = t_loop * len(probs) / len(idx)
+    res["loop_fp64"] = {"sample": len(idx), "sample_seconds": t_loop,
+                        "extrapolated_seconds": est, "converged_in_sample": conv_loop,
+                        "same_iteration_count": same,
+                        "note": "lp_create + lp_solve per problem (setup included); total = "
+                                "sample time x problems / sample size"}
+    res["speedup_vs_loop"] = est / (t_batch + t_setup)  # both with setup
+    return res
 
 
 def run_ours(args):
@@ -401,6 +494,8 @@ def run_ours(args):
                    "backward_ms": 1000 * float(np.median(bw)),
                    "backward_over_forward": float(np.median(bw) / np.median(fw))}
 
+    batched = run_batched(args, lp, stream, barrier) if not args.no_batch else None
+
     out = None
     if rank == 0:
         out = {"metric": "PDHG iterations/s (fp64 restarted PDHG, large mixed LP)", "value": value,
@@ -419,7 +514,7 @@ def run_ours(args):
                             "algorithmic_bytes": primal_b, "avg_launch_ms": primal_ms,
                             "dual_kernel_ms": dual_ms, "dual_algorithmic_bytes": dual_b},
                "clocks": clocks, "e2e": e2e, "mixed": mixed, "time_to_kkt": ttk,
-               "multicommodity": mcf, "adjoint": adjoint,
+               "multicommodity": mcf, "adjoint": adjoint, "batched": batched,
                "solver": {"eta": info0.eta, "sigma_max": info0.sigma_max,
                           "iters_done": info.iters, "restarts": info.restarts,
                           "rel_kkt_avg": info.kkt_avg[4], "rel_kkt_cur": info.kkt_cur[4],

@@ -76,6 +76,8 @@ typedef struct {
   int32_t spmv_unroll, spmv_unroll_rows; /* kernel variants in use (lp_options codes) */
   int32_t n_classes;    /* size classes present */
   int32_t class_k[8];   /* check period chosen per size class (0 = class empty) */
+  double class_iter_ms[8];  /* tuner: one iteration of the class running alone (ms) */
+  double class_check_ms[8]; /* tuner: one check of the class running alone (ms) */
   double tune_ms;       /* time spent by the tuner at create */
   double setup_ms;      /* total time of lp_batch_create */
 } lp_batch_info;

@@ -659,6 +659,7 @@ struct lp_batch {
   int32_t unroll_cols = -2, unroll_rows = -4;
   int grid_cols = 1, grid_rows = 1;
   double tune_ms = 0.0, setup_ms = 0.0;
+  double tune_iter_ms[kMaxClasses] = {0}, tune_check_ms[kMaxClasses] = {0};
   std::vector<double> eta, sigma_max;
   int64_t blocks = 0;
   cudaStream_t cap_stream = nullptr;
@@ -835,6 +836,96 @@ lp_status batch_start(lp_batch *h, double tol, cudaStream_t s) {
   LP_CU(cudaMemcpyAsync(&h->G->tol, &tol, sizeof(double), cudaMemcpyHostToDevice, s));
   h->launch_worklist(s);
   LP_CU(cudaGetLastError());
+  return LP_OK;
+}
+
+// Milliseconds per call of f (enqueued `reps` times on s after one warm-up
+// call), by CUDA events on s.
+template <class F>
+lp_status time_ms(cudaStream_t s, int reps, F f, double *out) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  LP_CU(cudaEventCreate(&e0));
+  LP_CU(cudaEventCreate(&e1));
+  f();
+  cudaEventRecord(e0, s);
+  for (int r = 0; r < reps; ++r) f();
+  cudaEventRecord(e1, s);
+  cudaError_t err = cudaEventSynchronize(e1);
+  float ms = 0.0f;
+  if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return cuda_fail(err, "tuner timing");
+  LP_CU(cudaGetLastError());
+  *out = ms / reps;
+  return LP_OK;
+}
+
+// The batch's tuner (run at create on the batch itself, from z = proj(0)):
+//  (1) kernel variants: for each pass, every unroll code of {2, 4, -2, -4}
+//      with one warp per slice or a grid of 8 blocks per SM (grid-stride
+//      over the work list), timed over 5 launches; the fastest is kept;
+//  (2) check period per size class: with only that class running, the
+//      cost of one iteration (both passes) and of one check (the whole
+//      chain, every problem due) are timed; the class gets the smallest
+//      K = K_base 2^s (s <= max_k_shift) with check <= budget x K x iteration.
+// Leaves the state dirty: the caller resets it.
+lp_status batch_tune(lp_batch *h, cudaStream_t s) {
+  lp_status e;
+  const int cands[4] = {2, 4, -2, -4};
+  const int g_full[2] = {blocks_for_slices(h->AT.nslices), blocks_for_slices(h->A.nslices)};
+  for (int pass = 0; pass < 2; ++pass) {
+    double best = 1e300;
+    int bu = pass ? h->unroll_rows : h->unroll_cols, bg = g_full[pass];
+    for (int u : cands) {
+      for (int gm = 0; gm < 2; ++gm) {
+        const int g = gm ? std::min(g_full[pass], 8 * h->nsm) : g_full[pass];
+        if (gm && g == g_full[pass]) continue;
+        (pass ? h->unroll_rows : h->unroll_cols) = u;
+        (pass ? h->grid_rows : h->grid_cols) = g;
+        double t = 0.0;
+        if (pass == 0) e = time_ms(s, 5, [&] { h->launch_primal(0, s); }, &t);
+        else e = time_ms(s, 5, [&] { h->launch_dual(0, s); }, &t);
+        if (e != LP_OK) return e;
+        if (t < best) {
+          best = t;
+          bu = u;
+          bg = g;
+        }
+      }
+    }
+    (pass ? h->unroll_rows : h->unroll_cols) = bu;
+    (pass ? h->grid_rows : h->grid_cols) = bg;
+  }
+  // check period per size class
+  std::vector<BInst> hi(h->count), run(h->count);
+  LP_CU(cudaMemcpy(hi.data(), h->I, sizeof(BInst) * h->count, cudaMemcpyDeviceToHost));
+  const int Kb = h->opt.check_every;
+  for (int c = 0; c < kMaxClasses; ++c) {
+    bool any = false;
+    for (int32_t q = 0; q < h->count; ++q) any |= (h->size_class[q] == c);
+    if (!any) continue;
+    for (int32_t q = 0; q < h->count; ++q) {
+      run[q] = hi[q];
+      run[q].status = (h->size_class[q] == c) ? kRunning : LP_ERR_NOT_SOLVED;
+      run[q].K = Kb;
+      run[q].since = 0;
+      run[q].iter_cap = INT64_MAX;
+    }
+    LP_CU(cudaMemcpyAsync(h->I, run.data(), sizeof(BInst) * h->count, cudaMemcpyHostToDevice, s));
+    h->launch_worklist(s);
+    double t_it = 0.0, t_ck = 0.0;
+    if ((e = time_ms(s, 4, [&] { h->launch_primal(0, s); h->launch_dual(0, s); }, &t_it)) != LP_OK)
+      return e;
+    if ((e = time_ms(s, 3, [&] { h->launch_check(s); }, &t_ck)) != LP_OK) return e;
+    int sh = 0;
+    while (sh < h->tune.max_k_shift && t_ck > h->tune.check_budget * (double)(Kb << sh) * t_it) ++sh;
+    h->class_k[c] = Kb << sh;
+    h->tune_iter_ms[c] = t_it;
+    h->tune_check_ms[c] = t_ck;
+  }
+  for (int32_t q = 0; q < h->count; ++q) hi[q].K = h->class_k[h->size_class[q]];
+  LP_CU(cudaMemcpy(h->I, hi.data(), sizeof(BInst) * h->count, cudaMemcpyHostToDevice));
   return LP_OK;
 }
 
@@ -1191,6 +1282,12 @@ lp_status lp_batch_create(int32_t count, const int32_t *host_row_start,
   LP_CU(cudaMemcpy(h->I, hi.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice));
   for (int q = 0; q < kMaxClasses; ++q) h->class_k[q] = 0;
   for (int32_t q = 0; q < count; ++q) h->class_k[h->size_class[q]] = opt.check_every;
+  if (tune.autotune) {
+    const auto t_tune = std::chrono::steady_clock::now();
+    if ((e = batch_reset(h.get(), s)) != LP_OK) return e;
+    if ((e = batch_tune(h.get(), s)) != LP_OK) return e;
+    h->tune_ms = ms_since(t_tune);
+  }
   if ((e = batch_reset(h.get(), s)) != LP_OK) return e;
   h->setup_ms = ms_since(t_start);
   *out = h.release();
@@ -1340,6 +1437,8 @@ lp_status lp_batch_get_info(lp_batch_handle h, lp_batch_info *info,
   int nc = 0;
   for (int q = 0; q < kMaxClasses; ++q) {
     info->class_k[q] = h->class_k[q];
+    info->class_iter_ms[q] = h->tune_iter_ms[q];
+    info->class_check_ms[q] = h->tune_check_ms[q];
     nc += h->class_k[q] > 0;
   }
   info->n_classes = nc;

@@ -65,8 +65,9 @@ class lp_batch_info(C.Structure):
     _fields_ = [("count", C.c_int32), ("running", C.c_int32), ("m", C.c_int32), ("n", C.c_int32),
                 ("nnz", C.c_int64), ("blocks", C.c_int64), ("k_base", C.c_int32),
                 ("spmv_unroll", C.c_int32), ("spmv_unroll_rows", C.c_int32),
-                ("n_classes", C.c_int32), ("class_k", C.c_int32 * 8), ("tune_ms", C.c_double),
-                ("setup_ms", C.c_double)]
+                ("n_classes", C.c_int32), ("class_k", C.c_int32 * 8),
+                ("class_iter_ms", C.c_double * 8), ("class_check_ms", C.c_double * 8),
+                ("tune_ms", C.c_double), ("setup_ms", C.c_double)]
 
 
 EXPORTED = ["lp_default_options", "lp_create", "lp_solve", "lp_iterate", "lp_get_solution",
@@ -560,5 +561,6 @@ class LPBatch:
                             tau=p.tau, sigma=p.sigma, rho_stored=p.rho_stored,
                             last_rho=p.last_rho))
         summary = {f: getattr(info, f) for f, _ in lp_batch_info._fields_}
-        summary["class_k"] = list(info.class_k)
+        for f in ("class_k", "class_iter_ms", "class_check_ms"):
+            summary[f] = list(getattr(info, f))
         return summary, per

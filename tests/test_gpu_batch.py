@@ -220,3 +220,28 @@ def test_batch_is_bitwise_reproducible(lpm):
             outs.append(g.state())
     for key in outs[0]:
         np.testing.assert_array_equal(outs[0][key], outs[1][key])
+
+
+def test_batch_tuner_choices_are_valid_and_consistent(lpm):
+    """The tuner's check periods are K_base 2^s (s <= max_k_shift) per size
+    class, and a tuned batch computes what an untuned batch given the same
+    periods computes (the kernel variants only change the launch shape)."""
+    probs = mixed_batch()
+    with lpm.LPBatch(probs, eta=0.05, check_every=16, max_iter=256,
+                     tuning={"autotune": 1, "max_k_shift": 2, "check_budget": 0.05}) as g:
+        summary, per = g.info()
+        assert summary["tune_ms"] > 0
+        ks = [p["check_every"] for p in per]
+        for p in per:
+            assert p["check_every"] in (16, 32, 64)
+            assert summary["class_k"][p["size_class"]] == p["check_every"]
+            assert summary["class_iter_ms"][p["size_class"]] > 0
+        assert summary["spmv_unroll"] in (2, 4, -2, -4)
+        g.solve(1e-300)
+        tuned = g.state()
+    with lpm.LPBatch(probs, eta=0.05, check_every=16, max_iter=256) as g:
+        g.set_check_every(ks)
+        g.solve(1e-300)
+        plain = g.state()
+    for key in tuned:
+        close(tuned[key], plain[key], 1e-12, key)
