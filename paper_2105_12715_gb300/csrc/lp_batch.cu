@@ -40,10 +40,15 @@
 #include "lp_internal.h"
 #include "spmv_core.cuh"
 
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
+
 namespace lpg {
 namespace {
 
 constexpr int kMaxClasses = 8;
+constexpr int kCheckChunk = 8;  // slices per warp and reduction in the check kernels
 constexpr int kStatusIterLimit = 4;
 constexpr int kListThreads = 1024;
 constexpr int kSearchWarps = 8;
@@ -57,6 +62,7 @@ constexpr size_t kSearchSmem = kSearchHistBytes + kSearchCntBytes + sizeof(doubl
 struct BInst {
   int32_t col0, ncol, row0, nrow;  // ranges in the permuted index spaces
   int32_t cs0, cs1, rs0, rs1;      // slice ranges in A^T and A
+  int32_t cc0, cc1, rc0, rc1;      // check-chunk ranges in A^T and A
   int32_t K;                       // check period (multiple of K_base)
   int32_t status;                  // kRunning or a final lp_status
   int32_t returned, restart_now, use_cur, due;
@@ -86,6 +92,7 @@ struct BGlobal {
 struct SearchArrays {
   uint64_t *keys[2];
   double *d2[2], *g2[2], *gd[2];
+  int32_t *cand[2];  // per-warp candidate lists, [n + m + 256 count] each
 };
 
 // ---------------------------------------------------------------- iteration
@@ -142,43 +149,49 @@ __global__ void b_pre_check_kernel(BInst *I, const BGlobal *G) {
   B.due = (B.since >= B.K) ? 1 : 0;
 }
 
-// Check epilogue over the due problems' slices; one partial sum per slice
-// and quantity (warp butterfly, fixed order) at spart[q * pstride + poff + s].
+// Check epilogue over the due problems' slices.  A warp takes a chunk of
+// up to kCheckChunk consecutive slices of one problem (chunk c covers slices
+// [chunk[c], chunk[c + 1]) ), accumulates every quantity in its lanes over
+// the whole chunk, and reduces once (warp butterfly, fixed order) into
+// spart[q * pstride + poff + c]: the FP64 reductions (2 operations per cycle
+// per SM on GB300) are paid per chunk, not per slice.
 template <class Epi>
 __global__ void __launch_bounds__(kBlock) b_check_kernel(SellMat A, const double *__restrict__ v0,
                                                          const double *__restrict__ v1, Epi epi,
                                                          const BInst *__restrict__ I,
                                                          const int32_t *__restrict__ sinst,
-                                                         const BGlobal *G, double *spart,
-                                                         int64_t pstride, int poff) {
+                                                         const int32_t *__restrict__ chunk,
+                                                         int nchunks, const BGlobal *G,
+                                                         double *spart, int64_t pstride, int poff) {
   const int scheme = G->scheme;
   epi.gap_a = (scheme == kSchemeAdaptive || scheme == kSchemeFlexible);
   epi.gap_c = (scheme == kSchemeFlexible);
   const int lane = threadIdx.x & (kWarp - 1);
   const int nwarps = (int)(gridDim.x * blockDim.x) >> 5;
-  for (int s = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); s < A.nslices; s += nwarps) {
-    const int i = sinst[s];
+  for (int c = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); c < nchunks; c += nwarps) {
+    const int s0 = chunk[c], s1 = chunk[c + 1];
+    const int i = sinst[s0];
     if (!I[i].due) continue;
     epi.sw = sqrt(I[i].omega);
     epi.isw = 1.0 / epi.sw;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) epi.q[q] = 0.0;
-    process_item<2, kUnroll2, false>(A, v0, v1, s, lane, epi);
+    for (int sl = s0; sl < s1; ++sl) process_item<2, kUnroll2, false>(A, v0, v1, sl, lane, epi);
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
       double v = epi.q[q];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-      if (lane == 0) spart[(size_t)q * pstride + poff + s] = v;
+      if (lane == 0) spart[(size_t)q * pstride + poff + c] = v;
     }
   }
 }
 
 // One block per problem: the due problem's check sums (warp q sums quantity
-// q over its slices in order), relative KKT, termination, search setup.
+// q over its chunks in order), relative KKT, termination, search setup.
 __global__ void __launch_bounds__(kBlock) b_finalize_kernel(BInst *I, const BGlobal *G,
                                                             const double *__restrict__ spart,
-                                                            int64_t pstride, int ncs) {
+                                                            int64_t pstride, int ncc) {
   BInst &B = I[blockIdx.x];
   if (!B.due) return;
   __shared__ double tot[NQ];
@@ -186,8 +199,8 @@ __global__ void __launch_bounds__(kBlock) b_finalize_kernel(BInst *I, const BGlo
   for (int q = warp; q < NQ; q += kBlock / kWarp) {
     const double *p = spart + (size_t)q * pstride;
     double acc = 0.0;
-    for (int s = B.cs0 + lane; s < B.cs1; s += kWarp) acc += p[s];
-    for (int s = B.rs0 + lane; s < B.rs1; s += kWarp) acc += p[ncs + s];
+    for (int c = B.cc0 + lane; c < B.cc1; c += kWarp) acc += p[c];
+    for (int c = B.rc0 + lane; c < B.rc1; c += kWarp) acc += p[ncc + c];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
     if (lane == 0) tot[q] = acc;
@@ -229,21 +242,76 @@ __global__ void __launch_bounds__(kBlock) b_finalize_kernel(BInst *I, const BGlo
 }
 
 // One block per (due problem, candidate): the multiplier search of
-// Section 6.3 over the problem's breakpoints -- the search of the
-// single-problem solver (8-bit radix passes over the bit patterns of the
+// Section 6.3 over the problem's breakpoints, with the bracket logic of the
+// single-problem solver (radix passes of 8 bits over the bit patterns of the
 // breakpoints, exact f at bucket edges, closed form on the final bracket),
-// with every pass's histogram and bracket selection inside the block.  Warp
-// w owns elements w*32 + 256 t + lane; within a warp, equal buckets are
-// summed by their lowest lane in lane order; warps are combined in order.
-__global__ void __launch_bounds__(kSearchThreads) b_search_kernel(BInst *I, int64_t nx_total,
+// organised for one block:
+//   * a first scan finds the smallest and largest breakpoint key; bits
+//     above their first difference are common to every key, so the passes
+//     start right below them (bracket [P, P + 2^(shift0+8)) with P the
+//     common prefix); if f exceeds r^2 already at P, lambda* lies below
+//     every breakpoint (closed form with all of them above it);
+//   * pass 0 scans every element; afterwards each warp gathers the elements
+//     of the chosen bucket into its own list (global scratch), and later
+//     passes scan only these lists;
+//   * full scans load four rounds of keys (and values) before using them.
+// Warp w owns elements w*32 + 256 t + lane; within a warp, equal buckets are
+// summed by their lowest lane in lane order; warps are combined in order:
+// the result is deterministic.
+constexpr int kScanUnroll = 4;
+constexpr int kMaxCluster = 8;          // blocks per problem in the clustered search
+constexpr int64_t kClusterMinElems = 8192;  // problems with at least n + m elements use it
+
+__device__ __forceinline__ void hist_add(bool act, int bk, double vd, double vg, double ve,
+                                         double (*hist)[kBuckets][3], unsigned (*cnt)[kBuckets],
+                                         double (*stage)[kWarp][3], int warp, int lane) {
+  if (__ballot_sync(kFull, act) == 0u) return;
+  const unsigned grp = __match_any_sync(kFull, act ? bk : -1);
+  const bool leader = act && (grp & ((1u << lane) - 1u)) == 0u;
+  if (act) {
+    stage[warp][lane][0] = vd;
+    stage[warp][lane][1] = vg;
+    stage[warp][lane][2] = ve;
+  }
+  __syncwarp();
+  if (leader) {
+    double sd = 0.0, sg = 0.0, se = 0.0;
+    unsigned gm = grp;
+    while (gm) {
+      const int l = __ffs(gm) - 1;
+      gm &= gm - 1u;
+      sd += stage[warp][l][0];
+      sg += stage[warp][l][1];
+      se += stage[warp][l][2];
+    }
+    hist[warp][bk][0] += sd;
+    hist[warp][bk][1] += sg;
+    hist[warp][bk][2] += se;
+    cnt[warp][bk] += (unsigned)__popc(grp);
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned long long v, int o) {
+  return (unsigned long long)__shfl_xor_sync(kFull, (long long)v, o);
+}
+
+template <int CS>
+__global__ void __launch_bounds__(kSearchThreads) b_search_kernel(BInst *I,
+                                                                  const int32_t *__restrict__ plist,
+                                                                  int64_t nx_total,
                                                                   SearchArrays sa) {
-  BInst &B = I[blockIdx.x];
+  const int pk = plist[blockIdx.x / CS];
+  BInst &B = I[pk];
   const int sidx = blockIdx.y;
   __shared__ LSearch L;
   __shared__ double bc[kBuckets], bsd[kBuckets], bsg[kBuckets], bse[kBuckets];
+  __shared__ double lb[CS > 1 ? 2 : 1][4][kBuckets];  // this block's bucket sums (cluster exchange)
   __shared__ double cum_d[kBuckets + 1], cum_e[kBuckets + 1], tail_g[kBuckets + 1];
   __shared__ double wt[3][8];
   __shared__ int kstar;
+  __shared__ unsigned long long wmin[kSearchWarps], wmax[kSearchWarps];
+  __shared__ int64_t wcnt[kSearchWarps];
   extern __shared__ __align__(16) unsigned char dsm[];
   double(*hist)[kBuckets][3] = reinterpret_cast<double(*)[kBuckets][3]>(dsm);
   unsigned(*cnt)[kBuckets] = reinterpret_cast<unsigned(*)[kBuckets]>(dsm + kSearchHistBytes);
@@ -252,7 +320,10 @@ __global__ void __launch_bounds__(kSearchThreads) b_search_kernel(BInst *I, int6
   const int tid = threadIdx.x;
   if (tid == 0) L = B.ls[sidx];
   __syncthreads();
-  if (!B.due || B.status != kRunning || L.done) return;  // uniform over the block
+  // every block of a cluster reads the same state: the whole cluster leaves together
+  if (!B.due || B.status != kRunning || L.done) return;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = CS > 1 ? (int)cluster.block_rank() : 0;
   const uint64_t *__restrict__ keys = sidx ? sa.keys[1] : sa.keys[0];
   const double *__restrict__ d2 = sidx ? sa.d2[1] : sa.d2[0];
   const double *__restrict__ g2 = sidx ? sa.g2[1] : sa.g2[0];
@@ -260,8 +331,72 @@ __global__ void __launch_bounds__(kSearchThreads) b_search_kernel(BInst *I, int6
   const int64_t nx = B.ncol, N = nx + B.nrow;
   const int64_t xbase = B.col0, ybase = nx_total + B.row0 - nx;
   const int lane = tid & (kWarp - 1), warp = tid >> 5;
-  for (int pass = 0; pass < kSearchPasses; ++pass) {
-    const int shift = 56 - 8 * pass;
+  const int gw = rank * kSearchWarps + warp;              // warp index in the cluster
+  constexpr int64_t kRound = (int64_t)CS * kSearchThreads;  // elements per round of a cluster
+  const int64_t cap = ((N + kRound - 1) / kRound) * kWarp;
+  int32_t *list = (sidx ? sa.cand[1] : sa.cand[0]) + (int64_t)B.col0 + B.row0 +
+                  (int64_t)kMaxCluster * kSearchThreads * pk + gw * cap;
+  auto elem = [&](int64_t v) { return v < nx ? xbase + v : ybase + v; };
+
+  // smallest and largest breakpoint key (over the cluster)
+  {
+    unsigned long long lo = ~0ull, hi = 0ull;
+    for (int64_t base = (int64_t)gw * kWarp; base < N; base += kScanUnroll * kRound) {
+      uint64_t k[kScanUnroll];
+#pragma unroll
+      for (int r = 0; r < kScanUnroll; ++r) {
+        const int64_t v = base + r * kRound + lane;
+        k[r] = v < N ? keys[elem(v)] : kNoKey;
+      }
+#pragma unroll
+      for (int r = 0; r < kScanUnroll; ++r) {
+        if (k[r] != kNoKey) {
+          lo = k[r] < lo ? k[r] : lo;
+          hi = k[r] > hi ? k[r] : hi;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long a = shfl_xor_u64(lo, o), b = shfl_xor_u64(hi, o);
+      lo = a < lo ? a : lo;
+      hi = b > hi ? b : hi;
+    }
+    if (lane == 0) {
+      wmin[warp] = lo;
+      wmax[warp] = hi;
+    }
+  }
+  if (CS > 1) cluster.sync();
+  else __syncthreads();
+  unsigned long long kmin = ~0ull, kmax = 0ull;
+  for (int r = 0; r < CS; ++r) {
+    const unsigned long long *rmin = CS > 1 ? cluster.map_shared_rank(wmin, r) : wmin;
+    const unsigned long long *rmax = CS > 1 ? cluster.map_shared_rank(wmax, r) : wmax;
+    for (int w = 0; w < kSearchWarps; ++w) {
+      kmin = rmin[w] < kmin ? rmin[w] : kmin;
+      kmax = rmax[w] > kmax ? rmax[w] : kmax;
+    }
+  }
+  if (kmin > kmax) {  // no finite breakpoint: every coordinate moves without bound
+    if (tid == 0 && rank == 0) {
+      L.lambda = sqrt(fmax(L.r2 - L.f_lo, 0.0) / L.f_hi);
+      L.rho_r = L.e_lo + L.lambda * L.f_hi;
+      L.done = 1;
+      B.ls[sidx] = L;
+    }
+    if (CS > 1) cluster.sync();  // no block leaves while another may read its memory
+    return;
+  }
+  const int cp = (kmin == kmax) ? 64 : __clzll((long long)(kmin ^ kmax));
+  // bucket bits [shift0, shift0 + 8) hold the first differing bit (63 - cp);
+  // every bit from shift0 + 8 up is common to all keys
+  const int shift0 = (56 - cp) > 0 ? ((56 - cp + 7) / 8) * 8 : 0;
+  if (tid == 0) L.prefix = (shift0 + 8 >= 64) ? 0ull : (kmin & ~((1ull << (shift0 + 8)) - 1ull));
+  if (tid < kSearchWarps) wcnt[tid] = 0;
+  __syncthreads();
+
+  for (int shift = shift0, pass = 0; shift >= 0; shift -= 8, ++pass) {
     const uint64_t pre = L.prefix;
     for (int i = tid; i < kSearchWarps * kBuckets; i += kSearchThreads) {
       double *h = &hist[0][0][0] + 3 * i;
@@ -271,60 +406,76 @@ __global__ void __launch_bounds__(kSearchThreads) b_search_kernel(BInst *I, int6
       (&cnt[0][0])[i] = 0u;
     }
     __syncthreads();
-    for (int64_t base = (int64_t)warp * kWarp; base < N; base += kSearchThreads) {
-      const int64_t v = base + lane;
-      bool act = false;
-      int bk = -1;
-      int64_t e = 0;
-      if (v < N) {
-        e = v < nx ? xbase + v : ybase + v;
-        const uint64_t k = keys[e];
-        if (k != kNoKey && (pass == 0 || (k >> (shift + 8)) == (pre >> (shift + 8)))) {
-          act = true;
-          bk = (int)((k >> shift) & 255u);
+    const bool full_prefix = (shift + 8 >= 64);
+    auto match = [&](uint64_t k) {
+      return k != kNoKey && (full_prefix || (k >> (shift + 8)) == (pre >> (shift + 8)));
+    };
+    if (pass == 0) {
+      for (int64_t base = (int64_t)gw * kWarp; base < N; base += kScanUnroll * kRound) {
+        uint64_t k[kScanUnroll];
+        double a[kScanUnroll], b[kScanUnroll], c[kScanUnroll];
+#pragma unroll
+        for (int r = 0; r < kScanUnroll; ++r) {
+          const int64_t v = base + r * kRound + lane;
+          k[r] = kNoKey;
+          if (v < N) {
+            const int64_t e = elem(v);
+            k[r] = keys[e];
+            a[r] = d2[e];
+            b[r] = g2[e];
+            c[r] = gd[e];
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < kScanUnroll; ++r) {
+          const bool act = match(k[r]);
+          hist_add(act, act ? (int)((k[r] >> shift) & 255u) : -1, act ? a[r] : 0.0,
+                   act ? b[r] : 0.0, act ? c[r] : 0.0, hist, cnt, stage, warp, lane);
         }
       }
-      if (__ballot_sync(kFull, act) == 0u) continue;
-      double vd = 0.0, vg = 0.0, ve = 0.0;
-      if (act) {
-        vd = d2[e];
-        vg = g2[e];
-        ve = gd[e];
-      }
-      const unsigned grp = __match_any_sync(kFull, bk);
-      const bool leader = act && (grp & ((1u << lane) - 1u)) == 0u;
-      if (act) {
-        stage[warp][lane][0] = vd;
-        stage[warp][lane][1] = vg;
-        stage[warp][lane][2] = ve;
-      }
-      __syncwarp();
-      if (leader) {
-        double sd = 0.0, sg = 0.0, se = 0.0;
-        unsigned gm = grp;
-        while (gm) {
-          const int l = __ffs(gm) - 1;
-          gm &= gm - 1u;
-          sd += stage[warp][l][0];
-          sg += stage[warp][l][1];
-          se += stage[warp][l][2];
+    } else {
+      const int64_t nl = wcnt[warp];
+      for (int64_t base = 0; base < nl; base += kWarp) {
+        const int64_t i = base + lane;
+        uint64_t k = kNoKey;
+        int32_t e = 0;
+        if (i < nl) {
+          e = list[i];
+          k = keys[e];
         }
-        hist[warp][bk][0] += sd;
-        hist[warp][bk][1] += sg;
-        hist[warp][bk][2] += se;
-        cnt[warp][bk] += (unsigned)__popc(grp);
+        const bool act = match(k);
+        hist_add(act, act ? (int)((k >> shift) & 255u) : -1, act ? d2[e] : 0.0,
+                 act ? g2[e] : 0.0, act ? gd[e] : 0.0, hist, cnt, stage, warp, lane);
       }
-      __syncwarp();
     }
     __syncthreads();
+    const int b = tid;
     {
-      const int b = tid;
       double c = 0.0, sd = 0.0, sg = 0.0, se = 0.0;
       for (int w = 0; w < kSearchWarps; ++w) {
         c += (double)cnt[w][b];
         sd += hist[w][b][0];
         sg += hist[w][b][1];
         se += hist[w][b][2];
+      }
+      if (CS > 1) {
+        double(*mine)[kBuckets] = lb[pass & 1];
+        mine[0][b] = c;
+        mine[1][b] = sd;
+        mine[2][b] = sg;
+        mine[3][b] = se;
+        // lb is double-buffered by pass parity: a block rewrites this buffer two
+        // passes later, after the next cluster barrier, which every reader of
+        // this pass has reached
+        cluster.sync();
+        c = sd = sg = se = 0.0;
+        for (int r = 0; r < CS; ++r) {  // blocks in rank order: the same sums in every block
+          const double *rem = cluster.map_shared_rank(&lb[pass & 1][0][0], r);
+          c += rem[b];
+          sd += rem[kBuckets + b];
+          sg += rem[2 * kBuckets + b];
+          se += rem[3 * kBuckets + b];
+        }
       }
       bc[b] = c;
       bsd[b] = sd;
@@ -333,7 +484,6 @@ __global__ void __launch_bounds__(kSearchThreads) b_search_kernel(BInst *I, int6
       if (b == 0) kstar = -1;
     }
     __syncthreads();
-    const int b = tid;
     const double pd = scan256(bsd[b], wt[0]);
     const double pe = scan256(bse[b], wt[1]);
     const double pg = scan256(bsg[kBuckets - 1 - b], wt[2]);  // reversed: suffix sums
@@ -356,7 +506,7 @@ __global__ void __launch_bounds__(kSearchThreads) b_search_kernel(BInst *I, int6
     }
     __syncthreads();
     {
-      const uint64_t edge_bits = L.prefix | ((uint64_t)b << shift);
+      const uint64_t edge_bits = pre | ((uint64_t)b << shift);
       const double edge = __longlong_as_double((long long)edge_bits);
       bool ok = false;
       if ((edge_bits >> 63) == 0ull && isfinite(edge)) {  // nonnegative finite edges only
@@ -367,30 +517,69 @@ __global__ void __launch_bounds__(kSearchThreads) b_search_kernel(BInst *I, int6
     }
     __syncthreads();
     if (tid == 0) {
-      const int k = kstar < 0 ? 0 : kstar;
-      L.f_lo += cum_d[k];
-      L.e_lo += cum_e[k];
-      L.f_hi += tail_g[k + 1];
-      L.prefix = L.prefix | ((uint64_t)k << shift);
-      if (bc[k] == 0.0 || pass == kSearchPasses - 1) {
-        if (bc[k] != 0.0) {  // last pass: breakpoints equal to the edge are clamped
-          L.f_lo += bsd[k];
-          L.e_lo += bse[k];
-        }
-        if (L.f_hi > 0.0) {
-          L.lambda = sqrt(fmax(L.r2 - L.f_lo, 0.0) / L.f_hi);
-          L.rho_r = L.e_lo + L.lambda * L.f_hi;
-        } else {
-          L.lambda = INFINITY;
-          L.rho_r = L.e_lo;
-        }
+      if (kstar < 0) {
+        // f > r^2 at the bracket's lower end (only possible in the first pass,
+        // at the common prefix): lambda* lies below every breakpoint
+        L.f_hi += tail_g[0];
+        L.lambda = sqrt(fmax(L.r2 - L.f_lo, 0.0) / L.f_hi);
+        L.rho_r = L.e_lo + L.lambda * L.f_hi;
         L.done = 1;
+      } else {
+        const int k = kstar;
+        L.f_lo += cum_d[k];
+        L.e_lo += cum_e[k];
+        L.f_hi += tail_g[k + 1];
+        L.prefix = pre | ((uint64_t)k << shift);
+        if (bc[k] == 0.0 || shift == 0) {
+          if (bc[k] != 0.0) {  // last pass: breakpoints equal to the edge are clamped
+            L.f_lo += bsd[k];
+            L.e_lo += bse[k];
+          }
+          if (L.f_hi > 0.0) {
+            L.lambda = sqrt(fmax(L.r2 - L.f_lo, 0.0) / L.f_hi);
+            L.rho_r = L.e_lo + L.lambda * L.f_hi;
+          } else {
+            L.lambda = INFINITY;
+            L.rho_r = L.e_lo;
+          }
+          L.done = 1;
+        }
       }
     }
     __syncthreads();
-    if (L.done) break;
+    if (L.done) break;  // the same decision in every block of the cluster
+    if (pass == 0) {
+      // gather the chosen bucket's elements (keys matching the new prefix
+      // down to bit shift) into this warp's list, in scan order
+      const uint64_t np = L.prefix;
+      int64_t n_out = 0;
+      for (int64_t base = (int64_t)gw * kWarp; base < N; base += kScanUnroll * kRound) {
+        uint64_t k[kScanUnroll];
+        int64_t e[kScanUnroll];
+#pragma unroll
+        for (int r = 0; r < kScanUnroll; ++r) {
+          const int64_t v = base + r * kRound + lane;
+          k[r] = kNoKey;
+          e[r] = 0;
+          if (v < N) {
+            e[r] = elem(v);
+            k[r] = keys[e[r]];
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < kScanUnroll; ++r) {
+          const bool keep = k[r] != kNoKey && (k[r] >> shift) == (np >> shift);
+          const unsigned bal = __ballot_sync(kFull, keep);
+          if (keep) list[n_out + __popc(bal & ((1u << lane) - 1u))] = (int32_t)e[r];
+          n_out += __popc(bal);
+        }
+      }
+      if (lane == 0) wcnt[warp] = n_out;
+      __syncthreads();
+    }
   }
-  if (tid == 0) B.ls[sidx] = L;
+  if (tid == 0 && rank == 0) B.ls[sidx] = L;
+  if (CS > 1) cluster.sync();  // no block leaves while another may read its memory
 }
 
 // Restart rule per due problem (Eq. adaptive-restart-scheme, flexible,
@@ -465,25 +654,35 @@ __global__ void __launch_bounds__(kListThreads) b_decide_kernel(BInst *I, BGloba
 
 // Restart of Algorithm 1 for the problems whose check decided one (the
 // flags are cleared for every problem at each check).
+// Grid (chunks, problems): block (x, k) copies elements x*kCopyChunk + ...
+// of problem k.
+constexpr int kCopyChunk = 4096;
 __global__ void __launch_bounds__(kBlock) b_restart_copy_kernel(DevVecs v, const BInst *I) {
-  const BInst &B = I[blockIdx.x];
+  const BInst &B = I[blockIdx.y];
   const int rs = B.restart_now, uc = B.use_cur;
   if (!rs && !uc) return;
-  for (int j = B.col0 + threadIdx.x; j < B.col0 + B.ncol; j += blockDim.x) {
-    const double s = uc ? v.x[j] : v.xbar[j];
-    if (rs) {
-      v.x0[j] = s;
-      v.x[j] = s;
+  const int64_t lo = (int64_t)blockIdx.x * kCopyChunk;
+  const int64_t nx = B.ncol, N = nx + B.nrow;
+  if (lo >= N) return;
+  const int64_t hi = lo + kCopyChunk < N ? lo + kCopyChunk : N;
+  for (int64_t t = lo + threadIdx.x; t < hi; t += blockDim.x) {
+    if (t < nx) {
+      const int64_t j = B.col0 + t;
+      const double s = uc ? v.x[j] : v.xbar[j];
+      if (rs) {
+        v.x0[j] = s;
+        v.x[j] = s;
+      }
+      v.xbar[j] = s;
+    } else {
+      const int64_t i = B.row0 + (t - nx);
+      const double s = uc ? v.y[i] : v.ybar[i];
+      if (rs) {
+        v.y0[i] = s;
+        v.y[i] = s;
+      }
+      v.ybar[i] = s;
     }
-    v.xbar[j] = s;
-  }
-  for (int i = B.row0 + threadIdx.x; i < B.row0 + B.nrow; i += blockDim.x) {
-    const double s = uc ? v.y[i] : v.ybar[i];
-    if (rs) {
-      v.y0[i] = s;
-      v.y[i] = s;
-    }
-    v.ybar[i] = s;
   }
 }
 
@@ -642,6 +841,9 @@ struct lp_batch {
   std::vector<void *> allocs;
   SellMat A{}, AT{};
   int32_t *sinst_a = nullptr, *sinst_at = nullptr;
+  int32_t *chunk_a = nullptr, *chunk_at = nullptr;  // check chunks: first slice, + end
+  int nchunk_a = 0, nchunk_at = 0;
+  int64_t max_elems = 0;  // largest n_k + m_k
   DevVecs v{};
   BInst *I = nullptr;
   BGlobal *G = nullptr;
@@ -653,6 +855,8 @@ struct lp_batch {
   int32_t *wl[2] = {nullptr, nullptr};
   int32_t *perm_x = nullptr, *perm_y = nullptr;
   double *tmp = nullptr, *tmp2 = nullptr;
+  int32_t *plist_big = nullptr, *plist_small = nullptr;  // search: clustered / one block
+  int n_big = 0, n_small = 0;
   std::vector<int32_t> row_start, col_start;
   std::vector<int32_t> size_class;
   int32_t class_k[kMaxClasses] = {0};
@@ -754,15 +958,33 @@ struct lp_batch {
     re.ga = ce.ga;
     re.gc = ce.gc;
     re.off = n;
-    b_check_kernel<CheckColsEpi><<<blocks_for_slices(AT.nslices), kBlock, 0, s>>>(
-        AT, v.ybar, v.y, ce, I, sinst_at, G, spart, pstride, 0);
-    b_check_kernel<CheckRowsEpi><<<blocks_for_slices(A.nslices), kBlock, 0, s>>>(
-        A, v.xbar, v.x, re, I, sinst_a, G, spart, pstride, AT.nslices);
-    b_finalize_kernel<<<count, kBlock, 0, s>>>(I, G, spart, pstride, AT.nslices);
-    if (nsearch > 0)
-      b_search_kernel<<<dim3(count, nsearch), kSearchThreads, kSearchSmem, s>>>(I, n, sa);
+    b_check_kernel<CheckColsEpi><<<blocks_for_slices(nchunk_at), kBlock, 0, s>>>(
+        AT, v.ybar, v.y, ce, I, sinst_at, chunk_at, nchunk_at, G, spart, pstride, 0);
+    b_check_kernel<CheckRowsEpi><<<blocks_for_slices(nchunk_a), kBlock, 0, s>>>(
+        A, v.xbar, v.x, re, I, sinst_a, chunk_a, nchunk_a, G, spart, pstride, nchunk_at);
+    b_finalize_kernel<<<count, kBlock, 0, s>>>(I, G, spart, pstride, nchunk_at);
+    if (nsearch > 0 && n_small > 0)
+      b_search_kernel<1><<<dim3(n_small, nsearch), kSearchThreads, kSearchSmem, s>>>(
+          I, plist_small, n, sa);
+    if (nsearch > 0 && n_big > 0) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      cfg.gridDim = dim3((unsigned)(n_big * kMaxCluster), (unsigned)nsearch);
+      cfg.blockDim = dim3(kSearchThreads);
+      cfg.dynamicSmemBytes = kSearchSmem;
+      cfg.stream = s;
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = kMaxCluster;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      cudaLaunchKernelEx(&cfg, b_search_kernel<kMaxCluster>, I, (const int32_t *)plist_big,
+                         (int64_t)n, sa);
+    }
     b_decide_kernel<<<1, kListThreads, 0, s>>>(I, G, wtab);
-    b_restart_copy_kernel<<<count, kBlock, 0, s>>>(v, I);
+    b_restart_copy_kernel<<<dim3((unsigned)((max_elems + kCopyChunk - 1) / kCopyChunk), count),
+                            kBlock, 0, s>>>(v, I);
     launch_worklist(s);
   }
 };
@@ -975,6 +1197,8 @@ lp_status lp_batch_create(int32_t count, const int32_t *host_row_start,
     if (cs[k + 1] <= cs[k]) return fail(LP_ERR_INVALID_ARG, "every problem needs at least one column");
   }
   const int32_t m = rs[count], n = cs[count];
+  if ((int64_t)m + n + (int64_t)kMaxCluster * kSearchThreads * count >= (int64_t(1) << 31))
+    return fail(LP_ERR_INVALID_ARG, "the batch needs m + n + 2048 count < 2^31");
   if (nnz < 0 || nnz >= (int64_t(1) << 31)) return fail(LP_ERR_INVALID_ARG, "nnz must lie in [0, 2^31)");
   if (!row_ptr || !c || !lb || !ub || (m > 0 && (!b || !row_type)) ||
       (nnz > 0 && (!col_idx || !val)))
@@ -1095,6 +1319,7 @@ lp_status lp_batch_create(int32_t count, const int32_t *host_row_start,
   // slice -> problem, problem -> slice ranges
   std::vector<BInst> hi(count);
   std::vector<int32_t> sa_host(HA.nslices), sat_host(HAT.nslices);
+  std::vector<int32_t> chk_a, chk_at;
   {
     int32_t k = 0;
     for (int32_t sl = 0; sl < HA.nslices; ++sl) {
@@ -1125,6 +1350,13 @@ lp_status lp_batch_create(int32_t count, const int32_t *host_row_start,
       BInst &B = hi[q];
       if (B.rs0 < 0) B.rs0 = B.rs1 = 0;
       if (B.cs0 < 0) B.cs0 = B.cs1 = 0;
+      // check chunks: consecutive runs of at most kCheckChunk slices of this problem
+      B.cc0 = (int32_t)chk_at.size();
+      for (int32_t sl = B.cs0; sl < B.cs1; sl += kCheckChunk) chk_at.push_back(sl);
+      B.cc1 = (int32_t)chk_at.size();
+      B.rc0 = (int32_t)chk_a.size();
+      for (int32_t sl = B.rs0; sl < B.rs1; sl += kCheckChunk) chk_a.push_back(sl);
+      B.rc1 = (int32_t)chk_a.size();
       B.col0 = cs[q];
       B.ncol = cs[q + 1] - cs[q];
       B.row0 = rs[q];
@@ -1133,7 +1365,12 @@ lp_status lp_batch_create(int32_t count, const int32_t *host_row_start,
       B.omega = opt.omega;
       B.status = kRunning;
       h->size_class[q] = class_of(rp[rs[q + 1]] - rp[rs[q]]);
+      h->max_elems = std::max<int64_t>(h->max_elems, (int64_t)B.ncol + B.nrow);
     }
+    chk_at.push_back(HAT.nslices);
+    chk_a.push_back(HA.nslices);
+    h->nchunk_at = (int)chk_at.size() - 1;
+    h->nchunk_a = (int)chk_a.size() - 1;
   }
 
   // permuted vectors
@@ -1161,6 +1398,8 @@ lp_status lp_batch_create(int32_t count, const int32_t *host_row_start,
   if ((e = h->upload_sell(HAT, h->AT)) != LP_OK) return e;
   if ((e = h->upload(&h->sinst_a, sa_host)) != LP_OK) return e;
   if ((e = h->upload(&h->sinst_at, sat_host)) != LP_OK) return e;
+  if ((e = h->upload(&h->chunk_a, chk_a)) != LP_OK) return e;
+  if ((e = h->upload(&h->chunk_at, chk_at)) != LP_OK) return e;
   if ((e = h->upload(&h->v.c, pc)) != LP_OK) return e;
   if ((e = h->upload(&h->v.lb, pl)) != LP_OK) return e;
   if ((e = h->upload(&h->v.ub, pu)) != LP_OK) return e;
@@ -1181,7 +1420,7 @@ lp_status lp_batch_create(int32_t count, const int32_t *host_row_start,
   if ((e = h->alloc(&h->I, count)) != LP_OK) return e;
   if ((e = h->alloc(&h->G, 1)) != LP_OK) return e;
   if ((e = h->alloc(&h->wtab, (int64_t)count * opt.check_every)) != LP_OK) return e;
-  h->pstride = (int64_t)HA.nslices + HAT.nslices;
+  h->pstride = (int64_t)h->nchunk_a + h->nchunk_at;
   if ((e = h->alloc(&h->spart, (int64_t)NQ * h->pstride)) != LP_OK) return e;
   if ((e = h->alloc(&h->wl[0], HAT.nslices)) != LP_OK) return e;
   if ((e = h->alloc(&h->wl[1], HA.nslices)) != LP_OK) return e;
@@ -1192,15 +1431,50 @@ lp_status lp_batch_create(int32_t count, const int32_t *host_row_start,
       h->sa.d2[1] = h->sa.d2[0];
       h->sa.g2[1] = h->sa.g2[0];
       h->sa.gd[1] = h->sa.gd[0];
+      h->sa.cand[1] = h->sa.cand[0];
       break;
     }
+    if ((e = h->alloc(&h->sa.cand[k], N + (int64_t)kMaxCluster * kSearchThreads * count)) != LP_OK)
+      return e;
     if ((e = h->alloc(&h->sa.keys[k], N)) != LP_OK) return e;
     if ((e = h->alloc(&h->sa.d2[k], N)) != LP_OK) return e;
     if ((e = h->alloc(&h->sa.g2[k], N)) != LP_OK) return e;
     if ((e = h->alloc(&h->sa.gd[k], N)) != LP_OK) return e;
   }
-  LP_CU(cudaFuncSetAttribute(b_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  LP_CU(cudaFuncSetAttribute(b_search_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kSearchSmem));
+  LP_CU(cudaFuncSetAttribute(b_search_kernel<kMaxCluster>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSearchSmem));
+  {
+    // problems with many elements search with a cluster of kMaxCluster blocks,
+    // if the device can hold such a cluster (else every problem uses one block)
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3(kMaxCluster);
+    cfg.blockDim = dim3(kSearchThreads);
+    cfg.dynamicSmemBytes = kSearchSmem;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kMaxCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, b_search_kernel<kMaxCluster>, &cfg) !=
+        cudaSuccess)
+      nclusters = 0;
+    cudaGetLastError();
+    std::vector<int32_t> big, small;
+    for (int32_t q = 0; q < count; ++q) {
+      const int64_t ne = (int64_t)hi[q].ncol + hi[q].nrow;
+      if (nclusters > 0 && ne >= kClusterMinElems) big.push_back(q);
+      else small.push_back(q);
+    }
+    h->n_big = (int)big.size();
+    h->n_small = (int)small.size();
+    if ((e = h->upload(&h->plist_big, big)) != LP_OK) return e;
+    if ((e = h->upload(&h->plist_small, small)) != LP_OK) return e;
+  }
   LP_CU(cudaMallocHost(&h->h_running, 2 * sizeof(int32_t)));
   LP_CU(cudaEventCreateWithFlags(&h->ev[0], cudaEventDisableTiming));
   LP_CU(cudaEventCreateWithFlags(&h->ev[1], cudaEventDisableTiming));
