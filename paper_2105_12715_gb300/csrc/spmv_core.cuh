@@ -212,6 +212,27 @@ struct StoreEpi {
   __device__ __forceinline__ void store(int r, double a, double, const Pre &) const { out[r] = a; }
 };
 
+// Sign, magnitude and class tests on a double's bit pattern (integer pipe;
+// GB300 issues 2 FP64 operations per cycle per SM, comparisons and min/max
+// included).  For non-NaN v: pos(v) <=> v > 0, neg(v) <=> v < 0.
+__device__ __forceinline__ long long dbits(double v) { return __double_as_longlong(v); }
+__device__ __forceinline__ bool pos_d(double v) { return dbits(v) > 0; }
+__device__ __forceinline__ bool neg_d(double v) {
+  const long long b = dbits(v);
+  return b < 0 && (b << 1) != 0;
+}
+__device__ __forceinline__ bool nonzero_d(double v) { return (dbits(v) << 1) != 0; }
+__device__ __forceinline__ bool finite_d(double v) {
+  return (dbits(v) & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
+}
+__device__ __forceinline__ double abs_d(double v) {
+  return __longlong_as_double(dbits(v) & 0x7fffffffffffffffll);
+}
+// max(v, +0) for non-NaN v (-0 maps to +0)
+__device__ __forceinline__ double pos_part(double v) { return dbits(v) < 0 ? 0.0 : v; }
+constexpr long long kNegInfBits = (long long)0xfff0000000000000ull;
+constexpr long long kPosInfBits = 0x7ff0000000000000ll;
+
 // One coordinate of the linear trust region of Section 6.3 in the
 // omega-rescaled space: objective component G, distance dist >= 0 to the
 // bound it moves toward (INFINITY if none), scales sd (distance) and sg
@@ -225,17 +246,17 @@ __device__ __forceinline__ void gap_elem(double G, double dist, double sd, doubl
                                          const GapOut &o, double &sum_d2, double &sum_gd,
                                          double &sum_g2inf) {
   uint64_t key = kNoKey;
-  if (G != 0.0) {
-    const double g = fabs(G) * sg;
-    if (isinf(dist)) {
+  if (nonzero_d(G)) {
+    const double g = abs_d(G) * sg;
+    if (!finite_d(dist)) {
       sum_g2inf += g * g;
     } else {
       const double d = dist * sd;
       const double lam = d / g;
-      if (isinf(lam)) {
+      if (!finite_d(lam)) {
         sum_g2inf += g * g;
       } else {
-        key = (uint64_t)__double_as_longlong(lam);
+        key = (uint64_t)dbits(lam);
         const double vd2 = d * d, vg2 = g * g, vgd = d * g;
         sum_d2 += vd2;
         sum_gd += vgd;
@@ -251,6 +272,9 @@ __device__ __forceinline__ void gap_elem(double G, double dist, double sd, doubl
 // Check epilogue over columns (x-space): reduced costs lam = c - A^T y for
 // both candidates, dual residual, dual-objective bound terms, primal
 // objective, and the x-part of the trust region with F_x = lam.
+// Lambda_j (the reduced-cost cone of column j) is R with both bounds, [0,inf)
+// with only l finite, (-inf,0] with only u finite, {0} if free: the
+// projection of lam keeps lam when its sign is allowed and is 0 otherwise.
 struct CheckColsEpi {
   const double *__restrict__ c;
   const double *__restrict__ lb;
@@ -268,42 +292,37 @@ struct CheckColsEpi {
     return {c[j], lb[j], ub[j], xbar[j], x[j], x0[j]};
   }
   __device__ __forceinline__ double init(const Pre &) const { return 0.0; }
+  __device__ __forceinline__ void candidate(int j, double lam, double xv, const Pre &p, bool lf,
+                                            bool uf, int qrd, int qdobj, int qpobj, int qrrx,
+                                            int qd2, int qgd, int qg2inf, bool gap,
+                                            const GapOut &go) {
+    const bool lp = pos_d(lam), ln = neg_d(lam);
+    const bool keep = (lp && lf) || (ln && uf);    // lam inside Lambda_j
+    const double off = keep ? 0.0 : lam;            // lam - proj(lam)
+    q[qrd] += off * off;
+    if (keep) q[qdobj] += (lp ? p.lb : p.ub) * lam;  // l proj(lam)^+ - u proj(lam)^-
+    q[qpobj] += p.c * xv;
+    if (gap) {
+      const double dx = xv - p.x0;
+      q[qrrx] += dx * dx;
+      double dist = INFINITY;
+      if (lp && lf) dist = pos_part(xv - p.lb);
+      if (ln && uf) dist = pos_part(p.ub - xv);
+      gap_elem(lam, dist, sw, isw, j, go, q[qd2], q[qgd], q[qg2inf]);
+    }
+  }
   __device__ __forceinline__ void store(int j, double aty_a, double aty_c, const Pre &p) {
-    const bool lf = p.lb > -INFINITY, uf = p.ub < INFINITY;
-    // Lambda_j: {0} free, [0,inf) only l finite, (-inf,0] only u finite, R both
-    const double lo = uf ? -INFINITY : 0.0;
-    const double hi = lf ? INFINITY : 0.0;
+    const bool lf = dbits(p.lb) != kNegInfBits, uf = dbits(p.ub) != kPosInfBits;
     const double lam_a = p.c - aty_a, lam_c = p.c - aty_c;
     if (lam_out0) {
       lam_out0[j] = lam_a;
       lam_out1[j] = lam_c;
     }
-    const double lt_a = fmin(fmax(lam_a, lo), hi), lt_c = fmin(fmax(lam_c, lo), hi);
-    q[Q_RD2_A] += sq(lam_a - lt_a);
-    q[Q_RD2_C] += sq(lam_c - lt_c);
-    if (lf && lt_a > 0.0) q[Q_DOBJ_A] += p.lb * lt_a;
-    if (uf && lt_a < 0.0) q[Q_DOBJ_A] += p.ub * lt_a;
-    if (lf && lt_c > 0.0) q[Q_DOBJ_C] += p.lb * lt_c;
-    if (uf && lt_c < 0.0) q[Q_DOBJ_C] += p.ub * lt_c;
-    q[Q_POBJ_A] += p.c * p.xb;
-    q[Q_POBJ_C] += p.c * p.x;
-    if (!(isfinite(lam_a) && isfinite(lam_c) && isfinite(p.xb) && isfinite(p.x))) q[Q_BAD] += 1.0;
-    if (gap_a) {
-      const double dx = p.xb - p.x0;
-      q[Q_RRX_A] += dx * dx;
-      double dist = INFINITY;
-      if (lam_a > 0.0 && lf) dist = fmax(p.xb - p.lb, 0.0);
-      if (lam_a < 0.0 && uf) dist = fmax(p.ub - p.xb, 0.0);
-      gap_elem(lam_a, dist, sw, isw, j, ga, q[Q_D2_A], q[Q_GD_A], q[Q_G2INF_A]);
-    }
-    if (gap_c) {
-      const double dx = p.x - p.x0;
-      q[Q_RRX_C] += dx * dx;
-      double dist = INFINITY;
-      if (lam_c > 0.0 && lf) dist = fmax(p.x - p.lb, 0.0);
-      if (lam_c < 0.0 && uf) dist = fmax(p.ub - p.x, 0.0);
-      gap_elem(lam_c, dist, sw, isw, j, gc, q[Q_D2_C], q[Q_GD_C], q[Q_G2INF_C]);
-    }
+    candidate(j, lam_a, p.xb, p, lf, uf, Q_RD2_A, Q_DOBJ_A, Q_POBJ_A, Q_RRX_A, Q_D2_A, Q_GD_A,
+              Q_G2INF_A, gap_a, ga);
+    candidate(j, lam_c, p.x, p, lf, uf, Q_RD2_C, Q_DOBJ_C, Q_POBJ_C, Q_RRX_C, Q_D2_C, Q_GD_C,
+              Q_G2INF_C, gap_c, gc);
+    if (!(finite_d(lam_a) && finite_d(lam_c) && finite_d(p.xb) && finite_d(p.x))) q[Q_BAD] += 1.0;
   }
 };
 
@@ -324,37 +343,32 @@ struct CheckRowsEpi {
   struct Pre { double b, yb, y, y0; int t; };
   __device__ __forceinline__ Pre load(int i) const { return {b[i], ybar[i], y[i], y0[i], (int)rt[i]}; }
   __device__ __forceinline__ double init(const Pre &) const { return 0.0; }
+  __device__ __forceinline__ void candidate(int i, double G, double yv, const Pre &p, int qrp,
+                                            int qdobj, int qrry, int qd2, int qgd, int qg2inf,
+                                            bool gap, const GapOut &go) {
+    const bool gp = pos_d(G), gn = neg_d(G);
+    // residual of A x >= b (GE) counts only G < 0, of A x <= b (LE) only G > 0
+    const double v = (p.t == 1 && !gn) || (p.t == 2 && !gp) ? 0.0 : G;
+    q[qrp] += v * v;
+    q[qdobj] += p.b * yv;
+    if (gap) {
+      const double dy = yv - p.y0;
+      q[qrry] += dy * dy;
+      double dist = INFINITY;
+      if (gp && p.t == 1) dist = pos_part(yv);
+      if (gn && p.t == 2) dist = pos_part(-yv);
+      gap_elem(G, dist, isw, sw, off + i, go, q[qd2], q[qgd], q[qg2inf]);
+    }
+  }
   __device__ __forceinline__ void store(int i, double ax_a, double ax_c, const Pre &p) {
-    double va = ax_a - p.b, vc = ax_c - p.b;
+    const double va = ax_a - p.b, vc = ax_c - p.b;
     if (gy_out0) {
       gy_out0[i] = va;
       gy_out1[i] = vc;
     }
-    if (p.t == 1) { va = fmin(va, 0.0); vc = fmin(vc, 0.0); }
-    if (p.t == 2) { va = fmax(va, 0.0); vc = fmax(vc, 0.0); }
-    q[Q_RP2_A] += va * va;
-    q[Q_RP2_C] += vc * vc;
-    q[Q_DOBJ_A] += p.b * p.yb;
-    q[Q_DOBJ_C] += p.b * p.y;
-    if (!(isfinite(ax_a) && isfinite(ax_c) && isfinite(p.yb) && isfinite(p.y))) q[Q_BAD] += 1.0;
-    if (gap_a) {
-      const double G = ax_a - p.b;
-      const double dy = p.yb - p.y0;
-      q[Q_RRY_A] += dy * dy;
-      double dist = INFINITY;
-      if (G > 0.0 && p.t == 1) dist = fmax(p.yb, 0.0);
-      if (G < 0.0 && p.t == 2) dist = fmax(-p.yb, 0.0);
-      gap_elem(G, dist, isw, sw, off + i, ga, q[Q_D2_A], q[Q_GD_A], q[Q_G2INF_A]);
-    }
-    if (gap_c) {
-      const double G = ax_c - p.b;
-      const double dy = p.y - p.y0;
-      q[Q_RRY_C] += dy * dy;
-      double dist = INFINITY;
-      if (G > 0.0 && p.t == 1) dist = fmax(p.y, 0.0);
-      if (G < 0.0 && p.t == 2) dist = fmax(-p.y, 0.0);
-      gap_elem(G, dist, isw, sw, off + i, gc, q[Q_D2_C], q[Q_GD_C], q[Q_G2INF_C]);
-    }
+    candidate(i, va, p.yb, p, Q_RP2_A, Q_DOBJ_A, Q_RRY_A, Q_D2_A, Q_GD_A, Q_G2INF_A, gap_a, ga);
+    candidate(i, vc, p.y, p, Q_RP2_C, Q_DOBJ_C, Q_RRY_C, Q_D2_C, Q_GD_C, Q_G2INF_C, gap_c, gc);
+    if (!(finite_d(ax_a) && finite_d(ax_c) && finite_d(p.yb) && finite_d(p.y))) q[Q_BAD] += 1.0;
   }
 };
 
