@@ -316,6 +316,37 @@ def run_batched(args, lp, stream, barrier):
                         "note": "lp_create + lp_solve per problem (setup included); total = "
                                 "sample time x problems / sample size"}
     res["speedup_vs_loop"] = est / (t_batch + t_setup)  # both with setup
+    # the FP32-mixed batch: same problems, same timing
+    barrier()
+    t0 = time.perf_counter()
+    g = lp.LPBatch(probs, stream=stream, check_every=K_CHECK, max_iter=args.batch_cap,
+                   tuning={"autotune": 1}, precision=lp.LP_PRECISION_MIXED)
+    torch.cuda.synchronize()
+    t_setup_m = time.perf_counter() - t0
+    g.iterate(2, 1e-300)
+    barrier()
+    e0.record(stream)
+    g.iterate(nb, 1e-300)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_block_m = e0.elapsed_time(e1) / nb
+    g.close()
+    g = lp.LPBatch(probs, stream=stream, check_every=K_CHECK, max_iter=args.batch_cap,
+                   tuning={"autotune": 1}, precision=lp.LP_PRECISION_MIXED)
+    barrier()
+    t0 = time.perf_counter()
+    g.solve(1e-8)
+    torch.cuda.synchronize()
+    t_mixed = time.perf_counter() - t0
+    summary, per = g.info()
+    its_m = np.array([p["iters"] for p in per])
+    conv_m = np.array([p["status"] == lp.LP_OK for p in per])
+    g.close()
+    res["mixed"] = {"iter_us": 1000.0 * ms_block_m / K_CHECK,
+                    "problem_iters_per_s": len(probs) * K_CHECK / (ms_block_m / 1000.0),
+                    "solve_seconds": t_mixed, "solve_seconds_with_setup": t_mixed + t_setup_m,
+                    "converged": int(conv_m.sum()), "iters_median": float(np.median(its_m)),
+                    "converged_both": int((conv & conv_m).sum())}
     return res
 
 

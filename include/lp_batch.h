@@ -87,8 +87,11 @@ void lp_batch_default_tuning(lp_batch_tuning *t);
 
 /*
  * Creates a batch.  count >= 1; the arrays are described in the header
- * comment (nnz < 2^31 for the whole batch).  opt applies to every problem
- * (NULL = lp_default_options); tuning may be NULL (no tuning).  The
+ * comment (nnz < 2^31, m + n + 2048 count < 2^31 for the whole batch).
+ * opt applies to every problem (NULL = lp_default_options), including
+ * opt->precision (LP_PRECISION_MIXED: the mixed-precision iteration of
+ * lp.h with a correction scale per problem); spmv_mode must be 0.  tuning
+ * may be NULL (no tuning).  The
  * starting point of every problem is zero projected onto X x Y.  Returns
  * LP_ERR_INVALID_ARG on any violation (message in lp_last_error),
  * LP_ERR_OOM, LP_ERR_CUDA, LP_ERR_NUMERICAL (sigma_max of a problem is 0

@@ -77,6 +77,7 @@ struct BInst {
   double rho_stored, last_rho, last_r;
   double kkt_a[5], kkt_c[5];
   double pw_est, pw_nw;
+  double mix_s;                    // mixed precision: scale of the current correction
   LSearch ls[2];
 };
 
@@ -87,6 +88,7 @@ struct BGlobal {
   int32_t running;     // problems still iterating after the last check
   int32_t pw_running;  // problems still in the power iteration after the last step
   int32_t wl_n[2];     // work-list lengths: [0] column slices, [1] row slices
+  int32_t mixed;       // 1: mixed-precision iterations
 };
 
 struct SearchArrays {
@@ -133,6 +135,50 @@ __global__ void __launch_bounds__(kBlock) b_dual_kernel(SellMat A, const double 
     epi.sigma = I[i].sigma;
     epi.w = wtab[(size_t)i * Kb + k];
     process_item<1, U, PIPE>(A, xhat, (const double *)nullptr, s, lane, epi);
+  }
+}
+
+// Mixed precision: the FP32 step on each problem's scaled correction (the
+// single-problem mixed kernels' epilogues), per-slice step and weight.
+template <int U, bool PIPE>
+__global__ void __launch_bounds__(kBlock) b_primal_mix_kernel(SellMat AT, const float *__restrict__ dy,
+                                                              PrimalMixEpi epi,
+                                                              const BInst *__restrict__ I,
+                                                              const int32_t *__restrict__ sinst,
+                                                              const int32_t *__restrict__ wl,
+                                                              const BGlobal *G,
+                                                              const double *__restrict__ wtab,
+                                                              int k) {
+  const int nwl = G->wl_n[0], Kb = G->Kb;
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int nwarps = (int)(gridDim.x * blockDim.x) >> 5;
+  for (int it = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); it < nwl; it += nwarps) {
+    const int s = wl[it];
+    const int i = sinst[s];
+    epi.tau = (float)I[i].tau;
+    epi.w = wtab[(size_t)i * Kb + k];
+    process_item<1, U, PIPE>(AT, dy, (const float *)nullptr, s, lane, epi);
+  }
+}
+
+template <int U, bool PIPE>
+__global__ void __launch_bounds__(kBlock) b_dual_mix_kernel(SellMat A, const float *__restrict__ dxhat,
+                                                            DualMixEpi epi,
+                                                            const BInst *__restrict__ I,
+                                                            const int32_t *__restrict__ sinst,
+                                                            const int32_t *__restrict__ wl,
+                                                            const BGlobal *G,
+                                                            const double *__restrict__ wtab,
+                                                            int k) {
+  const int nwl = G->wl_n[1], Kb = G->Kb;
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int nwarps = (int)(gridDim.x * blockDim.x) >> 5;
+  for (int it = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); it < nwl; it += nwarps) {
+    const int s = wl[it];
+    const int i = sinst[s];
+    epi.sigma = (float)I[i].sigma;
+    epi.w = wtab[(size_t)i * Kb + k];
+    process_item<1, U, PIPE>(A, dxhat, (const float *)nullptr, s, lane, epi);
   }
 }
 
@@ -630,6 +676,8 @@ __global__ void __launch_bounds__(kListThreads) b_decide_kernel(BInst *I, BGloba
         B.rho_stored = rho;
         B.restarts += 1;
         B.t0 = 0;
+        // mixed precision: the next correction is scaled by the distance moved
+        if (G->mixed && r > 0.0 && isfinite(r)) B.mix_s = fmin(1.0 / r, 1e12);
       } else {
         B.t0 = t;
       }
@@ -682,6 +730,84 @@ __global__ void __launch_bounds__(kBlock) b_restart_copy_kernel(DevVecs v, const
         v.y[i] = s;
       }
       v.ybar[i] = s;
+    }
+  }
+}
+
+// Mixed precision, grid (chunks, problems) like the restart copy.
+// b_combine: the FP64 iterate and average z = z^{n,0} + dz / s of each due
+// problem (every problem when forced), projected onto X x Y.
+__global__ void __launch_bounds__(kBlock) b_combine_kernel(DevVecs v, MixVecs mv, const BInst *I,
+                                                           int force) {
+  const BInst &B = I[blockIdx.y];
+  if (!force && !B.due) return;
+  const int64_t lo = (int64_t)blockIdx.x * kCopyChunk;
+  const int64_t nx = B.ncol, N = nx + B.nrow;
+  if (lo >= N) return;
+  const int64_t hi = lo + kCopyChunk < N ? lo + kCopyChunk : N;
+  const double inv = 1.0 / B.mix_s;
+  for (int64_t t = lo + threadIdx.x; t < hi; t += blockDim.x) {
+    if (t < nx) {
+      const int64_t j = B.col0 + t;
+      const double x0 = v.x0[j], l = v.lb[j], u = v.ub[j];
+      v.x[j] = fmin(fmax(fma((double)mv.dx[j], inv, x0), l), u);
+      v.xbar[j] = fmin(fmax(fma(mv.dxbar[j], inv, x0), l), u);
+    } else {
+      const int64_t r = B.row0 + (t - nx);
+      const int rt = v.row_type[r];
+      const double ylo = (rt == 1) ? 0.0 : -INFINITY, yhi = (rt == 2) ? 0.0 : INFINITY;
+      const double y0 = v.y0[r];
+      v.y[r] = fmin(fmax(fma((double)mv.dy[r], inv, y0), ylo), yhi);
+      v.ybar[r] = fmin(fmax(fma(mv.dybar[r], inv, y0), ylo), yhi);
+    }
+  }
+}
+
+// b_recenter: after a restart the correction data are re-formed in FP64 --
+// s times the residuals (from the check) of the chosen candidate at the new
+// restart point -- and dz restarts at 0; the flexible scheme's replacement
+// of the average by the current iterate is applied to dz.  Forced: every
+// problem, candidate 0 (set-up).
+__global__ void __launch_bounds__(kBlock) b_recenter_kernel(DevVecs v, MixVecs mv, const BInst *I,
+                                                            int force) {
+  const BInst &B = I[blockIdx.y];
+  const int rs = force ? 1 : B.restart_now, uc = force ? 0 : B.use_cur;
+  if (!rs && !uc) return;
+  const int64_t lo = (int64_t)blockIdx.x * kCopyChunk;
+  const int64_t nx = B.ncol, N = nx + B.nrow;
+  if (lo >= N) return;
+  const int64_t hi = lo + kCopyChunk < N ? lo + kCopyChunk : N;
+  const double sc = B.mix_s;
+  const double *lam = uc ? mv.lam[1] : mv.lam[0];
+  const double *gy = uc ? mv.gy[1] : mv.gy[0];
+  for (int64_t t = lo + threadIdx.x; t < hi; t += blockDim.x) {
+    if (t < nx) {
+      const int64_t j = B.col0 + t;
+      if (rs) {
+        const double x0 = v.x0[j];
+        mv.cf[j] = (float)(sc * lam[j]);
+        mv.lf[j] = (float)(sc * (v.lb[j] - x0));
+        mv.uf[j] = (float)(sc * (v.ub[j] - x0));
+        mv.dx[j] = 0.0f;
+        mv.dxhat[j] = 0.0f;
+        mv.dxbar[j] = 0.0;
+      } else {
+        mv.dxbar[j] = (double)mv.dx[j];
+      }
+    } else {
+      const int64_t r = B.row0 + (t - nx);
+      if (rs) {
+        const int rt = v.row_type[r];
+        const double ylo = (rt == 1) ? 0.0 : -INFINITY, yhi = (rt == 2) ? 0.0 : INFINITY;
+        const double y0 = v.y0[r];
+        mv.bf[r] = (float)(-sc * gy[r]);
+        mv.ylo[r] = (float)(sc * (ylo - y0));
+        mv.yhi[r] = (float)(sc * (yhi - y0));
+        mv.dy[r] = 0.0f;
+        mv.dybar[r] = 0.0;
+      } else {
+        mv.dybar[r] = (double)mv.dy[r];
+      }
     }
   }
 }
@@ -827,6 +953,20 @@ void b_dual_launch(int g, cudaStream_t s, const SellMat &A, const double *xhat, 
   b_dual_kernel<U, PIPE><<<g, kBlock, 0, s>>>(A, xhat, epi, I, sinst, wl, G, wtab, k);
 }
 
+template <int U, bool PIPE>
+void b_primal_mix_launch(int g, cudaStream_t s, const SellMat &AT, const float *dy,
+                         const PrimalMixEpi &epi, const BInst *I, const int32_t *sinst,
+                         const int32_t *wl, const BGlobal *G, const double *wtab, int k) {
+  b_primal_mix_kernel<U, PIPE><<<g, kBlock, 0, s>>>(AT, dy, epi, I, sinst, wl, G, wtab, k);
+}
+
+template <int U, bool PIPE>
+void b_dual_mix_launch(int g, cudaStream_t s, const SellMat &A, const float *dxhat,
+                       const DualMixEpi &epi, const BInst *I, const int32_t *sinst,
+                       const int32_t *wl, const BGlobal *G, const double *wtab, int k) {
+  b_dual_mix_kernel<U, PIPE><<<g, kBlock, 0, s>>>(A, dxhat, epi, I, sinst, wl, G, wtab, k);
+}
+
 }  // namespace
 }  // namespace lpg
 
@@ -845,6 +985,8 @@ struct lp_batch {
   int nchunk_a = 0, nchunk_at = 0;
   int64_t max_elems = 0;  // largest n_k + m_k
   DevVecs v{};
+  bool mixed = false;
+  MixVecs mv{};
   BInst *I = nullptr;
   BGlobal *G = nullptr;
   double *wtab = nullptr;
@@ -902,14 +1044,20 @@ struct lp_batch {
     return LP_OK;
   }
 
-  lp_status upload_sell(const HostSell &H, SellMat &M) {
+  lp_status upload_sell(const HostSell &H, SellMat &M, bool with_f32) {
     SliceInfo *info = nullptr;
     int32_t *ix = nullptr;
     double *vv = nullptr;
+    float *vf = nullptr;
     lp_status s;
     if ((s = upload(&info, H.info)) != LP_OK) return s;
     if ((s = upload(&ix, H.idx)) != LP_OK) return s;
     if ((s = upload(&vv, H.val)) != LP_OK) return s;
+    if (with_f32) {
+      std::vector<float> hf(H.val.size());
+      for (size_t q = 0; q < hf.size(); ++q) hf[q] = (float)H.val[q];
+      if ((s = upload(&vf, hf)) != LP_OK) return s;
+    }
     M.nrows = H.nrows;
     M.ncols = H.ncols;
     M.nslices = H.nslices;
@@ -917,13 +1065,23 @@ struct lp_batch {
     M.info = info;
     M.idx = ix;
     M.val = vv;
-    M.valf = nullptr;
+    M.valf = vf;
     return LP_OK;
   }
 
   void launch_primal(int k, cudaStream_t s) {
-    PrimalEpi epi{v.c, v.lbk, v.ubk, v.x, v.xhat, v.xbar, 0.0, 0.0, nullptr};
     const int g = grid_cols;
+    if (mixed) {
+      PrimalMixEpi me{mv.cf, mv.lf, mv.uf, mv.dx, mv.dxhat, mv.dxbar, 0.0f, 0.0};
+      switch (unroll_cols) {
+        case 2: b_primal_mix_launch<2, false>(g, s, AT, mv.dy, me, I, sinst_at, wl[0], G, wtab, k); break;
+        case 4: b_primal_mix_launch<4, false>(g, s, AT, mv.dy, me, I, sinst_at, wl[0], G, wtab, k); break;
+        case -4: b_primal_mix_launch<4, true>(g, s, AT, mv.dy, me, I, sinst_at, wl[0], G, wtab, k); break;
+        default: b_primal_mix_launch<2, true>(g, s, AT, mv.dy, me, I, sinst_at, wl[0], G, wtab, k); break;
+      }
+      return;
+    }
+    PrimalEpi epi{v.c, v.lbk, v.ubk, v.x, v.xhat, v.xbar, 0.0, 0.0, nullptr};
     switch (unroll_cols) {
       case 2: b_primal_launch<2, false>(g, s, AT, v.y, epi, I, sinst_at, wl[0], G, wtab, k); break;
       case 4: b_primal_launch<4, false>(g, s, AT, v.y, epi, I, sinst_at, wl[0], G, wtab, k); break;
@@ -933,8 +1091,18 @@ struct lp_batch {
   }
 
   void launch_dual(int k, cudaStream_t s) {
-    DualEpi epi{v.b, v.row_type, v.y, v.ybar, 0.0, 0.0, nullptr};
     const int g = grid_rows;
+    if (mixed) {
+      DualMixEpi me{mv.bf, mv.ylo, mv.yhi, mv.dy, mv.dybar, 0.0f, 0.0};
+      switch (unroll_rows) {
+        case 2: b_dual_mix_launch<2, false>(g, s, A, mv.dxhat, me, I, sinst_a, wl[1], G, wtab, k); break;
+        case 4: b_dual_mix_launch<4, false>(g, s, A, mv.dxhat, me, I, sinst_a, wl[1], G, wtab, k); break;
+        case -2: b_dual_mix_launch<2, true>(g, s, A, mv.dxhat, me, I, sinst_a, wl[1], G, wtab, k); break;
+        default: b_dual_mix_launch<4, true>(g, s, A, mv.dxhat, me, I, sinst_a, wl[1], G, wtab, k); break;
+      }
+      return;
+    }
+    DualEpi epi{v.b, v.row_type, v.y, v.ybar, 0.0, 0.0, nullptr};
     switch (unroll_rows) {
       case 2: b_dual_launch<2, false>(g, s, A, v.xhat, epi, I, sinst_a, wl[1], G, wtab, k); break;
       case 4: b_dual_launch<4, false>(g, s, A, v.xhat, epi, I, sinst_a, wl[1], G, wtab, k); break;
@@ -947,9 +1115,22 @@ struct lp_batch {
     b_worklist_kernel<<<1, kListThreads, 0, s>>>(I, G, wl[0], wl[1]);
   }
 
+  dim3 chunk_grid() const {
+    return dim3((unsigned)((max_elems + kCopyChunk - 1) / kCopyChunk), (unsigned)count);
+  }
+
+  void launch_combine(int force, cudaStream_t s) {
+    b_combine_kernel<<<chunk_grid(), kBlock, 0, s>>>(v, mv, I, force);
+  }
+
   void launch_check(cudaStream_t s) {
     b_pre_check_kernel<<<(count + kBlock - 1) / kBlock, kBlock, 0, s>>>(I, G);
+    if (mixed) launch_combine(0, s);
     CheckColsEpi ce{};
+    if (mixed) {
+      ce.lam_out0 = mv.lam[0];
+      ce.lam_out1 = mv.lam[1];
+    }
     ce.c = v.c; ce.lb = v.lb; ce.ub = v.ub; ce.xbar = v.xbar; ce.x = v.x; ce.x0 = v.x0;
     ce.ga = GapOut{sa.keys[0], sa.d2[0], sa.g2[0], sa.gd[0]};
     ce.gc = GapOut{sa.keys[1], sa.d2[1], sa.g2[1], sa.gd[1]};
@@ -958,6 +1139,10 @@ struct lp_batch {
     re.ga = ce.ga;
     re.gc = ce.gc;
     re.off = n;
+    if (mixed) {
+      re.gy_out0 = mv.gy[0];
+      re.gy_out1 = mv.gy[1];
+    }
     b_check_kernel<CheckColsEpi><<<blocks_for_slices(nchunk_at), kBlock, 0, s>>>(
         AT, v.ybar, v.y, ce, I, sinst_at, chunk_at, nchunk_at, G, spart, pstride, 0);
     b_check_kernel<CheckRowsEpi><<<blocks_for_slices(nchunk_a), kBlock, 0, s>>>(
@@ -983,8 +1168,8 @@ struct lp_batch {
                          (int64_t)n, sa);
     }
     b_decide_kernel<<<1, kListThreads, 0, s>>>(I, G, wtab);
-    b_restart_copy_kernel<<<dim3((unsigned)((max_elems + kCopyChunk - 1) / kCopyChunk), count),
-                            kBlock, 0, s>>>(v, I);
+    b_restart_copy_kernel<<<chunk_grid(), kBlock, 0, s>>>(v, I);
+    if (mixed) b_recenter_kernel<<<chunk_grid(), kBlock, 0, s>>>(v, mv, I, 0);
     launch_worklist(s);
   }
 };
@@ -1025,6 +1210,7 @@ lp_status batch_reset(lp_batch *h, cudaStream_t s) {
     for (int q = 0; q < 5; ++q) B.kkt_a[q] = B.kkt_c[q] = NAN;
     B.kkt_a[4] = B.kkt_c[4] = INFINITY;
     B.ls[0].done = B.ls[1].done = 1;
+    B.mix_s = 1.0;
   }
   LP_CU(cudaMemcpyAsync(h->I, hi.data(), sizeof(BInst) * h->count, cudaMemcpyHostToDevice, s));
   const int Kb = h->opt.check_every;
@@ -1035,6 +1221,10 @@ lp_status batch_reset(lp_batch *h, cudaStream_t s) {
   launch_fill(h->v.x, 0.0, h->n, s);
   launch_fill(h->v.y, 0.0, h->m, s);
   launch_project(h->v, h->n, h->m, s);
+  if (h->mixed) {  // correction data at the starting point, dz = 0, s = 1
+    launch_residuals(h->A, h->AT, h->v, h->mv, h->n, h->m, s);
+    b_recenter_kernel<<<h->chunk_grid(), kBlock, 0, s>>>(h->v, h->mv, h->I, 1);
+  }
   h->launch_worklist(s);
   LP_CU(cudaGetLastError());
   LP_CU(cudaStreamSynchronize(s));
@@ -1208,8 +1398,6 @@ lp_status lp_batch_create(int32_t count, const int32_t *host_row_start,
   else lp_default_options(&opt);
   lp_status st = validate_options(opt);
   if (st != LP_OK) return st;
-  if (opt.precision != LP_PRECISION_FP64)
-    return fail(LP_ERR_INVALID_ARG, "the batched solver runs in FP64 (precision must be LP_PRECISION_FP64)");
   if (opt.spmv_mode != 0) return fail(LP_ERR_INVALID_ARG, "the batched solver has spmv_mode 0 only");
   lp_batch_tuning tune{};
   tune.autotune = 0;
@@ -1394,8 +1582,9 @@ lp_status lp_batch_create(int32_t count, const int32_t *host_row_start,
 
   // ---- device buffers
   lp_status e;
-  if ((e = h->upload_sell(HA, h->A)) != LP_OK) return e;
-  if ((e = h->upload_sell(HAT, h->AT)) != LP_OK) return e;
+  h->mixed = (opt.precision == LP_PRECISION_MIXED);
+  if ((e = h->upload_sell(HA, h->A, h->mixed)) != LP_OK) return e;
+  if ((e = h->upload_sell(HAT, h->AT, h->mixed)) != LP_OK) return e;
   if ((e = h->upload(&h->sinst_a, sa_host)) != LP_OK) return e;
   if ((e = h->upload(&h->sinst_at, sat_host)) != LP_OK) return e;
   if ((e = h->upload(&h->chunk_a, chk_a)) != LP_OK) return e;
@@ -1417,6 +1606,21 @@ lp_status lp_batch_create(int32_t count, const int32_t *host_row_start,
     if ((e = h->alloc(p, m)) != LP_OK) return e;
   if ((e = h->alloc(&h->tmp, std::max(n, m))) != LP_OK) return e;
   if ((e = h->alloc(&h->tmp2, std::max(n, m))) != LP_OK) return e;
+  if (h->mixed) {
+    MixVecs &mv = h->mv;
+    float **fn[] = {&mv.cf, &mv.lf, &mv.uf, &mv.dx, &mv.dxhat};
+    for (float **p : fn)
+      if ((e = h->alloc(p, n)) != LP_OK) return e;
+    float **fm[] = {&mv.bf, &mv.ylo, &mv.yhi, &mv.dy};
+    for (float **p : fm)
+      if ((e = h->alloc(p, m)) != LP_OK) return e;
+    double **dn[] = {&mv.dxbar, &mv.lam[0], &mv.lam[1]};
+    for (double **p : dn)
+      if ((e = h->alloc(p, n)) != LP_OK) return e;
+    double **dm[] = {&mv.dybar, &mv.gy[0], &mv.gy[1]};
+    for (double **p : dm)
+      if ((e = h->alloc(p, m)) != LP_OK) return e;
+  }
   if ((e = h->alloc(&h->I, count)) != LP_OK) return e;
   if ((e = h->alloc(&h->G, 1)) != LP_OK) return e;
   if ((e = h->alloc(&h->wtab, (int64_t)count * opt.check_every)) != LP_OK) return e;
@@ -1491,6 +1695,7 @@ lp_status lp_batch_create(int32_t count, const int32_t *host_row_start,
   hg.scheme = opt.restart_scheme;
   hg.pw_max = opt.power_iters;
   hg.running = count;
+  hg.mixed = h->mixed ? 1 : 0;
   LP_CU(cudaMemcpy(h->G, &hg, sizeof(BGlobal), cudaMemcpyHostToDevice));
   LP_CU(cudaMemcpy(h->I, hi.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice));
   b_norms_kernel<<<count, kBlock, 0, s>>>(h->I, h->v.b, h->v.c);
@@ -1652,6 +1857,7 @@ lp_status lp_batch_get_solution(lp_batch_handle h, double *x, double *y, void *c
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   if (!h->solved) return fail(LP_ERR_NOT_SOLVED, "no solve has run on this batch");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (h->mixed) h->launch_combine(1, s);
   if (x) {
     b_select_kernel<<<h->count, kBlock, 0, s>>>(h->I, h->v.x, h->v.xbar, h->tmp2, 0);
     launch_scatter(h->tmp, h->tmp2, h->perm_x, h->n, s);
@@ -1673,6 +1879,7 @@ lp_status lp_batch_get_state(lp_batch_handle h, double *x, double *y, double *xb
   err_msg().clear();
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (h->mixed) h->launch_combine(1, s);
   struct Item { double *dst; const double *src; const int32_t *perm; int32_t len; };
   const Item items[] = {{x, h->v.x, h->perm_x, h->n},       {y, h->v.y, h->perm_y, h->m},
                         {xbar, h->v.xbar, h->perm_x, h->n}, {ybar, h->v.ybar, h->perm_y, h->m},

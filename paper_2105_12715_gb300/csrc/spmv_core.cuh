@@ -372,6 +372,49 @@ struct CheckRowsEpi {
   }
 };
 
+// --------------------------------------------------- mixed precision
+//
+// FP32 PDHG step on the correction dz = s (z - z^{n,0}): the same update as
+// Eq. (PDHG-update) with the correction's data (cf, bf, bounds lf/uf,
+// ylo/yhi), FP32 matrix values and FP32 accumulation; the running average
+// of the correction stays in FP64.
+struct PrimalMixEpi {
+  const float *__restrict__ cf;
+  const float *__restrict__ lf;
+  const float *__restrict__ uf;
+  float *dx, *dxhat;
+  double *dxbar;
+  float tau;
+  double w;
+  struct Pre { float c, l, u, x; double xb; };
+  __device__ __forceinline__ Pre load(int j) const { return {cf[j], lf[j], uf[j], dx[j], dxbar[j]}; }
+  __device__ __forceinline__ float init(const Pre &p) const { return -p.c; }
+  __device__ __forceinline__ void store(int j, float neg_g, float, const Pre &p) const {
+    const float xn = fminf(fmaxf(fmaf(tau, neg_g, p.x), p.l), p.u);
+    dx[j] = xn;
+    dxhat[j] = fmaf(2.0f, xn, -p.x);
+    dxbar[j] = fma(w, (double)xn - p.xb, p.xb);
+  }
+};
+
+struct DualMixEpi {
+  const float *__restrict__ bf;
+  const float *__restrict__ lo;
+  const float *__restrict__ hi;
+  float *dy;
+  double *dybar;
+  float sigma;
+  double w;
+  struct Pre { float b, l, h, y; double yb; };
+  __device__ __forceinline__ Pre load(int i) const { return {bf[i], lo[i], hi[i], dy[i], dybar[i]}; }
+  __device__ __forceinline__ float init(const Pre &p) const { return -p.b; }
+  __device__ __forceinline__ void store(int i, float r, float, const Pre &p) const {
+    const float yn = fminf(fmaxf(fmaf(-sigma, r, p.y), p.l), p.h);
+    dy[i] = yn;
+    dybar[i] = fma(w, (double)yn - p.yb, p.yb);
+  }
+};
+
 // ------------------------------------------------------ check helpers
 
 __device__ __forceinline__ void init_search(LSearch &L, double r, double d2, double gd, double g2inf) {

@@ -245,3 +245,42 @@ def test_batch_tuner_choices_are_valid_and_consistent(lpm):
         plain = g.state()
     for key in tuned:
         close(tuned[key], plain[key], 1e-12, key)
+
+
+def rel_err(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max()) / max(1.0, float(np.abs(b).max()))
+
+
+def test_batch_mixed_tracks_fp64_oracle(lpm, oracle_mod):
+    """Mixed precision in a batch: every problem's iterates follow the FP64
+    oracle to FP32 rounding (1e-5 relative, the single-problem mixed
+    path's stated error) with the same restart decisions."""
+    probs = mixed_batch()
+    eta = common_eta(oracle_mod, probs)
+    with lpm.LPBatch(probs, eta=eta, check_every=32, max_iter=192,
+                     precision=lpm.LP_PRECISION_MIXED) as g:
+        g.solve(1e-300)
+        summary, per = g.info()
+        sts = states_of(g, probs)
+    for k, d in enumerate(probs):
+        ref = osolve(oracle_mod, d, eta, tol=1e-300, max_iter=192, check_every=32)
+        assert per[k]["restarts"] == ref.restarts, k
+        for key in ("x", "y", "xbar", "ybar", "x0", "y0"):
+            assert rel_err(sts[k][key], getattr(ref, key)) <= 1e-5, (k, key)
+
+
+def test_batch_mixed_full_solve_reaches_fp64_tolerance(lpm, oracle_mod):
+    probs = [lpgen.tiny_standard_form(s, m=m, n=2 * m, per_col=5)
+             for s, m in [(0, 40), (1, 80), (9, 60)]]
+    with lpm.LPBatch(probs, check_every=64, max_iter=400000,
+                     precision=lpm.LP_PRECISION_MIXED) as g:
+        status = g.solve(1e-8)
+        summary, per = g.info()
+        x, y = g.solution()
+    assert status == lpm.LP_OK
+    xs, ys = g.split(x), g.split(y, rows=True)
+    for k, d in enumerate(probs):
+        kk = oracle_mod.kkt(d, xs[k], ys[k])
+        assert kk["rel"] <= 1e-8 * (1 + 1e-6), k
+        assert kk["pobj"] == pytest.approx(d.obj_star, rel=1e-7, abs=1e-7)
+        assert np.all(xs[k] >= d.lb)
