@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--batch-count", type=int, default=512)
     p.add_argument("--batch-cap", type=int, default=100_000)
     p.add_argument("--batch-loop-sample", type=int, default=16)
+    p.add_argument("--batch-only", action="store_true",
+                   help="run only the batched section and print its JSON (profiling)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--kernel-reps", type=int, default=50)  # >= 1
     return p.parse_args()
@@ -265,10 +267,12 @@ def run_batched(args, lp, stream, barrier):
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     nb = 8
+    torch.cuda.nvtx.range_push("batch_blocks")
     e0.record(stream)
     g.iterate(nb, 1e-300)
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     ms_block = e0.elapsed_time(e1) / nb
     pb, db = algorithmic_bytes(M, N, Z)
     res["iter_us"] = 1000.0 * ms_block / K_CHECK
@@ -297,7 +301,8 @@ def run_batched(args, lp, stream, barrier):
                     "iters_median": float(np.median(its)), "iters_sum": int(its.sum())}
     # the plain FP64 path, one problem at a time, on a seeded sample
     rng = np.random.default_rng(0)
-    idx = rng.choice(len(probs), size=min(args.batch_loop_sample, len(probs)), replace=False)
+    idx = rng.choice(len(probs), size=min(max(args.batch_loop_sample, 1), len(probs)),
+                     replace=False)
     t_loop, same, conv_loop = 0.0, 0, 0
     for k in idx:
         barrier()
@@ -348,6 +353,18 @@ def run_batched(args, lp, stream, barrier):
                     "converged": int(conv_m.sum()), "iters_median": float(np.median(its_m)),
                     "converged_both": int((conv & conv_m).sum())}
     return res
+
+
+def run_batch_only(args):
+    import torch
+
+    from paper_2105_12715_gb300 import lp
+
+    torch.cuda.set_device(0)
+    lp.load()
+    res = run_batched(args, lp, torch.cuda.current_stream(), torch.cuda.synchronize)
+    print(json.dumps({"batched": res}))
+    return 0
 
 
 def run_ours(args):
@@ -574,6 +591,8 @@ def main():
     args.kernel_reps = max(1, args.kernel_reps)
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch_only:
+        return run_batch_only(args)
     return run_ours(args)
 
 
