@@ -541,6 +541,33 @@ def run_ours(args):
                    "forward_recorded_ms": 1000 * float(np.median(fw)),
                    "backward_ms": 1000 * float(np.median(bw)),
                    "backward_over_forward": float(np.median(bw) / np.median(fw))}
+        # implicit-KKT active-set gradient (reported, not binding): on the face the
+        # solve reaches, w = A_B^T u on the interior set B gives d(w^T x)/db = u
+        d3 = lpgen.box_standard_form(100)
+        g3 = lp.LP(d3, stream=stream, check_every=100, max_iter=200_000)
+        st3 = g3.solve(1e-8)
+        xs, _ = g3.solution()
+        conv_iters = g3.info().iters
+        g3.close()
+        Bset = (xs > 1e-7) & (xs < 1 - 1e-7)
+        import scipy.sparse as sp
+
+        A3 = sp.csr_matrix((d3.val, d3.col_idx, d3.row_ptr), shape=(d3.m, d3.n))
+        u3 = np.random.default_rng(7).standard_normal(d3.m)
+        w3 = np.zeros(d3.n)
+        w3[Bset] = (A3[:, np.flatnonzero(Bset)].T @ u3)
+        imp = {"solve_status": lp.STATUS_NAMES.get(st3, st3), "interior": int(Bset.sum()),
+               "rows": d3.m}
+        for T in (2000, ((conv_iters + 400) // 100) * 100):
+            g3 = lp.LP(d3, stream=stream, check_every=100)
+            lp.lp_solve_recorded(g3.h, T, stream)
+            dc, db = np.empty(d3.n), np.empty(d3.m)
+            lp.lp_backward(g3.h, w3, None, dc, db, stream)
+            g3.close()
+            imp[f"iters_{T}"] = {
+                "cosine": float(db @ u3 / (np.linalg.norm(db) * np.linalg.norm(u3))),
+                "rel_err": float(np.linalg.norm(db - u3) / np.linalg.norm(u3))}
+        adjoint["implicit_kkt"] = imp
 
     batched = run_batched(args, lp, stream, barrier) if not args.no_batch else None
 

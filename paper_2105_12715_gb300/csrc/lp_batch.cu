@@ -63,6 +63,7 @@ struct BInst {
   int32_t col0, ncol, row0, nrow;  // ranges in the permuted index spaces
   int32_t cs0, cs1, rs0, rs1;      // slice ranges in A^T and A
   int32_t cc0, cc1, rc0, rc1;      // check-chunk ranges in A^T and A
+  int32_t wlc0, wlr0;              // this problem's offsets in the work lists (if running)
   int32_t K;                       // check period (multiple of K_base)
   int32_t status;                  // kRunning or a final lp_status
   int32_t returned, restart_now, use_cur, due;
@@ -184,8 +185,9 @@ __global__ void __launch_bounds__(kBlock) b_dual_mix_kernel(SellMat A, const flo
 
 // ------------------------------------------------------------------- check
 
-__global__ void b_pre_check_kernel(BInst *I, const BGlobal *G) {
+__global__ void b_pre_check_kernel(BInst *I, BGlobal *G) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) G->running = 0;  // counted again by b_decide
   if (i >= G->count) return;
   BInst &B = I[i];
   B.due = 0;
@@ -629,79 +631,66 @@ __global__ void __launch_bounds__(kSearchThreads) b_search_kernel(BInst *I,
 }
 
 // Restart rule per due problem (Eq. adaptive-restart-scheme, flexible,
-// fixed), counters and iteration limits, the next block's averaging weights
-// w[i][k] = 1 / (t0_i + k + 1), and the running count.
-__global__ void __launch_bounds__(kListThreads) b_decide_kernel(BInst *I, BGlobal *G,
-                                                                double *wtab) {
-  __shared__ int running;
-  if (threadIdx.x == 0) running = 0;
-  __syncthreads();
+// fixed), counters and iteration limits, and the running count (one thread
+// per problem; integer atomics, so the count is exact).
+__global__ void __launch_bounds__(kBlock) b_decide_kernel(BInst *I, BGlobal *G) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int count = G->count, Kb = G->Kb, scheme = G->scheme;
-  const double beta = G->beta;
-  int mine = 0;
-  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+  bool run = false;
+  if (i < count) {
     BInst &B = I[i];
     B.restart_now = 0;
     B.use_cur = 0;
-    if (B.status != kRunning) continue;
-    if (B.due) {
-      double rho = NAN, r = B.last_r;
-      int use_cur = 0;
-      if (scheme == kSchemeAdaptive || scheme == kSchemeFlexible) {
-        const LSearch &La = B.ls[0];
-        r = sqrt(La.r2);
-        rho = (La.r2 > 0.0) ? La.rho_r / r : 0.0;
-        if (scheme == kSchemeFlexible) {
-          const LSearch &Lc = B.ls[1];
-          const double rc = sqrt(Lc.r2);
-          const double rho_c = (Lc.r2 > 0.0) ? Lc.rho_r / rc : 0.0;
-          if (rho_c < rho) {
-            use_cur = 1;
-            rho = rho_c;
-            r = rc;
+    if (B.status == kRunning) {
+      if (B.due) {
+        double rho = NAN, r = B.last_r;
+        int use_cur = 0;
+        if (scheme == kSchemeAdaptive || scheme == kSchemeFlexible) {
+          const LSearch &La = B.ls[0];
+          r = sqrt(La.r2);
+          rho = (La.r2 > 0.0) ? La.rho_r / r : 0.0;
+          if (scheme == kSchemeFlexible) {
+            const LSearch &Lc = B.ls[1];
+            const double rc = sqrt(Lc.r2);
+            const double rho_c = (Lc.r2 > 0.0) ? Lc.rho_r / rc : 0.0;
+            if (rho_c < rho) {
+              use_cur = 1;
+              rho = rho_c;
+              r = rc;
+            }
           }
         }
-      }
-      const int64_t t = B.t0 + Kb;
-      int restart = 0;
-      if (scheme == kSchemeAdaptive || scheme == kSchemeFlexible)
-        restart = (B.restarts == 0) ? (t >= B.tau0) : (rho <= beta * B.rho_stored);
-      else if (scheme == kSchemeFixed)
-        restart = (t >= B.fixed_len);
-      B.last_rho = rho;
-      B.last_r = r;
-      B.use_cur = use_cur;
-      B.restart_now = restart;
-      if (restart) {
-        B.rho_stored = rho;
-        B.restarts += 1;
-        B.t0 = 0;
-        // mixed precision: the next correction is scaled by the distance moved
-        if (G->mixed && r > 0.0 && isfinite(r)) B.mix_s = fmin(1.0 / r, 1e12);
+        const int64_t t = B.t0 + Kb;
+        int restart = 0;
+        if (scheme == kSchemeAdaptive || scheme == kSchemeFlexible)
+          restart = (B.restarts == 0) ? (t >= B.tau0) : (rho <= G->beta * B.rho_stored);
+        else if (scheme == kSchemeFixed)
+          restart = (t >= B.fixed_len);
+        B.last_rho = rho;
+        B.last_r = r;
+        B.use_cur = use_cur;
+        B.restart_now = restart;
+        if (restart) {
+          B.rho_stored = rho;
+          B.restarts += 1;
+          B.t0 = 0;
+          // mixed precision: the next correction is scaled by the distance moved
+          if (G->mixed && r > 0.0 && isfinite(r)) B.mix_s = fmin(1.0 / r, 1e12);
+        } else {
+          B.t0 = t;
+        }
+        B.since = 0;
       } else {
-        B.t0 = t;
+        B.t0 += Kb;
       }
-      B.since = 0;
-    } else {
-      B.t0 += Kb;
+      if (B.iters >= B.iter_cap) B.status = kStatusIterLimit;  // the check's restart still happens
+      else run = true;
     }
-    if (B.iters >= B.iter_cap) {  // the check's restart (if any) still takes place
-      B.status = kStatusIterLimit;
-      continue;
-    }
-    ++mine;
   }
-  if (mine) atomicAdd(&running, mine);
-  __syncthreads();
-  if (threadIdx.x == 0) G->running = running;
-  for (int64_t e = threadIdx.x; e < (int64_t)count * Kb; e += blockDim.x) {
-    const int i = (int)(e / Kb), k = (int)(e - (int64_t)i * Kb);
-    wtab[e] = 1.0 / (double)(I[i].t0 + k + 1);
-  }
+  const unsigned bal = __ballot_sync(kFull, run);
+  if ((threadIdx.x & (kWarp - 1)) == 0 && bal) atomicAdd(&G->running, __popc(bal));
 }
 
-// Restart of Algorithm 1 for the problems whose check decided one (the
-// flags are cleared for every problem at each check).
 // Grid (chunks, problems): block (x, k) copies elements x*kCopyChunk + ...
 // of problem k.
 constexpr int kCopyChunk = 4096;
@@ -840,26 +829,28 @@ __device__ __forceinline__ int block_exscan(int v, int *warp_tot, int *total) {
   return before;
 }
 
-// Work lists of the next block: slices of the running problems, in order.
-__global__ void __launch_bounds__(kListThreads) b_worklist_kernel(const BInst *I, BGlobal *G,
-                                                                  int32_t *wl_c, int32_t *wl_r) {
+// Work lists of the next block (slices of the running problems, in problem
+// order): one block scans the running problems' slice counts into offsets;
+// then one block per running problem writes its slice ids and the averaging
+// weights w[k][kk] = 1 / (t0_k + kk + 1) of its next block.
+__global__ void __launch_bounds__(kListThreads) b_list_scan_kernel(BInst *I, BGlobal *G) {
   __shared__ int wt[kWarp];
   const int count = G->count;
   int carry_c = 0, carry_r = 0;
   for (int base = 0; base < count; base += kListThreads) {
     const int i = base + (int)threadIdx.x;
-    int nc = 0, nr = 0, c0 = 0, r0 = 0;
+    int nc = 0, nr = 0;
     if (i < count && I[i].status == kRunning) {
-      c0 = I[i].cs0;
-      r0 = I[i].rs0;
-      nc = I[i].cs1 - c0;
-      nr = I[i].rs1 - r0;
+      nc = I[i].cs1 - I[i].cs0;
+      nr = I[i].rs1 - I[i].rs0;
     }
     int tc = 0, tr = 0;
     const int oc = carry_c + block_exscan(nc, wt, &tc);
     const int orr = carry_r + block_exscan(nr, wt, &tr);
-    for (int t = 0; t < nc; ++t) wl_c[oc + t] = c0 + t;
-    for (int t = 0; t < nr; ++t) wl_r[orr + t] = r0 + t;
+    if (i < count) {
+      I[i].wlc0 = oc;
+      I[i].wlr0 = orr;
+    }
     carry_c += tc;
     carry_r += tr;
   }
@@ -867,6 +858,18 @@ __global__ void __launch_bounds__(kListThreads) b_worklist_kernel(const BInst *I
     G->wl_n[0] = carry_c;
     G->wl_n[1] = carry_r;
   }
+}
+
+__global__ void __launch_bounds__(kBlock) b_list_fill_kernel(const BInst *I, const BGlobal *G,
+                                                             int32_t *wl_c, int32_t *wl_r,
+                                                             double *wtab) {
+  const BInst &B = I[blockIdx.x];
+  if (B.status != kRunning) return;
+  const int Kb = G->Kb;
+  for (int t = threadIdx.x; t < B.cs1 - B.cs0; t += blockDim.x) wl_c[B.wlc0 + t] = B.cs0 + t;
+  for (int t = threadIdx.x; t < B.rs1 - B.rs0; t += blockDim.x) wl_r[B.wlr0 + t] = B.rs0 + t;
+  for (int k = threadIdx.x; k < Kb; k += blockDim.x)
+    wtab[(size_t)blockIdx.x * Kb + k] = 1.0 / (double)(B.t0 + k + 1);
 }
 
 // --------------------------------------------------------- setup kernels
@@ -1111,8 +1114,10 @@ struct lp_batch {
     }
   }
 
+  // work lists and averaging weights of the next block
   void launch_worklist(cudaStream_t s) {
-    b_worklist_kernel<<<1, kListThreads, 0, s>>>(I, G, wl[0], wl[1]);
+    b_list_scan_kernel<<<1, kListThreads, 0, s>>>(I, G);
+    b_list_fill_kernel<<<count, kBlock, 0, s>>>(I, G, wl[0], wl[1], wtab);
   }
 
   dim3 chunk_grid() const {
@@ -1167,7 +1172,7 @@ struct lp_batch {
       cudaLaunchKernelEx(&cfg, b_search_kernel<kMaxCluster>, I, (const int32_t *)plist_big,
                          (int64_t)n, sa);
     }
-    b_decide_kernel<<<1, kListThreads, 0, s>>>(I, G, wtab);
+    b_decide_kernel<<<(count + kBlock - 1) / kBlock, kBlock, 0, s>>>(I, G);
     b_restart_copy_kernel<<<chunk_grid(), kBlock, 0, s>>>(v, I);
     if (mixed) b_recenter_kernel<<<chunk_grid(), kBlock, 0, s>>>(v, mv, I, 0);
     launch_worklist(s);
@@ -1213,11 +1218,6 @@ lp_status batch_reset(lp_batch *h, cudaStream_t s) {
     B.mix_s = 1.0;
   }
   LP_CU(cudaMemcpyAsync(h->I, hi.data(), sizeof(BInst) * h->count, cudaMemcpyHostToDevice, s));
-  const int Kb = h->opt.check_every;
-  std::vector<double> w((size_t)h->count * Kb);
-  for (int32_t i = 0; i < h->count; ++i)
-    for (int k = 0; k < Kb; ++k) w[(size_t)i * Kb + k] = 1.0 / (double)(k + 1);
-  LP_CU(cudaMemcpyAsync(h->wtab, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice, s));
   launch_fill(h->v.x, 0.0, h->n, s);
   launch_fill(h->v.y, 0.0, h->m, s);
   launch_project(h->v, h->n, h->m, s);

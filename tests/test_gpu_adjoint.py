@@ -95,3 +95,34 @@ def test_autograd_function_gradient(oracle_mod):
     fd = (L(data.c + h * dcv, data.b + h * dbv) - L(data.c - h * dcv, data.b - h * dbv)) / (2 * h)
     got = float(c.grad.cpu().numpy() @ dcv + b.grad.cpu().numpy() @ dbv)
     assert got == pytest.approx(fd, rel=1e-4, abs=1e-6)
+
+
+def test_backward_matches_implicit_kkt_gradient_on_the_face(oracle_mod):
+    """Implicit-KKT active-set check.  At the converged face of a box LP
+    (interior set B from the oracle's solution), A_B x_B = b - A_N x_N, so the
+    loss w^T x with w = A_B^T u on B (0 elsewhere) has d/db = u whichever
+    point of the face the method reaches.  The adjoint of the unrolled map run
+    to convergence must return u."""
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_2105_12715_gb300 import lp
+
+    data = lpgen.box_standard_form(5, m=100, n=250, per_col=6)
+    eta = 0.9 / oracle_mod.sigma_max(data)
+    K = 64
+    ref = oracle_mod.solve(data, eta, tol=1e-10, max_iter=400000, check_every=K)
+    assert ref.status == 0
+    x = ref.x_sol
+    B = (x > 1e-7) & (x < 1 - 1e-7)
+    A = data.dense()
+    assert np.linalg.matrix_rank(A[:, B]) == data.m
+    u = np.random.default_rng(0).standard_normal(data.m)
+    w = np.zeros(data.n)
+    w[B] = A[:, B].T @ u
+    iters = ((ref.iters + 4 * K) // K) * K
+    with lp.LP(data, eta=eta, check_every=K) as g:
+        lp.lp_solve_recorded(g.h, iters)
+        dc, db = np.empty(data.n), np.empty(data.m)
+        lp.lp_backward(g.h, w, None, dc, db)
+    assert np.linalg.norm(db - u) <= 1e-6 * np.linalg.norm(u)
