@@ -108,6 +108,7 @@ __global__ void __launch_bounds__(kBlock) b_primal_kernel(SellMat AT, const doub
                                                           const int32_t *__restrict__ wl,
                                                           const BGlobal *G,
                                                           const double *__restrict__ wtab, int k) {
+  pdl_enter();
   const int nwl = G->wl_n[0], Kb = G->Kb;
   const int lane = threadIdx.x & (kWarp - 1);
   const int nwarps = (int)(gridDim.x * blockDim.x) >> 5;
@@ -127,6 +128,7 @@ __global__ void __launch_bounds__(kBlock) b_dual_kernel(SellMat A, const double 
                                                         const int32_t *__restrict__ wl,
                                                         const BGlobal *G,
                                                         const double *__restrict__ wtab, int k) {
+  pdl_enter();
   const int nwl = G->wl_n[1], Kb = G->Kb;
   const int lane = threadIdx.x & (kWarp - 1);
   const int nwarps = (int)(gridDim.x * blockDim.x) >> 5;
@@ -150,6 +152,7 @@ __global__ void __launch_bounds__(kBlock) b_primal_mix_kernel(SellMat AT, const 
                                                               const BGlobal *G,
                                                               const double *__restrict__ wtab,
                                                               int k) {
+  pdl_enter();
   const int nwl = G->wl_n[0], Kb = G->Kb;
   const int lane = threadIdx.x & (kWarp - 1);
   const int nwarps = (int)(gridDim.x * blockDim.x) >> 5;
@@ -171,6 +174,7 @@ __global__ void __launch_bounds__(kBlock) b_dual_mix_kernel(SellMat A, const flo
                                                             const BGlobal *G,
                                                             const double *__restrict__ wtab,
                                                             int k) {
+  pdl_enter();
   const int nwl = G->wl_n[1], Kb = G->Kb;
   const int lane = threadIdx.x & (kWarp - 1);
   const int nwarps = (int)(gridDim.x * blockDim.x) >> 5;
@@ -946,28 +950,28 @@ template <int U, bool PIPE>
 void b_primal_launch(int g, cudaStream_t s, const SellMat &AT, const double *y, const PrimalEpi &epi,
                      const BInst *I, const int32_t *sinst, const int32_t *wl, const BGlobal *G,
                      const double *wtab, int k) {
-  b_primal_kernel<U, PIPE><<<g, kBlock, 0, s>>>(AT, y, epi, I, sinst, wl, G, wtab, k);
+  launch_pdl(b_primal_kernel<U, PIPE>, g, kBlock, s, AT, y, epi, I, sinst, wl, G, wtab, k);
 }
 
 template <int U, bool PIPE>
 void b_dual_launch(int g, cudaStream_t s, const SellMat &A, const double *xhat, const DualEpi &epi,
                    const BInst *I, const int32_t *sinst, const int32_t *wl, const BGlobal *G,
                    const double *wtab, int k) {
-  b_dual_kernel<U, PIPE><<<g, kBlock, 0, s>>>(A, xhat, epi, I, sinst, wl, G, wtab, k);
+  launch_pdl(b_dual_kernel<U, PIPE>, g, kBlock, s, A, xhat, epi, I, sinst, wl, G, wtab, k);
 }
 
 template <int U, bool PIPE>
 void b_primal_mix_launch(int g, cudaStream_t s, const SellMat &AT, const float *dy,
                          const PrimalMixEpi &epi, const BInst *I, const int32_t *sinst,
                          const int32_t *wl, const BGlobal *G, const double *wtab, int k) {
-  b_primal_mix_kernel<U, PIPE><<<g, kBlock, 0, s>>>(AT, dy, epi, I, sinst, wl, G, wtab, k);
+  launch_pdl(b_primal_mix_kernel<U, PIPE>, g, kBlock, s, AT, dy, epi, I, sinst, wl, G, wtab, k);
 }
 
 template <int U, bool PIPE>
 void b_dual_mix_launch(int g, cudaStream_t s, const SellMat &A, const float *dxhat,
                        const DualMixEpi &epi, const BInst *I, const int32_t *sinst,
                        const int32_t *wl, const BGlobal *G, const double *wtab, int k) {
-  b_dual_mix_kernel<U, PIPE><<<g, kBlock, 0, s>>>(A, dxhat, epi, I, sinst, wl, G, wtab, k);
+  launch_pdl(b_dual_mix_kernel<U, PIPE>, g, kBlock, s, A, dxhat, epi, I, sinst, wl, G, wtab, k);
 }
 
 }  // namespace

@@ -1,5 +1,6 @@
-// Internal declarations shared by the two translation units of liblp.so
-// (lp_kernels.cu: device code and launchers; lp_api.cu: the C ABI).
+// Internal declarations shared by the translation units of liblp.so
+// (lp_kernels.cu: device code and launchers; lp_api.cu: the C ABI;
+// lp_batch.cu: the batched solver).
 #pragma once
 
 #include <cstdint>
@@ -164,6 +165,24 @@ struct CheckScratch {
   double *btot;            // [2][4][kBuckets] bucket totals of the current pass
   int32_t hist_grid;
 };
+
+// Launch with programmatic stream serialization: the kernel may be scheduled
+// while its predecessor in the stream finishes (it must call pdl_enter()
+// before reading the predecessor's results).  Works inside stream capture.
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kern)(KArgs...), int grid, int block, cudaStream_t s,
+                       Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
 
 // ---- launchers (lp_kernels.cu) ----
 void launch_primal_step(const SellMat &AT, const DevVecs &v, DevState *st,

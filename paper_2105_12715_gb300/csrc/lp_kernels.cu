@@ -34,6 +34,7 @@ template <int U, bool PIPE, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) primal_kernel(SellMat AT, const double *__restrict__ y,
                                                         PrimalEpi epi, const DevState *st,
                                                         const double *__restrict__ w, int k) {
+  pdl_enter();
   if (st->status != kRunning) return;
   epi.tau = st->tau;
   epi.w = w[k];
@@ -44,6 +45,7 @@ template <int U, bool PIPE, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) dual_kernel(SellMat A, const double *__restrict__ xhat,
                                                       DualEpi epi, const DevState *st,
                                                       const double *__restrict__ w, int k) {
+  pdl_enter();
   if (st->status != kRunning) return;
   epi.sigma = st->sigma;
   epi.w = w[k];
@@ -213,6 +215,7 @@ template <int U, bool PIPE>
 __global__ void __launch_bounds__(kBlock) primal_mix_kernel(SellMat AT, const float *__restrict__ dy,
                                                             PrimalMixEpi epi, const DevState *st,
                                                             const double *__restrict__ w, int k) {
+  pdl_enter();
   if (st->status != kRunning) return;
   epi.tau = (float)st->tau;
   epi.w = w[k];
@@ -223,6 +226,7 @@ template <int U, bool PIPE>
 __global__ void __launch_bounds__(kBlock) dual_mix_kernel(SellMat A, const float *__restrict__ dxhat,
                                                           DualMixEpi epi, const DevState *st,
                                                           const double *__restrict__ w, int k) {
+  pdl_enter();
   if (st->status != kRunning) return;
   epi.sigma = (float)st->sigma;
   epi.w = w[k];
@@ -1026,15 +1030,15 @@ int check_grid_for(const SellMat &A, int nsm) {
 template <int U, bool PIPE>
 void primal_launch(int occ, int g, cudaStream_t s, const SellMat &AT, const double *y,
                    const PrimalEpi &epi, DevState *st, const double *w, int k) {
-  if (occ) primal_kernel<U, PIPE, 5><<<g, kBlock, 0, s>>>(AT, y, epi, st, w, k);
-  else primal_kernel<U, PIPE, 1><<<g, kBlock, 0, s>>>(AT, y, epi, st, w, k);
+  if (occ) launch_pdl(primal_kernel<U, PIPE, 5>, g, kBlock, s, AT, y, epi, st, w, k);
+  else launch_pdl(primal_kernel<U, PIPE, 1>, g, kBlock, s, AT, y, epi, st, w, k);
 }
 
 template <int U, bool PIPE>
 void dual_launch(int occ, int g, cudaStream_t s, const SellMat &A, const double *xhat,
                  const DualEpi &epi, DevState *st, const double *w, int k) {
-  if (occ) dual_kernel<U, PIPE, 4><<<g, kBlock, 0, s>>>(A, xhat, epi, st, w, k);
-  else dual_kernel<U, PIPE, 1><<<g, kBlock, 0, s>>>(A, xhat, epi, st, w, k);
+  if (occ) launch_pdl(dual_kernel<U, PIPE, 4>, g, kBlock, s, A, xhat, epi, st, w, k);
+  else launch_pdl(dual_kernel<U, PIPE, 1>, g, kBlock, s, A, xhat, epi, st, w, k);
 }
 
 void launch_primal_step(const SellMat &AT, const DevVecs &v, DevState *st, const double *w,
@@ -1138,13 +1142,13 @@ void launch_check(const SellMat &A, const SellMat &AT, const DevVecs &v, DevStat
 void launch_primal_mix(const SellMat &AT, const MixVecs &mv, DevState *st, const double *w,
                        int k, cudaStream_t s) {
   PrimalMixEpi epi{mv.cf, mv.lf, mv.uf, mv.dx, mv.dxhat, mv.dxbar, 0.0f, 0.0};
-  primal_mix_kernel<2, true><<<item_grid(AT), kBlock, 0, s>>>(AT, mv.dy, epi, st, w, k);
+  launch_pdl(primal_mix_kernel<2, true>, item_grid(AT), kBlock, s, AT, mv.dy, epi, st, w, k);
 }
 
 void launch_dual_mix(const SellMat &A, const MixVecs &mv, const DevVecs &, DevState *st,
                      const double *w, int k, cudaStream_t s) {
   DualMixEpi epi{mv.bf, mv.ylo, mv.yhi, mv.dy, mv.dybar, 0.0f, 0.0};
-  dual_mix_kernel<4, true><<<item_grid(A), kBlock, 0, s>>>(A, mv.dxhat, epi, st, w, k);
+  launch_pdl(dual_mix_kernel<4, true>, item_grid(A), kBlock, s, A, mv.dxhat, epi, st, w, k);
 }
 
 void launch_combine(const DevVecs &v, const MixVecs &mv, DevState *st, int n, int m, int force,

@@ -19,6 +19,16 @@ constexpr int kSchemeFixed = 1, kSchemeAdaptive = 2, kSchemeFlexible = 3;
 
 __device__ __forceinline__ double sq(double v) { return v * v; }
 
+// Programmatic dependent launch (iteration kernels, launched with
+// launch_pdl): let the next kernel in the stream be scheduled while this one
+// drains, then wait until the previous kernel has completed and its writes
+// are visible -- before any read of its results.  Both are no-ops for a
+// kernel launched without the attribute.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.launch_dependents;");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // ------------------------------------------------------------------ SpMV core
 //
 // Row sums of one slice (one warp).  Each lane walks its row's elements
