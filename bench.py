@@ -243,6 +243,8 @@ def run_batched(args, lp, stream, barrier):
 
     from paper_2105_12715_gb300 import lpgen
 
+    from paper_2105_12715_gb300 import dist as pdist
+
     probs = lpgen.batch_standard_form(2, args.batch_count)
     M = sum(d.m for d in probs)
     N = sum(d.n for d in probs)
@@ -250,6 +252,14 @@ def run_batched(args, lp, stream, barrier):
     res = {"workload": f"batch_standard_form seed 2: {len(probs)} LPs, m log-uniform [50,20000], "
                        f"n=2m, 3-12 nnz/col, x>=0, EQ rows; total m={M} n={N} nnz={Z}",
            "check_every_base": K_CHECK}
+    ws, rank, _ = dist_env()
+    if ws > 1:  # shard by problem (balanced by nonzeros); no data-path collective
+        mine = pdist.shard_by_weight([d.nnz for d in probs], ws, rank)
+        probs = [probs[i] for i in mine]
+        M = sum(d.m for d in probs)
+        N = sum(d.n for d in probs)
+        Z = sum(d.nnz for d in probs)
+        res["sharding"] = f"{ws} ranks, problems balanced by nonzeros"
     barrier()
     t0 = time.perf_counter()
     g = lp.LPBatch(probs, stream=stream, check_every=K_CHECK, max_iter=args.batch_cap,
@@ -275,10 +285,12 @@ def run_batched(args, lp, stream, barrier):
     torch.cuda.nvtx.range_pop()
     ms_block = e0.elapsed_time(e1) / nb
     pb, db = algorithmic_bytes(M, N, Z)
-    res["iter_us"] = 1000.0 * ms_block / K_CHECK
-    res["problem_iters_per_s"] = len(probs) * K_CHECK / (ms_block / 1000.0)
-    res["achieved_gbs_per_iter"] = (pb + db) / (ms_block / K_CHECK / 1000.0) / 1e9
-    res["bytes_per_iter_algorithmic"] = pb + db
+    rate, slowest = pdist.job_throughput(len(probs) * K_CHECK * nb, ms_block * nb / 1000.0)
+    bytes_all = pdist.reduce_scalar(pb + db, "sum")
+    res["iter_us"] = 1e6 * slowest / (K_CHECK * nb)
+    res["problem_iters_per_s"] = rate
+    res["achieved_gbs_per_iter"] = bytes_all / (slowest / (K_CHECK * nb)) / 1e9
+    res["bytes_per_iter_algorithmic"] = bytes_all
     g.close()
     # time to 1e-8 (fresh batch; setup = create incl. power iterations and tuning)
     barrier()
@@ -295,10 +307,14 @@ def run_batched(args, lp, stream, barrier):
     its = np.array([p["iters"] for p in per])
     conv = np.array([p["status"] == lp.LP_OK for p in per])
     g.close()
+    t_batch = pdist.reduce_scalar(t_batch, "max")
+    t_setup = pdist.reduce_scalar(t_setup, "max")
     res["solve"] = {"tol": 1e-8, "cap_iters": args.batch_cap, "seconds": t_batch,
                     "seconds_with_setup": t_batch + t_setup,
-                    "converged": int(conv.sum()), "problems": len(probs),
-                    "iters_median": float(np.median(its)), "iters_sum": int(its.sum())}
+                    "converged": int(pdist.reduce_scalar(conv.sum(), "sum")),
+                    "problems": int(pdist.reduce_scalar(len(probs), "sum")),
+                    "iters_median": float(np.median(its)),
+                    "iters_sum": int(pdist.reduce_scalar(its.sum(), "sum"))}
     # the plain FP64 path, one problem at a time, on a seeded sample
     rng = np.random.default_rng(0)
     idx = rng.choice(len(probs), size=min(max(args.batch_loop_sample, 1), len(probs)),
@@ -314,12 +330,12 @@ def run_batched(args, lp, stream, barrier):
         conv_loop += int(st == lp.LP_OK)
         same += int(abs(h.info().iters - int(its[k])) <= K_CHECK)
         h.close()
-    est = t_loop * len(probs) / len(idx)
+    est = pdist.reduce_scalar(t_loop * len(probs) / len(idx), "max")  # ranks loop in parallel
     res["loop_fp64"] = {"sample": len(idx), "sample_seconds": t_loop,
                         "extrapolated_seconds": est, "converged_in_sample": conv_loop,
                         "same_iteration_count": same,
                         "note": "lp_create + lp_solve per problem (setup included); total = "
-                                "sample time x problems / sample size"}
+                                "sample time x problems / sample size (per rank, max over ranks)"}
     res["speedup_vs_loop"] = est / (t_batch + t_setup)  # both with setup
     # the FP32-mixed batch: same problems, same timing
     barrier()
@@ -347,11 +363,14 @@ def run_batched(args, lp, stream, barrier):
     its_m = np.array([p["iters"] for p in per])
     conv_m = np.array([p["status"] == lp.LP_OK for p in per])
     g.close()
-    res["mixed"] = {"iter_us": 1000.0 * ms_block_m / K_CHECK,
-                    "problem_iters_per_s": len(probs) * K_CHECK / (ms_block_m / 1000.0),
+    rate_m, slowest_m = pdist.job_throughput(len(probs) * K_CHECK * nb, ms_block_m * nb / 1000.0)
+    t_mixed = pdist.reduce_scalar(t_mixed, "max")
+    t_setup_m = pdist.reduce_scalar(t_setup_m, "max")
+    res["mixed"] = {"iter_us": 1e6 * slowest_m / (K_CHECK * nb), "problem_iters_per_s": rate_m,
                     "solve_seconds": t_mixed, "solve_seconds_with_setup": t_mixed + t_setup_m,
-                    "converged": int(conv_m.sum()), "iters_median": float(np.median(its_m)),
-                    "converged_both": int((conv & conv_m).sum())}
+                    "converged": int(pdist.reduce_scalar(conv_m.sum(), "sum")),
+                    "iters_median": float(np.median(its_m)),
+                    "converged_both": int(pdist.reduce_scalar((conv & conv_m).sum(), "sum"))}
     return res
 
 
@@ -405,12 +424,12 @@ def run_ours(args):
     barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
     iters = args.steps * K_CHECK
-    value = ws * iters / (ms / 1000.0)
+    from paper_2105_12715_gb300 import dist as pdist
+
+    # replicas: iterations of all ranks over the slowest rank's time
+    value, slowest = pdist.job_throughput(iters, ms / 1000.0, device="cuda")
+    ms = 1000.0 * slowest
     info = g.info()
     # per step: 2 K iteration kernels + 2 check passes, finalize, 8 x (hist, select), decide, copy
     launches_per_step = 2 * K_CHECK + 21
