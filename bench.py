@@ -232,6 +232,19 @@ def run_reference(args):
     return 0
 
 
+def gather_probe():
+    """Random-gather throughput of this GPU (csrc/probe_gather.cu): the rate the
+    iteration kernels' operand gathers are bounded by."""
+    try:
+        from paper_2105_12715_gb300 import build as b
+
+        exe = b.build_probe()
+        r = subprocess.run([exe], stdout=subprocess.PIPE, stderr=subprocess.STDOUT, timeout=120)
+        return json.loads(r.stdout.decode().strip().splitlines()[-1])
+    except Exception as e:  # the probe is context only
+        return {"error": str(e)[:200]}
+
+
 def run_batched(args, lp, stream, barrier):
     """Batched solver on 512 uneven standard-form LPs (m log-uniform in
     [50, 20000], n = 2m, 3-12 nonzeros per column): tuned create, aggregate
@@ -450,6 +463,13 @@ def run_ours(args):
     peak, peak_kind = peaks()
     achieved = primal_b / (primal_ms / 1000.0) / 1e9
     g.close()
+    probe = gather_probe() if rank == 0 else None
+    gather_bound = None
+    if probe and "global_1p6MB_ggathers_per_s" in probe:
+        ach_g = data.nnz / (primal_ms / 1000.0) / 1e9
+        gather_bound = {"gathers_per_launch": data.nnz, "achieved_ggathers_per_s": ach_g,
+                        "probe": probe,
+                        "frac_of_probe": ach_g / probe["global_1p6MB_ggathers_per_s"]}
 
     # end to end through the C ABI from host buffers
     e2e_vals, h2d = [], 0
@@ -606,7 +626,8 @@ def run_ours(args):
                             "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                             "peak_kind": peak_kind, "traffic": PRIMAL_TRAFFIC_BYTES,
                             "algorithmic_bytes": primal_b, "avg_launch_ms": primal_ms,
-                            "dual_kernel_ms": dual_ms, "dual_algorithmic_bytes": dual_b},
+                            "dual_kernel_ms": dual_ms, "dual_algorithmic_bytes": dual_b,
+                            "gather_bound": gather_bound},
                "clocks": clocks, "e2e": e2e, "mixed": mixed, "time_to_kkt": ttk,
                "multicommodity": mcf, "adjoint": adjoint, "batched": batched,
                "solver": {"eta": info0.eta, "sigma_max": info0.sigma_max,
