@@ -282,6 +282,7 @@ def run_batched(args, lp, stream, barrier):
     summary, per = g.info()
     res["tuner"] = {"spmv_unroll": summary["spmv_unroll"],
                     "spmv_unroll_rows": summary["spmv_unroll_rows"],
+                    "grid_cols": summary["grid_cols"], "grid_rows": summary["grid_rows"],
                     "class_k": summary["class_k"],
                     "class_iter_ms": [round(v, 4) for v in summary["class_iter_ms"]],
                     "class_check_ms": [round(v, 4) for v in summary["class_check_ms"]],

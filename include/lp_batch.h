@@ -74,6 +74,7 @@ typedef struct {
   int64_t blocks;       /* blocks of K_base iterations run by the batch */
   int32_t k_base;       /* K_base = opt->check_every */
   int32_t spmv_unroll, spmv_unroll_rows; /* kernel variants in use (lp_options codes) */
+  int32_t grid_cols, grid_rows;          /* blocks of the column / row pass launches */
   int32_t n_classes;    /* size classes present */
   int32_t class_k[8];   /* check period chosen per size class (0 = class empty) */
   double class_iter_ms[8];  /* tuner: one iteration of the class running alone (ms) */

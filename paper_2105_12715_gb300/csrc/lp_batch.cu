@@ -1919,6 +1919,8 @@ lp_status lp_batch_get_info(lp_batch_handle h, lp_batch_info *info,
   info->k_base = h->opt.check_every;
   info->spmv_unroll = h->unroll_cols;
   info->spmv_unroll_rows = h->unroll_rows;
+  info->grid_cols = h->grid_cols;
+  info->grid_rows = h->grid_rows;
   int nc = 0;
   for (int q = 0; q < kMaxClasses; ++q) {
     info->class_k[q] = h->class_k[q];

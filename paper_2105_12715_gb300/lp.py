@@ -65,7 +65,7 @@ class lp_batch_info(C.Structure):
     _fields_ = [("count", C.c_int32), ("running", C.c_int32), ("m", C.c_int32), ("n", C.c_int32),
                 ("nnz", C.c_int64), ("blocks", C.c_int64), ("k_base", C.c_int32),
                 ("spmv_unroll", C.c_int32), ("spmv_unroll_rows", C.c_int32),
-                ("n_classes", C.c_int32), ("class_k", C.c_int32 * 8),
+                ("grid_cols", C.c_int32), ("grid_rows", C.c_int32), ("n_classes", C.c_int32), ("class_k", C.c_int32 * 8),
                 ("class_iter_ms", C.c_double * 8), ("class_check_ms", C.c_double * 8),
                 ("tune_ms", C.c_double), ("setup_ms", C.c_double)]
 
