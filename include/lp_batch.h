@@ -139,6 +139,33 @@ lp_status lp_batch_get_state(lp_batch_handle h, double *x, double *y, double *xb
 lp_status lp_batch_get_info(lp_batch_handle h, lp_batch_info *host_info,
                             lp_batch_problem_info *host_problems, int32_t capacity);
 
+/*
+ * Unrolled forward for differentiation (the paper has no gradients): runs
+ * exactly `iters` iterations of every problem from the current state (iters
+ * a multiple of K_base = opt->check_every; FP64; adaptive, fixed or no
+ * restarts; no termination test), keeping a checkpoint of (x, y, xbar, ybar)
+ * of the whole batch and every problem's inner iteration count at the start
+ * of every block of K_base iterations, and whether each block's check
+ * restarted each problem.  The unrolled map of problem k is its running
+ * average (xbar_k, ybar_k) after the last block.  LP_ERR_NUMERICAL if a
+ * problem fails during the recording.
+ */
+lp_status lp_batch_solve_recorded(lp_batch_handle h, int64_t iters, void *cuda_stream);
+
+/*
+ * Adjoint of the recorded unrolled maps (c, b) -> (xbar, ybar), all problems
+ * at once: given dl_dx[n] = dL/dxbar and dl_dy[m] = dL/dybar (concatenated,
+ * caller's order; NULL = 0), writes dl_dc[n] and dl_db[m] (host or device).
+ * Per problem this is lp_backward of lp.h: restart decisions and clamp /
+ * projection masks held at the recorded ones, blocks recomputed from their
+ * checkpoints in reverse order, each adjoint step running the transposed
+ * products of the forward step with that problem's tau, sigma and averaging
+ * weights.  Leaves the state of the recorded solve.  LP_ERR_NOT_SOLVED
+ * without a recording.  Synchronizes the stream.
+ */
+lp_status lp_batch_backward(lp_batch_handle h, const double *dl_dx, const double *dl_dy,
+                            double *dl_dc, double *dl_db, void *cuda_stream);
+
 /* Releases every resource of the batch (NULL is a no-op). */
 void lp_batch_destroy(lp_batch_handle h);
 

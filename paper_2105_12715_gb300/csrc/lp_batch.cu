@@ -805,6 +805,125 @@ __global__ void __launch_bounds__(kBlock) b_recenter_kernel(DevVecs v, MixVecs m
   }
 }
 
+// ------------------------------------------------------------- adjoint
+//
+// Recording of the unrolled forward (lp_batch_solve_recorded): before each
+// block, every problem's inner count t0 and restart count; after it, whether
+// the block's check restarted the problem.
+__global__ void b_rec_pre_kernel(const BInst *I, int count, int64_t *t0, int64_t *restarts) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  t0[i] = I[i].t0;
+  restarts[i] = I[i].restarts;
+}
+
+__global__ void b_rec_post_kernel(const BInst *I, int count, const int64_t *restarts_before,
+                                  int8_t *restarted, int *stopped) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  restarted[i] = I[i].restarts > restarts_before[i] ? 1 : 0;
+  if (I[i].status != kRunning) atomicOr(stopped, 1);
+}
+
+// Averaging weights of a recorded block: w[i][k] = 1 / (t0_i + k + 1).
+__global__ void b_rec_weights_kernel(const int64_t *t0, int count, int K, double *wtab) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)count * K) return;
+  const int i = (int)(e / K), k = (int)(e - (int64_t)i * K);
+  wtab[e] = 1.0 / (double)(t0[i] + k + 1);
+}
+
+// Adjoint steps over every slice, with the slice's problem's tau, sigma and
+// weights of steps k and k - 1 (epilogues AdjColsEpi / AdjRowsEpi).
+__global__ void __launch_bounds__(kBlock) b_adj_cols_kernel(SellMat AT, const double *__restrict__ u,
+                                                            AdjColsEpi epi,
+                                                            const BInst *__restrict__ I,
+                                                            const int32_t *__restrict__ sinst,
+                                                            const double *__restrict__ wtab, int K,
+                                                            int k) {
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int nwarps = (int)(gridDim.x * blockDim.x) >> 5;
+  for (int s = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); s < AT.nslices; s += nwarps) {
+    const int i = sinst[s];
+    epi.tau = I[i].tau;
+    epi.sigma = I[i].sigma;
+    epi.w = wtab[(size_t)i * K + k];
+    process_item<1, 2, true>(AT, u, (const double *)nullptr, s, lane, epi);
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) b_adj_rows_kernel(SellMat A, const double *__restrict__ v,
+                                                            AdjRowsEpi epi,
+                                                            const BInst *__restrict__ I,
+                                                            const int32_t *__restrict__ sinst,
+                                                            const double *__restrict__ wtab, int K,
+                                                            int k) {
+  const int lane = threadIdx.x & (kWarp - 1);
+  const int nwarps = (int)(gridDim.x * blockDim.x) >> 5;
+  for (int s = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); s < A.nslices; s += nwarps) {
+    const int i = sinst[s];
+    epi.tau = I[i].tau;
+    epi.sigma = I[i].sigma;
+    epi.w_prev = k > 0 ? wtab[(size_t)i * K + k - 1] : 0.0;
+    process_item<1, 4, true>(A, v, (const double *)nullptr, s, lane, epi);
+  }
+}
+
+// Start of a reverse block, grid (chunks, problems): the restart after the
+// block (if problem k restarted there: ax moves into axb, ay into ayb), then
+// u of the block's last step.
+__global__ void __launch_bounds__(kBlock) b_adj_block_start_kernel(AdjVecs a, const BInst *I,
+                                                                   const int8_t *restarted,
+                                                                   const uint8_t *my_last,
+                                                                   const double *wtab, int K) {
+  const int p = blockIdx.y;
+  const BInst &B = I[p];
+  const int64_t lo = (int64_t)blockIdx.x * kCopyChunk;
+  const int64_t nx = B.ncol, N = nx + B.nrow;
+  if (lo >= N) return;
+  const int64_t hi = lo + kCopyChunk < N ? lo + kCopyChunk : N;
+  const int rs = restarted[p];
+  const double sigma = B.sigma, w = wtab[(size_t)p * K + K - 1];
+  for (int64_t t = lo + threadIdx.x; t < hi; t += blockDim.x) {
+    if (t < nx) {
+      const int64_t j = B.col0 + t;
+      if (rs) {
+        a.axb[j] += a.ax[j];
+        a.ax[j] = 0.0;
+      }
+    } else {
+      const int64_t r = B.row0 + (t - nx);
+      double ay = a.ay[r], yb = a.ayb[r];
+      if (rs) {
+        yb += ay;
+        ay = 0.0;
+        a.ay[r] = 0.0;
+      }
+      const double up = my_last[r] ? fma(w, yb, ay) : 0.0;
+      a.ab[r] = fma(sigma, up, a.ab[r]);
+      a.ayb[r] = (1.0 - w) * yb;
+      a.u[r] = up;
+    }
+  }
+}
+
+// z <- zbar for the problems whose recorded check restarted (replay of the
+// final block after the reverse sweep), grid (chunks, problems).
+__global__ void __launch_bounds__(kBlock) b_rec_restart_kernel(DevVecs v, const BInst *I,
+                                                               const int8_t *restarted) {
+  const int p = blockIdx.y;
+  if (!restarted[p]) return;
+  const BInst &B = I[p];
+  const int64_t lo = (int64_t)blockIdx.x * kCopyChunk;
+  const int64_t nx = B.ncol, N = nx + B.nrow;
+  if (lo >= N) return;
+  const int64_t hi = lo + kCopyChunk < N ? lo + kCopyChunk : N;
+  for (int64_t t = lo + threadIdx.x; t < hi; t += blockDim.x) {
+    if (t < nx) v.x[B.col0 + t] = v.xbar[B.col0 + t];
+    else v.y[B.row0 + (t - nx)] = v.ybar[B.row0 + (t - nx)];
+  }
+}
+
 // Block-wide exclusive scan of one int per thread (kListThreads threads);
 // returns the exclusive prefix, *total receives the block total.
 __device__ __forceinline__ int block_exscan(int v, int *warp_tot, int *total) {
@@ -1015,6 +1134,16 @@ struct lp_batch {
   double tune_iter_ms[kMaxClasses] = {0}, tune_check_ms[kMaxClasses] = {0};
   std::vector<double> eta, sigma_max;
   int64_t blocks = 0;
+  // unrolled-forward recording for lp_batch_backward
+  double *ckpt = nullptr;            // [blocks][2n + 2m]: x, y, xbar, ybar at block start
+  int64_t rec_blocks = 0;
+  int64_t *rec_t0 = nullptr;         // [blocks][count] inner count at block start
+  int64_t *rec_r0 = nullptr;         // [count] restart count before the current block
+  int8_t *rec_rs = nullptr;          // [blocks][count] the block's check restarted the problem
+  int *rec_stopped = nullptr;        // a problem left the running state while recording
+  double *wrec = nullptr;            // [count][K] weights of the block being recomputed
+  uint8_t *mask_x = nullptr, *mask_y = nullptr;  // [K][n], [K][m]
+  AdjVecs adj{};
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -1023,6 +1152,9 @@ struct lp_batch {
   bool solved = false;
 
   ~lp_batch() {
+    if (ckpt) cudaFree(ckpt);
+    if (rec_t0) cudaFree(rec_t0);
+    if (rec_rs) cudaFree(rec_rs);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     for (auto &e : ev)
@@ -1119,6 +1251,19 @@ struct lp_batch {
   }
 
   // work lists and averaging weights of the next block
+  // one forward step of the recorded iteration, writing the clamp and
+  // projection masks (weights from wtab_rec)
+  void launch_masked_step(int k, const double *wtab_rec, cudaStream_t s) {
+    const int K = opt.check_every;
+    PrimalEpi pe{v.c, v.lbk, v.ubk, v.x, v.xhat, v.xbar, 0.0, 0.0, mask_x + (int64_t)k * n};
+    b_primal_launch<2, true>(blocks_for_slices(AT.nslices), s, AT, v.y, pe, I, sinst_at, wl[0], G,
+                             wtab_rec, k);
+    DualEpi de{v.b, v.row_type, v.y, v.ybar, 0.0, 0.0, mask_y + (int64_t)k * std::max(m, 1)};
+    b_dual_launch<4, true>(blocks_for_slices(A.nslices), s, A, v.xhat, de, I, sinst_a, wl[1], G,
+                           wtab_rec, k);
+    (void)K;
+  }
+
   void launch_worklist(cudaStream_t s) {
     b_list_scan_kernel<<<1, kListThreads, 0, s>>>(I, G);
     b_list_fill_kernel<<<count, kBlock, 0, s>>>(I, G, wl[0], wl[1], wtab);
@@ -1956,6 +2101,153 @@ lp_status lp_batch_get_info(lp_batch_handle h, lp_batch_info *info,
       P.last_rho = B.last_rho;
     }
   }
+  return LP_OK;
+}
+
+lp_status lp_batch_solve_recorded(lp_batch_handle h, int64_t iters, void *cuda_stream) {
+  err_msg().clear();
+  if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
+  const int K = h->opt.check_every;
+  if (iters < K || iters % K != 0) return fail(LP_ERR_INVALID_ARG, "iters must be a positive multiple of check_every");
+  if (h->mixed) return fail(LP_ERR_INVALID_ARG, "recording needs LP_PRECISION_FP64");
+  if (h->opt.restart_scheme == LP_RESTART_FLEXIBLE)
+    return fail(LP_ERR_INVALID_ARG, "recording supports the adaptive, fixed and no-restart schemes");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  lp_status e = batch_build_graph(h);
+  if (e != LP_OK) return e;
+  const int64_t blocks = iters / K, slot = 2 * (int64_t)h->n + 2 * (int64_t)h->m;
+  const int count = h->count, n = h->n, m = h->m;
+  // every problem runs (no tolerance, no iteration cap) for exactly `iters`
+  std::vector<BInst> hi(count);
+  LP_CU(cudaMemcpyAsync(hi.data(), h->I, sizeof(BInst) * count, cudaMemcpyDeviceToHost, s));
+  LP_CU(cudaStreamSynchronize(s));
+  for (BInst &B : hi) {
+    if (B.status == kStatusNumerical) return fail(LP_ERR_NUMERICAL, "a problem has failed; reset the batch");
+    B.status = kRunning;
+    B.iter_cap = INT64_MAX;
+  }
+  LP_CU(cudaMemcpyAsync(h->I, hi.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice, s));
+  const double tiny = 1e-300;
+  LP_CU(cudaMemcpyAsync(&h->G->tol, &tiny, sizeof(double), cudaMemcpyHostToDevice, s));
+  h->launch_worklist(s);
+  // recording buffers
+  if (h->ckpt) cudaFree(h->ckpt);
+  if (h->rec_t0) cudaFree(h->rec_t0);
+  if (h->rec_rs) cudaFree(h->rec_rs);
+  h->ckpt = nullptr;
+  h->rec_t0 = nullptr;
+  h->rec_rs = nullptr;
+  h->rec_blocks = 0;
+  LP_CU(cudaMalloc(&h->ckpt, sizeof(double) * std::max<int64_t>(1, blocks * slot)));
+  LP_CU(cudaMalloc(&h->rec_t0, sizeof(int64_t) * blocks * count));
+  LP_CU(cudaMalloc(&h->rec_rs, sizeof(int8_t) * blocks * count));
+  if (!h->mask_x) {  // masks, adjoint vectors and small records, once per batch
+    if ((e = h->alloc(&h->mask_x, (int64_t)K * n)) != LP_OK) return e;
+    if ((e = h->alloc(&h->mask_y, (int64_t)K * std::max(m, 1))) != LP_OK) return e;
+    if ((e = h->alloc(&h->rec_r0, count)) != LP_OK) return e;
+    if ((e = h->alloc(&h->rec_stopped, 1)) != LP_OK) return e;
+    if ((e = h->alloc(&h->wrec, (int64_t)count * K)) != LP_OK) return e;
+    double **xs[] = {&h->adj.ax, &h->adj.axb, &h->adj.ac, &h->adj.v};
+    for (double **p : xs)
+      if ((e = h->alloc(p, n)) != LP_OK) return e;
+    double **ys[] = {&h->adj.ay, &h->adj.ayb, &h->adj.ab, &h->adj.u};
+    for (double **p : ys)
+      if ((e = h->alloc(p, std::max(m, 1))) != LP_OK) return e;
+  }
+  LP_CU(cudaMemsetAsync(h->rec_stopped, 0, sizeof(int), s));
+  const int pg = (count + kBlock - 1) / kBlock;
+  for (int64_t b = 0; b < blocks; ++b) {
+    double *c = h->ckpt + b * slot;
+    LP_CU(cudaMemcpyAsync(c, h->v.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    LP_CU(cudaMemcpyAsync(c + n, h->v.y, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    LP_CU(cudaMemcpyAsync(c + n + m, h->v.xbar, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    LP_CU(cudaMemcpyAsync(c + 2 * n + m, h->v.ybar, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    b_rec_pre_kernel<<<pg, kBlock, 0, s>>>(h->I, count, h->rec_t0 + b * count, h->rec_r0);
+    LP_CU(cudaGraphLaunch(h->exec, s));
+    b_rec_post_kernel<<<pg, kBlock, 0, s>>>(h->I, count, h->rec_r0, h->rec_rs + b * count,
+                                            h->rec_stopped);
+    LP_CU(cudaGetLastError());
+  }
+  h->blocks += blocks;
+  int stopped = 0;
+  LP_CU(cudaMemcpyAsync(&stopped, h->rec_stopped, sizeof(int), cudaMemcpyDeviceToHost, s));
+  LP_CU(cudaStreamSynchronize(s));
+  if (stopped) return fail(LP_ERR_NUMERICAL, "a problem stopped during recording");
+  h->rec_blocks = blocks;
+  h->solved = true;
+  return LP_OK;
+}
+
+lp_status lp_batch_backward(lp_batch_handle h, const double *dl_dx, const double *dl_dy,
+                            double *dl_dc, double *dl_db, void *cuda_stream) {
+  err_msg().clear();
+  if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
+  if (h->rec_blocks == 0) return fail(LP_ERR_NOT_SOLVED, "no recorded solve (lp_batch_solve_recorded)");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const int n = h->n, m = h->m, K = h->opt.check_every, count = h->count;
+  const int64_t slot = 2 * (int64_t)n + 2 * (int64_t)m;
+  const int wg = (int)std::max<int64_t>(1, ((int64_t)count * K + kBlock - 1) / kBlock);
+  AdjVecs &a = h->adj;
+  launch_fill(a.ax, 0.0, n, s);
+  launch_fill(a.ac, 0.0, n, s);
+  launch_fill(a.ay, 0.0, m, s);
+  launch_fill(a.ab, 0.0, m, s);
+  if (dl_dx) {
+    LP_CU(cudaMemcpyAsync(h->tmp, dl_dx, sizeof(double) * n, cudaMemcpyDefault, s));
+    launch_gather(a.axb, h->tmp, h->perm_x, n, s);
+  } else {
+    launch_fill(a.axb, 0.0, n, s);
+  }
+  if (dl_dy && m > 0) {
+    LP_CU(cudaMemcpyAsync(h->tmp, dl_dy, sizeof(double) * m, cudaMemcpyDefault, s));
+    launch_gather(a.ayb, h->tmp, h->perm_y, m, s);
+  } else {
+    launch_fill(a.ayb, 0.0, m, s);
+  }
+  auto restore = [&](int64_t b) -> lp_status {
+    const double *c = h->ckpt + b * slot;
+    LP_CU(cudaMemcpyAsync(h->v.x, c, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    LP_CU(cudaMemcpyAsync(h->v.y, c + n, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    LP_CU(cudaMemcpyAsync(h->v.xbar, c + n + m, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    LP_CU(cudaMemcpyAsync(h->v.ybar, c + 2 * n + m, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    b_rec_weights_kernel<<<wg, kBlock, 0, s>>>(h->rec_t0 + b * count, count, K, h->wrec);
+    for (int k = 0; k < K; ++k) h->launch_masked_step(k, h->wrec, s);
+    return LP_OK;
+  };
+  const int ga = blocks_for_slices(h->A.nslices), gat = blocks_for_slices(h->AT.nslices);
+  const int64_t mstride = std::max(m, 1);
+  for (int64_t b = h->rec_blocks - 1; b >= 0; --b) {
+    lp_status e = restore(b);  // recompute the block's steps with their masks
+    if (e != LP_OK) return e;
+    b_adj_block_start_kernel<<<h->chunk_grid(), kBlock, 0, s>>>(
+        a, h->I, h->rec_rs + b * count, h->mask_y + (int64_t)(K - 1) * mstride, h->wrec, K);
+    for (int k = K - 1; k >= 0; --k) {
+      AdjColsEpi ce{a.ax, a.axb, a.ac, a.v, h->mask_x + (int64_t)k * n, 0.0, 0.0, 0.0};
+      b_adj_cols_kernel<<<gat, kBlock, 0, s>>>(h->AT, a.u, ce, h->I, h->sinst_at, h->wrec, K, k);
+      AdjRowsEpi re{a.ay, a.ayb, a.ab, a.u, k > 0 ? h->mask_y + (int64_t)(k - 1) * mstride : nullptr,
+                    0.0, 0.0, 0.0, k > 0 ? 1 : 0};
+      b_adj_rows_kernel<<<ga, kBlock, 0, s>>>(h->A, a.v, re, h->I, h->sinst_a, h->wrec, K, k);
+    }
+    LP_CU(cudaGetLastError());
+  }
+  // restore the final state of the recorded solve: replay the last block
+  {
+    lp_status e = restore(h->rec_blocks - 1);
+    if (e != LP_OK) return e;
+    b_rec_restart_kernel<<<h->chunk_grid(), kBlock, 0, s>>>(h->v, h->I,
+                                                            h->rec_rs + (h->rec_blocks - 1) * count);
+  }
+  if (dl_dc) {
+    launch_scatter(h->tmp, a.ac, h->perm_x, n, s);
+    LP_CU(cudaMemcpyAsync(dl_dc, h->tmp, sizeof(double) * n, cudaMemcpyDefault, s));
+    LP_CU(cudaStreamSynchronize(s));
+  }
+  if (dl_db && m > 0) {
+    launch_scatter(h->tmp, a.ab, h->perm_y, m, s);
+    LP_CU(cudaMemcpyAsync(dl_db, h->tmp, sizeof(double) * m, cudaMemcpyDefault, s));
+  }
+  LP_CU(cudaGetLastError());
+  LP_CU(cudaStreamSynchronize(s));
   return LP_OK;
 }
 

@@ -351,46 +351,6 @@ __global__ void __launch_bounds__(kBlock) dual_mask_kernel(SellMat A,
   process_all<1, 4, true>(A, xhat, (const double *)nullptr, epi);
 }
 
-struct AdjColsEpi {
-  double *ax, *axb, *ac, *v;
-  const uint8_t *__restrict__ mx;
-  double tau, sigma, w;
-  struct Pre { double ax, axb, ac; int m; };
-  __device__ __forceinline__ Pre load(int j) const { return {ax[j], axb[j], ac[j], (int)mx[j]}; }
-  __device__ __forceinline__ double init(const Pre &) const { return 0.0; }
-  __device__ __forceinline__ void store(int j, double atu, double, const Pre &p) const {
-    const double adj_xhat = -sigma * atu;
-    const double adj_xp = fma(2.0, adj_xhat, fma(w, p.axb, p.ax));
-    const double vv = p.m ? adj_xp : 0.0;
-    ax[j] = vv - adj_xhat;
-    ac[j] = fma(-tau, vv, p.ac);
-    axb[j] = (1.0 - w) * p.axb;
-    v[j] = vv;
-  }
-};
-
-struct AdjRowsEpi {
-  double *ay, *ayb, *ab, *u;
-  const uint8_t *__restrict__ my_prev;
-  double tau, sigma, w_prev;
-  int has_prev;
-  struct Pre { double u, ayb, ab; int mp; };
-  __device__ __forceinline__ Pre load(int i) const {
-    return {u[i], ayb[i], ab[i], has_prev ? (int)my_prev[i] : 0};
-  }
-  __device__ __forceinline__ double init(const Pre &) const { return 0.0; }
-  __device__ __forceinline__ void store(int i, double av, double, const Pre &p) const {
-    const double ayk = fma(tau, av, p.u);
-    ay[i] = ayk;
-    if (has_prev) {
-      const double up = p.mp ? fma(w_prev, p.ayb, ayk) : 0.0;
-      ab[i] = fma(sigma, up, p.ab);
-      ayb[i] = (1.0 - w_prev) * p.ayb;
-      u[i] = up;
-    }
-  }
-};
-
 __global__ void __launch_bounds__(kBlock) adj_cols_kernel(SellMat AT, const double *__restrict__ u,
                                                           AdjColsEpi epi) {
   process_all<1, 2, true>(AT, u, (const double *)nullptr, epi);

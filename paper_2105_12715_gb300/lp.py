@@ -77,7 +77,8 @@ EXPORTED = ["lp_default_options", "lp_create", "lp_solve", "lp_iterate", "lp_get
             # include/lp_batch.h
             "lp_batch_default_tuning", "lp_batch_create", "lp_batch_set_check_every",
             "lp_batch_solve", "lp_batch_iterate", "lp_batch_get_solution", "lp_batch_get_state",
-            "lp_batch_get_info", "lp_batch_destroy"]
+            "lp_batch_get_info", "lp_batch_solve_recorded", "lp_batch_backward",
+            "lp_batch_destroy"]
 
 _lib = None
 
@@ -136,6 +137,8 @@ def load(build_if_missing: bool = True):
     lib.lp_batch_get_solution.argtypes = [P, P, P, P]
     lib.lp_batch_get_state.argtypes = [P, P, P, P, P, P, P, P]
     lib.lp_batch_get_info.argtypes = [P, C.POINTER(lp_batch_info), P, I32]
+    lib.lp_batch_solve_recorded.argtypes = [P, I64, P]
+    lib.lp_batch_backward.argtypes = [P, P, P, P, P, P]
     lib.lp_batch_destroy.argtypes = [P]
     lib.lp_batch_destroy.restype = None
     for name in ["lp_create", "lp_solve", "lp_iterate", "lp_get_solution", "lp_get_state",
@@ -143,7 +146,8 @@ def load(build_if_missing: bool = True):
                  "lp_normalized_gap_static", "lp_profile_kernel", "lp_select_omega",
                  "lp_solve_recorded", "lp_backward", "lp_batch_create",
                  "lp_batch_set_check_every", "lp_batch_solve", "lp_batch_iterate",
-                 "lp_batch_get_solution", "lp_batch_get_state", "lp_batch_get_info"]:
+                 "lp_batch_get_solution", "lp_batch_get_state", "lp_batch_get_info",
+                 "lp_batch_solve_recorded", "lp_batch_backward"]:
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -465,6 +469,17 @@ def lp_batch_get_info(h, count):
     return info, probs
 
 
+def lp_batch_solve_recorded(h, iters, stream=None):
+    return _check(load().lp_batch_solve_recorded(h, int(iters), _stream(stream)))
+
+
+def lp_batch_backward(h, dl_dx, dl_dy, dl_dc, dl_db, stream=None):
+    px, kx = _ptr(dl_dx, np.float64)
+    py, ky = _ptr(dl_dy, np.float64)
+    return _check(load().lp_batch_backward(h, px, py, _out_ptr(dl_dc), _out_ptr(dl_db),
+                                           _stream(stream)))
+
+
 def lp_batch_destroy(h):
     if h is not None and h.value:
         load().lp_batch_destroy(h)
@@ -547,6 +562,16 @@ class LPBatch:
                 np.empty(self.n), np.empty(self.m)]
         lp_batch_get_state(self.h, *arrs, stream=self.stream)
         return dict(zip(["x", "y", "xbar", "ybar", "x0", "y0"], arrs))
+
+    def solve_recorded(self, iters):
+        """Unrolled forward of exactly `iters` iterations, recorded for backward()."""
+        lp_batch_solve_recorded(self.h, iters, self.stream)
+
+    def backward(self, dl_dx=None, dl_dy=None):
+        """Gradients (dL/dc [n], dL/db [m]) of the recorded unrolled maps."""
+        dc, db = np.empty(self.n), np.empty(self.m)
+        lp_batch_backward(self.h, dl_dx, dl_dy, dc, db, self.stream)
+        return dc, db
 
     def info(self):
         """(batch summary, list of per-problem dicts)."""

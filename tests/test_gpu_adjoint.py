@@ -126,3 +126,116 @@ def test_backward_matches_implicit_kkt_gradient_on_the_face(oracle_mod):
         dc, db = np.empty(data.n), np.empty(data.m)
         lp.lp_backward(g.h, w, None, dc, db)
     assert np.linalg.norm(db - u) <= 1e-6 * np.linalg.norm(u)
+
+
+def _batch_boxes():
+    return [_box_lp(3), _box_lp(5), lpgen.box_standard_form(7, m=40, n=90, per_col=3)]
+
+
+def test_batch_backward_matches_oracle_finite_differences(oracle_mod):
+    """lp_batch_backward: every problem's gradient against central differences
+    of the oracle's unrolled map of that problem alone (its own restart
+    schedule), h = 1e-6."""
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_2105_12715_gb300 import lp
+
+    probs = _batch_boxes()
+    eta = 0.9 / max(oracle_mod.sigma_max(d) for d in probs)
+    K, iters = 32, 320
+    rng = np.random.default_rng(1)
+    wx = [rng.standard_normal(d.n) for d in probs]
+    wy = [0.5 * rng.standard_normal(d.m) for d in probs]
+    with lp.LPBatch(probs, eta=eta, check_every=K) as g:
+        g.solve_recorded(iters)
+        _, per = g.info()
+        st = g.state()
+        dc, db = g.backward(np.concatenate(wx), np.concatenate(wy))
+        st_after = g.state()
+    for key in st:  # the recorded state is left in place
+        np.testing.assert_array_equal(st[key], st_after[key])
+    co, ro = 0, 0
+    for k, d in enumerate(probs):
+        ref = oracle_mod.solve(d, eta, tol=1e-300, max_iter=iters, check_every=K)
+        flags = ref.trace[:, 2].astype(np.int8)
+        assert per[k]["restarts"] == ref.restarts == flags.sum() >= 1
+        np.testing.assert_allclose(st["xbar"][co:co + d.n], ref.xbar, rtol=0, atol=1e-9)
+
+        def loss(c, b):
+            dd = lpgen.LPData(**{**d.__dict__})
+            dd.c, dd.b = c, b
+            r = oracle_mod.solve(dd, eta, tol=1e-300, max_iter=iters, check_every=K,
+                                 restart_scheme=oracle_mod.RESTART_SCHEDULE, schedule=flags)
+            return wx[k] @ r.xbar + wy[k] @ r.ybar
+
+        h = 1e-6
+        for j in rng.choice(d.n, size=4, replace=False):
+            e = np.zeros(d.n)
+            e[j] = h
+            fd = (loss(d.c + e, d.b) - loss(d.c - e, d.b)) / (2 * h)
+            assert dc[co + j] == pytest.approx(fd, rel=1e-4, abs=1e-6), (k, "c", j)
+        for i in rng.choice(d.m, size=4, replace=False):
+            e = np.zeros(d.m)
+            e[i] = h
+            fd = (loss(d.c, d.b + e) - loss(d.c, d.b - e)) / (2 * h)
+            assert db[ro + i] == pytest.approx(fd, rel=1e-4, abs=1e-6), (k, "b", i)
+        co += d.n
+        ro += d.m
+
+
+def test_batch_backward_equals_single_problem_backward(oracle_mod):
+    """Each problem's batched gradient equals lp_backward on that problem alone."""
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_2105_12715_gb300 import lp
+
+    probs = _batch_boxes()
+    eta = 0.9 / max(oracle_mod.sigma_max(d) for d in probs)
+    K, iters = 32, 256
+    rng = np.random.default_rng(4)
+    wx = [rng.standard_normal(d.n) for d in probs]
+    with lp.LPBatch(probs, eta=eta, check_every=K) as g:
+        g.solve_recorded(iters)
+        dc, db = g.backward(np.concatenate(wx), None)
+    co, ro = 0, 0
+    for k, d in enumerate(probs):
+        with lp.LP(d, eta=eta, check_every=K) as s1:
+            lp.lp_solve_recorded(s1.h, iters)
+            c1, b1 = np.empty(d.n), np.empty(d.m)
+            lp.lp_backward(s1.h, wx[k], None, c1, b1)
+        np.testing.assert_allclose(dc[co:co + d.n], c1, rtol=1e-11, atol=1e-13)
+        np.testing.assert_allclose(db[ro:ro + d.m], b1, rtol=1e-11, atol=1e-13)
+        co += d.n
+        ro += d.m
+
+
+def test_batch_autograd_function(oracle_mod):
+    import torch
+
+    from paper_2105_12715_gb300.autodiff import unrolled_pdhg_batch
+
+    probs = _batch_boxes()
+    eta = 0.9 / max(oracle_mod.sigma_max(d) for d in probs)
+    c = torch.tensor(np.concatenate([d.c for d in probs]), dtype=torch.float64, device="cuda",
+                     requires_grad=True)
+    b = torch.tensor(np.concatenate([d.b for d in probs]), dtype=torch.float64, device="cuda",
+                     requires_grad=True)
+    w = torch.randn(c.shape[0], dtype=torch.float64, device="cuda",
+                    generator=torch.Generator("cuda").manual_seed(3))
+    xbar, ybar = unrolled_pdhg_batch(c, b, probs, 192, eta=eta, check_every=32)
+    (w * xbar).sum().backward()
+    # against the single-problem autograd path, problem by problem
+    from paper_2105_12715_gb300.autodiff import unrolled_pdhg
+
+    co, ro = 0, 0
+    for d in probs:
+        ck = torch.tensor(d.c, dtype=torch.float64, device="cuda", requires_grad=True)
+        bk = torch.tensor(d.b, dtype=torch.float64, device="cuda", requires_grad=True)
+        xk, _ = unrolled_pdhg(ck, bk, d, 192, eta=eta, check_every=32)
+        (w[co:co + d.n] * xk).sum().backward()
+        torch.testing.assert_close(c.grad[co:co + d.n], ck.grad, rtol=1e-11, atol=1e-13)
+        torch.testing.assert_close(b.grad[ro:ro + d.m], bk.grad, rtol=1e-11, atol=1e-13)
+        co += d.n
+        ro += d.m
