@@ -115,6 +115,8 @@ typedef struct {
   double last_radius;   /* its radius ||zbar - z^{n,0}|| */
   int64_t nnz_padded;   /* stored nonzeros of one copy of A including padding */
   int32_t n_long_rows, n_long_cols; /* rows of A / of A^T handled by a whole warp */
+  double setup_ms[4];   /* lp_create phases: input copy + validation, host layout (CSC,
+                           permutations, slices), device upload, power iteration */
 } lp_info;
 
 /* Defaults: beta = e^-1, K = 64, ADAPTIVE, tau0 = K, omega = 1, eta = 0

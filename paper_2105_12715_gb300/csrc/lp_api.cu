@@ -14,6 +14,7 @@
 // block of K iterations + check; lp_solve keeps two blocks in flight and
 // reads a 4-byte status per check.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -106,6 +107,7 @@ struct lp_problem {
   bool solved = false;
   int nsearch = 1;
   int grid_cap = 0;  // blocks of the per-slice iteration kernels (0: one warp per slice)
+  double setup_ms[4] = {0, 0, 0, 0};  // lp_create phases (lp_info.setup_ms)
 
   ~lp_problem() {
     if (ckpt) cudaFree(ckpt);
@@ -129,8 +131,8 @@ struct lp_problem {
     return LP_OK;
   }
 
-  template <class T>
-  lp_status upload(T **p, const std::vector<T> &h) {
+  template <class T, class Al>
+  lp_status upload(T **p, const std::vector<T, Al> &h) {
     lp_status s = alloc(p, (int64_t)h.size());
     if (s != LP_OK) return s;
     if (!h.empty()) LP_CU(cudaMemcpy(*p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
@@ -163,8 +165,10 @@ struct lp_problem {
     if ((s = upload(&ix, H.idx)) != LP_OK) return s;
     if ((s = upload(&vv, H.val)) != LP_OK) return s;
     if (with_f32) {
-      std::vector<float> hf(H.val.size());
-      for (size_t i = 0; i < hf.size(); ++i) hf[i] = (float)H.val[i];
+      uvec<float> hf(H.val.size());
+      parallel_for((int64_t)hf.size(), [&](int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi; ++i) hf[i] = (float)H.val[i];
+      });
       if ((s = upload(&vf, hf)) != LP_OK) return s;
     }
     M.valf = vf;
@@ -300,32 +304,32 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const double t_start = now_seconds();
 
-  // ---- copy in (host or device pointers) and validate
-  std::vector<int32_t> hrp32, hci;
-  std::vector<double> hv, hc, hb, hl, hu;
-  std::vector<int8_t> hrt;
+  // ---- inputs (host arrays read in place, device arrays copied) and validation
+  std::vector<int32_t> s_rp, s_ci;
+  std::vector<double> s_v, s_c, s_b, s_l, s_u;
+  std::vector<int8_t> s_rt;
   LP_CU(cudaStreamSynchronize(s));
-  if (!copy_in(hrp32, row_ptr, (int64_t)m + 1) || !copy_in(hci, col_idx, nnz) ||
-      !copy_in(hv, val, nnz) || !copy_in(hc, c, n) || !copy_in(hb, b, m) || !copy_in(hl, lb, n) ||
-      !copy_in(hu, ub, n) || !copy_in(hrt, row_type, m)) {
-    cudaGetLastError();
-    return fail(LP_ERR_INVALID_ARG, "could not read an input array (bad pointer?)");
-  }
+  bool readable = true;
+  const int32_t *hrp32 = host_view(row_ptr, (int64_t)m + 1, s_rp, &readable);
+  const int32_t *hci = host_view(col_idx, nnz, s_ci, &readable);
+  const double *hv = host_view(val, nnz, s_v, &readable);
+  const double *hc = host_view(c, n, s_c, &readable);
+  const double *hb = host_view(b, m, s_b, &readable);
+  const double *hl = host_view(lb, n, s_l, &readable);
+  const double *hu = host_view(ub, n, s_u, &readable);
+  const int8_t *hrt = host_view(row_type, m, s_rt, &readable);
+  if (!readable) return fail(LP_ERR_INVALID_ARG, "could not read an input array (bad pointer?)");
   if (hrp32[0] != 0) return fail(LP_ERR_INVALID_ARG, "row_ptr[0] must be 0");
   for (int32_t i = 0; i < m; ++i)
     if (hrp32[i + 1] < hrp32[i]) return fail(LP_ERR_INVALID_ARG, "row_ptr must be nondecreasing");
   if (hrp32[m] != nnz) return fail(LP_ERR_INVALID_ARG, "row_ptr[m] must equal nnz");
   {
-    std::vector<int32_t> mark(n, -1);
-    for (int32_t i = 0; i < m; ++i) {
-      for (int64_t p = hrp32[i]; p < hrp32[i + 1]; ++p) {
-        const int32_t j = hci[p];
-        if (j < 0 || j >= n) return fail(LP_ERR_INVALID_ARG, "col_idx out of range");
-        if (mark[j] == i) return fail(LP_ERR_INVALID_ARG, "duplicate column in a row");
-        mark[j] = i;
-        if (!std::isfinite(hv[p])) return fail(LP_ERR_INVALID_ARG, "non-finite matrix value");
-      }
-    }
+    std::atomic<int> bad{0};
+    parallel_for(nnz, [&](int64_t lo, int64_t hi) {
+      for (int64_t p = lo; p < hi; ++p)
+        if (!std::isfinite(hv[p])) bad.store(1, std::memory_order_relaxed);
+    });
+    if (bad.load()) return fail(LP_ERR_INVALID_ARG, "non-finite matrix value");
   }
   for (int32_t j = 0; j < n; ++j) {
     if (!std::isfinite(hc[j])) return fail(LP_ERR_INVALID_ARG, "non-finite objective c");
@@ -337,6 +341,12 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
     if (!std::isfinite(hb[i])) return fail(LP_ERR_INVALID_ARG, "non-finite right-hand side b");
     if (hrt[i] < LP_ROW_EQ || hrt[i] > LP_ROW_LE) return fail(LP_ERR_INVALID_ARG, "row_type must be 0, 1 or 2");
   }
+  // CSC copy (also checks the column indices and finds repeated columns in a row)
+  std::vector<int64_t> cp;
+  uvec<int32_t> ri;
+  uvec<double> cv;
+  if (!build_csc(m, n, hrp32, hci, hv, cp, ri, cv)) return fail(LP_ERR_INVALID_ARG, "col_idx out of range");
+  if (csc_has_duplicates(n, cp, ri)) return fail(LP_ERR_INVALID_ARG, "duplicate column in a row");
 
   std::unique_ptr<lp_problem> h(new lp_problem());
   h->m = m;
@@ -348,38 +358,25 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
   h->nsearch = (opt.restart_scheme == LP_RESTART_ADAPTIVE) ? 1
                : (opt.restart_scheme == LP_RESTART_FLEXIBLE) ? 2 : 0;
 
-  // ---- CSC by stable counting sort, permutations, SELL layouts
-  std::vector<int64_t> rp(m + 1), cp(n + 1, 0);
+  const double t_copied = now_seconds();
+
+  // ---- permutations by length (stable counting sorts), SELL layouts
+  std::vector<int64_t> rp((size_t)m + 1);
   for (int32_t i = 0; i <= m; ++i) rp[i] = hrp32[i];
-  for (int64_t p = 0; p < nnz; ++p) cp[hci[p] + 1]++;
-  for (int32_t j = 0; j < n; ++j) cp[j + 1] += cp[j];
-  std::vector<int32_t> ri(nnz);
-  std::vector<double> cv(nnz);
-  {
-    std::vector<int64_t> pos(cp.begin(), cp.end() - 1);
-    for (int32_t i = 0; i < m; ++i)
-      for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
-        const int64_t q = pos[hci[p]]++;
-        ri[q] = i;
-        cv[q] = hv[p];
-      }
-  }
   std::vector<int32_t> perm_y(m), perm_x(n), inv_y(m), inv_x(n);
-  for (int32_t i = 0; i < m; ++i) perm_y[i] = i;
-  for (int32_t j = 0; j < n; ++j) perm_x[j] = j;
-  std::stable_sort(perm_y.begin(), perm_y.end(),
-                   [&](int32_t a, int32_t bb) { return rp[a + 1] - rp[a] > rp[bb + 1] - rp[bb]; });
-  std::stable_sort(perm_x.begin(), perm_x.end(),
-                   [&](int32_t a, int32_t bb) { return cp[a + 1] - cp[a] > cp[bb + 1] - cp[bb]; });
+  sort_by_length_desc(rp.data(), 0, m, perm_y.data());
+  sort_by_length_desc(cp.data(), 0, n, perm_x.data());
   for (int32_t r = 0; r < m; ++r) inv_y[perm_y[r]] = r;
-  for (int32_t r = 0; r < n; ++r) inv_x[perm_x[r]] = r;
+  parallel_for(n, [&](int64_t lo, int64_t hi) {
+    for (int64_t r = lo; r < hi; ++r) inv_x[perm_x[r]] = (int32_t)r;
+  });
   HostSell HA, HAT;
   const LanePolicy policy{opt.long_row_threshold, opt.lane_steps, opt.single_lane_max};
   const int64_t target = (int64_t)opt.lane_auto * h->nsm;
   const LanePolicy pa = choose_policy(rp, perm_y, policy, target);
   const LanePolicy pat = choose_policy(cp, perm_x, policy, target);
   build_sell(m, n, rp, hci, hv, perm_y, inv_x, pa, HA);
-  build_sell(n, m, cp, ri, cv, perm_x, inv_y, pat, HAT);
+  build_sell(n, m, cp, ri.data(), cv.data(), perm_x, inv_y, pat, HAT);
   h->nnz_padded = (int64_t)HA.idx.size();
 
   // permuted vectors
@@ -394,6 +391,8 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
     pb[r] = hb[perm_y[r]];
     prt[r] = hrt[perm_y[r]];
   }
+
+  const double t_layout = now_seconds();
 
   // ---- device buffers
   lp_status e;
@@ -481,6 +480,9 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
   LP_CU(cudaEventCreateWithFlags(&h->ev[1], cudaEventDisableTiming));
   LP_CU(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
 
+  LP_CU(cudaDeviceSynchronize());
+  const double t_uploaded = now_seconds();
+
   // ---- device state: step sizes, norms, power iteration
   DevState hs{};
   hs.omega = opt.omega;
@@ -541,6 +543,11 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
     if (!(h->sigma_max > 0.0)) return fail(LP_ERR_NUMERICAL, "sigma_max(A) is zero or not finite; pass eta explicitly");
     h->eta = 0.9 / h->sigma_max;
   }
+  const double t_power = now_seconds();
+  h->setup_ms[0] = 1e3 * (t_copied - t_start);
+  h->setup_ms[1] = 1e3 * (t_layout - t_copied);
+  h->setup_ms[2] = 1e3 * (t_uploaded - t_layout);
+  h->setup_ms[3] = 1e3 * (t_power - t_uploaded);
   const double tau = h->eta / opt.omega, sigma = h->eta * opt.omega;
   LP_CU(cudaMemcpyAsync(&h->st->tau, &tau, sizeof(double), cudaMemcpyHostToDevice, s));
   LP_CU(cudaMemcpyAsync(&h->st->sigma, &sigma, sizeof(double), cudaMemcpyHostToDevice, s));
@@ -551,7 +558,6 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
   LP_CU(cudaGetLastError());
   if ((e = reset_state(h.get(), s)) != LP_OK) return e;
   LP_CU(cudaStreamSynchronize(s));
-  (void)t_start;
   *out = h.release();
   return LP_OK;
 }
@@ -705,6 +711,7 @@ lp_status lp_get_info(lp_handle h, lp_info *info) {
   info->nnz_padded = h->nnz_padded;
   info->n_long_rows = h->A.n_warp_rows;
   info->n_long_cols = h->AT.n_warp_rows;
+  for (int i = 0; i < 4; ++i) info->setup_ms[i] = h->setup_ms[i];
   return LP_OK;
 }
 

@@ -28,6 +28,7 @@
 // All reductions run in a fixed order: results are bitwise reproducible
 // for a given batch and launch configuration.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -1175,8 +1176,8 @@ struct lp_batch {
     return LP_OK;
   }
 
-  template <class T>
-  lp_status upload(T **p, const std::vector<T> &h) {
+  template <class T, class Al>
+  lp_status upload(T **p, const std::vector<T, Al> &h) {
     lp_status s = alloc(p, (int64_t)h.size());
     if (s != LP_OK) return s;
     if (!h.empty()) LP_CU(cudaMemcpy(*p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
@@ -1193,8 +1194,10 @@ struct lp_batch {
     if ((s = upload(&ix, H.idx)) != LP_OK) return s;
     if ((s = upload(&vv, H.val)) != LP_OK) return s;
     if (with_f32) {
-      std::vector<float> hf(H.val.size());
-      for (size_t q = 0; q < hf.size(); ++q) hf[q] = (float)H.val[q];
+      uvec<float> hf(H.val.size());
+      parallel_for((int64_t)hf.size(), [&](int64_t lo, int64_t hi) {
+        for (int64_t q = lo; q < hi; ++q) hf[q] = (float)H.val[q];
+      });
       if ((s = upload(&vf, hf)) != LP_OK) return s;
     }
     M.nrows = H.nrows;
@@ -1557,35 +1560,36 @@ lp_status lp_batch_create(int32_t count, const int32_t *host_row_start,
   if (!(tune.check_budget > 0.0)) return fail(LP_ERR_INVALID_ARG, "check_budget must be > 0");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
 
-  // ---- copy in and validate
-  std::vector<int32_t> hrp32, hci;
-  std::vector<double> hv, hc, hb, hl, hu;
-  std::vector<int8_t> hrt;
+  // ---- inputs (host arrays read in place, device arrays copied) and validation
+  std::vector<int32_t> s_rp, s_ci;
+  std::vector<double> s_v, s_c, s_b, s_l, s_u;
+  std::vector<int8_t> s_rt;
   LP_CU(cudaStreamSynchronize(s));
-  if (!copy_in(hrp32, row_ptr, (int64_t)m + 1) || !copy_in(hci, col_idx, nnz) ||
-      !copy_in(hv, val, nnz) || !copy_in(hc, c, n) || !copy_in(hb, b, m) || !copy_in(hl, lb, n) ||
-      !copy_in(hu, ub, n) || !copy_in(hrt, row_type, m)) {
-    cudaGetLastError();
-    return fail(LP_ERR_INVALID_ARG, "could not read an input array (bad pointer?)");
-  }
+  bool readable = true;
+  const int32_t *hrp32 = host_view(row_ptr, (int64_t)m + 1, s_rp, &readable);
+  const int32_t *hci = host_view(col_idx, nnz, s_ci, &readable);
+  const double *hv = host_view(val, nnz, s_v, &readable);
+  const double *hc = host_view(c, n, s_c, &readable);
+  const double *hb = host_view(b, m, s_b, &readable);
+  const double *hl = host_view(lb, n, s_l, &readable);
+  const double *hu = host_view(ub, n, s_u, &readable);
+  const int8_t *hrt = host_view(row_type, m, s_rt, &readable);
+  if (!readable) return fail(LP_ERR_INVALID_ARG, "could not read an input array (bad pointer?)");
   if (hrp32[0] != 0) return fail(LP_ERR_INVALID_ARG, "row_ptr[0] must be 0");
   for (int32_t i = 0; i < m; ++i)
     if (hrp32[i + 1] < hrp32[i]) return fail(LP_ERR_INVALID_ARG, "row_ptr must be nondecreasing");
   if (hrp32[m] != nnz) return fail(LP_ERR_INVALID_ARG, "row_ptr[m] must equal nnz");
   {
-    std::vector<int32_t> mark(n, -1);
-    for (int32_t k = 0; k < count; ++k) {
-      for (int32_t i = rs[k]; i < rs[k + 1]; ++i) {
-        for (int64_t p = hrp32[i]; p < hrp32[i + 1]; ++p) {
-          const int32_t j = hci[p];
-          if (j < cs[k] || j >= cs[k + 1])
-            return fail(LP_ERR_INVALID_ARG, "col_idx outside its problem's columns");
-          if (mark[j] == i) return fail(LP_ERR_INVALID_ARG, "duplicate column in a row");
-          mark[j] = i;
-          if (!std::isfinite(hv[p])) return fail(LP_ERR_INVALID_ARG, "non-finite matrix value");
+    std::atomic<int> outside{0}, nonfinite{0};
+    parallel_for(count, [&](int64_t k0, int64_t k1) {
+      for (int64_t k = k0; k < k1; ++k)
+        for (int64_t p = hrp32[rs[k]]; p < hrp32[rs[k + 1]]; ++p) {
+          if (hci[p] < cs[k] || hci[p] >= cs[k + 1]) outside.store(1, std::memory_order_relaxed);
+          if (!std::isfinite(hv[p])) nonfinite.store(1, std::memory_order_relaxed);
         }
-      }
-    }
+    }, 1);
+    if (outside.load()) return fail(LP_ERR_INVALID_ARG, "col_idx outside its problem's columns");
+    if (nonfinite.load()) return fail(LP_ERR_INVALID_ARG, "non-finite matrix value");
   }
   for (int32_t j = 0; j < n; ++j) {
     if (!std::isfinite(hc[j])) return fail(LP_ERR_INVALID_ARG, "non-finite objective c");
@@ -1597,6 +1601,11 @@ lp_status lp_batch_create(int32_t count, const int32_t *host_row_start,
     if (!std::isfinite(hb[i])) return fail(LP_ERR_INVALID_ARG, "non-finite right-hand side b");
     if (hrt[i] < LP_ROW_EQ || hrt[i] > LP_ROW_LE) return fail(LP_ERR_INVALID_ARG, "row_type must be 0, 1 or 2");
   }
+  std::vector<int64_t> cp;
+  uvec<int32_t> ri;
+  uvec<double> cv;
+  if (!build_csc(m, n, hrp32, hci, hv, cp, ri, cv)) return fail(LP_ERR_INVALID_ARG, "col_idx out of range");
+  if (csc_has_duplicates(n, cp, ri)) return fail(LP_ERR_INVALID_ARG, "duplicate column in a row");
 
   std::unique_ptr<lp_batch> h(new lp_batch());
   h->count = count;
@@ -1614,33 +1623,16 @@ lp_status lp_batch_create(int32_t count, const int32_t *host_row_start,
   h->unroll_cols = opt.spmv_unroll % 100;
   h->unroll_rows = opt.spmv_unroll_rows % 100;
 
-  // ---- CSC, per-problem permutations by length, sliced layouts
-  std::vector<int64_t> rp(m + 1), cp(n + 1, 0);
+  // ---- per-problem permutations by length (stable counting sorts), sliced layouts
+  std::vector<int64_t> rp((size_t)m + 1);
   for (int32_t i = 0; i <= m; ++i) rp[i] = hrp32[i];
-  for (int64_t p = 0; p < nnz; ++p) cp[hci[p] + 1]++;
-  for (int32_t j = 0; j < n; ++j) cp[j + 1] += cp[j];
-  std::vector<int32_t> ri(nnz);
-  std::vector<double> cv(nnz);
-  {
-    std::vector<int64_t> pos(cp.begin(), cp.end() - 1);
-    for (int32_t i = 0; i < m; ++i)
-      for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
-        const int64_t q = pos[hci[p]]++;
-        ri[q] = i;
-        cv[q] = hv[p];
-      }
-  }
   std::vector<int32_t> perm_y(m), perm_x(n), inv_y(m), inv_x(n);
-  std::iota(perm_y.begin(), perm_y.end(), 0);
-  std::iota(perm_x.begin(), perm_x.end(), 0);
-  for (int32_t k = 0; k < count; ++k) {
-    std::stable_sort(perm_y.begin() + rs[k], perm_y.begin() + rs[k + 1], [&](int32_t a, int32_t bb) {
-      return rp[a + 1] - rp[a] > rp[bb + 1] - rp[bb];
-    });
-    std::stable_sort(perm_x.begin() + cs[k], perm_x.begin() + cs[k + 1], [&](int32_t a, int32_t bb) {
-      return cp[a + 1] - cp[a] > cp[bb + 1] - cp[bb];
-    });
-  }
+  parallel_for(count, [&](int64_t k0, int64_t k1) {
+    for (int64_t k = k0; k < k1; ++k) {
+      sort_by_length_desc(rp.data(), rs[k], rs[k + 1], perm_y.data());
+      sort_by_length_desc(cp.data(), cs[k], cs[k + 1], perm_x.data());
+    }
+  }, 1);
   for (int32_t r = 0; r < m; ++r) inv_y[perm_y[r]] = r;
   for (int32_t r = 0; r < n; ++r) inv_x[perm_x[r]] = r;
   const std::vector<int32_t> brk_rows(rs.begin() + 1, rs.end() - 1);
@@ -1651,7 +1643,7 @@ lp_status lp_batch_create(int32_t count, const int32_t *host_row_start,
   const LanePolicy pa = choose_policy(rp, perm_y, policy, target, brk_rows);
   const LanePolicy pat = choose_policy(cp, perm_x, policy, target, brk_cols);
   build_sell(m, n, rp, hci, hv, perm_y, inv_x, pa, HA, brk_rows);
-  build_sell(n, m, cp, ri, cv, perm_x, inv_y, pat, HAT, brk_cols);
+  build_sell(n, m, cp, ri.data(), cv.data(), perm_x, inv_y, pat, HAT, brk_cols);
 
   // slice -> problem, problem -> slice ranges
   std::vector<BInst> hi(count);

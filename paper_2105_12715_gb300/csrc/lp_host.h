@@ -4,9 +4,13 @@
 #pragma once
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
+#include <new>
 #include <string>
+#include <thread>
+#include <utility>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -40,11 +44,138 @@ inline lp_status cuda_fail(cudaError_t e, const char *what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
   } while (0)
 
+// ---- host parallelism for the set-up (deterministic: fixed partitions)
+
+// Allocator whose construct() leaves elements uninitialized, so that
+// resize() of a large array the caller fills completely costs nothing.
+template <class T>
+struct UninitAlloc : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = UninitAlloc<U>;
+  };
+  UninitAlloc() = default;
+  template <class U>
+  UninitAlloc(const UninitAlloc<U> &) {}
+  template <class U>
+  void construct(U *) noexcept {}
+  template <class U, class... A>
+  void construct(U *p, A &&...a) {
+    ::new ((void *)p) U(std::forward<A>(a)...);
+  }
+};
+template <class T>
+using uvec = std::vector<T, UninitAlloc<T>>;
+
+inline int host_threads() {
+  static const int t = [] {
+    const unsigned h = std::thread::hardware_concurrency();
+    return (int)std::max(1u, std::min(h, 32u));
+  }();
+  return t;
+}
+
+// Runs f(t) for t = 0..nt-1, on nt threads (the calling thread takes the
+// chunks whose thread could not be started).
+template <class F>
+inline void run_threads(int nt, F f) {
+  if (nt <= 1) {
+    f(0);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve(nt - 1);
+  int started = 1;
+  try {
+    for (int t = 1; t < nt; ++t) {
+      th.emplace_back([&f, t] { f(t); });
+      started = t + 1;
+    }
+  } catch (...) {
+  }
+  f(0);
+  for (int t = started; t < nt; ++t) f(t);
+  for (auto &x : th) x.join();
+}
+
+// f(begin, end) over [0, n) in contiguous chunks, one per thread.
+template <class F>
+inline void parallel_for(int64_t n, F f, int64_t grain = 16384) {
+  const int nt = (int)std::min<int64_t>(host_threads(), std::max<int64_t>(1, n / grain));
+  run_threads(nt, [&](int t) { f(n * t / nt, n * (t + 1) / nt); });
+}
+
+// CSC copy (cp[n + 1], ri[nnz], cv[nnz]) of the CSR (rp[m + 1], ci, v) with
+// rows ascending within each column: a stable counting sort in which thread t
+// owns the columns [n t / T, n (t + 1) / T) and scans the whole CSR in row
+// order.  Returns false if a column index lies outside [0, n).
+inline bool build_csc(int32_t m, int32_t n, const int32_t *rp, const int32_t *ci, const double *v,
+                      std::vector<int64_t> &cp, uvec<int32_t> &ri, uvec<double> &cv) {
+  const int64_t nnz = rp[m];
+  cp.assign((size_t)n + 1, 0);
+  ri.resize((size_t)nnz);
+  cv.resize((size_t)nnz);
+  std::atomic<int> bad{0};
+  parallel_for(nnz, [&](int64_t lo, int64_t hi) {
+    for (int64_t p = lo; p < hi; ++p)
+      if (ci[p] < 0 || ci[p] >= n) bad.store(1, std::memory_order_relaxed);
+  });
+  if (bad.load()) return false;
+  const int nt = (int)std::min<int64_t>(host_threads(), std::max<int64_t>(1, nnz / 262144));
+  run_threads(nt, [&](int t) {
+    const int32_t lo = (int32_t)((int64_t)n * t / nt), hi = (int32_t)((int64_t)n * (t + 1) / nt);
+    for (int64_t p = 0; p < nnz; ++p) {
+      const int32_t j = ci[p];
+      if (j >= lo && j < hi) cp[(size_t)j + 1]++;
+    }
+  });
+  for (int32_t j = 0; j < n; ++j) cp[(size_t)j + 1] += cp[j];
+  run_threads(nt, [&](int t) {
+    const int32_t lo = (int32_t)((int64_t)n * t / nt), hi = (int32_t)((int64_t)n * (t + 1) / nt);
+    std::vector<int64_t> pos(cp.begin() + lo, cp.begin() + hi);
+    for (int32_t i = 0; i < m; ++i)
+      for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+        const int32_t j = ci[p];
+        if (j >= lo && j < hi) {
+          const int64_t q = pos[j - lo]++;
+          ri[q] = i;
+          cv[q] = v[p];
+        }
+      }
+  });
+  return true;
+}
+
+// True if some column of the CSC lists a row twice (rows are ascending, so
+// a repeat is adjacent): a column repeated within a row of the CSR.
+inline bool csc_has_duplicates(int32_t n, const std::vector<int64_t> &cp, const uvec<int32_t> &ri) {
+  std::atomic<int> dup{0};
+  parallel_for(n, [&](int64_t lo, int64_t hi) {
+    for (int64_t j = lo; j < hi; ++j)
+      for (int64_t p = cp[j] + 1; p < cp[j + 1]; ++p)
+        if (ri[p] == ri[p - 1]) dup.store(1, std::memory_order_relaxed);
+  });
+  return dup.load() != 0;
+}
+
+// perm[begin..end) <- begin..end-1 ordered by decreasing ptr[i+1] - ptr[i],
+// ties in index order (a stable counting sort on the length).
+template <class P>
+inline void sort_by_length_desc(const P *ptr, int32_t begin, int32_t end, int32_t *perm) {
+  if (end <= begin) return;
+  int64_t mx = 0;
+  for (int32_t i = begin; i < end; ++i) mx = std::max<int64_t>(mx, ptr[i + 1] - ptr[i]);
+  std::vector<int64_t> cnt((size_t)mx + 2, 0);
+  for (int32_t i = begin; i < end; ++i) cnt[(size_t)(mx - (ptr[i + 1] - ptr[i])) + 1]++;
+  for (size_t k = 1; k < cnt.size(); ++k) cnt[k] += cnt[k - 1];
+  for (int32_t i = begin; i < end; ++i) perm[begin + cnt[(size_t)(mx - (ptr[i + 1] - ptr[i]))]++] = i;
+}
+
 struct HostSell {
   int32_t nrows = 0, ncols = 0, nslices = 0, n_warp_rows = 0;
   std::vector<SliceInfo> info;
-  std::vector<int32_t> idx;
-  std::vector<double> val;
+  uvec<int32_t> idx;
+  uvec<double> val;
 };
 
 // Lanes per row: rows of at most single_max elements get one lane (no
@@ -114,7 +245,7 @@ inline LanePolicy choose_policy(const std::vector<int64_t> &ptr, const std::vect
 // it is full (32 / G rows), when the next row wants another G, or at a
 // break (no slice spans two batched problems).
 inline void build_sell(int32_t nrows, int32_t ncols, const std::vector<int64_t> &ptr,
-                       const std::vector<int32_t> &ind, const std::vector<double> &v,
+                       const int32_t *ind, const double *v,
                        const std::vector<int32_t> &perm, const std::vector<int32_t> &relabel,
                        const LanePolicy &policy, HostSell &S,
                        const std::vector<int32_t> &breaks = {}) {
@@ -143,21 +274,62 @@ inline void build_sell(int32_t nrows, int32_t ncols, const std::vector<int64_t> 
   }
   S.nslices = (int32_t)S.info.size();
   S.info.push_back(SliceInfo{off, nrows, 0});
-  S.idx.assign(off, 0);
-  S.val.assign(off, 0.0);
-  for (int32_t s = 0; s < S.nslices; ++s) {
-    const SliceInfo &a = S.info[s];
-    const int lg = a.len_g & 7, G = 1 << lg;
-    for (int32_t row = a.row0; row < S.info[s + 1].row0; ++row) {
-      const int64_t src = ptr[perm[row]];
-      const int64_t lane0 = (int64_t)(row - a.row0) * G;
-      for (int64_t k = 0; k < len(row); ++k) {
-        const int64_t dst = a.off + kWarp * (k >> lg) + lane0 + (k & (G - 1));
-        S.idx[dst] = relabel[ind[src + k]];
-        S.val[dst] = v[src + k];
+  S.idx.resize((size_t)off);
+  S.val.resize((size_t)off);
+  // slices in parallel, in chunks of about equal element counts; each slice
+  // zero-fills its region (padding) and writes its rows' elements
+  const int nt = (int)std::min<int64_t>(host_threads(), std::max<int64_t>(1, off / 65536));
+  run_threads(nt, [&](int t) {
+    const int64_t e_lo = off * t / nt, e_hi = off * (t + 1) / nt;
+    auto first_slice = [&](int64_t e) {  // first slice starting at or after element e
+      int32_t lo = 0, hi = S.nslices;
+      while (lo < hi) {
+        const int32_t mid = (lo + hi) / 2;
+        if (S.info[mid].off < e) lo = mid + 1;
+        else hi = mid;
+      }
+      return lo;
+    };
+    const int32_t s_lo = t == 0 ? 0 : first_slice(e_lo);
+    const int32_t s_hi = t == nt - 1 ? S.nslices : first_slice(e_hi);
+    for (int32_t sl = s_lo; sl < s_hi; ++sl) {
+      const SliceInfo &a = S.info[sl];
+      const int lg = a.len_g & 7, G = 1 << lg;
+      std::fill(S.idx.begin() + a.off, S.idx.begin() + S.info[sl + 1].off, 0);
+      std::fill(S.val.begin() + a.off, S.val.begin() + S.info[sl + 1].off, 0.0);
+      for (int32_t row = a.row0; row < S.info[sl + 1].row0; ++row) {
+        const int64_t src = ptr[perm[row]];
+        const int64_t lane0 = (int64_t)(row - a.row0) * G;
+        for (int64_t k = 0; k < len(row); ++k) {
+          const int64_t dst = a.off + kWarp * (k >> lg) + lane0 + (k & (G - 1));
+          S.idx[dst] = relabel[ind[src + k]];
+          S.val[dst] = v[src + k];
+        }
       }
     }
+  });
+}
+
+// A host-readable view of count elements at src: device memory is copied
+// into storage, host memory (pageable, pinned or managed) is read in place.
+// *ok becomes false if src cannot be read.
+template <class T>
+inline const T *host_view(const T *src, int64_t count, std::vector<T> &storage, bool *ok) {
+  if (count <= 0) return src;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, src) != cudaSuccess) {
+    cudaGetLastError();
+    *ok = false;
+    return nullptr;
   }
+  if (at.type != cudaMemoryTypeDevice) return src;
+  storage.resize((size_t)count);
+  if (cudaMemcpy(storage.data(), src, sizeof(T) * count, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    *ok = false;
+    return nullptr;
+  }
+  return storage.data();
 }
 
 template <class T>

@@ -45,7 +45,8 @@ class lp_info(C.Structure):
                 ("eta", C.c_double), ("sigma_max", C.c_double), ("omega", C.c_double),
                 ("tau", C.c_double), ("sigma", C.c_double), ("rho_stored", C.c_double),
                 ("last_rho", C.c_double), ("last_radius", C.c_double),
-                ("nnz_padded", C.c_int64), ("n_long_rows", C.c_int32), ("n_long_cols", C.c_int32)]
+                ("nnz_padded", C.c_int64), ("n_long_rows", C.c_int32), ("n_long_cols", C.c_int32),
+                ("setup_ms", C.c_double * 4)]
 
 
 class lp_batch_tuning(C.Structure):
@@ -330,6 +331,7 @@ class Info:
     nnz_padded: int
     n_long_rows: int
     n_long_cols: int
+    setup_ms: tuple = ()
 
     @property
     def rel_kkt(self) -> float:
@@ -391,7 +393,8 @@ class LP:
         i = lp_get_info(self.h)
         return Info(i.iters, i.restarts, i.checks, i.status, i.returned, tuple(i.kkt_avg),
                     tuple(i.kkt_cur), i.eta, i.sigma_max, i.omega, i.tau, i.sigma, i.rho_stored,
-                    i.last_rho, i.last_radius, i.nnz_padded, i.n_long_rows, i.n_long_cols)
+                    i.last_rho, i.last_radius, i.nnz_padded, i.n_long_rows, i.n_long_cols,
+                    tuple(i.setup_ms))
 
     def trace(self, capacity=1 << 20):
         return lp_get_trace(self.h, capacity)
