@@ -535,6 +535,26 @@ def run_ours(args):
                          "status": lp.STATUS_NAMES.get(st, st),
                          "rel_kkt": min(it.kkt_avg[4], it.kkt_cur[4])}
 
+    # time to relative KKT 1e-8 on a smaller LP that reaches it in seconds (FP64 vs mixed)
+    ttk8 = None
+    if not args.no_ttk:
+        from paper_2105_12715_gb300 import lpgen
+
+        small = lpgen.large_mixed(5, m=5000, n=25000)
+        ttk8 = {"lp": f"large_mixed m={small.m} n={small.n} nnz={small.nnz} seed 5", "tol": 1e-8}
+        for name, prec in (("fp64", lp.LP_PRECISION_FP64), ("mixed", lp.LP_PRECISION_MIXED)):
+            barrier()
+            t0 = time.perf_counter()
+            gt = lp.LP(small, stream=stream, check_every=K_CHECK, max_iter=3_000_000, precision=prec)
+            st = gt.solve(1e-8)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            it = gt.info()
+            gt.close()
+            ttk8[name] = {"seconds": dt, "iters": it.iters, "restarts": it.restarts,
+                          "status": lp.STATUS_NAMES.get(st, st),
+                          "rel_kkt": min(it.kkt_avg[4], it.kkt_cur[4])}
+
     # multicommodity flow LP (300 x 300 grid, 8 commodities): FP64 vs mixed throughput
     mcf = None
     if not args.no_mcf:
@@ -649,6 +669,7 @@ def run_ours(args):
                             "dual_kernel_ms": dual_ms, "dual_algorithmic_bytes": dual_b,
                             "gather_bound": gather_bound},
                "clocks": clocks, "e2e": e2e, "mixed": mixed, "time_to_kkt": ttk,
+               "time_to_kkt_1e8": ttk8,
                "multicommodity": mcf, "adjoint": adjoint, "batched": batched,
                "solver": {"eta": info0.eta, "sigma_max": info0.sigma_max,
                           "iters_done": info.iters, "restarts": info.restarts,
@@ -666,6 +687,14 @@ def run_ours(args):
                 ttk["oracle_extrapolated_seconds"] = ttk["fp64"]["iters"] / rate
                 ttk["oracle_note"] = ("oracle time = GPU FP64 iteration count / oracle iterations/s "
                                       "measured over 256 iterations (extrapolation)")
+            if ttk8 is not None:
+                import oracle
+
+                t0 = time.perf_counter()
+                r = oracle.solve(small, 0.9 / 11.0, tol=1e-300, max_iter=1024, check_every=K_CHECK)
+                rate = r.iters / (time.perf_counter() - t0)
+                ttk8["oracle_iters_per_s"] = rate
+                ttk8["oracle_extrapolated_seconds"] = ttk8["fp64"]["iters"] / rate
         print(json.dumps(out))
     if ws > 1:
         torch.distributed.barrier()

@@ -284,3 +284,57 @@ def test_batch_mixed_full_solve_reaches_fp64_tolerance(lpm, oracle_mod):
         assert kk["rel"] <= 1e-8 * (1 + 1e-6), k
         assert kk["pobj"] == pytest.approx(d.obj_star, rel=1e-7, abs=1e-7)
         assert np.all(xs[k] >= d.lb)
+
+
+def test_batch_of_many_tiny_problems(lpm, oracle_mod):
+    """1,500 problems (more than one 1,024-thread block of the work-list scan,
+    down to 3 rows): sampled problems against the oracle after 96 iterations."""
+    rng = np.random.default_rng(9)
+    probs = [lpgen.tiny_standard_form(int(s), m=int(m), n=2 * int(m), per_col=2)
+             for s, m in zip(range(1500), rng.integers(3, 25, 1500))]
+    eta = 0.1
+    with lpm.LPBatch(probs, eta=eta, check_every=32, max_iter=96) as g:
+        g.solve(1e-300)
+        summary, per = g.info()
+        st = g.state()
+    assert summary["count"] == 1500 and summary["running"] == 0
+    for k in [0, 1, 777, 1023, 1024, 1025, 1499]:
+        d = probs[k]
+        ref = osolve(oracle_mod, d, eta, tol=1e-300, max_iter=96, check_every=32)
+        assert per[k]["iters"] == 96 and per[k]["restarts"] == ref.restarts, k
+        xs = slice(int(g.col_start[k]), int(g.col_start[k + 1]))
+        ys = slice(int(g.row_start[k]), int(g.row_start[k + 1]))
+        close(st["x"][xs], ref.x, TOL, f"{k} x")
+        close(st["y"][ys], ref.y, TOL, f"{k} y")
+        close(st["xbar"][xs], ref.xbar, TOL, f"{k} xbar")
+
+
+def test_batch_device_input_arrays(lpm):
+    """The batch reads device arrays as well as host arrays (same result)."""
+    import torch
+
+    probs = mixed_batch()[:3]
+    with lpm.LPBatch(probs, eta=0.05, check_every=32, max_iter=128) as g:
+        g.solve(1e-300)
+        want = g.state()
+        rs, cs = g.row_start, g.col_start
+    ms = [d.m for d in probs]
+    rp = np.concatenate([[0]] + [np.asarray(d.row_ptr[1:], np.int64) + o for d, o in
+                                 zip(probs, np.cumsum([0] + [d.nnz for d in probs])[:-1])])
+    ci = np.concatenate([np.asarray(d.col_idx, np.int64) + c0 for d, c0 in zip(probs, cs[:-1])])
+    cat = lambda f, dt: torch.as_tensor(np.concatenate([np.asarray(getattr(d, f), dt) for d in probs])).cuda()
+    opt = lpm.lp_default_options()
+    opt.eta, opt.check_every, opt.max_iter = 0.05, 32, 128
+    h = lpm.lp_batch_create(rs, cs, int(rp[-1]), torch.as_tensor(rp.astype(np.int32)).cuda(),
+                            torch.as_tensor(ci.astype(np.int32)).cuda(), cat("val", np.float64),
+                            cat("c", np.float64), cat("b", np.float64), cat("lb", np.float64),
+                            cat("ub", np.float64), cat("row_type", np.int8), opt)
+    try:
+        lpm.lp_batch_solve(h, 1e-300)
+        got = {k: np.empty_like(v) for k, v in want.items()}
+        lpm.lp_batch_get_state(h, got["x"], got["y"], got["xbar"], got["ybar"], got["x0"], got["y0"])
+    finally:
+        lpm.lp_batch_destroy(h)
+    for k in want:
+        np.testing.assert_array_equal(got[k], want[k])
+    assert sum(ms) == int(rs[-1])
