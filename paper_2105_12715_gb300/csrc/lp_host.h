@@ -332,12 +332,6 @@ inline const T *host_view(const T *src, int64_t count, std::vector<T> &storage, 
   return storage.data();
 }
 
-template <class T>
-inline bool copy_in(std::vector<T> &dst, const T *src, int64_t count) {
-  dst.resize(count);
-  if (count == 0) return true;
-  return cudaMemcpy(dst.data(), src, sizeof(T) * count, cudaMemcpyDefault) == cudaSuccess;
-}
 
 inline lp_status validate_options(const lp_options &o) {
   if (!(o.beta > 0.0 && o.beta < 1.0)) return fail(LP_ERR_INVALID_ARG, "beta must lie in (0, 1)");
