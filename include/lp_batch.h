@@ -111,6 +111,11 @@ lp_status lp_batch_create(int32_t count, const int32_t *host_row_start,
  * state to the projection of zero.  Used to reproduce a schedule. */
 lp_status lp_batch_set_check_every(lp_batch_handle h, const int32_t *host_k, void *cuda_stream);
 
+/* Warm start: every problem restarts Algorithm 1 from z^{0,0} = proj(x, y)
+ * (concatenated in the caller's order, host or device; NULL = zero), with its
+ * counters and restart state reset.  Synchronizes the stream. */
+lp_status lp_batch_set_state(lp_batch_handle h, const double *x, const double *y, void *cuda_stream);
+
 /*
  * Runs every problem that has not met the tolerance (and has not failed)
  * until its relative KKT error is <= tol at one of its checks, or until it

@@ -1352,7 +1352,8 @@ lp_status batch_build_graph(lp_batch *h) {
 
 // Resets every problem's Algorithm-1 state to z^{0,0} = proj(0) (status
 // running, counters zero), the averaging weights and the work lists.
-lp_status batch_reset(lp_batch *h, cudaStream_t s) {
+lp_status batch_reset(lp_batch *h, cudaStream_t s, const double *x_start = nullptr,
+                      const double *y_start = nullptr) {
   std::vector<BInst> hi(h->count);
   LP_CU(cudaMemcpyAsync(hi.data(), h->I, sizeof(BInst) * h->count, cudaMemcpyDeviceToHost, s));
   LP_CU(cudaStreamSynchronize(s));
@@ -1370,8 +1371,19 @@ lp_status batch_reset(lp_batch *h, cudaStream_t s) {
     B.mix_s = 1.0;
   }
   LP_CU(cudaMemcpyAsync(h->I, hi.data(), sizeof(BInst) * h->count, cudaMemcpyHostToDevice, s));
-  launch_fill(h->v.x, 0.0, h->n, s);
-  launch_fill(h->v.y, 0.0, h->m, s);
+  // z^{0,0} = proj(start): the caller's point (caller order, host or device) or zero
+  if (x_start) {
+    LP_CU(cudaMemcpyAsync(h->tmp, x_start, sizeof(double) * h->n, cudaMemcpyDefault, s));
+    launch_gather(h->v.x, h->tmp, h->perm_x, h->n, s);
+  } else {
+    launch_fill(h->v.x, 0.0, h->n, s);
+  }
+  if (y_start && h->m > 0) {
+    LP_CU(cudaMemcpyAsync(h->tmp, y_start, sizeof(double) * h->m, cudaMemcpyDefault, s));
+    launch_gather(h->v.y, h->tmp, h->perm_y, h->m, s);
+  } else {
+    launch_fill(h->v.y, 0.0, h->m, s);
+  }
   launch_project(h->v, h->n, h->m, s);
   if (h->mixed) {  // correction data at the starting point, dz = 0, s = 1
     launch_residuals(h->A, h->AT, h->v, h->mv, h->n, h->m, s);
@@ -1912,6 +1924,13 @@ lp_status lp_batch_create(int32_t count, const int32_t *host_row_start,
   h->setup_ms = ms_since(t_start);
   *out = h.release();
   return LP_OK;
+}
+
+lp_status lp_batch_set_state(lp_batch_handle h, const double *x, const double *y,
+                             void *cuda_stream) {
+  err_msg().clear();
+  if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
+  return batch_reset(h, static_cast<cudaStream_t>(cuda_stream), x, y);
 }
 
 lp_status lp_batch_set_check_every(lp_batch_handle h, const int32_t *host_k, void *cuda_stream) {

@@ -79,7 +79,7 @@ EXPORTED = ["lp_default_options", "lp_create", "lp_solve", "lp_iterate", "lp_get
             "lp_batch_default_tuning", "lp_batch_create", "lp_batch_set_check_every",
             "lp_batch_solve", "lp_batch_iterate", "lp_batch_get_solution", "lp_batch_get_state",
             "lp_batch_get_info", "lp_batch_solve_recorded", "lp_batch_backward",
-            "lp_batch_destroy"]
+            "lp_batch_set_state", "lp_batch_destroy"]
 
 _lib = None
 
@@ -139,6 +139,7 @@ def load(build_if_missing: bool = True):
     lib.lp_batch_get_state.argtypes = [P, P, P, P, P, P, P, P]
     lib.lp_batch_get_info.argtypes = [P, C.POINTER(lp_batch_info), P, I32]
     lib.lp_batch_solve_recorded.argtypes = [P, I64, P]
+    lib.lp_batch_set_state.argtypes = [P, P, P, P]
     lib.lp_batch_backward.argtypes = [P, P, P, P, P, P]
     lib.lp_batch_destroy.argtypes = [P]
     lib.lp_batch_destroy.restype = None
@@ -148,7 +149,7 @@ def load(build_if_missing: bool = True):
                  "lp_solve_recorded", "lp_backward", "lp_batch_create",
                  "lp_batch_set_check_every", "lp_batch_solve", "lp_batch_iterate",
                  "lp_batch_get_solution", "lp_batch_get_state", "lp_batch_get_info",
-                 "lp_batch_solve_recorded", "lp_batch_backward"]:
+                 "lp_batch_solve_recorded", "lp_batch_backward", "lp_batch_set_state"]:
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -483,6 +484,12 @@ def lp_batch_backward(h, dl_dx, dl_dy, dl_dc, dl_db, stream=None):
                                            _stream(stream)))
 
 
+def lp_batch_set_state(h, x=None, y=None, stream=None):
+    px, kx = _ptr(x, np.float64)
+    py, ky = _ptr(y, np.float64)
+    return _check(load().lp_batch_set_state(h, px, py, _stream(stream)))
+
+
 def lp_batch_destroy(h):
     if h is not None and h.value:
         load().lp_batch_destroy(h)
@@ -547,6 +554,10 @@ class LPBatch:
 
     def iterate(self, n_blocks, tol=1e-8):
         return lp_batch_iterate(self.h, n_blocks, tol, self.stream)
+
+    def set_state(self, x=None, y=None):
+        """Warm start of every problem from proj(x, y) (concatenated vectors)."""
+        lp_batch_set_state(self.h, x, y, self.stream)
 
     def set_check_every(self, ks):
         lp_batch_set_check_every(self.h, ks, self.stream)

@@ -338,3 +338,29 @@ def test_batch_device_input_arrays(lpm):
     for k in want:
         np.testing.assert_array_equal(got[k], want[k])
     assert sum(ms) == int(rs[-1])
+
+
+def test_batch_warm_start_matches_oracle(lpm, oracle_mod):
+    """lp_batch_set_state: every problem restarts from the projection of the
+    given point (random, partly outside the bounds) and follows the oracle
+    started there."""
+    probs = mixed_batch()[:4]
+    eta = common_eta(oracle_mod, probs)
+    starts = [lpgen.random_state(d, 20 + k) for k, d in enumerate(probs)]
+    x0 = np.concatenate([s[0] for s in starts]) * 1.5  # some coordinates leave the box
+    y0 = np.concatenate([s[1] for s in starts])
+    with lpm.LPBatch(probs, eta=eta, check_every=32, max_iter=160) as g:
+        g.set_state(x0, y0)
+        g.solve(1e-300)
+        sts = states_of(g, probs)
+    co, ro = 0, 0
+    for k, d in enumerate(probs):
+        xs = np.clip(x0[co:co + d.n], d.lb, d.ub)
+        ys = y0[ro:ro + d.m].copy()
+        ys[d.row_type == 1] = np.maximum(ys[d.row_type == 1], 0.0)
+        ys[d.row_type == 2] = np.minimum(ys[d.row_type == 2], 0.0)
+        ref = oracle_mod.solve(d, eta, tol=1e-300, max_iter=160, check_every=32, x_init=xs,
+                               y_init=ys)
+        compare(sts[k], ref, TOL, f"problem {k}")
+        co += d.n
+        ro += d.m
