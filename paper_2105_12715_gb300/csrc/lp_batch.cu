@@ -12,19 +12,26 @@
 //   b_primal / b_dual (x K_base): one warp per slice of the running
 //       problems' work list, with that problem's tau or sigma and averaging
 //       weight 1 / (t + k + 1) -- the fused step and average of the
-//       single-problem kernels;
+//       single-problem kernels (FP32 correction steps in mixed precision),
+//       launched with programmatic dependent launch;
 //   b_pre_check: counters; a problem is due for its check every K_k
 //       iterations (K_k a multiple of K_base);
 //   b_check (columns, rows): the check epilogues on the due problems'
-//       slices, one fixed-order partial sum per slice and quantity;
+//       slices, each warp a chunk of 8 slices of one problem, one
+//       fixed-order partial sum per chunk and quantity;
 //   b_finalize: one block per due problem: its sums, relative KKT,
 //       termination, radius, search setup;
-//   b_search: one block per due problem: the whole multiplier search of
-//       Section 6.3 (8 radix passes over the breakpoints' bit patterns,
-//       shared-memory histograms per warp, bracket selection in-block);
-//   b_decide: restart rule, counters, next averaging weights, running count;
+//   b_search: one block (or an 8-block cluster for large problems) per due
+//       problem: the multiplier search of Section 6.3 (radix passes over
+//       the breakpoints' bit patterns from their common prefix down,
+//       per-warp histograms, per-warp candidate lists after the first pass,
+//       bracket selection in-block);
+//   b_decide: restart rule, counters, running count (one thread per problem);
 //   b_restart_copy: z^{n+1,0} <- zbar, z <- zbar for restarting problems;
-//   b_worklist: the next block's slice lists (running problems only).
+//   b_list_scan / b_list_fill: the next block's slice work lists and
+//       averaging weights (running problems only).
+// Also here: the batch tuner, mixed precision (combine / recenter per
+// problem), and the recorded forward and adjoint of the unrolled maps.
 // All reductions run in a fixed order: results are bitwise reproducible
 // for a given batch and launch configuration.
 #include <algorithm>
