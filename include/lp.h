@@ -99,6 +99,10 @@ typedef struct {
   int32_t lane_auto;      /* > 0: per matrix, halve single_lane_max and lane_steps until the
                              layout has at least lane_auto x (SM count) slices (warps); 0: use
                              the given lane policy as is (32) */
+  int32_t autotune;       /* 1: at lp_create, time every unroll variant of the column and row
+                             passes on this problem and keep the fastest (overrides spmv_unroll
+                             and spmv_unroll_rows; results do not depend on the variant: every
+                             variant sums each row in the same order); 0: use them as given (1) */
 } lp_options;
 
 typedef struct {
@@ -117,10 +121,11 @@ typedef struct {
   int32_t n_long_rows, n_long_cols; /* rows of A / of A^T handled by a whole warp */
   double setup_ms[4];   /* lp_create phases: input copy + validation, host layout (CSC,
                            permutations, slices), device upload, power iteration */
+  int32_t spmv_unroll, spmv_unroll_rows; /* kernel variants in use (tuned or given) */
 } lp_info;
 
 /* Defaults: beta = e^-1, K = 64, ADAPTIVE, tau0 = K, omega = 1, eta = 0
- * (auto), power_iters = 5000, power_tol = 1e-10, max_iter = 1e7. */
+ * (auto), power_iters = 5000, power_tol = 1e-10, max_iter = 1e7, autotune = 1. */
 void lp_default_options(lp_options *opt);
 
 /*

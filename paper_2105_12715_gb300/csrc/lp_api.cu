@@ -220,8 +220,8 @@ lp_status reset_state(lp_problem *h, cudaStream_t s) {
 
 void launch_iteration(lp_problem *h, int k, cudaStream_t s) {
   if (h->mixed) {
-    launch_primal_mix(h->AT, h->mv, h->st, h->w, k, s);
-    launch_dual_mix(h->A, h->mv, h->v, h->st, h->w, k, s);
+    launch_primal_mix(h->AT, h->mv, h->st, h->w, k, h->opt.spmv_unroll, s);
+    launch_dual_mix(h->A, h->mv, h->v, h->st, h->w, k, h->opt.spmv_unroll_rows, s);
   } else if (h->opt.spmv_mode == 1) {
     launch_primal_stream(h->AT, h->PAT, h->v, h->st, h->w, k, s);
     launch_dual_stream(h->A, h->PA, h->v, h->st, h->w, k, s);
@@ -254,6 +254,56 @@ lp_status set_run_params(lp_problem *h, double tol, cudaStream_t s) {
   return LP_OK;
 }
 
+// Kernel-variant tuner (lp_options.autotune): on this problem, times every
+// unroll variant of the column pass, then of the row pass (one warm-up and
+// four timed launches each, CUDA events on the stream) and keeps the
+// fastest.  Every variant sums each row in the same order, so the choice
+// changes speed, not results.  The launches advance the iterate: the caller
+// resets the state afterwards.
+lp_status tune_variants(lp_problem *h, cudaStream_t s) {
+  if (h->opt.spmv_mode != 0) return LP_OK;
+  const int cands[4] = {-2, -4, 2, 4};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  LP_CU(cudaEventCreate(&e0));
+  LP_CU(cudaEventCreate(&e1));
+  lp_status st = LP_OK;
+  for (int pass = 0; pass < 2 && st == LP_OK; ++pass) {
+    int32_t &u = pass ? h->opt.spmv_unroll_rows : h->opt.spmv_unroll;
+    int best_u = u;
+    float best = 1e30f;
+    for (int c : cands) {
+      u = c;
+      for (int r = 0; r < 5; ++r) {
+        if (r == 1) cudaEventRecord(e0, s);
+        if (h->mixed) {
+          if (pass == 0) launch_primal_mix(h->AT, h->mv, h->st, h->w, 0, u, s);
+          else launch_dual_mix(h->A, h->mv, h->v, h->st, h->w, 0, u, s);
+        } else if (pass == 0) {
+          launch_primal_step(h->AT, h->v, h->st, h->w, 0, u, h->grid_cap, s);
+        } else {
+          launch_dual_step(h->A, h->v, h->st, h->w, 0, u, h->grid_cap, s);
+        }
+      }
+      cudaEventRecord(e1, s);
+      float ms = 0.0f;
+      cudaError_t err = cudaEventSynchronize(e1);
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+      if (err != cudaSuccess) {
+        st = cuda_fail(err, "variant tuning");
+        break;
+      }
+      if (ms < best) {
+        best = ms;
+        best_u = c;
+      }
+    }
+    u = best_u;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
+
 }  // namespace
 
 extern "C" {
@@ -279,6 +329,7 @@ void lp_default_options(lp_options *o) {
   o->single_lane_max = 64;
   o->spmv_mode = 0;
   o->lane_auto = 32;
+  o->autotune = 1;
 }
 
 const char *lp_last_error(void) { return err_msg().c_str(); }
@@ -551,6 +602,7 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
   const double tau = h->eta / opt.omega, sigma = h->eta * opt.omega;
   LP_CU(cudaMemcpyAsync(&h->st->tau, &tau, sizeof(double), cudaMemcpyHostToDevice, s));
   LP_CU(cudaMemcpyAsync(&h->st->sigma, &sigma, sizeof(double), cudaMemcpyHostToDevice, s));
+  if (opt.autotune && (e = tune_variants(h.get(), s)) != LP_OK) return e;
   // z^{0,0} = proj(0)
   launch_fill(h->v.x, 0.0, n, s);
   launch_fill(h->v.y, 0.0, m, s);
@@ -711,6 +763,8 @@ lp_status lp_get_info(lp_handle h, lp_info *info) {
   info->nnz_padded = h->nnz_padded;
   info->n_long_rows = h->A.n_warp_rows;
   info->n_long_cols = h->AT.n_warp_rows;
+  info->spmv_unroll = h->opt.spmv_unroll;
+  info->spmv_unroll_rows = h->opt.spmv_unroll_rows;
   for (int i = 0; i < 4; ++i) info->setup_ms[i] = h->setup_ms[i];
   return LP_OK;
 }
@@ -982,8 +1036,8 @@ lp_status lp_profile_kernel(lp_handle h, int32_t which, int32_t reps, void *cuda
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   for (int32_t r = 0; r < reps; ++r) {
     if (h->mixed) {
-      if (which == 0) launch_primal_mix(h->AT, h->mv, h->st, h->w, 0, s);
-      else launch_dual_mix(h->A, h->mv, h->v, h->st, h->w, 0, s);
+      if (which == 0) launch_primal_mix(h->AT, h->mv, h->st, h->w, 0, h->opt.spmv_unroll, s);
+      else launch_dual_mix(h->A, h->mv, h->v, h->st, h->w, 0, h->opt.spmv_unroll_rows, s);
     } else if (h->opt.spmv_mode == 1) {
       if (which == 0) launch_primal_stream(h->AT, h->PAT, h->v, h->st, h->w, 0, s);
       else launch_dual_stream(h->A, h->PA, h->v, h->st, h->w, 0, s);

@@ -216,9 +216,9 @@ void launch_norms(const DevVecs &v, DevState *st, double *partials, int pstride,
                   int grid, int n, int m, cudaStream_t s);
 int check_grid_for(const SellMat &A, int num_sms);
 void launch_primal_mix(const SellMat &AT, const MixVecs &mv, DevState *st, const double *w,
-                       int k, cudaStream_t s);
+                       int k, int unroll, cudaStream_t s);
 void launch_dual_mix(const SellMat &A, const MixVecs &mv, const DevVecs &v, DevState *st,
-                     const double *w, int k, cudaStream_t s);
+                     const double *w, int k, int unroll, cudaStream_t s);
 void launch_combine(const DevVecs &v, const MixVecs &mv, DevState *st, int n, int m, int force,
                     cudaStream_t s);
 void launch_recenter(const DevVecs &v, const MixVecs &mv, DevState *st, int n, int m, int force,

@@ -1099,16 +1099,40 @@ void launch_check(const SellMat &A, const SellMat &AT, const DevVecs &v, DevStat
   }
 }
 
+template <int U, bool PIPE>
+void primal_mix_launch(int g, cudaStream_t s, const SellMat &AT, const float *dy,
+                       const PrimalMixEpi &epi, DevState *st, const double *w, int k) {
+  launch_pdl(primal_mix_kernel<U, PIPE>, g, kBlock, s, AT, dy, epi, st, w, k);
+}
+
+template <int U, bool PIPE>
+void dual_mix_launch(int g, cudaStream_t s, const SellMat &A, const float *dxhat,
+                     const DualMixEpi &epi, DevState *st, const double *w, int k) {
+  launch_pdl(dual_mix_kernel<U, PIPE>, g, kBlock, s, A, dxhat, epi, st, w, k);
+}
+
 void launch_primal_mix(const SellMat &AT, const MixVecs &mv, DevState *st, const double *w,
-                       int k, cudaStream_t s) {
+                       int k, int unroll, cudaStream_t s) {
   PrimalMixEpi epi{mv.cf, mv.lf, mv.uf, mv.dx, mv.dxhat, mv.dxbar, 0.0f, 0.0};
-  launch_pdl(primal_mix_kernel<2, true>, item_grid(AT), kBlock, s, AT, mv.dy, epi, st, w, k);
+  const int g = item_grid(AT);
+  switch (unroll % 100) {
+    case 2: primal_mix_launch<2, false>(g, s, AT, mv.dy, epi, st, w, k); break;
+    case 4: primal_mix_launch<4, false>(g, s, AT, mv.dy, epi, st, w, k); break;
+    case -4: primal_mix_launch<4, true>(g, s, AT, mv.dy, epi, st, w, k); break;
+    default: primal_mix_launch<2, true>(g, s, AT, mv.dy, epi, st, w, k); break;
+  }
 }
 
 void launch_dual_mix(const SellMat &A, const MixVecs &mv, const DevVecs &, DevState *st,
-                     const double *w, int k, cudaStream_t s) {
+                     const double *w, int k, int unroll, cudaStream_t s) {
   DualMixEpi epi{mv.bf, mv.ylo, mv.yhi, mv.dy, mv.dybar, 0.0f, 0.0};
-  launch_pdl(dual_mix_kernel<4, true>, item_grid(A), kBlock, s, A, mv.dxhat, epi, st, w, k);
+  const int g = item_grid(A);
+  switch (unroll % 100) {
+    case 2: dual_mix_launch<2, false>(g, s, A, mv.dxhat, epi, st, w, k); break;
+    case 4: dual_mix_launch<4, false>(g, s, A, mv.dxhat, epi, st, w, k); break;
+    case -2: dual_mix_launch<2, true>(g, s, A, mv.dxhat, epi, st, w, k); break;
+    default: dual_mix_launch<4, true>(g, s, A, mv.dxhat, epi, st, w, k); break;
+  }
 }
 
 void launch_combine(const DevVecs &v, const MixVecs &mv, DevState *st, int n, int m, int force,

@@ -35,7 +35,7 @@ class lp_options(C.Structure):
                 ("trace_capacity", C.c_int32), ("spmv_unroll", C.c_int32),
                 ("spmv_unroll_rows", C.c_int32), ("lane_steps", C.c_int32),
                 ("single_lane_max", C.c_int32), ("spmv_mode", C.c_int32),
-                ("precision", C.c_int32), ("lane_auto", C.c_int32)]
+                ("precision", C.c_int32), ("lane_auto", C.c_int32), ("autotune", C.c_int32)]
 
 
 class lp_info(C.Structure):
@@ -46,7 +46,8 @@ class lp_info(C.Structure):
                 ("tau", C.c_double), ("sigma", C.c_double), ("rho_stored", C.c_double),
                 ("last_rho", C.c_double), ("last_radius", C.c_double),
                 ("nnz_padded", C.c_int64), ("n_long_rows", C.c_int32), ("n_long_cols", C.c_int32),
-                ("setup_ms", C.c_double * 4)]
+                ("setup_ms", C.c_double * 4), ("spmv_unroll", C.c_int32),
+                ("spmv_unroll_rows", C.c_int32)]
 
 
 class lp_batch_tuning(C.Structure):
@@ -333,6 +334,8 @@ class Info:
     n_long_rows: int
     n_long_cols: int
     setup_ms: tuple = ()
+    spmv_unroll: int = 0
+    spmv_unroll_rows: int = 0
 
     @property
     def rel_kkt(self) -> float:
@@ -395,7 +398,7 @@ class LP:
         return Info(i.iters, i.restarts, i.checks, i.status, i.returned, tuple(i.kkt_avg),
                     tuple(i.kkt_cur), i.eta, i.sigma_max, i.omega, i.tau, i.sigma, i.rho_stored,
                     i.last_rho, i.last_radius, i.nnz_padded, i.n_long_rows, i.n_long_cols,
-                    tuple(i.setup_ms))
+                    tuple(i.setup_ms), i.spmv_unroll, i.spmv_unroll_rows)
 
     def trace(self, capacity=1 << 20):
         return lp_get_trace(self.h, capacity)

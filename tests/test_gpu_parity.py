@@ -40,7 +40,7 @@ def run_both(lpm, oracle_mod, data, iters, eta, K=64, omega=1.0, scheme=2, long_
              x_init=None, y_init=None, unroll=4, mode=1):
     with lpm.LP(data, eta=eta, omega=omega, check_every=K, restart_scheme=scheme,
                 max_iter=iters, long_row_threshold=long_thr, spmv_unroll=unroll,
-                spmv_unroll_rows=unroll, spmv_mode=mode) as g:
+                spmv_unroll_rows=unroll, spmv_mode=mode, autotune=0) as g:
         if x_init is not None:
             g.set_state(x_init, y_init)
         status = g.solve(1e-300)
@@ -274,3 +274,24 @@ def test_select_omega_matches_oracle_runs(lpm, oracle_mod):
         want.append(min(r.kkt_avg[4], r.kkt_cur[4]))
     np.testing.assert_allclose(kkt, want, rtol=1e-7)
     assert best == omegas[int(np.argmin(want))]
+
+
+def test_variant_tuner_picks_a_variant_and_keeps_results(lpm):
+    """lp_options.autotune times the unroll variants at lp_create: the chosen
+    variants are valid codes, and the iterates equal those of any fixed
+    variant (every variant sums each row in the same order)."""
+    data = lpgen.large_mixed(11, m=3001, n=15007)
+    states = []
+    for opts in ({"autotune": 1}, {"autotune": 0, "spmv_unroll": 2, "spmv_unroll_rows": 2},
+                 {"autotune": 0, "spmv_unroll": -4, "spmv_unroll_rows": 4}):
+        with lpm.LP(data, eta=0.05, check_every=32, max_iter=160, **opts) as g:
+            info = g.info()
+            if opts["autotune"]:
+                assert info.spmv_unroll in (2, 4, -2, -4) and info.spmv_unroll_rows in (2, 4, -2, -4)
+            else:
+                assert info.spmv_unroll == opts["spmv_unroll"]
+            g.solve(1e-300)
+            states.append(g.state())
+    for st in states[1:]:
+        for k in st:
+            np.testing.assert_array_equal(st[k], states[0][k])
