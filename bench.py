@@ -13,6 +13,12 @@ e2e   = the same metric through the C ABI from HOST buffers: lp_create
         (host arrays, H2D inside), lp_solve for a fixed iteration budget,
         lp_get_solution into host memory, lp_destroy, per step.
 
+Also reported (outside the timed region): time to relative KKT 1e-8 with the
+paper's recipe (primal weight by Section 7's grid search, then adaptive
+restarted PDHG), FP64 vs mixed, on the benchmark LP itself and on two
+smaller LPs; mixed-precision throughput; the multicommodity LP; the adjoint
+(single LP, implicit-KKT check, 64-LP batch); the 512-LP batched solver.
+
 --impl reference times the CPU oracle (plain C, FP64, 1 thread) on a
 bounded sample of the same workload and metric.
 """
@@ -31,6 +37,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 K_CHECK = 64
+OMEGA_GRID = [4.0 ** k for k in range(-3, 4)]  # Section 7's grid (powers of 4), 2000 iterations each
+OMEGA_ITERS = 2000
 FALLBACK_HBM_GBS = 6800.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one primal_kernel launch on
 # this workload with warm L2 (the benchmark's steady state), from a one-pass
@@ -55,7 +63,8 @@ def parse():
     p.add_argument("--no-mcf", action="store_true")
     p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--adjoint-lps", type=int, default=4)
-    p.add_argument("--ttk-tol", type=float, default=1e-6)
+    p.add_argument("--no-ttk-large", action="store_true")
+    p.add_argument("--ttk-large-cap", type=int, default=1_500_000)
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--batch-count", type=int, default=512)
     p.add_argument("--batch-cap", type=int, default=100_000)
@@ -516,45 +525,47 @@ def run_ours(args):
                  "primal_kernel_ms": mp_ms, "dual_kernel_ms": md_ms,
                  "primal_achieved_gbs": mp / (mp_ms / 1000.0) / 1e9}
 
-    # time to relative KKT on a medium LP that reaches the tolerance in seconds
-    ttk = None
+    # time to relative KKT 1e-8 (the paper's recipe: primal weight by the grid search of
+    # Section 7, then adaptive restarted PDHG), FP64 vs mixed, setup included
+    def ttk_run(d, tol, prec, select, cap):
+        barrier()
+        t0 = time.perf_counter()
+        gt = lp.LP(d, stream=stream, check_every=K_CHECK, max_iter=cap, precision=prec)
+        omega, t_sel = 1.0, 0.0
+        if select:
+            ts = time.perf_counter()
+            omega, _ = gt.select_omega(OMEGA_GRID, iters=OMEGA_ITERS)
+            t_sel = time.perf_counter() - ts
+        st = gt.solve(tol)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        it = gt.info()
+        gt.close()
+        return {"seconds": dt, "omega": omega, "omega_select_seconds": t_sel, "iters": it.iters,
+                "restarts": it.restarts, "status": lp.STATUS_NAMES.get(st, st),
+                "rel_kkt": min(it.kkt_avg[4], it.kkt_cur[4])}
+
+    ttk = ttk8 = ttk_large = None
     if not args.no_ttk:
         from paper_2105_12715_gb300 import lpgen
 
         med = lpgen.large_mixed(5, m=20_000, n=100_000)
-        ttk = {"lp": f"large_mixed m={med.m} n={med.n} nnz={med.nnz} seed 5", "tol": args.ttk_tol}
+        ttk = {"lp": f"large_mixed m={med.m} n={med.n} nnz={med.nnz} seed 5", "tol": 1e-8,
+               "omega": "grid search (Section 7)"}
         for name, prec in (("fp64", lp.LP_PRECISION_FP64), ("mixed", lp.LP_PRECISION_MIXED)):
-            barrier()
-            t0 = time.perf_counter()
-            gt = lp.LP(med, stream=stream, check_every=K_CHECK, max_iter=2_000_000, precision=prec)
-            st = gt.solve(args.ttk_tol)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-            it = gt.info()
-            gt.close()
-            ttk[name] = {"seconds": dt, "iters": it.iters, "restarts": it.restarts,
-                         "status": lp.STATUS_NAMES.get(st, st),
-                         "rel_kkt": min(it.kkt_avg[4], it.kkt_cur[4])}
-
-    # time to relative KKT 1e-8 on a smaller LP that reaches it in seconds (FP64 vs mixed)
-    ttk8 = None
-    if not args.no_ttk:
-        from paper_2105_12715_gb300 import lpgen
-
+            ttk[name] = ttk_run(med, 1e-8, prec, True, 3_000_000)
         small = lpgen.large_mixed(5, m=5000, n=25000)
         ttk8 = {"lp": f"large_mixed m={small.m} n={small.n} nnz={small.nnz} seed 5", "tol": 1e-8}
         for name, prec in (("fp64", lp.LP_PRECISION_FP64), ("mixed", lp.LP_PRECISION_MIXED)):
-            barrier()
-            t0 = time.perf_counter()
-            gt = lp.LP(small, stream=stream, check_every=K_CHECK, max_iter=3_000_000, precision=prec)
-            st = gt.solve(1e-8)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-            it = gt.info()
-            gt.close()
-            ttk8[name] = {"seconds": dt, "iters": it.iters, "restarts": it.restarts,
-                          "status": lp.STATUS_NAMES.get(st, st),
-                          "rel_kkt": min(it.kkt_avg[4], it.kkt_cur[4])}
+            ttk8[name + "_omega1"] = ttk_run(small, 1e-8, prec, False, 3_000_000)
+            ttk8[name] = ttk_run(small, 1e-8, prec, True, 3_000_000)
+    if not args.no_ttk and not args.no_ttk_large and ws == 1:
+        # the benchmark LP itself (m = 200k, n = 1M, nnz = 10M)
+        ttk_large = {"lp": config_of(args, data)["workload"], "tol": 1e-8,
+                     "omega": "grid search (Section 7)"}
+        for name, prec in (("fp64", lp.LP_PRECISION_FP64), ("mixed", lp.LP_PRECISION_MIXED)):
+            ttk_large[name] = ttk_run(data, 1e-8, prec, True, args.ttk_large_cap)
+        ttk_large["mixed_speedup"] = ttk_large["fp64"]["seconds"] / ttk_large["mixed"]["seconds"]
 
     # multicommodity flow LP (300 x 300 grid, 8 commodities): FP64 vs mixed throughput
     mcf = None
@@ -670,7 +681,7 @@ def run_ours(args):
                             "dual_kernel_ms": dual_ms, "dual_algorithmic_bytes": dual_b,
                             "gather_bound": gather_bound},
                "clocks": clocks, "e2e": e2e, "mixed": mixed, "time_to_kkt": ttk,
-               "time_to_kkt_1e8": ttk8,
+               "time_to_kkt_1e8": ttk8, "time_to_kkt_1e8_large": ttk_large,
                "multicommodity": mcf, "adjoint": adjoint, "batched": batched,
                "solver": {"eta": info0.eta, "sigma_max": info0.sigma_max,
                           "iters_done": info.iters, "restarts": info.restarts,
@@ -681,21 +692,17 @@ def run_ours(args):
             if ttk is not None:
                 import oracle
 
-                t0 = time.perf_counter()
-                r = oracle.solve(med, 0.9 / 11.0, tol=1e-300, max_iter=256, check_every=K_CHECK)
-                rate = r.iters / (time.perf_counter() - t0)
-                ttk["oracle_iters_per_s"] = rate
-                ttk["oracle_extrapolated_seconds"] = ttk["fp64"]["iters"] / rate
-                ttk["oracle_note"] = ("oracle time = GPU FP64 iteration count / oracle iterations/s "
-                                      "measured over 256 iterations (extrapolation)")
-            if ttk8 is not None:
-                import oracle
-
-                t0 = time.perf_counter()
-                r = oracle.solve(small, 0.9 / 11.0, tol=1e-300, max_iter=1024, check_every=K_CHECK)
-                rate = r.iters / (time.perf_counter() - t0)
-                ttk8["oracle_iters_per_s"] = rate
-                ttk8["oracle_extrapolated_seconds"] = ttk8["fp64"]["iters"] / rate
+                for key, entry, d_ in (("time_to_kkt", ttk, med), ("time_to_kkt_1e8", ttk8, small)):
+                    t0 = time.perf_counter()
+                    r = oracle.solve(d_, 0.9 / 11.0, tol=1e-300, max_iter=256, check_every=K_CHECK)
+                    rate = r.iters / (time.perf_counter() - t0)
+                    entry["oracle_iters_per_s"] = rate
+                    entry["oracle_extrapolated_seconds"] = entry["fp64"]["iters"] / rate
+                    entry["oracle_note"] = ("oracle time = GPU FP64 iteration count / oracle "
+                                            "iterations/s over 256 iterations (extrapolation)")
+            if ttk_large is not None:
+                rate = out["cpu_baseline"]["value"]
+                ttk_large["oracle_extrapolated_seconds"] = ttk_large["fp64"]["iters"] / rate
         print(json.dumps(out))
     if ws > 1:
         torch.distributed.barrier()
