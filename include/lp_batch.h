@@ -64,6 +64,7 @@ typedef struct {
   double eta, sigma_max, tau, sigma;
   double rho_stored;    /* gap stored at the last restart */
   double last_rho;      /* normalized duality gap at the last check */
+  double omega;         /* primal weight in use (tau = eta/omega, sigma = eta*omega) */
 } lp_batch_problem_info;
 
 typedef struct {
@@ -110,6 +111,22 @@ lp_status lp_batch_create(int32_t count, const int32_t *host_row_start,
  * positive multiple of K_base = opt->check_every) and resets the iteration
  * state to the projection of zero.  Used to reproduce a schedule. */
 lp_status lp_batch_set_check_every(lp_batch_handle h, const int32_t *host_k, void *cuda_stream);
+
+/*
+ * Primal-weight selection of Section 7 for every problem at once: for each
+ * omega in host_omegas[n_omegas] (each > 0), every problem restarts from the
+ * projection of zero and runs `iters` iterations (a multiple of K_base) of
+ * PDHG without restarts, with tau = eta_k/omega, sigma = eta_k*omega;
+ * host_kkt[k * n_omegas + j] (may be NULL) receives problem k's smaller
+ * relative KKT error of the average and the current iterate at its last
+ * check for omega j.  Each problem then keeps the omega with its smallest
+ * value (first on ties; host_best[count], may be NULL, receives it), the
+ * restart scheme is restored, and every problem is reset to the projection
+ * of zero.  Synchronizes the stream.
+ */
+lp_status lp_batch_select_omega(lp_batch_handle h, const double *host_omegas, int32_t n_omegas,
+                                int64_t iters, double *host_kkt, double *host_best,
+                                void *cuda_stream);
 
 /* Warm start: every problem restarts Algorithm 1 from z^{0,0} = proj(x, y)
  * (concatenated in the caller's order, host or device; NULL = zero), with its

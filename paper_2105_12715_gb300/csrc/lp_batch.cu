@@ -1940,6 +1940,71 @@ lp_status lp_batch_set_state(lp_batch_handle h, const double *x, const double *y
   return batch_reset(h, static_cast<cudaStream_t>(cuda_stream), x, y);
 }
 
+lp_status lp_batch_select_omega(lp_batch_handle h, const double *host_omegas, int32_t n_omegas,
+                                int64_t iters, double *host_kkt, double *host_best,
+                                void *cuda_stream) {
+  err_msg().clear();
+  if (!h || !host_omegas || n_omegas < 1) return fail(LP_ERR_INVALID_ARG, "bad arguments");
+  const int K = h->opt.check_every;
+  if (iters < K || iters % K != 0)
+    return fail(LP_ERR_INVALID_ARG, "iters must be a positive multiple of check_every");
+  for (int32_t k = 0; k < n_omegas; ++k)
+    if (!(host_omegas[k] > 0.0) || !std::isfinite(host_omegas[k]))
+      return fail(LP_ERR_INVALID_ARG, "every omega must be finite and > 0");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  lp_status e = batch_build_graph(h);
+  if (e != LP_OK) return e;
+  const int count = h->count;
+  auto set_scheme = [&](int32_t sch) -> lp_status {
+    LP_CU(cudaMemcpyAsync(&h->G->scheme, &sch, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    return LP_OK;
+  };
+  // every problem gets omega_k (or its own choice), tau = eta/omega, sigma = eta*omega
+  auto set_weights = [&](const std::vector<double> &om, bool unlimited) -> lp_status {
+    std::vector<BInst> hi(count);
+    LP_CU(cudaMemcpyAsync(hi.data(), h->I, sizeof(BInst) * count, cudaMemcpyDeviceToHost, s));
+    LP_CU(cudaStreamSynchronize(s));
+    for (int32_t q = 0; q < count; ++q) {
+      hi[q].omega = om[q];
+      hi[q].tau = h->eta[q] / om[q];
+      hi[q].sigma = h->eta[q] * om[q];
+      if (unlimited) hi[q].iter_cap = INT64_MAX;
+    }
+    LP_CU(cudaMemcpyAsync(h->I, hi.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice, s));
+    LP_CU(cudaStreamSynchronize(s));
+    return LP_OK;
+  };
+  std::vector<double> kkt((size_t)count * n_omegas, INFINITY);
+  if ((e = set_scheme(LP_RESTART_NONE)) != LP_OK) return e;
+  const double tiny = 1e-300;
+  for (int32_t k = 0; k < n_omegas; ++k) {
+    if ((e = batch_reset(h, s)) != LP_OK) return e;
+    if ((e = set_weights(std::vector<double>(count, host_omegas[k]), true)) != LP_OK) return e;
+    LP_CU(cudaMemcpyAsync(&h->G->tol, &tiny, sizeof(double), cudaMemcpyHostToDevice, s));
+    for (int64_t b = 0; b < iters / K; ++b) LP_CU(cudaGraphLaunch(h->exec, s));
+    std::vector<BInst> hi(count);
+    LP_CU(cudaMemcpyAsync(hi.data(), h->I, sizeof(BInst) * count, cudaMemcpyDeviceToHost, s));
+    LP_CU(cudaStreamSynchronize(s));
+    for (int32_t q = 0; q < count; ++q) {
+      const double v = std::fmin(hi[q].kkt_a[4], hi[q].kkt_c[4]);
+      kkt[(size_t)q * n_omegas + k] = std::isfinite(v) ? v : INFINITY;
+    }
+  }
+  std::vector<double> best(count);
+  for (int32_t q = 0; q < count; ++q) {
+    int32_t b = 0;
+    for (int32_t k = 1; k < n_omegas; ++k)
+      if (kkt[(size_t)q * n_omegas + k] < kkt[(size_t)q * n_omegas + b]) b = k;
+    best[q] = host_omegas[b];
+  }
+  if ((e = set_scheme(h->opt.restart_scheme)) != LP_OK) return e;
+  if ((e = batch_reset(h, s)) != LP_OK) return e;
+  if ((e = set_weights(best, false)) != LP_OK) return e;
+  if (host_kkt) std::copy(kkt.begin(), kkt.end(), host_kkt);
+  if (host_best) std::copy(best.begin(), best.end(), host_best);
+  return LP_OK;
+}
+
 lp_status lp_batch_set_check_every(lp_batch_handle h, const int32_t *host_k, void *cuda_stream) {
   err_msg().clear();
   if (!h || !host_k) return fail(LP_ERR_INVALID_ARG, "NULL argument");
@@ -2117,6 +2182,7 @@ lp_status lp_batch_get_info(lp_batch_handle h, lp_batch_info *info,
       P.sigma = B.sigma;
       P.rho_stored = B.rho_stored;
       P.last_rho = B.last_rho;
+      P.omega = B.omega;
     }
   }
   return LP_OK;

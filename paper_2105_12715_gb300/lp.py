@@ -60,7 +60,7 @@ class lp_batch_problem_info(C.Structure):
                 ("size_class", C.c_int32), ("kkt_avg", C.c_double * 5),
                 ("kkt_cur", C.c_double * 5), ("eta", C.c_double), ("sigma_max", C.c_double),
                 ("tau", C.c_double), ("sigma", C.c_double), ("rho_stored", C.c_double),
-                ("last_rho", C.c_double)]
+                ("last_rho", C.c_double), ("omega", C.c_double)]
 
 
 class lp_batch_info(C.Structure):
@@ -80,7 +80,7 @@ EXPORTED = ["lp_default_options", "lp_create", "lp_solve", "lp_iterate", "lp_get
             "lp_batch_default_tuning", "lp_batch_create", "lp_batch_set_check_every",
             "lp_batch_solve", "lp_batch_iterate", "lp_batch_get_solution", "lp_batch_get_state",
             "lp_batch_get_info", "lp_batch_solve_recorded", "lp_batch_backward",
-            "lp_batch_set_state", "lp_batch_destroy"]
+            "lp_batch_set_state", "lp_batch_select_omega", "lp_batch_destroy"]
 
 _lib = None
 
@@ -141,6 +141,7 @@ def load(build_if_missing: bool = True):
     lib.lp_batch_get_info.argtypes = [P, C.POINTER(lp_batch_info), P, I32]
     lib.lp_batch_solve_recorded.argtypes = [P, I64, P]
     lib.lp_batch_set_state.argtypes = [P, P, P, P]
+    lib.lp_batch_select_omega.argtypes = [P, P, I32, I64, P, P, P]
     lib.lp_batch_backward.argtypes = [P, P, P, P, P, P]
     lib.lp_batch_destroy.argtypes = [P]
     lib.lp_batch_destroy.restype = None
@@ -150,7 +151,8 @@ def load(build_if_missing: bool = True):
                  "lp_solve_recorded", "lp_backward", "lp_batch_create",
                  "lp_batch_set_check_every", "lp_batch_solve", "lp_batch_iterate",
                  "lp_batch_get_solution", "lp_batch_get_state", "lp_batch_get_info",
-                 "lp_batch_solve_recorded", "lp_batch_backward", "lp_batch_set_state"]:
+                 "lp_batch_solve_recorded", "lp_batch_backward", "lp_batch_set_state",
+                 "lp_batch_select_omega"]:
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -493,6 +495,18 @@ def lp_batch_set_state(h, x=None, y=None, stream=None):
     return _check(load().lp_batch_set_state(h, px, py, _stream(stream)))
 
 
+def lp_batch_select_omega(h, count, omegas, iters=2000, stream=None):
+    """Section 7's primal-weight grid for every problem of a batch: returns
+    (best omega per problem [count], relative KKT per problem and omega [count, len])."""
+    om = np.ascontiguousarray(omegas, dtype=np.float64)
+    kkt = np.empty((count, om.shape[0]))
+    best = np.empty(count)
+    _check(load().lp_batch_select_omega(h, C.c_void_p(om.ctypes.data), om.shape[0], int(iters),
+                                        C.c_void_p(kkt.ctypes.data), C.c_void_p(best.ctypes.data),
+                                        _stream(stream)))
+    return best, kkt
+
+
 def lp_batch_destroy(h):
     if h is not None and h.value:
         load().lp_batch_destroy(h)
@@ -562,6 +576,12 @@ class LPBatch:
         """Warm start of every problem from proj(x, y) (concatenated vectors)."""
         lp_batch_set_state(self.h, x, y, self.stream)
 
+    def select_omega(self, omegas=None, iters=2000):
+        """Primal weight per problem by the grid of Section 7 (4^-3 .. 4^3 by default)."""
+        if omegas is None:
+            omegas = 4.0 ** np.arange(-3, 4)
+        return lp_batch_select_omega(self.h, self.count, omegas, iters, self.stream)
+
     def set_check_every(self, ks):
         lp_batch_set_check_every(self.h, ks, self.stream)
 
@@ -601,7 +621,7 @@ class LPBatch:
                             size_class=p.size_class, kkt_avg=tuple(p.kkt_avg),
                             kkt_cur=tuple(p.kkt_cur), eta=p.eta, sigma_max=p.sigma_max,
                             tau=p.tau, sigma=p.sigma, rho_stored=p.rho_stored,
-                            last_rho=p.last_rho))
+                            last_rho=p.last_rho, omega=p.omega))
         summary = {f: getattr(info, f) for f, _ in lp_batch_info._fields_}
         for f in ("class_k", "class_iter_ms", "class_check_ms"):
             summary[f] = list(getattr(info, f))

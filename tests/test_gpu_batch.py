@@ -364,3 +364,28 @@ def test_batch_warm_start_matches_oracle(lpm, oracle_mod):
         compare(sts[k], ref, TOL, f"problem {k}")
         co += d.n
         ro += d.m
+
+
+def test_batch_select_omega_matches_oracle(lpm, oracle_mod):
+    """Section 7's primal-weight grid for every problem at once: each problem's
+    relative KKT per omega (no restarts, 256 iterations) against the oracle's,
+    the same choice per problem, and afterwards each problem iterates with its
+    own omega exactly as the oracle does."""
+    probs = mixed_batch()[:4]
+    eta = common_eta(oracle_mod, probs)
+    grid = [0.25, 1.0, 4.0]
+    with lpm.LPBatch(probs, eta=eta, check_every=32, max_iter=192) as g:
+        best, kkt = g.select_omega(grid, iters=256)
+        _, per = g.info()
+        g.solve(1e-300)
+        sts = states_of(g, probs)
+    for k, d in enumerate(probs):
+        ref = [osolve(oracle_mod, d, eta, omega=om, tol=1e-300, max_iter=256, check_every=32,
+                      restart_scheme=0) for om in grid]
+        ref_kkt = [min(r.kkt_avg[4], r.kkt_cur[4]) for r in ref]
+        np.testing.assert_allclose(kkt[k], ref_kkt, rtol=1e-7)
+        assert best[k] == grid[int(np.argmin(ref_kkt))]
+        assert per[k]["omega"] == best[k]
+        assert per[k]["tau"] == pytest.approx(eta / best[k], rel=1e-15)
+        after = osolve(oracle_mod, d, eta, omega=best[k], tol=1e-300, max_iter=192, check_every=32)
+        compare(sts[k], after, 1e-8, f"problem {k} after selection")
