@@ -315,7 +315,7 @@ def run_batched(args, lp, stream, barrier):
     res["achieved_gbs_per_iter"] = bytes_all / (slowest / (K_CHECK * nb)) / 1e9
     res["bytes_per_iter_algorithmic"] = bytes_all
     g.close()
-    # time to 1e-8 (fresh batch; setup = create incl. power iterations and tuning; omega = 1:
+    # time to 1e-8 (fresh batch; setup = create incl. the sigma_max estimate and tuning; omega = 1:
     # on these problems the grid of Section 7 converges fewer of them within the cap)
     barrier()
     t0 = time.perf_counter()
@@ -484,6 +484,10 @@ def run_ours(args):
         gather_bound = {"gathers_per_launch": data.nnz, "achieved_ggathers_per_s": ach_g,
                         "probe": probe,
                         "frac_of_probe": ach_g / probe["global_1p6MB_ggathers_per_s"]}
+        if probe.get("sliced_spmv_epilogue_ggathers_per_s"):
+            # against the simplest kernel with the column pass's memory traffic
+            gather_bound["frac_of_sliced_epilogue"] = (
+                ach_g / probe["sliced_spmv_epilogue_ggathers_per_s"])
 
     # end to end through the C ABI from host buffers
     e2e_vals, h2d = [], 0

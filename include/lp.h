@@ -71,6 +71,13 @@ enum {
   LP_RESTART_FLEXIBLE = 3
 };
 
+/* Estimators of sigma_max(A) for eta = 0.9 / sigma_max(A) (Section 7).
+ * Both work on A^T A from the same start vector: the power iteration's
+ * Rayleigh quotient, or the largest Ritz value of the Lanczos process
+ * (the same quantity from the same products, converging in far fewer
+ * steps; both approach sigma_max^2 from below). */
+enum { LP_SIGMA_POWER = 0, LP_SIGMA_LANCZOS = 1 };
+
 typedef struct {
   double beta;            /* restart contraction factor (Remark on the choice of beta: e^-1) */
   int32_t check_every;    /* K: restart/termination checks every K iterations (Section 7 uses 30) */
@@ -78,9 +85,9 @@ typedef struct {
   int64_t tau0;           /* first restart length for n = 0 (iterations; 0 = K) */
   int64_t fixed_len;      /* restart length of LP_RESTART_FIXED (iterations) */
   double omega;           /* primal weight: tau = eta/omega, sigma = eta*omega (Section 7) */
-  double eta;             /* base step; 0 = 0.9 / sigma_max(A) by power iteration */
-  int32_t power_iters;    /* power-iteration cap for sigma_max (default 5000) */
-  double power_tol;       /* relative change of the Rayleigh estimate to stop (1e-10) */
+  double eta;             /* base step; 0 = 0.9 / sigma_max(A) (estimator: sigma_method) */
+  int32_t power_iters;    /* step cap of the sigma_max estimator (default 5000) */
+  double power_tol;       /* relative change of the sigma_max^2 estimate to stop (1e-10) */
   int64_t max_iter;       /* iteration limit of one lp_solve call */
   int32_t long_row_threshold; /* rows at least this long get a whole warp (32 lanes) (512) */
   int32_t trace_capacity; /* per-check trace rows kept on device (65536) */
@@ -103,6 +110,10 @@ typedef struct {
                              passes on this problem and keep the fastest (overrides spmv_unroll
                              and spmv_unroll_rows; results do not depend on the variant: every
                              variant sums each row in the same order); 0: use them as given (1) */
+  int32_t sigma_method;   /* estimator of sigma_max(A) when eta = 0: LP_SIGMA_LANCZOS (default;
+                             at most min(power_iters, 1024) steps) or LP_SIGMA_POWER (Section 7's
+                             power iteration); both stop when the estimate of sigma_max^2 changes
+                             by at most power_tol (relative) */
 } lp_options;
 
 typedef struct {
@@ -120,17 +131,20 @@ typedef struct {
   int64_t nnz_padded;   /* stored nonzeros of one copy of A including padding */
   int32_t n_long_rows, n_long_cols; /* rows of A / of A^T handled by a whole warp */
   double setup_ms[4];   /* lp_create phases: input copy + validation, host layout (CSC,
-                           permutations, slices), device upload, power iteration */
+                           permutations, slices), device upload, sigma_max estimate */
   int32_t spmv_unroll, spmv_unroll_rows; /* kernel variants in use (tuned or given) */
+  int32_t sigma_steps;  /* steps of the sigma_max estimator (0 when eta was given) */
 } lp_info;
 
 /* Defaults: beta = e^-1, K = 64, ADAPTIVE, tau0 = K, omega = 1, eta = 0
- * (auto), power_iters = 5000, power_tol = 1e-10, max_iter = 1e7, autotune = 1. */
+ * (auto), power_iters = 5000, power_tol = 1e-10, max_iter = 1e7, autotune = 1,
+ * sigma_method = LP_SIGMA_LANCZOS. */
 void lp_default_options(lp_options *opt);
 
 /*
  * Creates a problem handle (the LP data of Eq. LP-Lag and the setup of
- * Section 7: eta = 0.9 / sigma_max(A) by power iteration unless opt->eta > 0).
+ * Section 7: eta = 0.9 / sigma_max(A), sigma_max estimated on A^T A as
+ * opt->sigma_method says, unless opt->eta > 0).
  *   row_ptr[m+1], col_idx[nnz], val[nnz]: CSR of A; row_ptr[0] = 0,
  *     nondecreasing, row_ptr[m] = nnz; col_idx in [0, n); a column may
  *     appear at most once per row (duplicates are rejected).

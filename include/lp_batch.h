@@ -65,6 +65,7 @@ typedef struct {
   double rho_stored;    /* gap stored at the last restart */
   double last_rho;      /* normalized duality gap at the last check */
   double omega;         /* primal weight in use (tau = eta/omega, sigma = eta*omega) */
+  int32_t sigma_steps;  /* steps of the sigma_max estimator (0 when eta was given) */
 } lp_batch_problem_info;
 
 typedef struct {

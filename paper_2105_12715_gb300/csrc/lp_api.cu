@@ -108,6 +108,7 @@ struct lp_problem {
   int nsearch = 1;
   int grid_cap = 0;  // blocks of the per-slice iteration kernels (0: one warp per slice)
   double setup_ms[4] = {0, 0, 0, 0};  // lp_create phases (lp_info.setup_ms)
+  int32_t sigma_steps = 0;            // Lanczos / power-iteration steps taken for sigma_max
 
   ~lp_problem() {
     if (ckpt) cudaFree(ckpt);
@@ -330,6 +331,7 @@ void lp_default_options(lp_options *o) {
   o->spmv_mode = 0;
   o->lane_auto = 32;
   o->autotune = 1;
+  o->sigma_method = LP_SIGMA_LANCZOS;
 }
 
 const char *lp_last_error(void) { return err_msg().c_str(); }
@@ -534,7 +536,7 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
   LP_CU(cudaDeviceSynchronize());
   const double t_uploaded = now_seconds();
 
-  // ---- device state: step sizes, norms, power iteration
+  // ---- device state: step sizes, norms, sigma_max estimate
   DevState hs{};
   hs.omega = opt.omega;
   hs.beta = opt.beta;
@@ -556,7 +558,8 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
   if (opt.eta > 0.0) {
     h->eta = opt.eta;
   } else {
-    // Section 7: eta = 0.9 / sigma_max(A), sigma_max by power iteration
+    // Section 7: eta = 0.9 / sigma_max(A); sigma_max^2 is the largest eigenvalue of
+    // A^T A, estimated by Lanczos (default) or Section 7's power iteration
     double *pv = h->v.x, *pav = h->v.y, *pw = h->v.xhat;
     {
       // start vector v_j = 0.5 + u_j (u_j in [0,1) from SplitMix64 at counter j, the
@@ -576,16 +579,50 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
       for (int32_t r = 0; r < n; ++r) v0[r] /= nv;
       LP_CU(cudaMemcpy(pv, v0.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
     }
-    const int chunk = 25;
-    for (int it = 0; it < opt.power_iters; it += chunk) {
-      for (int k = 0; k < chunk; ++k)
-        launch_power_iteration_step(h->A, h->AT, pv, pav, pw, h->st, cs.partials, cs.pstride,
-                                    rgrid, n, m, s);
-      LP_CU(cudaGetLastError());
-      int32_t done = 0;
-      LP_CU(cudaMemcpyAsync(&done, &h->st->pw_done, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if (opt.sigma_method == LP_SIGMA_LANCZOS) {
+      // three rotating n-vectors: v_{k-1}, v_k and w (which becomes v_{k+1})
+      LanczosT T{nullptr, nullptr, std::min<int32_t>(opt.power_iters, kLanczosMax)};
+      double *coef = nullptr;
+      if (cudaMalloc(&coef, sizeof(double) * 2 * T.cap) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LP_ERR_OOM, "cudaMalloc of the Lanczos coefficients failed");
+      }
+      struct Free {
+        double *p;
+        ~Free() { cudaFree(p); }
+      } free_coef{coef};
+      T.alpha = coef;
+      T.beta = coef + T.cap;
+      double *P[3] = {pv, pw, h->v.xbar};
+      for (int k = 0; k < T.cap; ++k) {
+        launch_lanczos_step(h->A, h->AT, P[k % 3], pav, P[(k + 1) % 3], P[(k + 2) % 3], h->st, T,
+                            k, (k + 1) % 4 == 0, cs.partials, cs.pstride, rgrid, n, s);
+        if ((k + 1) % 16 != 0 && k + 1 != T.cap) continue;
+        LP_CU(cudaGetLastError());
+        int32_t done = 0;
+        LP_CU(cudaMemcpyAsync(&done, &h->st->pw_done, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LP_CU(cudaStreamSynchronize(s));
+        if (done) break;
+      }
       LP_CU(cudaStreamSynchronize(s));
-      if (done) break;
+    } else {
+      const int chunk = 25;
+      for (int it = 0; it < opt.power_iters; it += chunk) {
+        for (int k = 0; k < chunk; ++k)
+          launch_power_iteration_step(h->A, h->AT, pv, pav, pw, h->st, cs.partials, cs.pstride,
+                                      rgrid, n, m, s);
+        LP_CU(cudaGetLastError());
+        int32_t done = 0;
+        LP_CU(cudaMemcpyAsync(&done, &h->st->pw_done, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LP_CU(cudaStreamSynchronize(s));
+        if (done) break;
+      }
+    }
+    {
+      int32_t steps = 0;
+      LP_CU(cudaMemcpyAsync(&steps, &h->st->pw_iters, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      LP_CU(cudaStreamSynchronize(s));
+      h->sigma_steps = steps;
     }
     double est = 0.0;
     LP_CU(cudaMemcpyAsync(&est, &h->st->pw_est, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -766,6 +803,7 @@ lp_status lp_get_info(lp_handle h, lp_info *info) {
   info->spmv_unroll = h->opt.spmv_unroll;
   info->spmv_unroll_rows = h->opt.spmv_unroll_rows;
   for (int i = 0; i < 4; ++i) info->setup_ms[i] = h->setup_ms[i];
+  info->sigma_steps = h->sigma_steps;
   return LP_OK;
 }
 

@@ -95,7 +95,7 @@ struct BGlobal {
   double tol, beta, pw_tol;
   int32_t count, Kb, scheme, pw_max;
   int32_t running;     // problems still iterating after the last check
-  int32_t pw_running;  // problems still in the power iteration after the last step
+  int32_t pw_running;  // problems still estimating sigma_max after the last step
   int32_t wl_n[2];     // work-list lengths: [0] column slices, [1] row slices
   int32_t mixed;       // 1: mixed-precision iterations
 };
@@ -1019,6 +1019,74 @@ __device__ double block_sum_sq(const double *p, int64_t begin, int64_t end, doub
   return r;
 }
 
+__device__ double block_sum(double s, double *red) {
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// One Lanczos step on A_k^T A_k per problem still running (one block per
+// problem), after w = A^T (A v) over the whole batch: alpha = v . w,
+// w <- w - alpha v - beta_prev v_prev, beta = ||w||, then v_next = w / beta.
+// alpha and beta go to the problem's row of the coefficient tables
+// (cap entries each); every few steps, at beta = 0 (invariant subspace) or
+// at the cap, warp 0 evaluates the largest Ritz value (tridiag_top_eig) and
+// the problem stops when it changed by at most pw_tol relative since the
+// previous evaluation.  The same recurrence as the single-problem kernels.
+__global__ void __launch_bounds__(kBlock) b_lanczos_kernel(BInst *I, BGlobal *G,
+                                                           const double *vprev, const double *v,
+                                                           double *w, double *alpha,
+                                                           double *beta, int cap, int k,
+                                                           int evaluate) {
+  BInst &B = I[blockIdx.x];
+  if (B.pw_done) return;
+  __shared__ double red[kBlock];
+  __shared__ int stop;
+  const int64_t c0 = B.col0, c1 = (int64_t)B.col0 + B.ncol;
+  double s = 0.0;
+  for (int64_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) s += v[j] * w[j];
+  const double a = block_sum(s, red);
+  double *al = alpha + (size_t)blockIdx.x * cap, *be = beta + (size_t)blockIdx.x * cap;
+  const double bprev = k > 0 ? be[k - 1] : 0.0;
+  double q = 0.0;
+  for (int64_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
+    double r = w[j] - a * v[j];
+    if (k > 0) r -= bprev * vprev[j];
+    w[j] = r;
+    q += r * r;
+  }
+  const double bk = sqrt(block_sum(q, red));
+  if (threadIdx.x == 0) {
+    al[k] = a;
+    be[k] = bk;
+    stop = 0;
+  }
+  __syncthreads();
+  const bool last = (k + 1 >= cap) || !(bk > 0.0);
+  if ((evaluate || last) && threadIdx.x < kWarp) {
+    const double theta = tridiag_top_eig(al, be, k + 1);
+    if (threadIdx.x == 0) {
+      const int conv = (B.pw_iters > 0 && fabs(theta - B.pw_est) <= G->pw_tol * theta);
+      B.pw_est = theta;
+      B.pw_iters = k + 1;
+      stop = (conv || last) ? 1 : 0;
+    }
+  }
+  __syncthreads();
+  if (stop) {
+    if (threadIdx.x == 0) B.pw_done = 1;
+    return;
+  }
+  if (threadIdx.x == 0) atomicAdd(&G->pw_running, 1);
+  for (int64_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) w[j] = w[j] / bk;
+}
+
 // One power-iteration step per problem (Section 7: sigma_max(A_k)^2 as the
 // Rayleigh quotient of A_k^T A_k), after av = A v and w = A^T av over the
 // whole batch: ray = ||A v||^2 (||v|| = 1), stop when |ray - est| <= tol ray
@@ -1141,6 +1209,7 @@ struct lp_batch {
   double tune_ms = 0.0, setup_ms = 0.0;
   double tune_iter_ms[kMaxClasses] = {0}, tune_check_ms[kMaxClasses] = {0};
   std::vector<double> eta, sigma_max;
+  std::vector<int32_t> sigma_steps;  // steps of the sigma_max estimator per problem
   int64_t blocks = 0;
   // unrolled-forward recording for lp_batch_backward
   double *ckpt = nullptr;            // [blocks][2n + 2m]: x, y, xbar, ybar at block start
@@ -1864,6 +1933,7 @@ lp_status lp_batch_create(int32_t count, const int32_t *host_row_start,
   // ---- step sizes (Section 7): eta_k = 0.9 / sigma_max(A_k) per problem
   h->eta.assign(count, opt.eta);
   h->sigma_max.assign(count, NAN);
+  h->sigma_steps.assign(count, 0);
   if (!(opt.eta > 0.0)) {
     // start vector per problem: v_j = 0.5 + u_j, u_j from SplitMix64 at the
     // problem-local original column index j, normalized per problem
@@ -1887,24 +1957,59 @@ lp_status lp_batch_create(int32_t count, const int32_t *host_row_start,
     }
     double *pv = h->v.x, *pav = h->v.y, *pw = h->v.xhat;
     LP_CU(cudaMemcpy(pv, v0.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
-    const int chunk = 25;
-    for (int it = 0; it < opt.power_iters; it += chunk) {
-      for (int q = 0; q < chunk; ++q) {
-        LP_CU(cudaMemsetAsync(&h->G->pw_running, 0, sizeof(int32_t), s));
-        launch_spmv(h->A, pv, pav, s, nullptr);
-        launch_spmv(h->AT, pav, pw, s, nullptr);
-        b_power_kernel<<<count, kBlock, 0, s>>>(h->I, h->G, pv, pav, pw);
+    if (opt.sigma_method == LP_SIGMA_LANCZOS) {
+      // coefficient tables of count x cap doubles (cap shrinks for very large
+      // batches so that the two tables stay within 1 GiB)
+      const int cap = (int)std::min<int64_t>(
+          std::min<int64_t>(opt.power_iters, kLanczosMax),
+          std::max<int64_t>(64, ((int64_t)1 << 26) / std::max<int32_t>(count, 1)));
+      double *coef = nullptr;
+      if (cudaMalloc(&coef, sizeof(double) * 2 * (size_t)count * cap) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LP_ERR_OOM, "cudaMalloc of the Lanczos coefficients failed");
       }
-      LP_CU(cudaGetLastError());
-      int32_t left = 0;
-      LP_CU(cudaMemcpyAsync(&left, &h->G->pw_running, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      struct Free {
+        double *p;
+        ~Free() { cudaFree(p); }
+      } free_coef{coef};
+      double *P[3] = {pv, pw, h->v.xbar};
+      for (int k = 0; k < cap; ++k) {
+        LP_CU(cudaMemsetAsync(&h->G->pw_running, 0, sizeof(int32_t), s));
+        launch_spmv(h->A, P[k % 3], pav, s, nullptr);
+        launch_spmv(h->AT, pav, P[(k + 1) % 3], s, nullptr);
+        b_lanczos_kernel<<<count, kBlock, 0, s>>>(h->I, h->G, P[(k + 2) % 3], P[k % 3],
+                                                  P[(k + 1) % 3], coef,
+                                                  coef + (size_t)count * cap, cap, k,
+                                                  (k + 1) % 4 == 0 ? 1 : 0);
+        if ((k + 1) % 16 != 0 && k + 1 != cap) continue;
+        LP_CU(cudaGetLastError());
+        int32_t left = 0;
+        LP_CU(cudaMemcpyAsync(&left, &h->G->pw_running, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LP_CU(cudaStreamSynchronize(s));
+        if (left == 0) break;
+      }
       LP_CU(cudaStreamSynchronize(s));
-      if (left == 0) break;
+    } else {
+      const int chunk = 25;
+      for (int it = 0; it < opt.power_iters; it += chunk) {
+        for (int q = 0; q < chunk; ++q) {
+          LP_CU(cudaMemsetAsync(&h->G->pw_running, 0, sizeof(int32_t), s));
+          launch_spmv(h->A, pv, pav, s, nullptr);
+          launch_spmv(h->AT, pav, pw, s, nullptr);
+          b_power_kernel<<<count, kBlock, 0, s>>>(h->I, h->G, pv, pav, pw);
+        }
+        LP_CU(cudaGetLastError());
+        int32_t left = 0;
+        LP_CU(cudaMemcpyAsync(&left, &h->G->pw_running, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LP_CU(cudaStreamSynchronize(s));
+        if (left == 0) break;
+      }
     }
     LP_CU(cudaStreamSynchronize(s));
     LP_CU(cudaMemcpy(hi.data(), h->I, sizeof(BInst) * count, cudaMemcpyDeviceToHost));
     for (int32_t q = 0; q < count; ++q) {
       h->sigma_max[q] = std::sqrt(hi[q].pw_est);
+      h->sigma_steps[q] = hi[q].pw_iters;
       if (!(h->sigma_max[q] > 0.0) || !std::isfinite(h->sigma_max[q]))
         return fail(LP_ERR_NUMERICAL, "sigma_max of problem " + std::to_string(q) +
                                           " is zero or not finite; pass eta explicitly");
@@ -2178,6 +2283,7 @@ lp_status lp_batch_get_info(lp_batch_handle h, lp_batch_info *info,
       }
       P.eta = h->eta[q];
       P.sigma_max = h->sigma_max[q];
+      P.sigma_steps = h->sigma_steps.empty() ? 0 : h->sigma_steps[q];
       P.tau = B.tau;
       P.sigma = B.sigma;
       P.rho_stored = B.rho_stored;

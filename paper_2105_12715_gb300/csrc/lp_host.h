@@ -358,6 +358,8 @@ inline lp_status validate_options(const lp_options &o) {
   if (o.spmv_mode != 0 && o.spmv_mode != 1) return fail(LP_ERR_INVALID_ARG, "spmv_mode must be 0 or 1");
   if (o.lane_auto < 0) return fail(LP_ERR_INVALID_ARG, "lane_auto must be >= 0");
   if (o.autotune != 0 && o.autotune != 1) return fail(LP_ERR_INVALID_ARG, "autotune must be 0 or 1");
+  if (o.sigma_method != LP_SIGMA_POWER && o.sigma_method != LP_SIGMA_LANCZOS)
+    return fail(LP_ERR_INVALID_ARG, "sigma_method must be LP_SIGMA_POWER or LP_SIGMA_LANCZOS");
   if (o.precision != LP_PRECISION_FP64 && o.precision != LP_PRECISION_MIXED)
     return fail(LP_ERR_INVALID_ARG, "precision must be LP_PRECISION_FP64 or LP_PRECISION_MIXED");
   return LP_OK;

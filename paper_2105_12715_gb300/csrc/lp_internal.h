@@ -108,7 +108,8 @@ struct DevState {
   int32_t trace_cap;
   int32_t given_radius; // standalone gap evaluation: radius taken from r_given
   double r_given;
-  // power iteration
+  // sigma_max estimator (power iteration or Lanczos): estimate of sigma_max^2,
+  // steps taken, done flag
   double pw_est, pw_nw;
   int32_t pw_done;
   int32_t pw_iters;
@@ -153,6 +154,14 @@ struct AdjVecs {
   double *ax, *axb, *ac, *v;  // [n]
   double *ay, *ayb, *ab, *u;  // [m]
 };
+
+// Coefficients of the Lanczos tridiagonal matrix (sigma_max estimate):
+// alpha[0..cap-1] on the diagonal, beta[0..cap-1] below it.
+struct LanczosT {
+  double *alpha, *beta;
+  int32_t cap;
+};
+constexpr int kLanczosMax = 1024;  // longest Lanczos run (steps)
 
 // Scratch of the check and of the multiplier search.
 struct CheckScratch {
@@ -205,6 +214,10 @@ void launch_power_iteration_step(const SellMat &A, const SellMat &AT,
                                  double *v, double *av, double *w,
                                  DevState *st, double *partials, int pstride,
                                  int grid, int n, int m, cudaStream_t s);
+void launch_lanczos_step(const SellMat &A, const SellMat &AT, const double *v, double *av,
+                         double *w, const double *vprev, DevState *st, const LanczosT &T, int k,
+                         bool evaluate, double *partials, int pstride, int grid, int n,
+                         cudaStream_t s);
 void launch_gather(double *out, const double *in, const int32_t *perm, int64_t n,
                    cudaStream_t s);
 void launch_scatter(double *out, const double *in, const int32_t *perm, int64_t n,

@@ -893,6 +893,81 @@ __global__ void power_scale_kernel(double *v, const double *w, int64_t n, const 
     v[i] = w[i] / nw;
 }
 
+// ------------------------------------------------------- Lanczos (sigma_max)
+//
+// sigma_max(A)^2 is the largest eigenvalue of A^T A; the Lanczos process on
+// A^T A estimates it by the largest eigenvalue (Ritz value) of the
+// tridiagonal matrix it builds, in far fewer products than the power
+// iteration.  Step k, with w = A^T A v_k from two SpMVs:
+//   alpha_k = v_k . w,  w <- w - alpha_k v_k - beta_{k-1} v_{k-1},
+//   beta_k = ||w||,     v_{k+1} = w / beta_k.
+// The Ritz value is evaluated every few steps; the run stops when it changes
+// by at most pw_tol relative to the previous evaluation, at beta_k = 0 (an
+// invariant subspace: the Ritz value is exact) or at the step cap.  Every
+// block re-sums the block partials of a reduction in the same fixed order,
+// so all blocks see the same alpha_k and beta_k.
+__global__ void __launch_bounds__(kBlock) lz_dot_kernel(const double *__restrict__ v,
+                                                        const double *__restrict__ w, int64_t n,
+                                                        double *partials, int pstride,
+                                                        const DevState *st) {
+  if (st->pw_done) return;
+  double q[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    q[0] += v[i] * w[i];
+  block_reduce_store<1>(q, partials, pstride, (int)blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kBlock) lz_update_kernel(double *w, const double *v,
+                                                           const double *vprev, int64_t n,
+                                                           double *partials, int pstride,
+                                                           int nparts, const DevState *st,
+                                                           LanczosT T, int k) {
+  if (st->pw_done) return;
+  __shared__ double red[kBlock];
+  const double alpha = sum_fixed(partials, nparts, red);
+  if (blockIdx.x == 0 && threadIdx.x == 0) T.alpha[k] = alpha;
+  const double bprev = k > 0 ? T.beta[k - 1] : 0.0;
+  double q[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double r = w[i] - alpha * v[i];
+    if (k > 0) r -= bprev * vprev[i];
+    w[i] = r;
+    q[0] += r * r;
+  }
+  block_reduce_store<1>(q, partials + pstride, pstride, (int)blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kBlock) lz_scale_kernel(double *w, int64_t n,
+                                                          const double *partials, int pstride,
+                                                          int nparts, const DevState *st,
+                                                          LanczosT T, int k) {
+  if (st->pw_done) return;
+  __shared__ double red[kBlock];
+  const double beta = sqrt(sum_fixed(partials + pstride, nparts, red));
+  if (blockIdx.x == 0 && threadIdx.x == 0) T.beta[k] = beta;
+  if (!(beta > 0.0)) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    w[i] = w[i] / beta;
+}
+
+// One warp.  After step k: the Ritz value of the (k+1) x (k+1) matrix.
+__global__ void lz_ritz_kernel(DevState *st, LanczosT T, int k, int evaluate) {
+  if (st->pw_done) return;
+  const double beta = T.beta[k];
+  const bool last = (k + 1 >= T.cap) || !(beta > 0.0);
+  if (!evaluate && !last) return;
+  const double theta = tridiag_top_eig(T.alpha, T.beta, k + 1);
+  if (threadIdx.x == 0) {
+    const int conv = (st->pw_iters > 0 && fabs(theta - st->pw_est) <= st->pw_tol * theta);
+    st->pw_est = theta;
+    st->pw_iters = k + 1;
+    if (conv || last) st->pw_done = 1;
+  }
+}
+
 __global__ void norms_finalize_kernel(DevState *st, const double *partials, int pstride,
                                       int nparts) {
   __shared__ double red[kBlock];
@@ -1200,6 +1275,18 @@ void launch_power_iteration_step(const SellMat &A, const SellMat &AT, double *v,
   sumsq_kernel<<<grid, kBlock, 0, s>>>(w, n, partials, pstride, 1, st);
   power_finalize_kernel<<<1, kBlock, 0, s>>>(st, partials, pstride, grid);
   power_scale_kernel<<<grid_for(n, num_sms()), kBlock, 0, s>>>(v, w, n, st);
+}
+
+void launch_lanczos_step(const SellMat &A, const SellMat &AT, const double *v, double *av,
+                         double *w, const double *vprev, DevState *st, const LanczosT &T, int k,
+                         bool evaluate, double *partials, int pstride, int grid, int n,
+                         cudaStream_t s) {
+  launch_spmv(A, v, av, s, st);
+  launch_spmv(AT, av, w, s, st);
+  lz_dot_kernel<<<grid, kBlock, 0, s>>>(v, w, n, partials, pstride, st);
+  lz_update_kernel<<<grid, kBlock, 0, s>>>(w, v, vprev, n, partials, pstride, grid, st, T, k);
+  lz_scale_kernel<<<grid, kBlock, 0, s>>>(w, n, partials, pstride, grid, st, T, k);
+  lz_ritz_kernel<<<1, kWarp, 0, s>>>(st, T, k, evaluate ? 1 : 0);
 }
 
 void launch_norms(const DevVecs &v, DevState *st, double *partials, int pstride, int grid, int n,

@@ -516,5 +516,63 @@ __device__ __forceinline__ double scan256(double v, double *warp_tot) {
 }
 
 
+// ------------------------------------------------- Lanczos Ritz value
+//
+// Largest eigenvalue of the symmetric tridiagonal Lanczos matrix T_k
+// (diagonal a[0..k-1], off-diagonal b[0..k-2]) by Sturm-sequence
+// multisection (the bisection method for symmetric tridiagonal matrices,
+// Golub & Van Loan, Matrix Computations, Section 8.4.1), run by one full
+// warp: each round, lane l counts the eigenvalues below the l-th of 32
+// interior points of the bracket [lo, hi] and the bracket shrinks to the
+// interval where the count first reaches k.  lo starts at the largest
+// diagonal entry (a lower bound on the largest eigenvalue), hi at the
+// largest Gershgorin row bound (an upper bound).  Returns the bracket's
+// midpoint (exactly lo when lo = hi, e.g. a 1 x 1 or zero matrix).
+__device__ __forceinline__ int sturm_count_below(const double *a, const double *b, int k,
+                                                 double x, double pivmin) {
+  int c = 0;
+  double d = 1.0;
+  for (int i = 0; i < k; ++i) {
+    d = (i == 0) ? a[0] - x : a[i] - x - b[i - 1] * b[i - 1] / d;
+    if (fabs(d) < pivmin) d = -pivmin;
+    c += d < 0.0;
+  }
+  return c;
+}
+
+__device__ double tridiag_top_eig(const double *a, const double *b, int k) {
+  const int lane = threadIdx.x & (kWarp - 1);
+  double lo = -INFINITY, hi = -INFINITY, bmax2 = 0.0;
+  for (int i = lane; i < k; i += kWarp) {
+    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < k ? fabs(b[i]) : 0.0);
+    lo = fmax(lo, a[i]);
+    hi = fmax(hi, a[i] + r);
+    if (i + 1 < k) bmax2 = fmax(bmax2, b[i] * b[i]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmax(lo, __shfl_xor_sync(kFull, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(kFull, hi, o));
+    bmax2 = fmax(bmax2, __shfl_xor_sync(kFull, bmax2, o));
+  }
+  // the largest eigenvalue lies in [lo, hi]; when no point of a round has all
+  // k eigenvalues below it, it lies above the last point
+  const double pivmin = 2.2250738585072014e-308 * fmax(1.0, bmax2);
+  for (int round = 0; round < 24 && hi - lo > 2.0 * 2.220446049250313e-16 * fmax(fabs(lo), fabs(hi));
+       ++round) {
+    const double w = (hi - lo) / 33.0;
+    const double x = lo + w * (double)(lane + 1);
+    const unsigned all = __ballot_sync(kFull, sturm_count_below(a, b, k, x, pivmin) >= k);
+    if (all == 0u) {
+      lo = lo + w * 32.0;
+    } else {
+      const int f = __ffs(all) - 1;
+      const double nlo = lo + w * (double)f, nhi = lo + w * (double)(f + 1);
+      lo = nlo;
+      hi = nhi;
+    }
+  }
+  return 0.5 * (lo + hi);
+}
+
 }  // namespace
 }  // namespace lpg

@@ -22,6 +22,7 @@ LP_ERR_NUMERICAL, LP_ERR_TIMEOUT, LP_ERR_NOT_SOLVED = 5, 6, 7
 LP_ROW_EQ, LP_ROW_GE, LP_ROW_LE = 0, 1, 2
 LP_RESTART_NONE, LP_RESTART_FIXED, LP_RESTART_ADAPTIVE, LP_RESTART_FLEXIBLE = 0, 1, 2, 3
 LP_PRECISION_FP64, LP_PRECISION_MIXED = 0, 1
+LP_SIGMA_POWER, LP_SIGMA_LANCZOS = 0, 1
 
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "ITER_LIMIT",
                 5: "NUMERICAL", 6: "TIMEOUT", 7: "NOT_SOLVED"}
@@ -35,7 +36,8 @@ class lp_options(C.Structure):
                 ("trace_capacity", C.c_int32), ("spmv_unroll", C.c_int32),
                 ("spmv_unroll_rows", C.c_int32), ("lane_steps", C.c_int32),
                 ("single_lane_max", C.c_int32), ("spmv_mode", C.c_int32),
-                ("precision", C.c_int32), ("lane_auto", C.c_int32), ("autotune", C.c_int32)]
+                ("precision", C.c_int32), ("lane_auto", C.c_int32), ("autotune", C.c_int32),
+                ("sigma_method", C.c_int32)]
 
 
 class lp_info(C.Structure):
@@ -47,7 +49,7 @@ class lp_info(C.Structure):
                 ("last_rho", C.c_double), ("last_radius", C.c_double),
                 ("nnz_padded", C.c_int64), ("n_long_rows", C.c_int32), ("n_long_cols", C.c_int32),
                 ("setup_ms", C.c_double * 4), ("spmv_unroll", C.c_int32),
-                ("spmv_unroll_rows", C.c_int32)]
+                ("spmv_unroll_rows", C.c_int32), ("sigma_steps", C.c_int32)]
 
 
 class lp_batch_tuning(C.Structure):
@@ -60,7 +62,7 @@ class lp_batch_problem_info(C.Structure):
                 ("size_class", C.c_int32), ("kkt_avg", C.c_double * 5),
                 ("kkt_cur", C.c_double * 5), ("eta", C.c_double), ("sigma_max", C.c_double),
                 ("tau", C.c_double), ("sigma", C.c_double), ("rho_stored", C.c_double),
-                ("last_rho", C.c_double), ("omega", C.c_double)]
+                ("last_rho", C.c_double), ("omega", C.c_double), ("sigma_steps", C.c_int32)]
 
 
 class lp_batch_info(C.Structure):
@@ -338,6 +340,7 @@ class Info:
     setup_ms: tuple = ()
     spmv_unroll: int = 0
     spmv_unroll_rows: int = 0
+    sigma_steps: int = 0
 
     @property
     def rel_kkt(self) -> float:
@@ -400,7 +403,7 @@ class LP:
         return Info(i.iters, i.restarts, i.checks, i.status, i.returned, tuple(i.kkt_avg),
                     tuple(i.kkt_cur), i.eta, i.sigma_max, i.omega, i.tau, i.sigma, i.rho_stored,
                     i.last_rho, i.last_radius, i.nnz_padded, i.n_long_rows, i.n_long_cols,
-                    tuple(i.setup_ms), i.spmv_unroll, i.spmv_unroll_rows)
+                    tuple(i.setup_ms), i.spmv_unroll, i.spmv_unroll_rows, i.sigma_steps)
 
     def trace(self, capacity=1 << 20):
         return lp_get_trace(self.h, capacity)
@@ -621,7 +624,7 @@ class LPBatch:
                             size_class=p.size_class, kkt_avg=tuple(p.kkt_avg),
                             kkt_cur=tuple(p.kkt_cur), eta=p.eta, sigma_max=p.sigma_max,
                             tau=p.tau, sigma=p.sigma, rho_stored=p.rho_stored,
-                            last_rho=p.last_rho, omega=p.omega))
+                            last_rho=p.last_rho, omega=p.omega, sigma_steps=p.sigma_steps))
         summary = {f: getattr(info, f) for f, _ in lp_batch_info._fields_}
         for f in ("class_k", "class_iter_ms", "class_check_ms"):
             summary[f] = list(getattr(info, f))

@@ -141,10 +141,23 @@ def test_batch_flexible_and_fixed_schemes(lpm, oracle_mod):
             compare(sts[k], ref, 1e-8, f"scheme {scheme} problem {k}")
 
 
-def test_batch_sigma_max_per_problem(lpm, oracle_mod):
-    """Power iteration per problem (Section 7) against the oracle's."""
+def test_batch_sigma_max_per_problem(lpm):
+    """Lanczos per problem (the default estimator of sigma_max for Section 7's
+    step size) against each problem's largest singular value (dense SVD)."""
     probs = mixed_batch()
     with lpm.LPBatch(probs) as g:
+        summary, per = g.info()
+    for k, d in enumerate(probs):
+        want = float(np.linalg.norm(d.dense(), 2))
+        assert per[k]["sigma_max"] == pytest.approx(want, rel=1e-9), k
+        assert per[k]["eta"] == pytest.approx(0.9 / per[k]["sigma_max"], rel=1e-15)
+        assert 0 < per[k]["sigma_steps"] <= 200
+
+
+def test_batch_sigma_max_power_iteration(lpm, oracle_mod):
+    """Power iteration per problem (Section 7) against the oracle's."""
+    probs = mixed_batch()
+    with lpm.LPBatch(probs, sigma_method=lpm.LP_SIGMA_POWER) as g:
         summary, per = g.info()
     for k, d in enumerate(probs):
         s_ref = oracle_mod.sigma_max(d)

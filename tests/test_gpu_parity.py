@@ -130,12 +130,59 @@ def test_flexible_and_fixed_schemes(lpm, oracle_mod):
 
 
 def test_power_iteration_sigma_max(lpm, oracle_mod):
+    """Section 7's power iteration (sigma_method = LP_SIGMA_POWER) against the oracle's."""
     for data in [lpgen.tiny_standard_form(0), lpgen.adversarial(3)]:
-        with lpm.LP(data) as g:
+        with lpm.LP(data, sigma_method=lpm.LP_SIGMA_POWER) as g:
             info = g.info()
         want = oracle_mod.sigma_max(data)
         assert info.sigma_max == pytest.approx(want, rel=1e-8)
         assert info.eta == pytest.approx(0.9 / want, rel=1e-8)
+        assert info.sigma_steps > 0
+
+
+def _one_by_one():
+    return lpgen.LPData(1, 1, np.array([0, 1], np.int32), np.array([0], np.int32),
+                        np.array([-3.0]), np.array([1.0]), np.array([4.0]), np.zeros(1),
+                        np.full(1, np.inf), np.zeros(1, np.int8))
+
+
+def test_lanczos_sigma_max_exact(lpm):
+    """The default estimator (Lanczos on A^T A) against the largest singular
+    value from a dense SVD; the 1 x 1 problem breaks down at the first step
+    (beta_0 = 0), where the Ritz value is exact."""
+    cases = [lpgen.tiny_standard_form(0), lpgen.adversarial(3), lpgen.adversarial(5),
+             lpgen.large_mixed(3, m=300, n=1200), lpgen.tiny_standard_form(2, m=5, n=9, per_col=2),
+             _one_by_one()]
+    for data in cases:
+        with lpm.LP(data, autotune=0) as g:
+            info = g.info()
+        want = float(np.linalg.norm(data.dense(), 2))
+        assert info.sigma_max == pytest.approx(want, rel=1e-9), data.name
+        assert info.eta == pytest.approx(0.9 / info.sigma_max, rel=1e-15)
+        assert 0 < info.sigma_steps <= 200
+    with lpm.LP(_one_by_one(), autotune=0) as g:
+        assert g.info().sigma_steps == 1
+
+
+def test_lanczos_takes_fewer_steps_than_power_iteration(lpm):
+    data = lpgen.large_mixed(4, m=2000, n=9000)
+    steps = {}
+    for method in (lpm.LP_SIGMA_POWER, lpm.LP_SIGMA_LANCZOS):
+        with lpm.LP(data, autotune=0, sigma_method=method) as g:
+            steps[method] = (g.info().sigma_steps, g.info().sigma_max)
+    assert steps[lpm.LP_SIGMA_LANCZOS][0] < steps[lpm.LP_SIGMA_POWER][0]
+    assert steps[lpm.LP_SIGMA_LANCZOS][1] == pytest.approx(steps[lpm.LP_SIGMA_POWER][1], rel=1e-6)
+
+
+def test_zero_matrix_needs_explicit_eta(lpm):
+    """sigma_max(A) = 0 leaves no step size: both estimators refuse."""
+    m, n = 3, 4
+    d = lpgen.LPData(m, n, np.zeros(m + 1, np.int32), np.zeros(0, np.int32), np.zeros(0),
+                     np.ones(n), np.zeros(m), np.zeros(n), np.full(n, 1.0), np.zeros(m, np.int8))
+    for method in (lpm.LP_SIGMA_POWER, lpm.LP_SIGMA_LANCZOS):
+        with pytest.raises(lpm.LPError) as e:
+            lpm.LP(d, sigma_method=method)
+        assert e.value.status == lpm.LP_ERR_NUMERICAL
 
 
 def test_normalized_gap_vs_algorithm2(lpm, oracle_mod):
