@@ -490,7 +490,7 @@ def run_ours(args):
                 ach_g / probe["sliced_spmv_epilogue_ggathers_per_s"])
 
     # end to end through the C ABI from host buffers
-    e2e_vals, h2d = [], 0
+    e2e_vals, h2d, e2e_setup = [], 0, None
     host = [np.ascontiguousarray(a) for a in (data.row_ptr, data.col_idx, data.val, data.c, data.b,
                                               data.lb, data.ub, data.row_type)]
     pinned = [torch.from_numpy(a).pin_memory() for a in host]
@@ -507,13 +507,16 @@ def run_ours(args):
         h = lp.lp_create(data.m, data.n, data.nnz, *pinned, opt=opt, stream=stream)
         lp.lp_solve(h, 1e-300, stream)
         lp.lp_get_solution(h, xo, yo, stream)
+        e2e_setup = list(lp.lp_get_info(h).setup_ms)
         lp.lp_destroy(h)
         barrier()
         e2e_vals.append(args.e2e_iters / (time.perf_counter() - t))
     e2e = {"value": ws * float(np.median(e2e_vals)) if e2e_vals else None, "unit": "iters/s",
            "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h,
-           "what": f"lp_create(host arrays)+lp_solve({args.e2e_iters} iters)+lp_get_solution(host)"}
+           "what": f"lp_create(host arrays)+lp_solve({args.e2e_iters} iters)+lp_get_solution(host)",
+           "lp_create_ms": (dict(zip(["inputs", "layout", "upload", "sigma_max"], e2e_setup))
+                            if e2e_setup else None)}
 
     # mixed precision on the same workload (same step, same timing rules)
     mixed = None
@@ -692,6 +695,9 @@ def run_ours(args):
                "time_to_kkt_1e8": ttk8, "time_to_kkt_1e8_large": ttk_large,
                "multicommodity": mcf, "adjoint": adjoint, "batched": batched,
                "solver": {"eta": info0.eta, "sigma_max": info0.sigma_max,
+                          "sigma_steps": info0.sigma_steps,
+                          "setup_ms": dict(zip(["inputs", "layout", "upload", "sigma_max"],
+                                               info0.setup_ms)),
                           "iters_done": info.iters, "restarts": info.restarts,
                           "rel_kkt_avg": info.kkt_avg[4], "rel_kkt_cur": info.kkt_cur[4],
                           "nnz_padded": info.nnz_padded}}

@@ -528,6 +528,8 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
   cs.hist_grid = (int)std::min<int64_t>(std::max<int64_t>(1, (N + 2047) / 2048), 4 * h->nsm);
   if ((e = h->alloc(&cs.hpart, (int64_t)2 * cs.hist_grid * 4 * kBuckets)) != LP_OK) return e;
   if ((e = h->alloc(&cs.btot, (int64_t)2 * 4 * kBuckets)) != LP_OK) return e;
+  if ((e = h->alloc(&cs.pair_x, (int64_t)2 * n)) != LP_OK) return e;
+  if ((e = h->alloc(&cs.pair_y, (int64_t)2 * m)) != LP_OK) return e;
   LP_CU(cudaMallocHost(&h->h_status, 2 * sizeof(int32_t)));
   LP_CU(cudaEventCreateWithFlags(&h->ev[0], cudaEventDisableTiming));
   LP_CU(cudaEventCreateWithFlags(&h->ev[1], cudaEventDisableTiming));
@@ -876,6 +878,7 @@ lp_status lp_normalized_gap(lp_handle h, const double *x, const double *y, doubl
   hs.r_given = r;
   LP_CU(cudaMemcpyAsync(st, &hs, sizeof(DevState), cudaMemcpyHostToDevice, s));
   LP_CU(cudaStreamSynchronize(s));
+  cs.pair_x = cs.pair_y = nullptr;  // the handle's pair buffers belong to its solve
   launch_check(h->A, h->AT, v, st, nullptr, cs, n, m, 1, nullptr, false, s);
   LP_CU(cudaGetLastError());
   LSearch L{};
@@ -1214,6 +1217,7 @@ extern "C" lp_status lp_normalized_gap_static(lp_handle h, const double *x, cons
   hs.given_radius = 1;
   hs.r_given = r;
   LP_CU(cudaMemcpyAsync(st, &hs, sizeof(DevState), cudaMemcpyHostToDevice, s));
+  cs.pair_x = cs.pair_y = nullptr;  // the handle's pair buffers belong to its solve
   launch_check(h->A, h->AT, v, st, nullptr, cs, n, m, 1, nullptr, false, s);
   LP_CU(cudaGetLastError());
   LSearch L{};

@@ -173,6 +173,8 @@ struct CheckScratch {
   double *hpart;           // [2][hist_grid][4][kBuckets]
   double *btot;            // [2][4][kBuckets] bucket totals of the current pass
   int32_t hist_grid;
+  double *pair_x, *pair_y; // [2n], [2m]: (xbar, x) and (ybar, y) interleaved for the check's
+                           // gathers (16-byte aligned); null: gather the two vectors apart
 };
 
 // Launch with programmatic stream serialization: the kernel may be scheduled

@@ -392,7 +392,8 @@ __global__ void adj_block_start_kernel(double *ax, double *axb, double *ay, doub
 
 // ---------------------------------------------------------------- check
 
-template <class Epi>
+// PAIR: v0 holds the two gathered vectors interleaved (pack_pairs_kernel), v1 is unused.
+template <class Epi, bool PAIR>
 __global__ void __launch_bounds__(kBlock) check_kernel(SellMat A, const double *__restrict__ v0,
                                                        const double *__restrict__ v1, Epi epi,
                                                        const DevState *st, double *partials,
@@ -407,8 +408,20 @@ __global__ void __launch_bounds__(kBlock) check_kernel(SellMat A, const double *
   epi.isw = 1.0 / epi.sw;
 #pragma unroll
   for (int i = 0; i < NQ; ++i) epi.q[i] = 0.0;
-  process_all<2, kUnroll2>(A, v0, v1, epi);
+  process_all<2, kUnroll2, false, PAIR>(A, v0, v1, epi);
   block_reduce_store<NQ>(epi.q, partials, pstride, poff + (int)blockIdx.x);
+}
+
+// out[2i] = a[i], out[2i+1] = b[i]: the two vectors a check pass gathers,
+// interleaved so that one 16-byte gather serves both.
+__global__ void __launch_bounds__(kBlock) pack_pairs_kernel(const double *__restrict__ a,
+                                                            const double *__restrict__ b,
+                                                            int64_t n, double2 *out,
+                                                            const DevState *st) {
+  if (st->status != kRunning) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = make_double2(a[i], b[i]);
 }
 
 // Reduction of the check's partial sums: block q sums quantity q over the
@@ -1151,10 +1164,23 @@ void launch_check(const SellMat &A, const SellMat &AT, const DevVecs &v, DevStat
     re.gy_out0 = mv->gy[0];
     re.gy_out1 = mv->gy[1];
   }
-  check_kernel<CheckColsEpi><<<cs.cols_grid, kBlock, 0, s>>>(AT, v.ybar, v.y, ce, st, cs.partials,
-                                                             cs.pstride, 0);
-  check_kernel<CheckRowsEpi><<<cs.rows_grid, kBlock, 0, s>>>(A, v.xbar, v.x, re, st, cs.partials,
-                                                             cs.pstride, cs.cols_grid);
+  if (cs.pair_y && cs.pair_x) {
+    if (m > 0)
+      pack_pairs_kernel<<<grid_for(m, num_sms()), kBlock, 0, s>>>(
+          v.ybar, v.y, m, reinterpret_cast<double2 *>(cs.pair_y), st);
+    if (n > 0)
+      pack_pairs_kernel<<<grid_for(n, num_sms()), kBlock, 0, s>>>(
+          v.xbar, v.x, n, reinterpret_cast<double2 *>(cs.pair_x), st);
+    check_kernel<CheckColsEpi, true><<<cs.cols_grid, kBlock, 0, s>>>(
+        AT, cs.pair_y, nullptr, ce, st, cs.partials, cs.pstride, 0);
+    check_kernel<CheckRowsEpi, true><<<cs.rows_grid, kBlock, 0, s>>>(
+        A, cs.pair_x, nullptr, re, st, cs.partials, cs.pstride, cs.cols_grid);
+  } else {
+    check_kernel<CheckColsEpi, false><<<cs.cols_grid, kBlock, 0, s>>>(
+        AT, v.ybar, v.y, ce, st, cs.partials, cs.pstride, 0);
+    check_kernel<CheckRowsEpi, false><<<cs.rows_grid, kBlock, 0, s>>>(
+        A, v.xbar, v.x, re, st, cs.partials, cs.pstride, cs.cols_grid);
+  }
   check_finalize_kernel<<<NQ, kBlock, 0, s>>>(st, cs.partials, cs.pstride,
                                              cs.cols_grid + cs.rows_grid);
   if (nsearch > 0) {

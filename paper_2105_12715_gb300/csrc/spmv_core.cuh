@@ -40,12 +40,15 @@ __device__ __forceinline__ void pdl_enter() {
 // operands are loaded before the row loop.  NV = 1 or 2 gathered vectors.
 // T is the value type of the matrix copy, of the gathered vectors and of
 // the accumulators (double for the FP64 path, float for the mixed path).
+// PAIR (NV = 2, double): the two vectors are stored interleaved at v0
+// (element i of both in one 16-byte pair), so one 16-byte gather, one
+// sector, fetches both operands of an element; the sums are the same.
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ const double *vals_of(const SellMat &A, double) { return A.val; }
 __device__ __forceinline__ const float *vals_of(const SellMat &A, float) { return A.valf; }
 
-template <int NV, int U, bool PIPE, typename T, class Epi>
+template <int NV, int U, bool PIPE, bool PAIR = false, typename T, class Epi>
 __device__ __forceinline__ void process_item(const SellMat &A, const T *__restrict__ v0,
                                              const T *__restrict__ v1, int item, int lane,
                                              Epi &epi) {
@@ -85,8 +88,14 @@ __device__ __forceinline__ void process_item(const SellMat &A, const T *__restri
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (t + u < steps) {
-        g[u] = __ldg(v0 + j[u]);
-        if (NV == 2) h[u] = __ldg(v1 + j[u]);
+        if constexpr (PAIR) {
+          const double2 p = __ldg(reinterpret_cast<const double2 *>(v0) + j[u]);
+          g[u] = p.x;
+          h[u] = p.y;
+        } else {
+          g[u] = __ldg(v0 + j[u]);
+          if (NV == 2) h[u] = __ldg(v1 + j[u]);
+        }
       }
     }
     int32_t jn[U];
@@ -122,14 +131,14 @@ __device__ __forceinline__ void process_item(const SellMat &A, const T *__restri
   if (owner) epi.store(row, a0, a1, pre);
 }
 
-template <int NV, int U, bool PIPE = false, typename T, class Epi>
+template <int NV, int U, bool PIPE = false, bool PAIR = false, typename T, class Epi>
 __device__ __forceinline__ void process_all(const SellMat &A, const T *v0, const T *v1,
                                             Epi &epi) {
   const int lane = threadIdx.x & (kWarp - 1);
   const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nwarps = (int)(gridDim.x * blockDim.x) >> 5;
   for (int it = warp; it < A.nslices; it += nwarps)
-    process_item<NV, U, PIPE>(A, v0, v1, it, lane, epi);
+    process_item<NV, U, PIPE, PAIR>(A, v0, v1, it, lane, epi);
 }
 
 // Fixed-order block reduction of NV2 per-thread values; thread q < NV2 of
