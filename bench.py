@@ -552,9 +552,18 @@ def run_ours(args):
         dt = time.perf_counter() - t0
         it = gt.info()
         gt.close()
-        return {"seconds": dt, "omega": omega, "omega_select_seconds": t_sel, "iters": it.iters,
-                "restarts": it.restarts, "status": lp.STATUS_NAMES.get(st, st),
-                "rel_kkt": min(it.kkt_avg[4], it.kkt_cur[4])}
+        pobj = it.kkt_avg[2] if it.returned == 0 else it.kkt_cur[2]
+        out = {"seconds": dt, "omega": omega, "omega_select_seconds": t_sel, "iters": it.iters,
+               "restarts": it.restarts, "status": lp.STATUS_NAMES.get(st, st),
+               "rel_kkt": min(it.kkt_avg[4], it.kkt_cur[4]), "pobj": pobj}
+        if d.obj_star is not None:  # the planted optimum's objective (unique)
+            out["obj_rel_err_vs_planted"] = abs(pobj - d.obj_star) / max(1.0, abs(d.obj_star))
+        return out
+
+    def mixed_error(res):
+        """The mixed-precision result against the FP64 one on the same LP."""
+        f, m_ = res["fp64"]["pobj"], res["mixed"]["pobj"]
+        res["mixed_vs_fp64_obj_rel"] = abs(m_ - f) / max(1.0, abs(f))
 
     ttk = ttk8 = ttk_large = None
     if not args.no_ttk:
@@ -565,11 +574,13 @@ def run_ours(args):
                "omega": "grid search (Section 7)"}
         for name, prec in (("fp64", lp.LP_PRECISION_FP64), ("mixed", lp.LP_PRECISION_MIXED)):
             ttk[name] = ttk_run(med, 1e-8, prec, True, 3_000_000)
+        mixed_error(ttk)
         small = lpgen.large_mixed(5, m=5000, n=25000)
         ttk8 = {"lp": f"large_mixed m={small.m} n={small.n} nnz={small.nnz} seed 5", "tol": 1e-8}
         for name, prec in (("fp64", lp.LP_PRECISION_FP64), ("mixed", lp.LP_PRECISION_MIXED)):
             ttk8[name + "_omega1"] = ttk_run(small, 1e-8, prec, False, 3_000_000)
             ttk8[name] = ttk_run(small, 1e-8, prec, True, 3_000_000)
+        mixed_error(ttk8)
     if not args.no_ttk and not args.no_ttk_large and ws == 1:
         # the benchmark LP itself (m = 200k, n = 1M, nnz = 10M)
         ttk_large = {"lp": config_of(args, data)["workload"], "tol": 1e-8,
@@ -577,6 +588,7 @@ def run_ours(args):
         for name, prec in (("fp64", lp.LP_PRECISION_FP64), ("mixed", lp.LP_PRECISION_MIXED)):
             ttk_large[name] = ttk_run(data, 1e-8, prec, True, args.ttk_large_cap)
         ttk_large["mixed_speedup"] = ttk_large["fp64"]["seconds"] / ttk_large["mixed"]["seconds"]
+        mixed_error(ttk_large)
 
     # multicommodity flow LP (300 x 300 grid, 8 commodities): FP64 vs mixed throughput
     mcf = None
