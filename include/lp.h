@@ -114,6 +114,9 @@ typedef struct {
                              at most min(power_iters, 1024) steps) or LP_SIGMA_POWER (Section 7's
                              power iteration); both stop when the estimate of sigma_max^2 changes
                              by at most power_tol (relative) */
+  int32_t device_layout;  /* 1: build the library's layout (CSC copy, length orders, slices) on the
+                             GPU (default); 0: on the host cores.  Both give the same arrays.
+                             spmv_mode = 1 always builds on the host */
 } lp_options;
 
 typedef struct {
@@ -138,7 +141,7 @@ typedef struct {
 
 /* Defaults: beta = e^-1, K = 64, ADAPTIVE, tau0 = K, omega = 1, eta = 0
  * (auto), power_iters = 5000, power_tol = 1e-10, max_iter = 1e7, autotune = 1,
- * sigma_method = LP_SIGMA_LANCZOS. */
+ * sigma_method = LP_SIGMA_LANCZOS, device_layout = 1. */
 void lp_default_options(lp_options *opt);
 
 /*

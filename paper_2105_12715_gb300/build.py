@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblp.so")
-SOURCES = ["lp_api.cu", "lp_kernels.cu", "lp_batch.cu"]
+SOURCES = ["lp_api.cu", "lp_kernels.cu", "lp_batch.cu", "lp_layout.cu"]
 HEADERS = [os.path.join(CSRC, h) for h in ("lp_internal.h", "lp_host.h", "spmv_core.cuh")] + [
     os.path.join(ROOT, "include", h) for h in ("lp.h", "lp_batch.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -22,6 +22,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/lp.h"
@@ -305,58 +306,16 @@ lp_status tune_variants(lp_problem *h, cudaStream_t s) {
   return st;
 }
 
-}  // namespace
-
-extern "C" {
-
-void lp_default_options(lp_options *o) {
-  if (!o) return;
-  std::memset(o, 0, sizeof(*o));
-  o->beta = std::exp(-1.0);
-  o->check_every = 64;
-  o->restart_scheme = LP_RESTART_ADAPTIVE;
-  o->tau0 = 0;
-  o->fixed_len = 0;
-  o->omega = 1.0;
-  o->eta = 0.0;
-  o->power_iters = 5000;
-  o->power_tol = 1e-10;
-  o->max_iter = 10000000;
-  o->long_row_threshold = 512;
-  o->trace_capacity = 65536;
-  o->spmv_unroll = -2;
-  o->spmv_unroll_rows = -4;
-  o->lane_steps = 16;
-  o->single_lane_max = 64;
-  o->spmv_mode = 0;
-  o->lane_auto = 32;
-  o->autotune = 1;
-  o->sigma_method = LP_SIGMA_LANCZOS;
-}
-
-const char *lp_last_error(void) { return err_msg().c_str(); }
-
-lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
-                    const int32_t *col_idx, const double *val, const double *c, const double *b,
-                    const double *lb, const double *ub, const int8_t *row_type,
-                    const lp_options *opt_in, void *cuda_stream, lp_handle *out) {
-  err_msg().clear();
-  if (!out) return fail(LP_ERR_INVALID_ARG, "out is NULL");
-  *out = nullptr;
-  if (m < 0 || n < 1) return fail(LP_ERR_INVALID_ARG, "need m >= 0 and n >= 1");
-  if (nnz < 0 || nnz >= (int64_t(1) << 31)) return fail(LP_ERR_INVALID_ARG, "nnz must lie in [0, 2^31)");
-  if (!row_ptr || !c || !lb || !ub || (m > 0 && (!b || !row_type)) ||
-      (nnz > 0 && (!col_idx || !val)))
-    return fail(LP_ERR_INVALID_ARG, "NULL array argument");
-  lp_options opt;
-  if (opt_in) opt = *opt_in;
-  else lp_default_options(&opt);
-  lp_status st = validate_options(opt);
-  if (st != LP_OK) return st;
-  if (opt.tau0 == 0) opt.tau0 = opt.check_every;
-  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  const double t_start = now_seconds();
-
+// Layout built on the host cores (lp_host.h) from host-readable views of the
+// inputs, then uploaded: the CSC copy, the length orders, both slice layouts,
+// the permuted vectors and the orders themselves.
+lp_status host_layout(lp_problem *h, const int32_t *row_ptr, const int32_t *col_idx,
+                      const double *val, const double *c, const double *b, const double *lb,
+                      const double *ub, const int8_t *row_type, cudaStream_t s,
+                      double *t_copied, double *t_layout) {
+  const int32_t m = h->m, n = h->n;
+  const int64_t nnz = h->nnz;
+  const lp_options &opt = h->opt;
   // ---- inputs (host arrays read in place, device arrays copied) and validation
   std::vector<int32_t> s_rp, s_ci;
   std::vector<double> s_v, s_c, s_b, s_l, s_u;
@@ -401,17 +360,7 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
   if (!build_csc(m, n, hrp32, hci, hv, cp, ri, cv)) return fail(LP_ERR_INVALID_ARG, "col_idx out of range");
   if (csc_has_duplicates(n, cp, ri)) return fail(LP_ERR_INVALID_ARG, "duplicate column in a row");
 
-  std::unique_ptr<lp_problem> h(new lp_problem());
-  h->m = m;
-  h->n = n;
-  h->nnz = nnz;
-  h->opt = opt;
-  LP_CU(cudaGetDevice(&h->device));
-  LP_CU(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device));
-  h->nsearch = (opt.restart_scheme == LP_RESTART_ADAPTIVE) ? 1
-               : (opt.restart_scheme == LP_RESTART_FLEXIBLE) ? 2 : 0;
-
-  const double t_copied = now_seconds();
+  *t_copied = now_seconds();
 
   // ---- permutations by length (stable counting sorts), SELL layouts
   std::vector<int64_t> rp((size_t)m + 1);
@@ -445,11 +394,10 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
     prt[r] = hrt[perm_y[r]];
   }
 
-  const double t_layout = now_seconds();
+  *t_layout = now_seconds();
 
   // ---- device buffers
   lp_status e;
-  h->mixed = (opt.precision == LP_PRECISION_MIXED);
   if ((e = h->upload_sell(HA, h->A, h->mixed)) != LP_OK) return e;
   if ((e = h->upload_sell(HAT, h->AT, h->mixed)) != LP_OK) return e;
   if (opt.spmv_mode == 1) {
@@ -479,6 +427,351 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
   if ((e = h->upload(&h->v.row_type, prt)) != LP_OK) return e;
   if ((e = h->upload(&h->perm_x, perm_x)) != LP_OK) return e;
   if ((e = h->upload(&h->perm_y, perm_y)) != LP_OK) return e;
+  return LP_OK;
+}
+
+// Layout built on the GPU (lp_layout.cu): the same arrays as host_layout,
+// from device copies of the inputs (host inputs are copied in; device inputs
+// are read in place).  Scratch is freed on return.
+lp_status device_layout(lp_problem *h, const int32_t *row_ptr, const int32_t *col_idx,
+                        const double *val, const double *c, const double *b, const double *lb,
+                        const double *ub, const int8_t *row_type, cudaStream_t s,
+                        double *t_copied, double *t_layout) {
+  const int32_t m = h->m, n = h->n;
+  const int64_t nnz = h->nnz;
+  const lp_options &opt = h->opt;
+  const int nsm = h->nsm;
+  std::vector<void *> scratch;
+  struct Guard {
+    std::vector<void *> &v;
+    ~Guard() {
+      for (void *p : v) cudaFree(p);
+    }
+  } guard{scratch};
+  auto tmp = [&](auto **p, int64_t count) -> lp_status {
+    void *q = nullptr;
+    const size_t bytes = std::max<size_t>(16, sizeof(**p) * (size_t)std::max<int64_t>(count, 1));
+    const cudaError_t err = cudaMalloc(&q, bytes);
+    if (err != cudaSuccess) return cuda_fail(err, "cudaMalloc (layout scratch)");
+    scratch.push_back(q);
+    *p = static_cast<std::remove_reference_t<decltype(*p)>>(q);
+    return LP_OK;
+  };
+  // device views of the inputs
+  auto dview = [&](const auto *src, int64_t count, const auto **out) -> lp_status {
+    using T = std::remove_const_t<std::remove_pointer_t<decltype(src)>>;
+    *out = src;
+    if (count <= 0) return LP_OK;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, src) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(LP_ERR_INVALID_ARG, "could not read an input array (bad pointer?)");
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return LP_OK;
+    T *d = nullptr;
+    lp_status e = tmp(&d, count);
+    if (e != LP_OK) return e;
+    LP_CU(cudaMemcpyAsync(d, src, sizeof(T) * count, cudaMemcpyHostToDevice, s));
+    *out = d;
+    return LP_OK;
+  };
+  lp_status e;
+  const int32_t *drp = nullptr, *dci = nullptr;
+  const double *dv = nullptr, *dc = nullptr, *db = nullptr, *dl = nullptr, *du = nullptr;
+  const int8_t *drt = nullptr;
+  if ((e = dview(row_ptr, (int64_t)m + 1, &drp)) != LP_OK) return e;
+  if ((e = dview(col_idx, nnz, &dci)) != LP_OK) return e;
+  if ((e = dview(val, nnz, &dv)) != LP_OK) return e;
+  if ((e = dview(c, n, &dc)) != LP_OK) return e;
+  if ((e = dview(b, m, &db)) != LP_OK) return e;
+  if ((e = dview(lb, n, &dl)) != LP_OK) return e;
+  if ((e = dview(ub, n, &du)) != LP_OK) return e;
+  if ((e = dview(row_type, m, &drt)) != LP_OK) return e;
+
+  // validation (before anything indexes by row_ptr or col_idx)
+  int64_t *small = nullptr;  // [0] flags (int32), [1] max row length, [2] max column length
+  if ((e = tmp(&small, 4)) != LP_OK) return e;
+  int32_t *flags = reinterpret_cast<int32_t *>(small);
+  LP_CU(cudaMemsetAsync(small, 0, sizeof(int64_t) * 4, s));
+  lay_validate(drp, m, nnz, dci, n, dv, dc, dl, du, db, drt, flags, nsm, s);
+  LP_CU(cudaGetLastError());
+  auto check_flags = [&](int32_t f) -> lp_status {
+    if (f & kLayBadRowPtr)
+      return fail(LP_ERR_INVALID_ARG, "row_ptr must start at 0, be nondecreasing and end at nnz");
+    if (f & kLayBadVal) return fail(LP_ERR_INVALID_ARG, "non-finite matrix value");
+    if (f & kLayBadC) return fail(LP_ERR_INVALID_ARG, "non-finite objective c");
+    if (f & kLayBadBounds)
+      return fail(LP_ERR_INVALID_ARG, "invalid bounds (need lb <= ub, lb < inf, ub > -inf)");
+    if (f & kLayBadB) return fail(LP_ERR_INVALID_ARG, "non-finite right-hand side b");
+    if (f & kLayBadRowType) return fail(LP_ERR_INVALID_ARG, "row_type must be 0, 1 or 2");
+    if (f & kLayBadColIdx) return fail(LP_ERR_INVALID_ARG, "col_idx out of range");
+    if (f & kLayDuplicate) return fail(LP_ERR_INVALID_ARG, "duplicate column in a row");
+    return LP_OK;
+  };
+  int64_t hsmall[4] = {0, 0, 0, 0};
+  LP_CU(cudaMemcpyAsync(hsmall, small, sizeof(hsmall), cudaMemcpyDeviceToHost, s));
+  LP_CU(cudaStreamSynchronize(s));
+  if ((e = check_flags((int32_t)hsmall[0])) != LP_OK) return e;
+  *t_copied = now_seconds();
+
+  // radix-sort scratch for the largest sort (nnz, m or n elements)
+  const int64_t most = std::max<int64_t>(std::max<int64_t>(nnz, m), n);
+  const int64_t ntiles = lay_radix_tiles(most);
+  int64_t *gh = nullptr, *goff = nullptr, *sums = nullptr;
+  const int64_t scan_len = std::max<int64_t>(256 * ntiles, most + 1);
+  if ((e = tmp(&gh, 256 * ntiles)) != LP_OK) return e;
+  if ((e = tmp(&goff, 256 * ntiles)) != LP_OK) return e;
+  if ((e = tmp(&sums, lay_scan_scratch(scan_len))) != LP_OK) return e;
+  uint32_t *k0 = nullptr, *k1 = nullptr;
+  int32_t *p0 = nullptr, *p1 = nullptr;
+  if ((e = tmp(&k0, most)) != LP_OK) return e;
+  if ((e = tmp(&k1, most)) != LP_OK) return e;
+  if ((e = tmp(&p0, most)) != LP_OK) return e;
+  if ((e = tmp(&p1, most)) != LP_OK) return e;
+  auto bitlen = [](uint64_t v) {
+    int b = 0;
+    while (v) {
+      ++b;
+      v >>= 1;
+    }
+    return b;
+  };
+
+  // CSC: stable sort of the CSR positions by column
+  int32_t *row_of = nullptr, *ri = nullptr;
+  double *cv = nullptr;
+  int64_t *cnt = nullptr, *cp = nullptr;
+  if ((e = tmp(&row_of, nnz)) != LP_OK) return e;
+  if ((e = tmp(&ri, nnz)) != LP_OK) return e;
+  if ((e = tmp(&cv, nnz)) != LP_OK) return e;
+  if ((e = tmp(&cnt, (int64_t)n + 1)) != LP_OK) return e;
+  if ((e = tmp(&cp, (int64_t)n + 1)) != LP_OK) return e;
+  lay_row_of(drp, m, nnz, row_of, nsm, s);
+  if (nnz > 0) LP_CU(cudaMemcpyAsync(k0, dci, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, s));
+  lay_iota(p0, nnz, nsm, s);
+  bool alt = false;
+  lay_radix_sort(k0, p0, k1, p1, nnz, bitlen((uint64_t)(n - 1)), gh, goff, sums, s, &alt);
+  const uint32_t *col_sorted = alt ? k1 : k0;
+  const int32_t *pos_sorted = alt ? p1 : p0;
+  LP_CU(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * ((size_t)n + 1), s));
+  lay_col_count(dci, nnz, cnt, nsm, s);
+  lay_exclusive_scan(cnt, (int64_t)n + 1, cp, sums, s);
+  lay_csc_gather(pos_sorted, row_of, dv, nnz, ri, cv, nsm, s);
+  lay_dup(col_sorted, ri, nnz, flags, nsm, s);
+  // lengths: maxima first
+  lay_lengths<int32_t>(drp, m, &small[1], nullptr, 0, nullptr, nsm, s);
+  lay_lengths<int64_t>(cp, n, &small[2], nullptr, 0, nullptr, nsm, s);
+  LP_CU(cudaGetLastError());
+  LP_CU(cudaMemcpyAsync(hsmall, small, sizeof(hsmall), cudaMemcpyDeviceToHost, s));
+  LP_CU(cudaStreamSynchronize(s));
+  if ((e = check_flags((int32_t)hsmall[0])) != LP_OK) return e;
+  const int64_t mx_r = hsmall[1], mx_c = hsmall[2];
+
+  // orders by decreasing length (stable), their inverses, length histograms
+  int32_t *perm_y = nullptr, *perm_x = nullptr, *inv_y = nullptr, *inv_x = nullptr;
+  int64_t *hist_r = nullptr, *hist_c = nullptr;
+  if ((e = h->alloc(&perm_y, m)) != LP_OK) return e;
+  if ((e = h->alloc(&perm_x, n)) != LP_OK) return e;
+  if ((e = tmp(&inv_y, m)) != LP_OK) return e;
+  if ((e = tmp(&inv_x, n)) != LP_OK) return e;
+  if ((e = tmp(&hist_r, mx_r + 1)) != LP_OK) return e;
+  if ((e = tmp(&hist_c, mx_c + 1)) != LP_OK) return e;
+  auto order = [&](auto *ptr, int32_t count, int64_t mx, int64_t *hist, int32_t *perm) -> lp_status {
+    LP_CU(cudaMemsetAsync(hist, 0, sizeof(int64_t) * ((size_t)mx + 1), s));
+    if (count == 0) return LP_OK;
+    lay_lengths(ptr, count, nullptr, k0, mx, hist, nsm, s);
+    lay_iota(p0, count, nsm, s);
+    bool a = false;
+    lay_radix_sort(k0, p0, k1, p1, count, bitlen((uint64_t)mx), gh, goff, sums, s, &a);
+    LP_CU(cudaMemcpyAsync(perm, a ? p1 : p0, sizeof(int32_t) * count, cudaMemcpyDeviceToDevice, s));
+    return LP_OK;
+  };
+  if ((e = order(drp, m, mx_r, hist_r, perm_y)) != LP_OK) return e;
+  if ((e = order(cp, n, mx_c, hist_c, perm_x)) != LP_OK) return e;
+  lay_inverse(perm_y, m, inv_y, nsm, s);
+  lay_inverse(perm_x, n, inv_x, nsm, s);
+  std::vector<int64_t> hr((size_t)mx_r + 1), hc((size_t)mx_c + 1);
+  LP_CU(cudaMemcpyAsync(hr.data(), hist_r, sizeof(int64_t) * hr.size(), cudaMemcpyDeviceToHost, s));
+  LP_CU(cudaMemcpyAsync(hc.data(), hist_c, sizeof(int64_t) * hc.size(), cudaMemcpyDeviceToHost, s));
+  LP_CU(cudaStreamSynchronize(s));
+
+  // lane policy (the host layout's choose_policy, from the length histogram)
+  // and the runs of equal lane count in the sorted order
+  // (the lane count is nondecreasing in the length, so each of the at most 6
+  // lane counts forms one run; false if that ever failed)
+  auto runs_of = [](const std::vector<int64_t> &hist, const LanePolicy &p, LayRuns *runs,
+                    int64_t *nslices, int64_t *warp_rows) {
+    LayRuns R{};
+    int64_t g = 0, ns = 0, wr = 0;
+    for (int64_t len = (int64_t)hist.size() - 1; len >= 0; --len) {
+      if (hist[(size_t)len] == 0) continue;
+      const int lg = lanes_log2(len, p);
+      if (R.count == 0 || R.lg[R.count - 1] != lg) {
+        if (R.count == 6) return false;
+        R.lg[R.count] = lg;
+        R.g0[R.count] = g;
+        R.s0[R.count] = 0;
+        ++R.count;
+      }
+      g += hist[(size_t)len];
+      if (lg == 5) wr += hist[(size_t)len];
+    }
+    for (int q = 0; q < R.count; ++q) {  // slices: ceil(rows / (32 >> lg)) per run
+      const int64_t rows = (q + 1 < R.count ? R.g0[q + 1] : g) - R.g0[q];
+      R.s0[q] = ns;
+      ns += (rows + (kWarp >> R.lg[q]) - 1) / (kWarp >> R.lg[q]);
+    }
+    if (runs) *runs = R;
+    *nslices = ns;
+    if (warp_rows) *warp_rows = wr;
+    return true;
+  };
+  auto choose = [&](const std::vector<int64_t> &hist, LanePolicy p) {
+    const int64_t target = (int64_t)opt.lane_auto * nsm;
+    if (target <= 0) return p;
+    int64_t ns = 0;
+    for (;;) {
+      if (!runs_of(hist, p, nullptr, &ns, nullptr)) break;
+      if (ns >= target || !(p.single_max > 1 || p.lane_steps > 1)) break;
+      p.single_max = p.single_max / 2;
+      p.lane_steps = std::max(1, p.lane_steps / 2);
+    }
+    return p;
+  };
+  const LanePolicy policy{opt.long_row_threshold, opt.lane_steps, opt.single_lane_max};
+
+  // slices and fill of one operator
+  auto make = [&](auto *ptr, int32_t nrows, int32_t ncols, const std::vector<int64_t> &hist,
+                  const int32_t *perm, const int32_t *ind, const double *vals,
+                  const int32_t *relabel, SellMat &M) -> lp_status {
+    LayRuns runs{};
+    int64_t ns = 0, wr = 0;
+    if (!runs_of(hist, choose(hist, policy), &runs, &ns, &wr))
+      return fail(LP_ERR_INVALID_ARG, "lane policy gives more than 6 runs");
+    SliceInfo *info = nullptr;
+    int64_t *width = nullptr, *off = nullptr;
+    if ((e = h->alloc(&info, ns + 1)) != LP_OK) return e;
+    if ((e = tmp(&width, ns)) != LP_OK) return e;
+    if ((e = tmp(&off, ns)) != LP_OK) return e;
+    lay_slices(runs, perm, ptr, ns, nrows, info, width, off, sums, nsm, s);
+    SliceInfo last{};
+    LP_CU(cudaMemcpyAsync(&last, info + ns, sizeof(SliceInfo), cudaMemcpyDeviceToHost, s));
+    LP_CU(cudaStreamSynchronize(s));
+    int32_t *ix = nullptr;
+    double *vv = nullptr;
+    float *vf = nullptr;
+    if ((e = h->alloc(&ix, last.off)) != LP_OK) return e;
+    if ((e = h->alloc(&vv, last.off)) != LP_OK) return e;
+    if (h->mixed && (e = h->alloc(&vf, last.off)) != LP_OK) return e;
+    lay_fill(info, ns, perm, ptr, ind, vals, relabel, ix, vv, vf, nsm, s);
+    LP_CU(cudaGetLastError());
+    M.nrows = nrows;
+    M.ncols = ncols;
+    M.nslices = (int32_t)ns;
+    M.n_warp_rows = (int32_t)wr;
+    M.info = info;
+    M.idx = ix;
+    M.val = vv;
+    M.valf = vf;
+    return LP_OK;
+  };
+  if ((e = make(drp, m, n, hr, perm_y, dci, dv, inv_x, h->A)) != LP_OK) return e;
+  if ((e = make(cp, n, m, hc, perm_x, ri, cv, inv_y, h->AT)) != LP_OK) return e;
+  {
+    SliceInfo last{};
+    LP_CU(cudaMemcpyAsync(&last, h->A.info + h->A.nslices, sizeof(SliceInfo),
+                          cudaMemcpyDeviceToHost, s));
+    LP_CU(cudaStreamSynchronize(s));
+    h->nnz_padded = last.off;
+  }
+  *t_layout = now_seconds();
+
+  // permuted vectors and the orders
+  if ((e = h->alloc(&h->v.c, n)) != LP_OK) return e;
+  if ((e = h->alloc(&h->v.lb, n)) != LP_OK) return e;
+  if ((e = h->alloc(&h->v.ub, n)) != LP_OK) return e;
+  if ((e = h->alloc(&h->v.lbk, n)) != LP_OK) return e;
+  if ((e = h->alloc(&h->v.ubk, n)) != LP_OK) return e;
+  if ((e = h->alloc(&h->v.b, m)) != LP_OK) return e;
+  if ((e = h->alloc(&h->v.row_type, m)) != LP_OK) return e;
+  lay_vectors(perm_x, n, dc, dl, du, h->v.c, h->v.lb, h->v.ub, h->v.lbk, h->v.ubk, perm_y, m, db,
+              drt, h->v.b, h->v.row_type, nsm, s);
+  LP_CU(cudaGetLastError());
+  h->perm_x = perm_x;
+  h->perm_y = perm_y;
+  LP_CU(cudaStreamSynchronize(s));  // scratch is freed on return
+  return LP_OK;
+}
+}  // namespace
+
+extern "C" {
+
+void lp_default_options(lp_options *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->beta = std::exp(-1.0);
+  o->check_every = 64;
+  o->restart_scheme = LP_RESTART_ADAPTIVE;
+  o->tau0 = 0;
+  o->fixed_len = 0;
+  o->omega = 1.0;
+  o->eta = 0.0;
+  o->power_iters = 5000;
+  o->power_tol = 1e-10;
+  o->max_iter = 10000000;
+  o->long_row_threshold = 512;
+  o->trace_capacity = 65536;
+  o->spmv_unroll = -2;
+  o->spmv_unroll_rows = -4;
+  o->lane_steps = 16;
+  o->single_lane_max = 64;
+  o->spmv_mode = 0;
+  o->lane_auto = 32;
+  o->autotune = 1;
+  o->sigma_method = LP_SIGMA_LANCZOS;
+  o->device_layout = 1;
+}
+
+const char *lp_last_error(void) { return err_msg().c_str(); }
+
+lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
+                    const int32_t *col_idx, const double *val, const double *c, const double *b,
+                    const double *lb, const double *ub, const int8_t *row_type,
+                    const lp_options *opt_in, void *cuda_stream, lp_handle *out) {
+  err_msg().clear();
+  if (!out) return fail(LP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (m < 0 || n < 1) return fail(LP_ERR_INVALID_ARG, "need m >= 0 and n >= 1");
+  if (nnz < 0 || nnz >= (int64_t(1) << 31)) return fail(LP_ERR_INVALID_ARG, "nnz must lie in [0, 2^31)");
+  if (!row_ptr || !c || !lb || !ub || (m > 0 && (!b || !row_type)) ||
+      (nnz > 0 && (!col_idx || !val)))
+    return fail(LP_ERR_INVALID_ARG, "NULL array argument");
+  lp_options opt;
+  if (opt_in) opt = *opt_in;
+  else lp_default_options(&opt);
+  lp_status st = validate_options(opt);
+  if (st != LP_OK) return st;
+  if (opt.tau0 == 0) opt.tau0 = opt.check_every;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const double t_start = now_seconds();
+
+  std::unique_ptr<lp_problem> h(new lp_problem());
+  h->m = m;
+  h->n = n;
+  h->nnz = nnz;
+  h->opt = opt;
+  LP_CU(cudaGetDevice(&h->device));
+  LP_CU(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device));
+  h->nsearch = (opt.restart_scheme == LP_RESTART_ADAPTIVE) ? 1
+               : (opt.restart_scheme == LP_RESTART_FLEXIBLE) ? 2 : 0;
+  h->mixed = (opt.precision == LP_PRECISION_MIXED);
+  double t_copied = t_start, t_layout = t_start;
+  lp_status e = (opt.device_layout && opt.spmv_mode == 0)
+                    ? device_layout(h.get(), row_ptr, col_idx, val, c, b, lb, ub, row_type, s,
+                                    &t_copied, &t_layout)
+                    : host_layout(h.get(), row_ptr, col_idx, val, c, b, lb, ub, row_type, s,
+                                  &t_copied, &t_layout);
+  if (e != LP_OK) return e;
   double **xs[] = {&h->v.x, &h->v.xhat, &h->v.xbar, &h->v.x0};
   for (double **p : xs)
     if ((e = h->alloc(p, n)) != LP_OK) return e;
@@ -563,24 +856,11 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
     // Section 7: eta = 0.9 / sigma_max(A); sigma_max^2 is the largest eigenvalue of
     // A^T A, estimated by Lanczos (default) or Section 7's power iteration
     double *pv = h->v.x, *pav = h->v.y, *pw = h->v.xhat;
-    {
-      // start vector v_j = 0.5 + u_j (u_j in [0,1) from SplitMix64 at counter j, the
-      // original column index), normalized; the all-ones vector can be orthogonal
-      // to the top singular vector (symmetric network matrices)
-      std::vector<double> v0(n);
-      double nv = 0.0;
-      for (int32_t r = 0; r < n; ++r) {
-        uint64_t z = ((uint64_t)perm_x[r] + 1) * 0x9E3779B97F4A7C15ull;
-        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-        z ^= z >> 31;
-        v0[r] = 0.5 + (double)(z >> 11) * 0x1.0p-53;
-        nv += v0[r] * v0[r];
-      }
-      nv = std::sqrt(nv);
-      for (int32_t r = 0; r < n; ++r) v0[r] /= nv;
-      LP_CU(cudaMemcpy(pv, v0.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
-    }
+    // start vector v_j = 0.5 + u_j (u_j in [0,1) from SplitMix64 at counter j, the
+    // original column index), normalized; the all-ones vector can be orthogonal
+    // to the top singular vector (symmetric network matrices)
+    launch_start_vector(h->perm_x, pv, n, cs.partials, cs.pstride, rgrid, s);
+    LP_CU(cudaGetLastError());
     if (opt.sigma_method == LP_SIGMA_LANCZOS) {
       // three rotating n-vectors: v_{k-1}, v_k and w (which becomes v_{k+1})
       LanczosT T{nullptr, nullptr, std::min<int32_t>(opt.power_iters, kLanczosMax)};

@@ -360,6 +360,8 @@ inline lp_status validate_options(const lp_options &o) {
   if (o.autotune != 0 && o.autotune != 1) return fail(LP_ERR_INVALID_ARG, "autotune must be 0 or 1");
   if (o.sigma_method != LP_SIGMA_POWER && o.sigma_method != LP_SIGMA_LANCZOS)
     return fail(LP_ERR_INVALID_ARG, "sigma_method must be LP_SIGMA_POWER or LP_SIGMA_LANCZOS");
+  if (o.device_layout != 0 && o.device_layout != 1)
+    return fail(LP_ERR_INVALID_ARG, "device_layout must be 0 or 1");
   if (o.precision != LP_PRECISION_FP64 && o.precision != LP_PRECISION_MIXED)
     return fail(LP_ERR_INVALID_ARG, "precision must be LP_PRECISION_FP64 or LP_PRECISION_MIXED");
   return LP_OK;

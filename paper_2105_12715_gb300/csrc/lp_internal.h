@@ -195,6 +195,56 @@ inline void launch_pdl(void (*kern)(KArgs...), int grid, int block, cudaStream_t
   cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
+// ---- device layout construction (lp_layout.cu) ----
+// Input error bits of lay_validate (and lay_dup).
+enum : int32_t {
+  kLayBadRowPtr = 1, kLayBadColIdx = 2, kLayBadVal = 4, kLayBadC = 8, kLayBadBounds = 16,
+  kLayBadB = 32, kLayBadRowType = 64, kLayDuplicate = 128
+};
+// Runs of equal lane count in the length-sorted order: run q holds rows
+// [g0[q], g0[q] + ...) with 2^lg[q] lanes per row; its slices start at
+// slice index s0[q] (runs in order, empty runs left out).
+struct LayRuns {
+  int32_t count;
+  int32_t lg[6];
+  int64_t g0[6];
+  int64_t s0[6];
+};
+void lay_validate(const int32_t *rp, int32_t m, int64_t nnz, const int32_t *ci, int32_t n,
+                  const double *v, const double *c, const double *lb, const double *ub,
+                  const double *b, const int8_t *rt, int32_t *flags, int nsm, cudaStream_t s);
+void lay_row_of(const int32_t *rp, int32_t m, int64_t nnz, int32_t *row_of, int nsm,
+                cudaStream_t s);
+void lay_iota(int32_t *a, int64_t count, int nsm, cudaStream_t s);
+int64_t lay_scan_scratch(int64_t len);
+void lay_exclusive_scan(const int64_t *in, int64_t len, int64_t *out, int64_t *sums,
+                        cudaStream_t s);
+int64_t lay_radix_tiles(int64_t count);
+void lay_radix_sort(uint32_t *keys, int32_t *pay, uint32_t *keys_alt, int32_t *pay_alt,
+                    int64_t count, int bits, int64_t *gh, int64_t *goff, int64_t *sums,
+                    cudaStream_t s, bool *in_alt);
+void lay_col_count(const int32_t *ci, int64_t nnz, int64_t *cnt, int nsm, cudaStream_t s);
+void lay_csc_gather(const int32_t *pos, const int32_t *row_of, const double *v, int64_t nnz,
+                    int32_t *ri, double *cv, int nsm, cudaStream_t s);
+void lay_dup(const uint32_t *col, const int32_t *ri, int64_t nnz, int32_t *flags, int nsm,
+             cudaStream_t s);
+template <class P>
+void lay_lengths(const P *ptr, int32_t count, int64_t *mx, uint32_t *key, int64_t mxv,
+                 int64_t *hist, int nsm, cudaStream_t s);
+void lay_inverse(const int32_t *perm, int32_t count, int32_t *inv, int nsm, cudaStream_t s);
+template <class P>
+void lay_slices(const LayRuns &runs, const int32_t *perm, const P *ptr, int64_t nslices,
+                int32_t nrows, SliceInfo *info, int64_t *width, int64_t *off, int64_t *sums,
+                int nsm, cudaStream_t s);
+template <class P>
+void lay_fill(const SliceInfo *info, int64_t nslices, const int32_t *perm, const P *ptr,
+              const int32_t *ind, const double *val, const int32_t *relabel, int32_t *idx,
+              double *vout, float *vf, int nsm, cudaStream_t s);
+void lay_vectors(const int32_t *perm_x, int32_t n, const double *c, const double *lb,
+                 const double *ub, double *pc, double *pl, double *pu, long long *lk,
+                 long long *uk, const int32_t *perm_y, int32_t m, const double *b,
+                 const int8_t *rt, double *pb, int8_t *prt, int nsm, cudaStream_t s);
+
 // ---- launchers (lp_kernels.cu) ----
 void launch_primal_step(const SellMat &AT, const DevVecs &v, DevState *st,
                         const double *w, int k, int unroll, int grid_cap, cudaStream_t s);
@@ -220,6 +270,8 @@ void launch_lanczos_step(const SellMat &A, const SellMat &AT, const double *v, d
                          double *w, const double *vprev, DevState *st, const LanczosT &T, int k,
                          bool evaluate, double *partials, int pstride, int grid, int n,
                          cudaStream_t s);
+void launch_start_vector(const int32_t *perm, double *v, int n, double *partials, int pstride,
+                         int grid, cudaStream_t s);
 void launch_gather(double *out, const double *in, const int32_t *perm, int64_t n,
                    cudaStream_t s);
 void launch_scatter(double *out, const double *in, const int32_t *perm, int64_t n,

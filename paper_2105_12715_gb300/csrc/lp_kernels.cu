@@ -981,6 +981,32 @@ __global__ void lz_ritz_kernel(DevState *st, LanczosT T, int k, int evaluate) {
   }
 }
 
+// Start vector of the sigma_max estimators: v_r = 0.5 + u(perm[r]), u(j) the
+// top 53 bits of SplitMix64 (Steele, Lea and Flood, 2014) at counter j (the
+// original column index) as a fraction in [0, 1); then v /= ||v|| with the
+// norm from fixed-order block partials.
+__global__ void __launch_bounds__(kBlock) start_vector_kernel(const int32_t *__restrict__ perm,
+                                                              double *v, int64_t n) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = ((uint64_t)perm[r] + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    v[r] = 0.5 + (double)(z >> 11) * 0x1.0p-53;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) scale_inv_norm_kernel(double *v, int64_t n,
+                                                                const double *partials,
+                                                                int nparts) {
+  __shared__ double red[kBlock];
+  const double nv = sqrt(sum_fixed(partials, nparts, red));
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x)
+    v[r] = v[r] / nv;
+}
+
 __global__ void norms_finalize_kernel(DevState *st, const double *partials, int pstride,
                                       int nparts) {
   __shared__ double red[kBlock];
@@ -1313,6 +1339,13 @@ void launch_lanczos_step(const SellMat &A, const SellMat &AT, const double *v, d
   lz_update_kernel<<<grid, kBlock, 0, s>>>(w, v, vprev, n, partials, pstride, grid, st, T, k);
   lz_scale_kernel<<<grid, kBlock, 0, s>>>(w, n, partials, pstride, grid, st, T, k);
   lz_ritz_kernel<<<1, kWarp, 0, s>>>(st, T, k, evaluate ? 1 : 0);
+}
+
+void launch_start_vector(const int32_t *perm, double *v, int n, double *partials, int pstride,
+                         int grid, cudaStream_t s) {
+  start_vector_kernel<<<grid, kBlock, 0, s>>>(perm, v, n);
+  sumsq_kernel<<<grid, kBlock, 0, s>>>(v, n, partials, pstride, 0, nullptr);
+  scale_inv_norm_kernel<<<grid, kBlock, 0, s>>>(v, n, partials, grid);
 }
 
 void launch_norms(const DevVecs &v, DevState *st, double *partials, int pstride, int grid, int n,

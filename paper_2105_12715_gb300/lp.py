@@ -37,7 +37,7 @@ class lp_options(C.Structure):
                 ("spmv_unroll_rows", C.c_int32), ("lane_steps", C.c_int32),
                 ("single_lane_max", C.c_int32), ("spmv_mode", C.c_int32),
                 ("precision", C.c_int32), ("lane_auto", C.c_int32), ("autotune", C.c_int32),
-                ("sigma_method", C.c_int32)]
+                ("sigma_method", C.c_int32), ("device_layout", C.c_int32)]
 
 
 class lp_info(C.Structure):
