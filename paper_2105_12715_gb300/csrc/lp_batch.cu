@@ -237,11 +237,15 @@ __global__ void __launch_bounds__(kBlock) b_check_kernel(SellMat A, const double
 #pragma unroll
     for (int q = 0; q < NQ; ++q) epi.q[q] = 0.0;
     for (int sl = s0; sl < s1; ++sl) process_item<2, kUnroll2, false>(A, v0, v1, sl, lane, epi);
+    // only the quantities this epilogue accumulates are reduced (the others are 0)
+    const uint32_t used = Epi::kUsed | (epi.gap_c ? Epi::kUsedGapC : 0u);
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
       double v = epi.q[q];
+      if ((used >> q) & 1u) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+      }
       if (lane == 0) spart[(size_t)q * pstride + poff + c] = v;
     }
   }

@@ -409,7 +409,8 @@ __global__ void __launch_bounds__(kBlock) check_kernel(SellMat A, const double *
 #pragma unroll
   for (int i = 0; i < NQ; ++i) epi.q[i] = 0.0;
   process_all<2, kUnroll2, false, PAIR>(A, v0, v1, epi);
-  block_reduce_store<NQ>(epi.q, partials, pstride, poff + (int)blockIdx.x);
+  block_reduce_store_mask<NQ>(epi.q, Epi::kUsed | (epi.gap_c ? Epi::kUsedGapC : 0u), partials,
+                              pstride, poff + (int)blockIdx.x);
 }
 
 // out[2i] = a[i], out[2i+1] = b[i]: the two vectors a check pass gathers,
@@ -1089,10 +1090,23 @@ int num_sms() {
 
 }  // namespace
 
+// One wave of resident blocks (the check kernels loop over the slices): the
+// per-block reduction of the check's quantities is paid once per resident
+// block.
 int check_grid_for(const SellMat &A, int nsm) {
+  static const int per_sm = [] {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, check_kernel<CheckColsEpi, true>, kBlock,
+                                                      0) != cudaSuccess ||
+        b < 1) {
+      cudaGetLastError();
+      b = 2;
+    }
+    return b;
+  }();
   const int64_t items = A.nslices;
   int64_t g = (items + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  const int64_t cap = (int64_t)nsm * 4;
+  const int64_t cap = (int64_t)nsm * per_sm;
   if (g > cap) g = cap;
   if (g < 1) g = 1;
   return (int)g;

@@ -163,6 +163,34 @@ __device__ __forceinline__ void block_reduce_store(const double (&q)[NV2], doubl
   }
 }
 
+// The same for the quantities whose bit is set in mask (uniform across the
+// block); the others are stored as 0 without a reduction.  The check
+// kernels use it to skip the quantities their epilogue never touches: on
+// GB300 each FP64 addition of the butterflies costs as much as a nonzero's
+// FMA.
+template <int NV2>
+__device__ __forceinline__ void block_reduce_store_mask(const double (&q)[NV2], uint32_t mask,
+                                                        double *partials, int pstride,
+                                                        int col) {
+  __shared__ double sh[kBlock / kWarp][NV2];
+  const int lane = threadIdx.x & (kWarp - 1), warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV2; ++i) {
+    if (!((mask >> i) & 1u)) continue;
+    double v = q[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    if (lane == 0) sh[warp][i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV2) {
+    double s = 0.0;
+    if ((mask >> threadIdx.x) & 1u)
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w][threadIdx.x];
+    partials[(size_t)threadIdx.x * pstride + col] = s;
+  }
+}
+
 // -------------------------------------------------------------- epilogues
 
 // Order-preserving map of a double's bit pattern to a signed integer
@@ -295,6 +323,14 @@ __device__ __forceinline__ void gap_elem(double G, double dist, double sd, doubl
 // with only l finite, (-inf,0] with only u finite, {0} if free: the
 // projection of lam keeps lam when its sign is allowed and is 0 otherwise.
 struct CheckColsEpi {
+  // quantities the epilogue accumulates (the current iterate's gap data only
+  // under the flexible scheme)
+  static constexpr uint32_t kUsed =
+      (1u << Q_RD2_A) | (1u << Q_RD2_C) | (1u << Q_POBJ_A) | (1u << Q_POBJ_C) |
+      (1u << Q_DOBJ_A) | (1u << Q_DOBJ_C) | (1u << Q_RRX_A) | (1u << Q_D2_A) | (1u << Q_GD_A) |
+      (1u << Q_G2INF_A) | (1u << Q_BAD);
+  static constexpr uint32_t kUsedGapC =
+      (1u << Q_RRX_C) | (1u << Q_D2_C) | (1u << Q_GD_C) | (1u << Q_G2INF_C);
   const double *__restrict__ c;
   const double *__restrict__ lb;
   const double *__restrict__ ub;
@@ -348,6 +384,11 @@ struct CheckColsEpi {
 // Check epilogue over rows (y-space): primal residual by row sense, b^T y,
 // and the y-part of the trust region with F_y = A x - b.
 struct CheckRowsEpi {
+  static constexpr uint32_t kUsed =
+      (1u << Q_RP2_A) | (1u << Q_RP2_C) | (1u << Q_DOBJ_A) | (1u << Q_DOBJ_C) | (1u << Q_RRY_A) |
+      (1u << Q_D2_A) | (1u << Q_GD_A) | (1u << Q_G2INF_A) | (1u << Q_BAD);
+  static constexpr uint32_t kUsedGapC =
+      (1u << Q_RRY_C) | (1u << Q_D2_C) | (1u << Q_GD_C) | (1u << Q_G2INF_C);
   const double *__restrict__ b;
   const int8_t *__restrict__ rt;
   const double *__restrict__ ybar;
