@@ -116,7 +116,7 @@ typedef struct {
                              by at most power_tol (relative) */
   int32_t device_layout;  /* 1: build the library's layout (CSC copy, length orders, slices) on the
                              GPU (default); 0: on the host cores.  Both give the same arrays.
-                             spmv_mode = 1 always builds on the host */
+                             spmv_mode = 1 and lp_batch_create always build on the host */
 } lp_options;
 
 typedef struct {

@@ -820,6 +820,20 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
   }
   cs.hist_grid = (int)std::min<int64_t>(std::max<int64_t>(1, (N + 2047) / 2048), 4 * h->nsm);
   if ((e = h->alloc(&cs.hpart, (int64_t)2 * cs.hist_grid * 4 * kBuckets)) != LP_OK) return e;
+  {
+    // a histogram warp scans at most kWarp * ceil(N / stride) elements
+    const int64_t nw = (int64_t)cs.hist_grid * kHistWarps, stride = nw * kWarp;
+    cs.cand_cap = (int64_t)kWarp * ((N + stride - 1) / stride);
+    for (int k = 0; k < 2; ++k) {
+      if (k == 1 && h->nsearch < 2) {
+        cs.cand[1] = cs.cand[0];
+        cs.ccnt[1] = cs.ccnt[0];
+        break;
+      }
+      if ((e = h->alloc(&cs.cand[k], nw * cs.cand_cap)) != LP_OK) return e;
+      if ((e = h->alloc(&cs.ccnt[k], nw)) != LP_OK) return e;
+    }
+  }
   if ((e = h->alloc(&cs.btot, (int64_t)2 * 4 * kBuckets)) != LP_OK) return e;
   if ((e = h->alloc(&cs.pair_x, (int64_t)2 * n)) != LP_OK) return e;
   if ((e = h->alloc(&cs.pair_y, (int64_t)2 * m)) != LP_OK) return e;
@@ -1159,6 +1173,7 @@ lp_status lp_normalized_gap(lp_handle h, const double *x, const double *y, doubl
   LP_CU(cudaMemcpyAsync(st, &hs, sizeof(DevState), cudaMemcpyHostToDevice, s));
   LP_CU(cudaStreamSynchronize(s));
   cs.pair_x = cs.pair_y = nullptr;  // the handle's pair buffers belong to its solve
+  cs.cand[0] = cs.cand[1] = nullptr;  // and so do its candidate lists: full scans
   launch_check(h->A, h->AT, v, st, nullptr, cs, n, m, 1, nullptr, false, s);
   LP_CU(cudaGetLastError());
   LSearch L{};
@@ -1498,6 +1513,7 @@ extern "C" lp_status lp_normalized_gap_static(lp_handle h, const double *x, cons
   hs.r_given = r;
   LP_CU(cudaMemcpyAsync(st, &hs, sizeof(DevState), cudaMemcpyHostToDevice, s));
   cs.pair_x = cs.pair_y = nullptr;  // the handle's pair buffers belong to its solve
+  cs.cand[0] = cs.cand[1] = nullptr;  // and so do its candidate lists: full scans
   launch_check(h->A, h->AT, v, st, nullptr, cs, n, m, 1, nullptr, false, s);
   LP_CU(cudaGetLastError());
   LSearch L{};

@@ -175,6 +175,10 @@ struct CheckScratch {
   int32_t hist_grid;
   double *pair_x, *pair_y; // [2n], [2m]: (xbar, x) and (ybar, y) interleaved for the check's
                            // gathers (16-byte aligned); null: gather the two vectors apart
+  // multiplier search candidate lists: per histogram warp cand_cap slots (elements of
+  // the bracket after the first pass) and a count; null: every pass scans all elements
+  int32_t *cand[2], *ccnt[2];
+  int64_t cand_cap;
 };
 
 // Launch with programmatic stream serialization: the kernel may be scheduled

@@ -518,7 +518,8 @@ __global__ void __launch_bounds__(kHistWarps *kWarp) ls_hist_kernel(
     const double *__restrict__ g20, const double *__restrict__ gd0,
     const uint64_t *__restrict__ keys1, const double *__restrict__ d21,
     const double *__restrict__ g21, const double *__restrict__ gd1, int64_t N,
-    const DevState *st, int pass, double *hpart) {
+    const DevState *st, int pass, double *hpart, int32_t *cand0, int32_t *cand1, int32_t *ccnt0,
+    int32_t *ccnt1, int64_t wcap) {
   const int sidx = blockIdx.y;
   const LSearch &L = st->ls[sidx];
   if (L.done) return;
@@ -539,19 +540,27 @@ __global__ void __launch_bounds__(kHistWarps *kWarp) ls_hist_kernel(
   }
   __syncthreads();
   const int lane = threadIdx.x & (kWarp - 1), warp = threadIdx.x >> 5;
-  const int64_t stride = (int64_t)gridDim.x * kHistWarps * kWarp;
-  for (int64_t base = ((int64_t)blockIdx.x * kHistWarps + warp) * kWarp; base < N; base += stride) {
-    const int64_t e = base + lane;
-    bool act = false;
-    int bk = -1;
-    if (e < N) {
+  // Candidate lists: in pass 1 each warp keeps, in its scan order, the
+  // elements inside the bracket of pass 0; later passes read only that list
+  // (its elements are a superset of every later bracket's).  Without lists
+  // (cand0 null) every pass scans all N elements.
+  const int64_t gw = (int64_t)blockIdx.x * kHistWarps + warp;
+  int32_t *cand = cand0 ? (sidx ? cand1 : cand0) + gw * wcap : nullptr;
+  int32_t *ccnt = sidx ? ccnt1 : ccnt0;
+  // element e (or -1): is it in the current bracket, and in which bucket
+  auto classify = [&](int64_t e, bool &act, int &bk) {
+    act = false;
+    bk = -1;
+    if (e >= 0) {
       const uint64_t k = keys[e];
       if (k != kNoKey && (pass == 0 || (k >> (shift + 8)) == (pre >> (shift + 8)))) {
         act = true;
         bk = (int)((k >> shift) & 255u);
       }
     }
-    if (__ballot_sync(kFull, act) == 0u) continue;
+  };
+  auto add = [&](int64_t e, bool act, int bk) {
+    if (__ballot_sync(kFull, act) == 0u) return;
     double vd = 0.0, vg = 0.0, ve = 0.0;
     if (act) {
       vd = d2[e];
@@ -612,6 +621,32 @@ __global__ void __launch_bounds__(kHistWarps *kWarp) ls_hist_kernel(
       }
     }
     __syncwarp();
+  };
+  if (cand && pass >= 2) {
+    const int32_t count = ccnt[gw];
+    for (int32_t i0 = 0; i0 < count; i0 += kWarp) {
+      const int64_t e = i0 + lane < count ? (int64_t)cand[i0 + lane] : -1;
+      bool act;
+      int bk;
+      classify(e, act, bk);
+      add(e, act, bk);
+    }
+  } else {
+    const int64_t stride = (int64_t)gridDim.x * kHistWarps * kWarp;
+    int32_t count = 0;
+    for (int64_t base = gw * kWarp; base < N; base += stride) {
+      const int64_t e = base + lane < N ? base + lane : -1;
+      bool act;
+      int bk;
+      classify(e, act, bk);
+      if (cand && pass == 1) {
+        const unsigned bal = __ballot_sync(kFull, act);
+        if (act) cand[count + __popc(bal & ((1u << lane) - 1u))] = (int32_t)e;
+        count += __popc(bal);
+      }
+      add(e, act, bk);
+    }
+    if (cand && pass == 1 && lane == 0) ccnt[gw] = count;
   }
   __syncthreads();
   double *out = hpart + ((size_t)sidx * gridDim.x + blockIdx.x) * 4 * kBuckets;
@@ -1228,7 +1263,7 @@ void launch_check(const SellMat &A, const SellMat &AT, const DevVecs &v, DevStat
     for (int p = 0; p < kSearchPasses; ++p) {
       ls_hist_kernel<<<dim3(cs.hist_grid, nsearch), kHistWarps * kWarp, 0, s>>>(
           cs.keys[0], cs.d2[0], cs.g2[0], cs.gd[0], cs.keys[1], cs.d2[1], cs.g2[1], cs.gd[1], N,
-          st, p, cs.hpart);
+          st, p, cs.hpart, cs.cand[0], cs.cand[1], cs.ccnt[0], cs.ccnt[1], cs.cand_cap);
       ls_select_kernel<<<dim3(kBuckets, nsearch), kBuckets, 0, s>>>(st, p, cs.hpart, cs.btot,
                                                                  cs.hist_grid);
     }
