@@ -41,9 +41,10 @@ OMEGA_GRID = [4.0 ** k for k in range(-3, 4)]  # Section 7 grid (powers of 4), 2
 OMEGA_ITERS = 2048  # a multiple of the check period (the batch needs one)
 FALLBACK_HBM_GBS = 6800.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one primal_kernel launch on
-# this workload with warm L2 (the benchmark's steady state), from a one-pass
-# ncu capture; set to None when the kernel changes.
-PRIMAL_TRAFFIC_BYTES = 128.0e6
+# this workload with warm L2 (the benchmark's steady state), per column-pass
+# variant (lp_info.spmv_unroll), from one-pass ncu captures; a variant missing
+# here, or a kernel changed since, reports null.
+PRIMAL_TRAFFIC_BYTES = {-2: 127.6e6, -4: 124.0e6, 2: 123.9e6, 4: 123.9e6}
 
 
 def parse():
@@ -73,6 +74,8 @@ def parse():
                    help="run only the batched section and print its JSON (profiling)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--kernel-reps", type=int, default=50)  # >= 1
+    p.add_argument("--spmv-unroll", type=int, default=None, choices=[-4, -2, 2, 4],
+                   help="fix the column-pass variant (no tuner) for the headline solver")
     return p.parse_args()
 
 
@@ -430,7 +433,9 @@ def run_ours(args):
     lp.load()
     data = workload(args)
     stream = torch.cuda.current_stream()
-    g = lp.LP(data, stream=stream, check_every=K_CHECK)
+    fixed = ({} if args.spmv_unroll is None
+             else {"autotune": 0, "spmv_unroll": args.spmv_unroll})
+    g = lp.LP(data, stream=stream, check_every=K_CHECK, **fixed)
     info0 = g.info()
 
     def barrier():
@@ -699,7 +704,9 @@ def run_ours(args):
                "achieved_gbs_per_iter": (primal_b + dual_b) * value / ws / 1e9,
                "roofline": {"bound": "hbm", "kernel": "primal_kernel", "achieved": achieved,
                             "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                            "peak_kind": peak_kind, "traffic": PRIMAL_TRAFFIC_BYTES,
+                            "peak_kind": peak_kind,
+                            "traffic": PRIMAL_TRAFFIC_BYTES.get(info0.spmv_unroll),
+                            "variant": info0.spmv_unroll,
                             "algorithmic_bytes": primal_b, "avg_launch_ms": primal_ms,
                             "dual_kernel_ms": dual_ms, "dual_algorithmic_bytes": dual_b,
                             "gather_bound": gather_bound},

@@ -264,42 +264,48 @@ lp_status set_run_params(lp_problem *h, double tol, cudaStream_t s) {
 // resets the state afterwards.
 lp_status tune_variants(lp_problem *h, cudaStream_t s) {
   if (h->opt.spmv_mode != 0) return LP_OK;
-  const int cands[4] = {-2, -4, 2, 4};
+  constexpr int kCands = 4, kRounds = 3, kReps = 3;
+  const int cands[kCands] = {-2, -4, 2, 4};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   LP_CU(cudaEventCreate(&e0));
   LP_CU(cudaEventCreate(&e1));
   lp_status st = LP_OK;
+  // Rounds visit the candidates in rotated order (no candidate always runs
+  // first after the previous pass); each candidate keeps its best time.
   for (int pass = 0; pass < 2 && st == LP_OK; ++pass) {
     int32_t &u = pass ? h->opt.spmv_unroll_rows : h->opt.spmv_unroll;
-    int best_u = u;
-    float best = 1e30f;
-    for (int c : cands) {
-      u = c;
-      for (int r = 0; r < 5; ++r) {
-        if (r == 1) cudaEventRecord(e0, s);
-        if (h->mixed) {
-          if (pass == 0) launch_primal_mix(h->AT, h->mv, h->st, h->w, 0, u, s);
-          else launch_dual_mix(h->A, h->mv, h->v, h->st, h->w, 0, u, s);
-        } else if (pass == 0) {
-          launch_primal_step(h->AT, h->v, h->st, h->w, 0, u, h->grid_cap, s);
-        } else {
-          launch_dual_step(h->A, h->v, h->st, h->w, 0, u, h->grid_cap, s);
+    float best[kCands];
+    for (float &b : best) b = 1e30f;
+    for (int round = 0; round < kRounds && st == LP_OK; ++round) {
+      for (int i = 0; i < kCands; ++i) {
+        const int ci = (i + round) % kCands;
+        u = cands[ci];
+        for (int r = 0; r <= kReps; ++r) {
+          if (r == 1) cudaEventRecord(e0, s);
+          if (h->mixed) {
+            if (pass == 0) launch_primal_mix(h->AT, h->mv, h->st, h->w, 0, u, s);
+            else launch_dual_mix(h->A, h->mv, h->v, h->st, h->w, 0, u, s);
+          } else if (pass == 0) {
+            launch_primal_step(h->AT, h->v, h->st, h->w, 0, u, h->grid_cap, s);
+          } else {
+            launch_dual_step(h->A, h->v, h->st, h->w, 0, u, h->grid_cap, s);
+          }
         }
-      }
-      cudaEventRecord(e1, s);
-      float ms = 0.0f;
-      cudaError_t err = cudaEventSynchronize(e1);
-      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
-      if (err != cudaSuccess) {
-        st = cuda_fail(err, "variant tuning");
-        break;
-      }
-      if (ms < best) {
-        best = ms;
-        best_u = c;
+        cudaEventRecord(e1, s);
+        float ms = 0.0f;
+        cudaError_t err = cudaEventSynchronize(e1);
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err != cudaSuccess) {
+          st = cuda_fail(err, "variant tuning");
+          break;
+        }
+        best[ci] = std::min(best[ci], ms);
       }
     }
-    u = best_u;
+    int pick = 0;
+    for (int ci = 1; ci < kCands; ++ci)
+      if (best[ci] < best[pick]) pick = ci;
+    u = cands[pick];
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
