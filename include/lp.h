@@ -137,6 +137,8 @@ typedef struct {
                            permutations, slices), device upload, sigma_max estimate */
   int32_t spmv_unroll, spmv_unroll_rows; /* kernel variants in use (tuned or given) */
   int32_t sigma_steps;  /* steps of the sigma_max estimator (0 when eta was given) */
+  int32_t graph_kernels; /* kernel launches per replay of the graph of K iterations + check
+                            (0 until the first lp_solve / lp_iterate builds it) */
 } lp_info;
 
 /* Defaults: beta = e^-1, K = 64, ADAPTIVE, tau0 = K, omega = 1, eta = 0

@@ -110,6 +110,7 @@ struct lp_problem {
   int grid_cap = 0;  // blocks of the per-slice iteration kernels (0: one warp per slice)
   double setup_ms[4] = {0, 0, 0, 0};  // lp_create phases (lp_info.setup_ms)
   int32_t sigma_steps = 0;            // Lanczos / power-iteration steps taken for sigma_max
+  int32_t graph_kernels = 0;          // kernel nodes of the K-iteration graph
 
   ~lp_problem() {
     if (ckpt) cudaFree(ckpt);
@@ -245,6 +246,18 @@ lp_status build_graph(lp_problem *h) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
   h->graph = g;
   LP_CU(cudaGraphInstantiate(&h->exec, g, 0));
+  // kernel launches per replay (lp_info.graph_kernels)
+  size_t count = 0;
+  LP_CU(cudaGraphGetNodes(g, nullptr, &count));
+  std::vector<cudaGraphNode_t> nodes(count);
+  if (count > 0) LP_CU(cudaGraphGetNodes(g, nodes.data(), &count));
+  int32_t kernels = 0;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    LP_CU(cudaGraphNodeGetType(nd, &t));
+    kernels += (t == cudaGraphNodeTypeKernel);
+  }
+  h->graph_kernels = kernels;
   return LP_OK;
 }
 
@@ -257,9 +270,9 @@ lp_status set_run_params(lp_problem *h, double tol, cudaStream_t s) {
 }
 
 // Kernel-variant tuner (lp_options.autotune): on this problem, times every
-// unroll variant of the column pass, then of the row pass (one warm-up and
-// four timed launches each, CUDA events on the stream) and keeps the
-// fastest.  Every variant sums each row in the same order, so the choice
+// unroll variant of the column pass, then of the row pass (three rounds, each
+// a warm-up and three timed launches per variant, CUDA events on the stream)
+// and keeps the fastest.  Every variant sums each row in the same order, so the choice
 // changes speed, not results.  The launches advance the iterate: the caller
 // resets the state afterwards.
 lp_status tune_variants(lp_problem *h, cudaStream_t s) {
@@ -1106,6 +1119,7 @@ lp_status lp_get_info(lp_handle h, lp_info *info) {
   info->spmv_unroll_rows = h->opt.spmv_unroll_rows;
   for (int i = 0; i < 4; ++i) info->setup_ms[i] = h->setup_ms[i];
   info->sigma_steps = h->sigma_steps;
+  info->graph_kernels = h->graph_kernels;
   return LP_OK;
 }
 

@@ -49,7 +49,8 @@ class lp_info(C.Structure):
                 ("last_rho", C.c_double), ("last_radius", C.c_double),
                 ("nnz_padded", C.c_int64), ("n_long_rows", C.c_int32), ("n_long_cols", C.c_int32),
                 ("setup_ms", C.c_double * 4), ("spmv_unroll", C.c_int32),
-                ("spmv_unroll_rows", C.c_int32), ("sigma_steps", C.c_int32)]
+                ("spmv_unroll_rows", C.c_int32), ("sigma_steps", C.c_int32),
+                ("graph_kernels", C.c_int32)]
 
 
 class lp_batch_tuning(C.Structure):
@@ -341,6 +342,7 @@ class Info:
     spmv_unroll: int = 0
     spmv_unroll_rows: int = 0
     sigma_steps: int = 0
+    graph_kernels: int = 0
 
     @property
     def rel_kkt(self) -> float:
@@ -403,7 +405,8 @@ class LP:
         return Info(i.iters, i.restarts, i.checks, i.status, i.returned, tuple(i.kkt_avg),
                     tuple(i.kkt_cur), i.eta, i.sigma_max, i.omega, i.tau, i.sigma, i.rho_stored,
                     i.last_rho, i.last_radius, i.nnz_padded, i.n_long_rows, i.n_long_cols,
-                    tuple(i.setup_ms), i.spmv_unroll, i.spmv_unroll_rows, i.sigma_steps)
+                    tuple(i.setup_ms), i.spmv_unroll, i.spmv_unroll_rows, i.sigma_steps,
+                    i.graph_kernels)
 
     def trace(self, capacity=1 << 20):
         return lp_get_trace(self.h, capacity)

@@ -342,3 +342,14 @@ def test_variant_tuner_picks_a_variant_and_keeps_results(lpm):
     for st in states[1:]:
         for k in st:
             np.testing.assert_array_equal(st[k], states[0][k])
+
+
+def test_graph_kernel_count(lpm):
+    """lp_info.graph_kernels: none before the first solve; then the 2K iteration
+    kernels and the check's 23 (two pair packs, two check passes, finalize,
+    eight search passes of two kernels, decision, restart copy)."""
+    data = lpgen.tiny_standard_form(0)
+    with lpm.LP(data, eta=0.05, check_every=32, max_iter=64, autotune=0) as g:
+        assert g.info().graph_kernels == 0
+        g.solve(1e-300)
+        assert g.info().graph_kernels == 2 * 32 + 23
