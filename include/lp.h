@@ -117,6 +117,11 @@ typedef struct {
   int32_t device_layout;  /* 1: build the library's layout (CSC copy, length orders, slices) on the
                              GPU (default); 0: on the host cores.  Both give the same arrays.
                              spmv_mode = 1 and lp_batch_create always build on the host */
+  int32_t split_row_len;  /* a row of A or A^T with a whole warp (long_row_threshold or more
+                             elements) longer than this is cut into chunks of at most this many
+                             elements, one warp each, whose partial sums the last chunk to finish
+                             adds in chunk order: no warp walks a very long row alone.  A positive
+                             multiple of 32, or 0 for never (2048; spmv_mode = 1 never splits) */
 } lp_options;
 
 typedef struct {
@@ -139,11 +144,12 @@ typedef struct {
   int32_t sigma_steps;  /* steps of the sigma_max estimator (0 when eta was given) */
   int32_t graph_kernels; /* kernel launches per replay of the graph of K iterations + check
                             (0 until the first lp_solve / lp_iterate builds it) */
+  int32_t n_split_slices; /* chunk slices of split rows in A and A^T together (split_row_len) */
 } lp_info;
 
 /* Defaults: beta = e^-1, K = 64, ADAPTIVE, tau0 = K, omega = 1, eta = 0
  * (auto), power_iters = 5000, power_tol = 1e-10, max_iter = 1e7, autotune = 1,
- * sigma_method = LP_SIGMA_LANCZOS, device_layout = 1. */
+ * sigma_method = LP_SIGMA_LANCZOS, device_layout = 1, split_row_len = 2048. */
 void lp_default_options(lp_options *opt);
 
 /*

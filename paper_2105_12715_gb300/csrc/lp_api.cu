@@ -182,6 +182,23 @@ struct lp_problem {
     M.info = info;
     M.idx = ix;
     M.val = vv;
+    SplitSlice *split = nullptr;
+    if (!H.split.empty() && (s = upload(&split, H.split)) != LP_OK) return s;
+    return attach_split(M, split, (int64_t)H.split.size());
+  }
+
+  // Chunk-slice table of split rows, their partial sums and arrival counters
+  // (zero between passes).
+  lp_status attach_split(SellMat &M, const SplitSlice *split, int64_t nsplit) {
+    M.nsplit = (int32_t)nsplit;
+    M.split = split;
+    M.split_part = nullptr;
+    M.split_cnt = nullptr;
+    if (nsplit == 0) return LP_OK;
+    lp_status s;
+    if ((s = alloc(&M.split_part, 2 * nsplit)) != LP_OK) return s;
+    if ((s = alloc(&M.split_cnt, nsplit)) != LP_OK) return s;
+    LP_CU(cudaMemset(M.split_cnt, 0, sizeof(int32_t) * (size_t)nsplit));
     return LP_OK;
   }
 };
@@ -396,8 +413,9 @@ lp_status host_layout(lp_problem *h, const int32_t *row_ptr, const int32_t *col_
   const int64_t target = (int64_t)opt.lane_auto * h->nsm;
   const LanePolicy pa = choose_policy(rp, perm_y, policy, target);
   const LanePolicy pat = choose_policy(cp, perm_x, policy, target);
-  build_sell(m, n, rp, hci, hv, perm_y, inv_x, pa, HA);
-  build_sell(n, m, cp, ri.data(), cv.data(), perm_x, inv_y, pat, HAT);
+  const int32_t split_len = opt.spmv_mode == 0 ? opt.split_row_len : 0;
+  build_sell(m, n, rp, hci, hv, perm_y, inv_x, pa, HA, {}, split_len);
+  build_sell(n, m, cp, ri.data(), cv.data(), perm_x, inv_y, pat, HAT, {}, split_len);
   h->nnz_padded = (int64_t)HA.idx.size();
 
   // permuted vectors
@@ -658,21 +676,45 @@ lp_status device_layout(lp_problem *h, const int32_t *row_ptr, const int32_t *co
     return p;
   };
   const LanePolicy policy{opt.long_row_threshold, opt.lane_steps, opt.single_lane_max};
+  const int32_t split_len = opt.split_row_len;
 
   // slices and fill of one operator
   auto make = [&](auto *ptr, int32_t nrows, int32_t ncols, const std::vector<int64_t> &hist,
                   const int32_t *perm, const int32_t *ind, const double *vals,
                   const int32_t *relabel, SellMat &M) -> lp_status {
+    const LanePolicy pol = choose(hist, policy);
+    // split rows: whole-warp rows longer than split_len, the longest rows, so
+    // the first nsr of the sorted order; the ordinary runs follow them
+    std::vector<int64_t> rest = hist;
+    int64_t nsr = 0, nsplit = 0;
+    if (split_len > 0)
+      for (int64_t len = (int64_t)hist.size() - 1; len > split_len; --len)
+        if (hist[(size_t)len] > 0 && lanes_log2(len, pol) == 5) {
+          nsr += hist[(size_t)len];
+          nsplit += hist[(size_t)len] * ((len + split_len - 1) / split_len);
+          rest[(size_t)len] = 0;
+        }
     LayRuns runs{};
     int64_t ns = 0, wr = 0;
-    if (!runs_of(hist, choose(hist, policy), &runs, &ns, &wr))
+    if (!runs_of(rest, pol, &runs, &ns, &wr))
       return fail(LP_ERR_INVALID_ARG, "lane policy gives more than 6 runs");
+    for (int q = 0; q < runs.count; ++q) {
+      runs.g0[q] += nsr;
+      runs.s0[q] += nsplit;
+    }
+    ns += nsplit;
+    wr += nsr;
     SliceInfo *info = nullptr;
-    int64_t *width = nullptr, *off = nullptr;
+    SplitSlice *split = nullptr;
+    int64_t *width = nullptr, *off = nullptr, *nch = nullptr, *cstart = nullptr;
     if ((e = h->alloc(&info, ns + 1)) != LP_OK) return e;
+    if ((e = h->alloc(&split, nsplit)) != LP_OK) return e;
     if ((e = tmp(&width, ns)) != LP_OK) return e;
     if ((e = tmp(&off, ns)) != LP_OK) return e;
-    lay_slices(runs, perm, ptr, ns, nrows, info, width, off, sums, nsm, s);
+    if ((e = tmp(&nch, nsr)) != LP_OK) return e;
+    if ((e = tmp(&cstart, nsr)) != LP_OK) return e;
+    lay_slices(runs, perm, ptr, ns, nrows, info, width, off, sums, nsm, s, nsr, nsplit, split_len,
+               split, nch, cstart);
     SliceInfo last{};
     LP_CU(cudaMemcpyAsync(&last, info + ns, sizeof(SliceInfo), cudaMemcpyDeviceToHost, s));
     LP_CU(cudaStreamSynchronize(s));
@@ -682,7 +724,8 @@ lp_status device_layout(lp_problem *h, const int32_t *row_ptr, const int32_t *co
     if ((e = h->alloc(&ix, last.off)) != LP_OK) return e;
     if ((e = h->alloc(&vv, last.off)) != LP_OK) return e;
     if (h->mixed && (e = h->alloc(&vf, last.off)) != LP_OK) return e;
-    lay_fill(info, ns, perm, ptr, ind, vals, relabel, ix, vv, vf, nsm, s);
+    lay_fill(info, ns, perm, ptr, ind, vals, relabel, ix, vv, vf, nsm, s, split, nsplit,
+             split_len);
     LP_CU(cudaGetLastError());
     M.nrows = nrows;
     M.ncols = ncols;
@@ -692,7 +735,7 @@ lp_status device_layout(lp_problem *h, const int32_t *row_ptr, const int32_t *co
     M.idx = ix;
     M.val = vv;
     M.valf = vf;
-    return LP_OK;
+    return h->attach_split(M, split, nsplit);
   };
   if ((e = make(drp, m, n, hr, perm_y, dci, dv, inv_x, h->A)) != LP_OK) return e;
   if ((e = make(cp, n, m, hc, perm_x, ri, cv, inv_y, h->AT)) != LP_OK) return e;
@@ -749,6 +792,7 @@ void lp_default_options(lp_options *o) {
   o->autotune = 1;
   o->sigma_method = LP_SIGMA_LANCZOS;
   o->device_layout = 1;
+  o->split_row_len = 2048;
 }
 
 const char *lp_last_error(void) { return err_msg().c_str(); }
@@ -821,7 +865,8 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
   CheckScratch &cs = h->cs;
   cs.cols_grid = check_grid_for(h->AT, h->nsm);
   cs.rows_grid = check_grid_for(h->A, h->nsm);
-  cs.pstride = std::max(cs.cols_grid + cs.rows_grid, 8 * h->nsm);
+  cs.pstride = std::max(cs.cols_grid + cs.rows_grid + split_grid(h->A) + split_grid(h->AT),
+                        8 * h->nsm);
   if ((e = h->alloc(&cs.partials, (int64_t)NQ * cs.pstride)) != LP_OK) return e;
   const int64_t N = (int64_t)n + m;
   for (int k = 0; k < 2; ++k) {
@@ -1120,6 +1165,7 @@ lp_status lp_get_info(lp_handle h, lp_info *info) {
   for (int i = 0; i < 4; ++i) info->setup_ms[i] = h->setup_ms[i];
   info->sigma_steps = h->sigma_steps;
   info->graph_kernels = h->graph_kernels;
+  info->n_split_slices = h->A.nsplit + h->AT.nsplit;
   return LP_OK;
 }
 

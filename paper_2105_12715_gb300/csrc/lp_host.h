@@ -174,6 +174,7 @@ inline void sort_by_length_desc(const P *ptr, int32_t begin, int32_t end, int32_
 struct HostSell {
   int32_t nrows = 0, ncols = 0, nslices = 0, n_warp_rows = 0;
   std::vector<SliceInfo> info;
+  std::vector<SplitSlice> split;  // chunk slices of split rows (slices 0 .. split.size() - 1)
   uvec<int32_t> idx;
   uvec<double> val;
 };
@@ -243,22 +244,42 @@ inline LanePolicy choose_policy(const std::vector<int64_t> &ptr, const std::vect
 // is original row perm[r] of the CSR (ptr, ind, v); column indices
 // relabeled by relabel.  Rows come longest first, so a slice is closed when
 // it is full (32 / G rows), when the next row wants another G, or at a
-// break (no slice spans two batched problems).
+// break (no slice spans two batched problems).  With split_len > 0 (no
+// breaks), a whole-warp row longer than split_len becomes ceil(len /
+// split_len) chunk slices of at most split_len elements; being the longest,
+// these rows come first, so their chunk slices are slices 0 .. nsplit - 1.
 inline void build_sell(int32_t nrows, int32_t ncols, const std::vector<int64_t> &ptr,
                        const int32_t *ind, const double *v,
                        const std::vector<int32_t> &perm, const std::vector<int32_t> &relabel,
                        const LanePolicy &policy, HostSell &S,
-                       const std::vector<int32_t> &breaks = {}) {
+                       const std::vector<int32_t> &breaks = {}, int32_t split_len = 0) {
   S.nrows = nrows;
   S.ncols = ncols;
   auto len = [&](int32_t r) { return ptr[perm[r] + 1] - ptr[perm[r]]; };
   S.info.clear();
+  S.split.clear();
   int64_t off = 0;
   int32_t r = 0;
   size_t bi = 0;
   while (r < nrows) {
     const int32_t lim = slice_limit(breaks, &bi, r, nrows);
     const int lg = lanes_log2(len(r), policy);
+    if (split_len > 0 && breaks.empty() && lg == 5 && len(r) > split_len &&
+        S.split.size() == S.info.size()) {
+      const int64_t L = len(r);
+      const int32_t nch = (int32_t)((L + split_len - 1) / split_len);
+      const int32_t first = (int32_t)S.info.size();
+      for (int32_t c = 0; c < nch; ++c) {
+        const int64_t clen = std::min<int64_t>(split_len, L - (int64_t)c * split_len);
+        const int64_t steps = (clen + kWarp - 1) / kWarp;
+        S.info.push_back(SliceInfo{off, r, (int32_t)((steps << 3) | 5)});
+        S.split.push_back(SplitSlice{c, nch, first, c * split_len});
+        off += steps * kWarp;
+      }
+      S.n_warp_rows += 1;
+      ++r;
+      continue;
+    }
     const int cap = kWarp >> lg;
     int32_t q = r;
     int64_t mx = 0;
@@ -297,6 +318,16 @@ inline void build_sell(int32_t nrows, int32_t ncols, const std::vector<int64_t> 
       const int lg = a.len_g & 7, G = 1 << lg;
       std::fill(S.idx.begin() + a.off, S.idx.begin() + S.info[sl + 1].off, 0);
       std::fill(S.val.begin() + a.off, S.val.begin() + S.info[sl + 1].off, 0.0);
+      if (sl < (int32_t)S.split.size()) {  // a chunk of a split row (G = 32)
+        const SplitSlice &sp = S.split[sl];
+        const int64_t src = ptr[perm[a.row0]] + sp.begin;
+        const int64_t clen = std::min<int64_t>(split_len, len(a.row0) - sp.begin);
+        for (int64_t k = 0; k < clen; ++k) {
+          S.idx[a.off + k] = relabel[ind[src + k]];
+          S.val[a.off + k] = v[src + k];
+        }
+        continue;
+      }
       for (int32_t row = a.row0; row < S.info[sl + 1].row0; ++row) {
         const int64_t src = ptr[perm[row]];
         const int64_t lane0 = (int64_t)(row - a.row0) * G;
@@ -362,6 +393,8 @@ inline lp_status validate_options(const lp_options &o) {
     return fail(LP_ERR_INVALID_ARG, "sigma_method must be LP_SIGMA_POWER or LP_SIGMA_LANCZOS");
   if (o.device_layout != 0 && o.device_layout != 1)
     return fail(LP_ERR_INVALID_ARG, "device_layout must be 0 or 1");
+  if (o.split_row_len < 0 || o.split_row_len % 32 != 0)
+    return fail(LP_ERR_INVALID_ARG, "split_row_len must be 0 or a positive multiple of 32");
   if (o.precision != LP_PRECISION_FP64 && o.precision != LP_PRECISION_MIXED)
     return fail(LP_ERR_INVALID_ARG, "precision must be LP_PRECISION_FP64 or LP_PRECISION_MIXED");
   return LP_OK;

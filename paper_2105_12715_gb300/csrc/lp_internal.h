@@ -33,6 +33,20 @@ struct SliceInfo {
 // load of the matrix stream is 32 consecutive elements.  Rows are padded
 // with zero values up to the slice's longest row (a multiple of G).
 // info has nslices + 1 entries; the last one holds the end offset and nrows.
+//
+// Split rows: a row longer than the split length (a whole-warp row) is cut
+// into chunks of at most that many elements, one warp slice each (G = 32),
+// so that no warp walks a very long row alone.  These chunk slices come
+// first (the split rows are the longest); split[s] says which chunk slice s
+// is.  Each chunk writes its partial sums to split_part; the last chunk of
+// a row to finish (arrival counter split_cnt[first], reset by it) adds the
+// partials in chunk order and runs the row's epilogue.
+struct SplitSlice {
+  int32_t chunk;    // chunk index within its row
+  int32_t nchunks;  // chunks of the row
+  int32_t first;    // slice index of the row's chunk 0 (its counter index)
+  int32_t begin;    // element offset of the chunk within the row
+};
 struct SellMat {
   int32_t nrows;
   int32_t ncols;
@@ -42,6 +56,10 @@ struct SellMat {
   const int32_t *idx;
   const double *val;
   const float *valf;        // FP32 copy of val (mixed precision), or null
+  int32_t nsplit = 0;                  // chunk slices (slices 0 .. nsplit - 1)
+  const SplitSlice *split = nullptr;   // [nsplit]
+  double *split_part = nullptr;        // [2 nsplit] partial sums of the chunks
+  int32_t *split_cnt = nullptr;        // [nsplit] arrival counters (at index first), zero between passes
 };
 
 // Work plan of the staged (TMA) SpMV kernels.  A segment is at most
@@ -236,14 +254,19 @@ template <class P>
 void lay_lengths(const P *ptr, int32_t count, int64_t *mx, uint32_t *key, int64_t mxv,
                  int64_t *hist, int nsm, cudaStream_t s);
 void lay_inverse(const int32_t *perm, int32_t count, int32_t *inv, int nsm, cudaStream_t s);
+// Slices of one operator: the chunk slices of the nsr split rows first
+// (nsplit of them, SplitSlice records in split; nch and cstart are nsr-long
+// scratch), then the runs of ordinary rows from slice nsplit on.
 template <class P>
 void lay_slices(const LayRuns &runs, const int32_t *perm, const P *ptr, int64_t nslices,
                 int32_t nrows, SliceInfo *info, int64_t *width, int64_t *off, int64_t *sums,
-                int nsm, cudaStream_t s);
+                int nsm, cudaStream_t s, int64_t nsr, int64_t nsplit, int32_t split_len,
+                SplitSlice *split, int64_t *nch, int64_t *cstart);
 template <class P>
 void lay_fill(const SliceInfo *info, int64_t nslices, const int32_t *perm, const P *ptr,
               const int32_t *ind, const double *val, const int32_t *relabel, int32_t *idx,
-              double *vout, float *vf, int nsm, cudaStream_t s);
+              double *vout, float *vf, int nsm, cudaStream_t s, const SplitSlice *split,
+              int64_t nsplit, int32_t split_len);
 void lay_vectors(const int32_t *perm_x, int32_t n, const double *c, const double *lb,
                  const double *ub, double *pc, double *pl, double *pu, long long *lk,
                  long long *uk, const int32_t *perm_y, int32_t m, const double *b,
@@ -286,6 +309,7 @@ void launch_weights(DevState *st, double *w, cudaStream_t s);
 void launch_norms(const DevVecs &v, DevState *st, double *partials, int pstride,
                   int grid, int n, int m, cudaStream_t s);
 int check_grid_for(const SellMat &A, int num_sms);
+int split_grid(const SellMat &A);
 void launch_primal_mix(const SellMat &AT, const MixVecs &mv, DevState *st, const double *w,
                        int k, int unroll, cudaStream_t s);
 void launch_dual_mix(const SellMat &A, const MixVecs &mv, const DevVecs &v, DevState *st,

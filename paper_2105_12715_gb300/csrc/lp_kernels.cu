@@ -30,7 +30,8 @@ namespace {
 
 // ------------------------------------------------------------ iteration
 
-template <int U, bool PIPE, int MINB>
+// SPLIT: the chunk slices of split rows (a second, small launch; see SellMat).
+template <int U, bool PIPE, int MINB, bool SPLIT = false>
 __global__ void __launch_bounds__(kBlock, MINB) primal_kernel(SellMat AT, const double *__restrict__ y,
                                                         PrimalEpi epi, const DevState *st,
                                                         const double *__restrict__ w, int k) {
@@ -38,10 +39,10 @@ __global__ void __launch_bounds__(kBlock, MINB) primal_kernel(SellMat AT, const 
   if (st->status != kRunning) return;
   epi.tau = st->tau;
   epi.w = w[k];
-  process_all<1, U, PIPE>(AT, y, (const double *)nullptr, epi);
+  process_all<1, U, PIPE, false, SPLIT>(AT, y, (const double *)nullptr, epi);
 }
 
-template <int U, bool PIPE, int MINB>
+template <int U, bool PIPE, int MINB, bool SPLIT = false>
 __global__ void __launch_bounds__(kBlock, MINB) dual_kernel(SellMat A, const double *__restrict__ xhat,
                                                       DualEpi epi, const DevState *st,
                                                       const double *__restrict__ w, int k) {
@@ -49,13 +50,14 @@ __global__ void __launch_bounds__(kBlock, MINB) dual_kernel(SellMat A, const dou
   if (st->status != kRunning) return;
   epi.sigma = st->sigma;
   epi.w = w[k];
-  process_all<1, U, PIPE>(A, xhat, (const double *)nullptr, epi);
+  process_all<1, U, PIPE, false, SPLIT>(A, xhat, (const double *)nullptr, epi);
 }
 
+template <bool SPLIT = false>
 __global__ void __launch_bounds__(kBlock) spmv_kernel(SellMat A, const double *__restrict__ v,
                                                       StoreEpi epi, const DevState *st) {
   if (st && (st->status != kRunning || st->pw_done)) return;
-  process_all<1, kUnroll>(A, v, (const double *)nullptr, epi);
+  process_all<1, kUnroll, false, false, SPLIT>(A, v, (const double *)nullptr, epi);
 }
 
 // ------------------------------------------------ staged (TMA) iteration
@@ -211,7 +213,7 @@ __global__ void __launch_bounds__(kStreamWarps *kWarp) dual_stream_kernel(
   stream_warp(A, P, xhat, epi, st);
 }
 
-template <int U, bool PIPE>
+template <int U, bool PIPE, bool SPLIT = false>
 __global__ void __launch_bounds__(kBlock) primal_mix_kernel(SellMat AT, const float *__restrict__ dy,
                                                             PrimalMixEpi epi, const DevState *st,
                                                             const double *__restrict__ w, int k) {
@@ -219,10 +221,10 @@ __global__ void __launch_bounds__(kBlock) primal_mix_kernel(SellMat AT, const fl
   if (st->status != kRunning) return;
   epi.tau = (float)st->tau;
   epi.w = w[k];
-  process_all<1, U, PIPE>(AT, dy, (const float *)nullptr, epi);
+  process_all<1, U, PIPE, false, SPLIT>(AT, dy, (const float *)nullptr, epi);
 }
 
-template <int U, bool PIPE>
+template <int U, bool PIPE, bool SPLIT = false>
 __global__ void __launch_bounds__(kBlock) dual_mix_kernel(SellMat A, const float *__restrict__ dxhat,
                                                           DualMixEpi epi, const DevState *st,
                                                           const double *__restrict__ w, int k) {
@@ -230,7 +232,7 @@ __global__ void __launch_bounds__(kBlock) dual_mix_kernel(SellMat A, const float
   if (st->status != kRunning) return;
   epi.sigma = (float)st->sigma;
   epi.w = w[k];
-  process_all<1, U, PIPE>(A, dxhat, (const float *)nullptr, epi);
+  process_all<1, U, PIPE, false, SPLIT>(A, dxhat, (const float *)nullptr, epi);
 }
 
 __device__ __forceinline__ double clampd(double v, double lo, double hi) {
@@ -335,30 +337,34 @@ __global__ void residuals_kernel(DevVecs v, MixVecs mv, const double *aty, const
 // (x <- xbar) moves ax into axb.
 
 // Forward step with masks, for the recomputation of one block.
+template <bool SPLIT = false>
 __global__ void __launch_bounds__(kBlock) primal_mask_kernel(SellMat AT,
                                                              const double *__restrict__ y,
                                                              PrimalEpi epi, double tau, double w) {
   epi.tau = tau;
   epi.w = w;
-  process_all<1, 2, true>(AT, y, (const double *)nullptr, epi);
+  process_all<1, 2, true, false, SPLIT>(AT, y, (const double *)nullptr, epi);
 }
 
+template <bool SPLIT = false>
 __global__ void __launch_bounds__(kBlock) dual_mask_kernel(SellMat A,
                                                            const double *__restrict__ xhat,
                                                            DualEpi epi, double sigma, double w) {
   epi.sigma = sigma;
   epi.w = w;
-  process_all<1, 4, true>(A, xhat, (const double *)nullptr, epi);
+  process_all<1, 4, true, false, SPLIT>(A, xhat, (const double *)nullptr, epi);
 }
 
+template <bool SPLIT = false>
 __global__ void __launch_bounds__(kBlock) adj_cols_kernel(SellMat AT, const double *__restrict__ u,
                                                           AdjColsEpi epi) {
-  process_all<1, 2, true>(AT, u, (const double *)nullptr, epi);
+  process_all<1, 2, true, false, SPLIT>(AT, u, (const double *)nullptr, epi);
 }
 
+template <bool SPLIT = false>
 __global__ void __launch_bounds__(kBlock) adj_rows_kernel(SellMat A, const double *__restrict__ v,
                                                           AdjRowsEpi epi) {
-  process_all<1, 4, true>(A, v, (const double *)nullptr, epi);
+  process_all<1, 4, true, false, SPLIT>(A, v, (const double *)nullptr, epi);
 }
 
 // Start of a reverse block: the restart after the block (if any), then u of
@@ -393,7 +399,7 @@ __global__ void adj_block_start_kernel(double *ax, double *axb, double *ay, doub
 // ---------------------------------------------------------------- check
 
 // PAIR: v0 holds the two gathered vectors interleaved (pack_pairs_kernel), v1 is unused.
-template <class Epi, bool PAIR>
+template <class Epi, bool PAIR, bool SPLIT = false>
 __global__ void __launch_bounds__(kBlock) check_kernel(SellMat A, const double *__restrict__ v0,
                                                        const double *__restrict__ v1, Epi epi,
                                                        const DevState *st, double *partials,
@@ -408,7 +414,7 @@ __global__ void __launch_bounds__(kBlock) check_kernel(SellMat A, const double *
   epi.isw = 1.0 / epi.sw;
 #pragma unroll
   for (int i = 0; i < NQ; ++i) epi.q[i] = 0.0;
-  process_all<2, kUnroll2, false, PAIR>(A, v0, v1, epi);
+  process_all<2, kUnroll2, false, PAIR, SPLIT>(A, v0, v1, epi);
   block_reduce_store_mask<NQ>(epi.q, Epi::kUsed | (epi.gap_c ? Epi::kUsedGapC : 0u), partials,
                               pstride, poff + (int)blockIdx.x);
 }
@@ -1112,6 +1118,16 @@ int item_grid(const SellMat &A) {
   return (int)g;
 }
 
+}  // namespace
+
+// Blocks of the second launch that handles the chunk slices of split rows
+// (one warp per chunk slice); 0 when the matrix has none.
+int split_grid(const SellMat &A) {
+  return A.nsplit > 0 ? (A.nsplit + kWarpsPerBlock - 1) / kWarpsPerBlock : 0;
+}
+
+namespace {
+
 int g_num_sms = 0;
 int num_sms() {
   if (g_num_sms == 0) {
@@ -1155,6 +1171,8 @@ void primal_launch(int occ, int g, cudaStream_t s, const SellMat &AT, const doub
                    const PrimalEpi &epi, DevState *st, const double *w, int k) {
   if (occ) launch_pdl(primal_kernel<U, PIPE, 5>, g, kBlock, s, AT, y, epi, st, w, k);
   else launch_pdl(primal_kernel<U, PIPE, 1>, g, kBlock, s, AT, y, epi, st, w, k);
+  if (AT.nsplit > 0)
+    launch_pdl(primal_kernel<U, PIPE, 1, true>, split_grid(AT), kBlock, s, AT, y, epi, st, w, k);
 }
 
 template <int U, bool PIPE>
@@ -1162,6 +1180,8 @@ void dual_launch(int occ, int g, cudaStream_t s, const SellMat &A, const double 
                  const DualEpi &epi, DevState *st, const double *w, int k) {
   if (occ) launch_pdl(dual_kernel<U, PIPE, 4>, g, kBlock, s, A, xhat, epi, st, w, k);
   else launch_pdl(dual_kernel<U, PIPE, 1>, g, kBlock, s, A, xhat, epi, st, w, k);
+  if (A.nsplit > 0)
+    launch_pdl(dual_kernel<U, PIPE, 1, true>, split_grid(A), kBlock, s, A, xhat, epi, st, w, k);
 }
 
 void launch_primal_step(const SellMat &AT, const DevVecs &v, DevState *st, const double *w,
@@ -1256,8 +1276,27 @@ void launch_check(const SellMat &A, const SellMat &AT, const DevVecs &v, DevStat
     check_kernel<CheckRowsEpi, false><<<cs.rows_grid, kBlock, 0, s>>>(
         A, v.xbar, v.x, re, st, cs.partials, cs.pstride, cs.cols_grid);
   }
-  check_finalize_kernel<<<NQ, kBlock, 0, s>>>(st, cs.partials, cs.pstride,
-                                             cs.cols_grid + cs.rows_grid);
+  // chunk slices of split rows: their blocks' sums go to the partial slots
+  // after the ordinary passes' (the gathered vectors as above)
+  const int sc = split_grid(AT), sr = split_grid(A);
+  const int pbase = cs.cols_grid + cs.rows_grid;
+  if (sc > 0) {
+    if (cs.pair_y && cs.pair_x)
+      check_kernel<CheckColsEpi, true, true><<<sc, kBlock, 0, s>>>(
+          AT, cs.pair_y, nullptr, ce, st, cs.partials, cs.pstride, pbase);
+    else
+      check_kernel<CheckColsEpi, false, true><<<sc, kBlock, 0, s>>>(
+          AT, v.ybar, v.y, ce, st, cs.partials, cs.pstride, pbase);
+  }
+  if (sr > 0) {
+    if (cs.pair_y && cs.pair_x)
+      check_kernel<CheckRowsEpi, true, true><<<sr, kBlock, 0, s>>>(
+          A, cs.pair_x, nullptr, re, st, cs.partials, cs.pstride, pbase + sc);
+    else
+      check_kernel<CheckRowsEpi, false, true><<<sr, kBlock, 0, s>>>(
+          A, v.xbar, v.x, re, st, cs.partials, cs.pstride, pbase + sc);
+  }
+  check_finalize_kernel<<<NQ, kBlock, 0, s>>>(st, cs.partials, cs.pstride, pbase + sc + sr);
   if (nsearch > 0) {
     const int64_t N = (int64_t)n + m;
     for (int p = 0; p < kSearchPasses; ++p) {
@@ -1279,12 +1318,16 @@ template <int U, bool PIPE>
 void primal_mix_launch(int g, cudaStream_t s, const SellMat &AT, const float *dy,
                        const PrimalMixEpi &epi, DevState *st, const double *w, int k) {
   launch_pdl(primal_mix_kernel<U, PIPE>, g, kBlock, s, AT, dy, epi, st, w, k);
+  if (AT.nsplit > 0)
+    launch_pdl(primal_mix_kernel<U, PIPE, true>, split_grid(AT), kBlock, s, AT, dy, epi, st, w, k);
 }
 
 template <int U, bool PIPE>
 void dual_mix_launch(int g, cudaStream_t s, const SellMat &A, const float *dxhat,
                      const DualMixEpi &epi, DevState *st, const double *w, int k) {
   launch_pdl(dual_mix_kernel<U, PIPE>, g, kBlock, s, A, dxhat, epi, st, w, k);
+  if (A.nsplit > 0)
+    launch_pdl(dual_mix_kernel<U, PIPE, true>, split_grid(A), kBlock, s, A, dxhat, epi, st, w, k);
 }
 
 void launch_primal_mix(const SellMat &AT, const MixVecs &mv, DevState *st, const double *w,
@@ -1334,8 +1377,10 @@ void launch_forward_masked(const SellMat &A, const SellMat &AT, const DevVecs &v
                            double sigma, double w, uint8_t *mx, uint8_t *my, cudaStream_t s) {
   PrimalEpi pe{v.c, v.lbk, v.ubk, v.x, v.xhat, v.xbar, 0.0, 0.0, mx};
   primal_mask_kernel<<<item_grid(AT), kBlock, 0, s>>>(AT, v.y, pe, tau, w);
+  if (AT.nsplit > 0) primal_mask_kernel<true><<<split_grid(AT), kBlock, 0, s>>>(AT, v.y, pe, tau, w);
   DualEpi de{v.b, v.row_type, v.y, v.ybar, 0.0, 0.0, my};
   dual_mask_kernel<<<item_grid(A), kBlock, 0, s>>>(A, v.xhat, de, sigma, w);
+  if (A.nsplit > 0) dual_mask_kernel<true><<<split_grid(A), kBlock, 0, s>>>(A, v.xhat, de, sigma, w);
 }
 
 void launch_adjoint_step(const SellMat &A, const SellMat &AT, const AdjVecs &a,
@@ -1343,8 +1388,10 @@ void launch_adjoint_step(const SellMat &A, const SellMat &AT, const AdjVecs &a,
                          double w, double w_prev, int has_prev, cudaStream_t s) {
   AdjColsEpi ce{a.ax, a.axb, a.ac, a.v, mx, tau, sigma, w};
   adj_cols_kernel<<<item_grid(AT), kBlock, 0, s>>>(AT, a.u, ce);
+  if (AT.nsplit > 0) adj_cols_kernel<true><<<split_grid(AT), kBlock, 0, s>>>(AT, a.u, ce);
   AdjRowsEpi re{a.ay, a.ayb, a.ab, a.u, my_prev, tau, sigma, w_prev, has_prev};
   adj_rows_kernel<<<item_grid(A), kBlock, 0, s>>>(A, a.v, re);
+  if (A.nsplit > 0) adj_rows_kernel<true><<<split_grid(A), kBlock, 0, s>>>(A, a.v, re);
 }
 
 void launch_adjoint_block_start(const AdjVecs &a, const uint8_t *my_last, int restarted,
@@ -1365,6 +1412,7 @@ void launch_spmv(const SellMat &A, const double *v, double *out, cudaStream_t s,
                  DevState *st_guard) {
   StoreEpi epi{out};
   spmv_kernel<<<item_grid(A), kBlock, 0, s>>>(A, v, epi, st_guard);
+  if (A.nsplit > 0) spmv_kernel<true><<<split_grid(A), kBlock, 0, s>>>(A, v, epi, st_guard);
 }
 
 void launch_power_iteration_step(const SellMat &A, const SellMat &AT, double *v, double *av,

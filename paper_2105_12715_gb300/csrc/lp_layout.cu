@@ -296,9 +296,9 @@ template <class P>
 __global__ void __launch_bounds__(kLayBlock) lay_slices_kernel(LayRuns runs,
                                                                const int32_t *__restrict__ perm,
                                                                const P *__restrict__ ptr,
-                                                               int64_t nslices, SliceInfo *info,
-                                                               int64_t *width) {
-  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nslices;
+                                                               int64_t s_begin, int64_t nslices,
+                                                               SliceInfo *info, int64_t *width) {
+  for (int64_t s = s_begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nslices;
        s += (int64_t)gridDim.x * blockDim.x) {
     int q = 0;
     while (q + 1 < runs.count && s >= runs.s0[q + 1]) ++q;
@@ -310,6 +310,42 @@ __global__ void __launch_bounds__(kLayBlock) lay_slices_kernel(LayRuns runs,
     info[s].row0 = (int32_t)row0;
     info[s].len_g = (int32_t)((steps << 3) | lg);
     width[s] = steps * kWarp;
+  }
+}
+
+// Split rows (the first nsr rows of the sorted order): chunk counts, then,
+// from their exclusive scan cstart, each chunk's slice (G = 32, at most
+// split_len elements) and its SplitSlice record.
+template <class P>
+__global__ void __launch_bounds__(kLayBlock) lay_split_count_kernel(
+    const int32_t *__restrict__ perm, const P *__restrict__ ptr, int64_t nsr, int32_t split_len,
+    int64_t *nch) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nsr;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t q = perm[r];
+    const int64_t len = (int64_t)ptr[q + 1] - (int64_t)ptr[q];
+    nch[r] = (len + split_len - 1) / split_len;
+  }
+}
+
+template <class P>
+__global__ void __launch_bounds__(kLayBlock) lay_split_slices_kernel(
+    const int32_t *__restrict__ perm, const P *__restrict__ ptr, int64_t nsr, int32_t split_len,
+    const int64_t *__restrict__ cstart, SliceInfo *info, int64_t *width, SplitSlice *split) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nsr;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t q = perm[r];
+    const int64_t len = (int64_t)ptr[q + 1] - (int64_t)ptr[q];
+    const int32_t nch = (int32_t)((len + split_len - 1) / split_len);
+    const int64_t first = cstart[r];
+    for (int32_t c = 0; c < nch; ++c) {
+      const int64_t clen = min((int64_t)split_len, len - (int64_t)c * split_len);
+      const int64_t steps = (clen + kWarp - 1) / kWarp;
+      info[first + c].row0 = (int32_t)r;
+      info[first + c].len_g = (int32_t)((steps << 3) | 5);
+      width[first + c] = steps * kWarp;
+      split[first + c] = SplitSlice{c, nch, (int32_t)first, c * split_len};
+    }
   }
 }
 
@@ -333,7 +369,8 @@ template <class P>
 __global__ void __launch_bounds__(kLayBlock) lay_fill_kernel(
     const SliceInfo *__restrict__ info, int64_t nslices, const int32_t *__restrict__ perm,
     const P *__restrict__ ptr, const int32_t *__restrict__ ind, const double *__restrict__ val,
-    const int32_t *__restrict__ relabel, int32_t *idx, double *vout, float *vf) {
+    const int32_t *__restrict__ relabel, int32_t *idx, double *vout, float *vf,
+    const SplitSlice *__restrict__ split, int64_t nsplit, int32_t split_len) {
   const int lane = threadIdx.x & (kWarp - 1);
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; s < nslices; s += nw) {
@@ -344,7 +381,12 @@ __global__ void __launch_bounds__(kLayBlock) lay_fill_kernel(
     const int32_t row = a.row0 + (lane >> lg);
     const int sub = lane & (G - 1);
     int64_t src = 0, len = 0;
-    if (row < row_end) {
+    if (s < nsplit) {  // chunk of a split row (G = 32: every lane on row a.row0)
+      const int32_t r = perm[a.row0];
+      const int64_t begin = split[s].begin;
+      src = ptr[r] + begin;
+      len = min((int64_t)split_len, (int64_t)ptr[r + 1] - (int64_t)ptr[r] - begin);
+    } else if (row < row_end) {
       const int32_t r = perm[row];
       src = ptr[r];
       len = (int64_t)ptr[r + 1] - src;
@@ -491,36 +533,48 @@ void lay_inverse(const int32_t *perm, int32_t count, int32_t *inv, int nsm, cuda
 template <class P>
 void lay_slices(const LayRuns &runs, const int32_t *perm, const P *ptr, int64_t nslices,
                 int32_t nrows, SliceInfo *info, int64_t *width, int64_t *off, int64_t *sums,
-                int nsm, cudaStream_t s) {
-  if (nslices > 0) {
-    lay_slices_kernel<P><<<lay_grid(nslices, nsm), kLayBlock, 0, s>>>(runs, perm, ptr, nslices,
-                                                                      info, width);
-    lay_exclusive_scan(width, nslices, off, sums, s);
+                int nsm, cudaStream_t s, int64_t nsr, int64_t nsplit, int32_t split_len,
+                SplitSlice *split, int64_t *nch, int64_t *cstart) {
+  if (nsr > 0) {
+    lay_split_count_kernel<P><<<lay_grid(nsr, nsm), kLayBlock, 0, s>>>(perm, ptr, nsr, split_len,
+                                                                       nch);
+    lay_exclusive_scan(nch, nsr, cstart, sums, s);
+    lay_split_slices_kernel<P><<<lay_grid(nsr, nsm), kLayBlock, 0, s>>>(
+        perm, ptr, nsr, split_len, cstart, info, width, split);
   }
+  if (nslices > nsplit)
+    lay_slices_kernel<P><<<lay_grid(nslices - nsplit, nsm), kLayBlock, 0, s>>>(
+        runs, perm, ptr, nsplit, nslices, info, width);
+  if (nslices > 0) lay_exclusive_scan(width, nslices, off, sums, s);
   lay_slice_offsets_kernel<<<lay_grid(nslices + 1, nsm), kLayBlock, 0, s>>>(info, off, width,
                                                                             nslices, nrows);
 }
 template void lay_slices<int32_t>(const LayRuns &, const int32_t *, const int32_t *, int64_t,
                                   int32_t, SliceInfo *, int64_t *, int64_t *, int64_t *, int,
-                                  cudaStream_t);
+                                  cudaStream_t, int64_t, int64_t, int32_t, SplitSlice *, int64_t *,
+                                  int64_t *);
 template void lay_slices<int64_t>(const LayRuns &, const int32_t *, const int64_t *, int64_t,
                                   int32_t, SliceInfo *, int64_t *, int64_t *, int64_t *, int,
-                                  cudaStream_t);
+                                  cudaStream_t, int64_t, int64_t, int32_t, SplitSlice *, int64_t *,
+                                  int64_t *);
 
 template <class P>
 void lay_fill(const SliceInfo *info, int64_t nslices, const int32_t *perm, const P *ptr,
               const int32_t *ind, const double *val, const int32_t *relabel, int32_t *idx,
-              double *vout, float *vf, int nsm, cudaStream_t s) {
+              double *vout, float *vf, int nsm, cudaStream_t s, const SplitSlice *split,
+              int64_t nsplit, int32_t split_len) {
   if (nslices > 0)
     lay_fill_kernel<P><<<lay_grid(nslices * kWarp, nsm), kLayBlock, 0, s>>>(
-        info, nslices, perm, ptr, ind, val, relabel, idx, vout, vf);
+        info, nslices, perm, ptr, ind, val, relabel, idx, vout, vf, split, nsplit, split_len);
 }
 template void lay_fill<int32_t>(const SliceInfo *, int64_t, const int32_t *, const int32_t *,
                                 const int32_t *, const double *, const int32_t *, int32_t *,
-                                double *, float *, int, cudaStream_t);
+                                double *, float *, int, cudaStream_t, const SplitSlice *, int64_t,
+                                int32_t);
 template void lay_fill<int64_t>(const SliceInfo *, int64_t, const int32_t *, const int64_t *,
                                 const int32_t *, const double *, const int32_t *, int32_t *,
-                                double *, float *, int, cudaStream_t);
+                                double *, float *, int, cudaStream_t, const SplitSlice *, int64_t,
+                                int32_t);
 
 void lay_vectors(const int32_t *perm_x, int32_t n, const double *c, const double *lb,
                  const double *ub, double *pc, double *pl, double *pu, long long *lk,

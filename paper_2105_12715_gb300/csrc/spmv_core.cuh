@@ -131,14 +131,98 @@ __device__ __forceinline__ void process_item(const SellMat &A, const T *__restri
   if (owner) epi.store(row, a0, a1, pre);
 }
 
-template <int NV, int U, bool PIPE = false, bool PAIR = false, typename T, class Epi>
+// One chunk slice of a split row (see SellMat): the warp sums its chunk in
+// the order of process_item (U loads, U gathers, U FMAs per lane, then the
+// 32-lane butterfly); chunk 0 starts from the epilogue's initial value.
+// Lane 0 publishes the partial sums; the last chunk of the row to arrive
+// adds all partials in chunk order and runs the epilogue, then resets the
+// row's counter for the next pass.  Every chunk's sum, and their order, is
+// fixed, so the result is deterministic.
+template <int NV, int U, bool PIPE, bool PAIR, typename T, class Epi>
+__device__ __forceinline__ void process_split_item(const SellMat &A, const T *__restrict__ v0,
+                                                const T *__restrict__ v1, int item, int lane,
+                                                Epi &epi) {
+  const SliceInfo a = A.info[item];
+  const SplitSlice sp = A.split[item];
+  const int steps = a.len_g >> 3;  // G = 32: one row, lane l holds elements l, l + 32, ...
+  const int row = a.row0;
+  T a0 = T(0), a1 = T(0);
+  if (sp.chunk == 0 && lane == 0) {
+    const typename Epi::Pre pre = epi.load(row);
+    a0 = epi.init(pre);
+  }
+  const int32_t *ip = A.idx + a.off + lane;
+  const T *vp = vals_of(A, T(0)) + a.off + lane;
+  for (int t = 0; t < steps; t += U) {
+    int32_t j[U];
+    T c[U], g[U], h[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (t + u < steps) {
+        j[u] = __ldcs(ip + (size_t)kWarp * (t + u));
+        c[u] = __ldcs(vp + (size_t)kWarp * (t + u));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (t + u < steps) {
+        if constexpr (PAIR) {
+          const double2 p = __ldg(reinterpret_cast<const double2 *>(v0) + j[u]);
+          g[u] = p.x;
+          h[u] = p.y;
+        } else {
+          g[u] = __ldg(v0 + j[u]);
+          if (NV == 2) h[u] = __ldg(v1 + j[u]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (t + u < steps) {
+        a0 = fma_t(c[u], g[u], a0);
+        if (NV == 2) a1 = fma_t(c[u], h[u], a1);
+      }
+    }
+  }
+  for (int o = kWarp >> 1; o > 0; o >>= 1) {
+    a0 += __shfl_xor_sync(kFull, a0, o);
+    if (NV == 2) a1 += __shfl_xor_sync(kFull, a1, o);
+  }
+  if (lane != 0) return;
+  A.split_part[2 * (size_t)item] = (double)a0;
+  A.split_part[2 * (size_t)item + 1] = (double)a1;
+  __threadfence();
+  if (atomicAdd(&A.split_cnt[sp.first], 1) != sp.nchunks - 1) return;
+  __threadfence();
+  const volatile double *part = A.split_part;
+  T s0 = T(0), s1 = T(0);
+  for (int c = 0; c < sp.nchunks; ++c) {
+    s0 += (T)part[2 * (size_t)(sp.first + c)];
+    s1 += (T)part[2 * (size_t)(sp.first + c) + 1];
+  }
+  A.split_cnt[sp.first] = 0;
+  const typename Epi::Pre pre = epi.load(row);
+  epi.store(row, s0, s1, pre);
+}
+
+// The slices of a pass, one warp per slice.  SPLIT = false: the ordinary
+// slices (from nsplit on); SPLIT = true: the chunk slices of split rows, in a
+// separate instantiation of the kernel that the launchers add only for
+// matrices that have them, so the ordinary kernels are compiled as before.
+template <int NV, int U, bool PIPE = false, bool PAIR = false, bool SPLIT = false, typename T,
+          class Epi>
 __device__ __forceinline__ void process_all(const SellMat &A, const T *v0, const T *v1,
                                             Epi &epi) {
   const int lane = threadIdx.x & (kWarp - 1);
   const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nwarps = (int)(gridDim.x * blockDim.x) >> 5;
-  for (int it = warp; it < A.nslices; it += nwarps)
-    process_item<NV, U, PIPE, PAIR>(A, v0, v1, it, lane, epi);
+  if constexpr (SPLIT) {
+    for (int it = warp; it < A.nsplit; it += nwarps)
+      process_split_item<NV, U, PIPE, PAIR>(A, v0, v1, it, lane, epi);
+  } else {
+    for (int it = A.nsplit + warp; it < A.nslices; it += nwarps)
+      process_item<NV, U, PIPE, PAIR>(A, v0, v1, it, lane, epi);
+  }
 }
 
 // Fixed-order block reduction of NV2 per-thread values; thread q < NV2 of

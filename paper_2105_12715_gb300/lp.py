@@ -37,7 +37,8 @@ class lp_options(C.Structure):
                 ("spmv_unroll_rows", C.c_int32), ("lane_steps", C.c_int32),
                 ("single_lane_max", C.c_int32), ("spmv_mode", C.c_int32),
                 ("precision", C.c_int32), ("lane_auto", C.c_int32), ("autotune", C.c_int32),
-                ("sigma_method", C.c_int32), ("device_layout", C.c_int32)]
+                ("sigma_method", C.c_int32), ("device_layout", C.c_int32),
+                ("split_row_len", C.c_int32)]
 
 
 class lp_info(C.Structure):
@@ -50,7 +51,7 @@ class lp_info(C.Structure):
                 ("nnz_padded", C.c_int64), ("n_long_rows", C.c_int32), ("n_long_cols", C.c_int32),
                 ("setup_ms", C.c_double * 4), ("spmv_unroll", C.c_int32),
                 ("spmv_unroll_rows", C.c_int32), ("sigma_steps", C.c_int32),
-                ("graph_kernels", C.c_int32)]
+                ("graph_kernels", C.c_int32), ("n_split_slices", C.c_int32)]
 
 
 class lp_batch_tuning(C.Structure):
@@ -343,6 +344,7 @@ class Info:
     spmv_unroll_rows: int = 0
     sigma_steps: int = 0
     graph_kernels: int = 0
+    n_split_slices: int = 0
 
     @property
     def rel_kkt(self) -> float:
@@ -406,7 +408,7 @@ class LP:
                     tuple(i.kkt_cur), i.eta, i.sigma_max, i.omega, i.tau, i.sigma, i.rho_stored,
                     i.last_rho, i.last_radius, i.nnz_padded, i.n_long_rows, i.n_long_cols,
                     tuple(i.setup_ms), i.spmv_unroll, i.spmv_unroll_rows, i.sigma_steps,
-                    i.graph_kernels)
+                    i.graph_kernels, i.n_split_slices)
 
     def trace(self, capacity=1 << 20):
         return lp_get_trace(self.h, capacity)

@@ -425,3 +425,39 @@ def box_standard_form(seed: int = 3, m: int = 2000, n: int = 5000, per_col: int 
     d.ub = np.ones(n)
     d.name = f"box_standard_form(m={m},n={n},seed={seed})"
     return d
+
+
+def with_dense_lines(base: LPData, seed: int = 0, row_frac: float = 1.0,
+                     col_frac: float = 1.0) -> LPData:
+    """``base`` plus one dense EQ row and one dense column, keeping the planted
+    optimum optimal: the new row has N(0,1) entries on a random ``row_frac``
+    share of the columns, b = a x* and y* = 0 (so c is unchanged); the new
+    column (x >= 0, x* = 0) has N(0,1) entries on a random ``col_frac`` share
+    of the rows (the new row included) and reduced cost s ~ U(0,1) > 0.
+    Rows and columns this long take a whole warp and, past the split length,
+    several (the layout's split rows)."""
+    rng = np.random.default_rng(seed)
+    m, n = base.m, base.n
+    rows = np.repeat(np.arange(m, dtype=np.int64), np.diff(base.row_ptr).astype(np.int64))
+    cols = base.col_idx.astype(np.int64)
+    vals = base.val.astype(np.float64)
+    # dense row m over the old columns
+    rc = np.sort(rng.choice(n, size=max(1, int(round(row_frac * n))), replace=False))
+    rv = rng.standard_normal(rc.shape[0])
+    # dense column n over the old rows and the new one
+    cr = np.sort(rng.choice(m + 1, size=max(1, int(round(col_frac * (m + 1)))), replace=False))
+    cv = rng.standard_normal(cr.shape[0])
+    rows = np.concatenate([rows, np.full(rc.shape[0], m, dtype=rows.dtype), cr.astype(rows.dtype)])
+    cols = np.concatenate([cols, rc.astype(cols.dtype), np.full(cr.shape[0], n, dtype=cols.dtype)])
+    vals = np.concatenate([vals, rv, cv])
+    x_star = np.concatenate([base.x_star, [0.0]])
+    y_star = np.concatenate([base.y_star, [0.0]])
+    b = np.concatenate([base.b, [float(np.dot(rv, base.x_star[rc]))]])
+    s_new = rng.random() + 0.1
+    c = np.concatenate([base.c, [float(np.dot(cv, y_star[cr])) + s_new]])
+    lb = np.concatenate([base.lb, [0.0]])
+    ub = np.concatenate([base.ub, [np.inf]])
+    row_type = np.concatenate([base.row_type, np.array([ROW_EQ], dtype=np.int8)])
+    row_ptr, col_idx, val = _coo_to_csr(m + 1, rows, cols, vals)
+    return LPData(m + 1, n + 1, row_ptr, col_idx, val, c, b, lb, ub, row_type, x_star, y_star,
+                  name=f"{base.name}+dense row/column(seed={seed})")
