@@ -62,6 +62,7 @@ def parse():
     p.add_argument("--no-mixed", action="store_true")
     p.add_argument("--no-ttk", action="store_true")
     p.add_argument("--no-mcf", action="store_true")
+    p.add_argument("--no-long-row", action="store_true")
     p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--adjoint-lps", type=int, default=4)
     p.add_argument("--no-ttk-large", action="store_true")
@@ -595,6 +596,26 @@ def run_ours(args):
         ttk_large["mixed_speedup"] = ttk_large["fp64"]["seconds"] / ttk_large["mixed"]["seconds"]
         mixed_error(ttk_large)
 
+    # an LP with one dense row and one dense column: split rows (lp_options.split_row_len)
+    # against one warp per long row
+    long_row = None
+    if not args.no_long_row:
+        from paper_2105_12715_gb300 import lpgen
+
+        dl = lpgen.with_dense_lines(lpgen.large_mixed(7, m=20_000, n=200_000), seed=1)
+        long_row = {"lp": f"large_mixed m=20000 n=200000 seed 7 + a dense row ({dl.n} elements) "
+                          f"and a dense column ({dl.m} elements): m={dl.m} n={dl.n} nnz={dl.nnz}"}
+        for name, split in (("one_warp_per_row", 0), ("split_2048", 2048)):
+            gl = lp.LP(dl, stream=stream, check_every=K_CHECK, split_row_len=split)
+            gl.iterate(args.warmup, 1e-300)
+            barrier()
+            lms = time_steps(lp, gl, stream, 20)
+            long_row[name] = {"iters_per_s": 20 * K_CHECK / (lms / 1000.0),
+                              "split_slices": gl.info().n_split_slices}
+            gl.close()
+        long_row["speedup"] = (long_row["split_2048"]["iters_per_s"]
+                               / long_row["one_warp_per_row"]["iters_per_s"])
+
     # multicommodity flow LP (300 x 300 grid, 8 commodities): FP64 vs mixed throughput
     mcf = None
     if not args.no_mcf:
@@ -712,7 +733,8 @@ def run_ours(args):
                             "gather_bound": gather_bound},
                "clocks": clocks, "e2e": e2e, "mixed": mixed, "time_to_kkt": ttk,
                "time_to_kkt_1e8": ttk8, "time_to_kkt_1e8_large": ttk_large,
-               "multicommodity": mcf, "adjoint": adjoint, "batched": batched,
+               "multicommodity": mcf, "long_row": long_row, "adjoint": adjoint,
+               "batched": batched,
                "solver": {"eta": info0.eta, "sigma_max": info0.sigma_max,
                           "sigma_steps": info0.sigma_steps,
                           "setup_ms": dict(zip(["inputs", "layout", "upload", "sigma_max"],
