@@ -605,7 +605,7 @@ def run_ours(args):
         dl = lpgen.with_dense_lines(lpgen.large_mixed(7, m=20_000, n=200_000), seed=1)
         long_row = {"lp": f"large_mixed m=20000 n=200000 seed 7 + a dense row ({dl.n} elements) "
                           f"and a dense column ({dl.m} elements): m={dl.m} n={dl.n} nnz={dl.nnz}"}
-        for name, split in (("one_warp_per_row", 0), ("split_2048", 2048)):
+        for name, split in (("one_warp_per_row", 0), ("split_512", 512)):
             gl = lp.LP(dl, stream=stream, check_every=K_CHECK, split_row_len=split)
             gl.iterate(args.warmup, 1e-300)
             barrier()
@@ -613,7 +613,7 @@ def run_ours(args):
             long_row[name] = {"iters_per_s": 20 * K_CHECK / (lms / 1000.0),
                               "split_slices": gl.info().n_split_slices}
             gl.close()
-        long_row["speedup"] = (long_row["split_2048"]["iters_per_s"]
+        long_row["speedup"] = (long_row["split_512"]["iters_per_s"]
                                / long_row["one_warp_per_row"]["iters_per_s"])
 
     # multicommodity flow LP (300 x 300 grid, 8 commodities): FP64 vs mixed throughput

@@ -121,7 +121,8 @@ typedef struct {
                              elements) longer than this is cut into chunks of at most this many
                              elements, one warp each, whose partial sums the last chunk to finish
                              adds in chunk order: no warp walks a very long row alone.  A positive
-                             multiple of 32, or 0 for never (2048; spmv_mode = 1 never splits) */
+                             multiple of 32, or 0 for never (512 = 32 x lane_steps: a chunk takes no
+                             more steps than an ordinary slice; spmv_mode = 1 never splits) */
 } lp_options;
 
 typedef struct {
@@ -149,7 +150,7 @@ typedef struct {
 
 /* Defaults: beta = e^-1, K = 64, ADAPTIVE, tau0 = K, omega = 1, eta = 0
  * (auto), power_iters = 5000, power_tol = 1e-10, max_iter = 1e7, autotune = 1,
- * sigma_method = LP_SIGMA_LANCZOS, device_layout = 1, split_row_len = 2048. */
+ * sigma_method = LP_SIGMA_LANCZOS, device_layout = 1, split_row_len = 512. */
 void lp_default_options(lp_options *opt);
 
 /*

@@ -792,7 +792,7 @@ void lp_default_options(lp_options *o) {
   o->autotune = 1;
   o->sigma_method = LP_SIGMA_LANCZOS;
   o->device_layout = 1;
-  o->split_row_len = 2048;
+  o->split_row_len = 512;
 }
 
 const char *lp_last_error(void) { return err_msg().c_str(); }

@@ -1169,19 +1169,21 @@ int check_grid_for(const SellMat &A, int nsm) {
 template <int U, bool PIPE>
 void primal_launch(int occ, int g, cudaStream_t s, const SellMat &AT, const double *y,
                    const PrimalEpi &epi, DevState *st, const double *w, int k) {
-  if (occ) launch_pdl(primal_kernel<U, PIPE, 5>, g, kBlock, s, AT, y, epi, st, w, k);
-  else launch_pdl(primal_kernel<U, PIPE, 1>, g, kBlock, s, AT, y, epi, st, w, k);
   if (AT.nsplit > 0)
-    launch_pdl(primal_kernel<U, PIPE, 1, true>, split_grid(AT), kBlock, s, AT, y, epi, st, w, k);
+    launch_pdl(primal_kernel<U, PIPE, 1, true>, split_grid(AT) + g, kBlock, s, AT, y, epi, st, w,
+               k);
+  else if (occ) launch_pdl(primal_kernel<U, PIPE, 5>, g, kBlock, s, AT, y, epi, st, w, k);
+  else launch_pdl(primal_kernel<U, PIPE, 1>, g, kBlock, s, AT, y, epi, st, w, k);
 }
 
 template <int U, bool PIPE>
 void dual_launch(int occ, int g, cudaStream_t s, const SellMat &A, const double *xhat,
                  const DualEpi &epi, DevState *st, const double *w, int k) {
-  if (occ) launch_pdl(dual_kernel<U, PIPE, 4>, g, kBlock, s, A, xhat, epi, st, w, k);
-  else launch_pdl(dual_kernel<U, PIPE, 1>, g, kBlock, s, A, xhat, epi, st, w, k);
   if (A.nsplit > 0)
-    launch_pdl(dual_kernel<U, PIPE, 1, true>, split_grid(A), kBlock, s, A, xhat, epi, st, w, k);
+    launch_pdl(dual_kernel<U, PIPE, 1, true>, split_grid(A) + g, kBlock, s, A, xhat, epi, st, w,
+               k);
+  else if (occ) launch_pdl(dual_kernel<U, PIPE, 4>, g, kBlock, s, A, xhat, epi, st, w, k);
+  else launch_pdl(dual_kernel<U, PIPE, 1>, g, kBlock, s, A, xhat, epi, st, w, k);
 }
 
 void launch_primal_step(const SellMat &AT, const DevVecs &v, DevState *st, const double *w,
@@ -1259,44 +1261,40 @@ void launch_check(const SellMat &A, const SellMat &AT, const DevVecs &v, DevStat
     re.gy_out0 = mv->gy[0];
     re.gy_out1 = mv->gy[1];
   }
-  if (cs.pair_y && cs.pair_x) {
+  const bool pair = cs.pair_y && cs.pair_x;
+  if (pair) {
     if (m > 0)
       pack_pairs_kernel<<<grid_for(m, num_sms()), kBlock, 0, s>>>(
           v.ybar, v.y, m, reinterpret_cast<double2 *>(cs.pair_y), st);
     if (n > 0)
       pack_pairs_kernel<<<grid_for(n, num_sms()), kBlock, 0, s>>>(
           v.xbar, v.x, n, reinterpret_cast<double2 *>(cs.pair_x), st);
-    check_kernel<CheckColsEpi, true><<<cs.cols_grid, kBlock, 0, s>>>(
-        AT, cs.pair_y, nullptr, ce, st, cs.partials, cs.pstride, 0);
-    check_kernel<CheckRowsEpi, true><<<cs.rows_grid, kBlock, 0, s>>>(
-        A, cs.pair_x, nullptr, re, st, cs.partials, cs.pstride, cs.cols_grid);
-  } else {
-    check_kernel<CheckColsEpi, false><<<cs.cols_grid, kBlock, 0, s>>>(
-        AT, v.ybar, v.y, ce, st, cs.partials, cs.pstride, 0);
-    check_kernel<CheckRowsEpi, false><<<cs.rows_grid, kBlock, 0, s>>>(
-        A, v.xbar, v.x, re, st, cs.partials, cs.pstride, cs.cols_grid);
   }
-  // chunk slices of split rows: their blocks' sums go to the partial slots
-  // after the ordinary passes' (the gathered vectors as above)
+  // with split rows, the SPLIT instantiation with the chunk blocks in front;
+  // every block writes one partial slot, columns' slots first
   const int sc = split_grid(AT), sr = split_grid(A);
-  const int pbase = cs.cols_grid + cs.rows_grid;
-  if (sc > 0) {
-    if (cs.pair_y && cs.pair_x)
-      check_kernel<CheckColsEpi, true, true><<<sc, kBlock, 0, s>>>(
-          AT, cs.pair_y, nullptr, ce, st, cs.partials, cs.pstride, pbase);
-    else
-      check_kernel<CheckColsEpi, false, true><<<sc, kBlock, 0, s>>>(
-          AT, v.ybar, v.y, ce, st, cs.partials, cs.pstride, pbase);
-  }
-  if (sr > 0) {
-    if (cs.pair_y && cs.pair_x)
-      check_kernel<CheckRowsEpi, true, true><<<sr, kBlock, 0, s>>>(
-          A, cs.pair_x, nullptr, re, st, cs.partials, cs.pstride, pbase + sc);
-    else
-      check_kernel<CheckRowsEpi, false, true><<<sr, kBlock, 0, s>>>(
-          A, v.xbar, v.x, re, st, cs.partials, cs.pstride, pbase + sc);
-  }
-  check_finalize_kernel<<<NQ, kBlock, 0, s>>>(st, cs.partials, cs.pstride, pbase + sc + sr);
+  const int gc = sc + cs.cols_grid, gr = sr + cs.rows_grid;
+  const double *c0 = pair ? cs.pair_y : v.ybar, *c1 = pair ? nullptr : v.y;
+  const double *r0 = pair ? cs.pair_x : v.xbar, *r1 = pair ? nullptr : v.x;
+  double *P = cs.partials;
+  const int ps = cs.pstride;
+  if (sc > 0 && pair)
+    check_kernel<CheckColsEpi, true, true><<<gc, kBlock, 0, s>>>(AT, c0, c1, ce, st, P, ps, 0);
+  else if (sc > 0)
+    check_kernel<CheckColsEpi, false, true><<<gc, kBlock, 0, s>>>(AT, c0, c1, ce, st, P, ps, 0);
+  else if (pair)
+    check_kernel<CheckColsEpi, true><<<gc, kBlock, 0, s>>>(AT, c0, c1, ce, st, P, ps, 0);
+  else
+    check_kernel<CheckColsEpi, false><<<gc, kBlock, 0, s>>>(AT, c0, c1, ce, st, P, ps, 0);
+  if (sr > 0 && pair)
+    check_kernel<CheckRowsEpi, true, true><<<gr, kBlock, 0, s>>>(A, r0, r1, re, st, P, ps, gc);
+  else if (sr > 0)
+    check_kernel<CheckRowsEpi, false, true><<<gr, kBlock, 0, s>>>(A, r0, r1, re, st, P, ps, gc);
+  else if (pair)
+    check_kernel<CheckRowsEpi, true><<<gr, kBlock, 0, s>>>(A, r0, r1, re, st, P, ps, gc);
+  else
+    check_kernel<CheckRowsEpi, false><<<gr, kBlock, 0, s>>>(A, r0, r1, re, st, P, ps, gc);
+  check_finalize_kernel<<<NQ, kBlock, 0, s>>>(st, cs.partials, cs.pstride, gc + gr);
   if (nsearch > 0) {
     const int64_t N = (int64_t)n + m;
     for (int p = 0; p < kSearchPasses; ++p) {
@@ -1317,17 +1315,19 @@ void launch_check(const SellMat &A, const SellMat &AT, const DevVecs &v, DevStat
 template <int U, bool PIPE>
 void primal_mix_launch(int g, cudaStream_t s, const SellMat &AT, const float *dy,
                        const PrimalMixEpi &epi, DevState *st, const double *w, int k) {
-  launch_pdl(primal_mix_kernel<U, PIPE>, g, kBlock, s, AT, dy, epi, st, w, k);
   if (AT.nsplit > 0)
-    launch_pdl(primal_mix_kernel<U, PIPE, true>, split_grid(AT), kBlock, s, AT, dy, epi, st, w, k);
+    launch_pdl(primal_mix_kernel<U, PIPE, true>, split_grid(AT) + g, kBlock, s, AT, dy, epi, st, w,
+               k);
+  else launch_pdl(primal_mix_kernel<U, PIPE>, g, kBlock, s, AT, dy, epi, st, w, k);
 }
 
 template <int U, bool PIPE>
 void dual_mix_launch(int g, cudaStream_t s, const SellMat &A, const float *dxhat,
                      const DualMixEpi &epi, DevState *st, const double *w, int k) {
-  launch_pdl(dual_mix_kernel<U, PIPE>, g, kBlock, s, A, dxhat, epi, st, w, k);
   if (A.nsplit > 0)
-    launch_pdl(dual_mix_kernel<U, PIPE, true>, split_grid(A), kBlock, s, A, dxhat, epi, st, w, k);
+    launch_pdl(dual_mix_kernel<U, PIPE, true>, split_grid(A) + g, kBlock, s, A, dxhat, epi, st, w,
+               k);
+  else launch_pdl(dual_mix_kernel<U, PIPE>, g, kBlock, s, A, dxhat, epi, st, w, k);
 }
 
 void launch_primal_mix(const SellMat &AT, const MixVecs &mv, DevState *st, const double *w,
@@ -1376,22 +1376,30 @@ void launch_residuals(const SellMat &A, const SellMat &AT, const DevVecs &v, con
 void launch_forward_masked(const SellMat &A, const SellMat &AT, const DevVecs &v, double tau,
                            double sigma, double w, uint8_t *mx, uint8_t *my, cudaStream_t s) {
   PrimalEpi pe{v.c, v.lbk, v.ubk, v.x, v.xhat, v.xbar, 0.0, 0.0, mx};
-  primal_mask_kernel<<<item_grid(AT), kBlock, 0, s>>>(AT, v.y, pe, tau, w);
-  if (AT.nsplit > 0) primal_mask_kernel<true><<<split_grid(AT), kBlock, 0, s>>>(AT, v.y, pe, tau, w);
+  if (AT.nsplit > 0)
+    primal_mask_kernel<true><<<split_grid(AT) + item_grid(AT), kBlock, 0, s>>>(AT, v.y, pe, tau, w);
+  else
+    primal_mask_kernel<<<item_grid(AT), kBlock, 0, s>>>(AT, v.y, pe, tau, w);
   DualEpi de{v.b, v.row_type, v.y, v.ybar, 0.0, 0.0, my};
-  dual_mask_kernel<<<item_grid(A), kBlock, 0, s>>>(A, v.xhat, de, sigma, w);
-  if (A.nsplit > 0) dual_mask_kernel<true><<<split_grid(A), kBlock, 0, s>>>(A, v.xhat, de, sigma, w);
+  if (A.nsplit > 0)
+    dual_mask_kernel<true><<<split_grid(A) + item_grid(A), kBlock, 0, s>>>(A, v.xhat, de, sigma, w);
+  else
+    dual_mask_kernel<<<item_grid(A), kBlock, 0, s>>>(A, v.xhat, de, sigma, w);
 }
 
 void launch_adjoint_step(const SellMat &A, const SellMat &AT, const AdjVecs &a,
                          const uint8_t *mx, const uint8_t *my_prev, double tau, double sigma,
                          double w, double w_prev, int has_prev, cudaStream_t s) {
   AdjColsEpi ce{a.ax, a.axb, a.ac, a.v, mx, tau, sigma, w};
-  adj_cols_kernel<<<item_grid(AT), kBlock, 0, s>>>(AT, a.u, ce);
-  if (AT.nsplit > 0) adj_cols_kernel<true><<<split_grid(AT), kBlock, 0, s>>>(AT, a.u, ce);
+  if (AT.nsplit > 0)
+    adj_cols_kernel<true><<<split_grid(AT) + item_grid(AT), kBlock, 0, s>>>(AT, a.u, ce);
+  else
+    adj_cols_kernel<<<item_grid(AT), kBlock, 0, s>>>(AT, a.u, ce);
   AdjRowsEpi re{a.ay, a.ayb, a.ab, a.u, my_prev, tau, sigma, w_prev, has_prev};
-  adj_rows_kernel<<<item_grid(A), kBlock, 0, s>>>(A, a.v, re);
-  if (A.nsplit > 0) adj_rows_kernel<true><<<split_grid(A), kBlock, 0, s>>>(A, a.v, re);
+  if (A.nsplit > 0)
+    adj_rows_kernel<true><<<split_grid(A) + item_grid(A), kBlock, 0, s>>>(A, a.v, re);
+  else
+    adj_rows_kernel<<<item_grid(A), kBlock, 0, s>>>(A, a.v, re);
 }
 
 void launch_adjoint_block_start(const AdjVecs &a, const uint8_t *my_last, int restarted,
@@ -1411,8 +1419,10 @@ void launch_weights(DevState *st, double *w, cudaStream_t s) {
 void launch_spmv(const SellMat &A, const double *v, double *out, cudaStream_t s,
                  DevState *st_guard) {
   StoreEpi epi{out};
-  spmv_kernel<<<item_grid(A), kBlock, 0, s>>>(A, v, epi, st_guard);
-  if (A.nsplit > 0) spmv_kernel<true><<<split_grid(A), kBlock, 0, s>>>(A, v, epi, st_guard);
+  if (A.nsplit > 0)
+    spmv_kernel<true><<<split_grid(A) + item_grid(A), kBlock, 0, s>>>(A, v, epi, st_guard);
+  else
+    spmv_kernel<<<item_grid(A), kBlock, 0, s>>>(A, v, epi, st_guard);
 }
 
 void launch_power_iteration_step(const SellMat &A, const SellMat &AT, double *v, double *av,

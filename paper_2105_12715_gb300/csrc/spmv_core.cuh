@@ -205,24 +205,30 @@ __device__ __forceinline__ void process_split_item(const SellMat &A, const T *__
   epi.store(row, s0, s1, pre);
 }
 
-// The slices of a pass, one warp per slice.  SPLIT = false: the ordinary
-// slices (from nsplit on); SPLIT = true: the chunk slices of split rows, in a
-// separate instantiation of the kernel that the launchers add only for
-// matrices that have them, so the ordinary kernels are compiled as before.
+// The slices of a pass, one warp per slice.  SPLIT = false: matrices
+// without split rows (the kernels compiled as always).  SPLIT = true (a
+// separate instantiation the launchers pick only for matrices with split
+// rows, launched with split_grid(A) extra blocks in front): the first
+// blocks take the chunk slices, one warp each, and the others the ordinary
+// slices, so the chunks, started first, overlap the rest of the pass.
 template <int NV, int U, bool PIPE = false, bool PAIR = false, bool SPLIT = false, typename T,
           class Epi>
 __device__ __forceinline__ void process_all(const SellMat &A, const T *v0, const T *v1,
                                             Epi &epi) {
   const int lane = threadIdx.x & (kWarp - 1);
-  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int nwarps = (int)(gridDim.x * blockDim.x) >> 5;
+  int first_block = 0;
   if constexpr (SPLIT) {
-    for (int it = warp; it < A.nsplit; it += nwarps)
-      process_split_item<NV, U, PIPE, PAIR>(A, v0, v1, it, lane, epi);
-  } else {
-    for (int it = A.nsplit + warp; it < A.nslices; it += nwarps)
-      process_item<NV, U, PIPE, PAIR>(A, v0, v1, it, lane, epi);
+    first_block = (A.nsplit + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if ((int)blockIdx.x < first_block) {
+      const int it = (int)blockIdx.x * kWarpsPerBlock + (int)(threadIdx.x >> 5);
+      if (it < A.nsplit) process_split_item<NV, U, PIPE, PAIR>(A, v0, v1, it, lane, epi);
+      return;
+    }
   }
+  const int warp = (int)(((blockIdx.x - first_block) * blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)((gridDim.x - first_block) * blockDim.x) >> 5;
+  for (int it = A.nsplit + warp; it < A.nslices; it += nwarps)
+    process_item<NV, U, PIPE, PAIR>(A, v0, v1, it, lane, epi);
 }
 
 // Fixed-order block reduction of NV2 per-thread values; thread q < NV2 of

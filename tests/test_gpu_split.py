@@ -38,12 +38,15 @@ def close(got, want, tol, what):
     assert err <= tol * scale, f"{what}: {err:.3e} (scale {scale:.3e})"
 
 
-# split lengths: the default (only the dense row and column are cut), and a
-# forced one that also cuts every row of A (~35 elements) into 32-element chunks
-SPLITS = [dict(split_row_len=2048), dict(split_row_len=32, long_row_threshold=34)]
+# split lengths: the default 512 and 2048 (only the dense row and column are
+# cut), and a forced one that also cuts every row of A (~35 elements) into
+# 32-element chunks
+SPLITS = [dict(split_row_len=512), dict(split_row_len=2048),
+          dict(split_row_len=32, long_row_threshold=34)]
+SPLIT_IDS = ["512", "2048", "forced"]
 
 
-@pytest.mark.parametrize("opts", SPLITS, ids=["default", "forced"])
+@pytest.mark.parametrize("opts", SPLITS, ids=SPLIT_IDS)
 def test_split_iterates_match_oracle(lpm, oracle_mod, opts):
     data = dense_lp()
     eta = 0.9 / oracle_mod.sigma_max(data)
@@ -73,7 +76,7 @@ def test_split_matches_unsplit(lpm, precision):
             g.solve(1e-300)
             out[split] = (g.state(), g.info(), g.trace())
     (s0, i0, t0), (s1, i1, t1) = out[0], out[2048]
-    assert i0.n_split_slices == 0 and i1.n_split_slices == 5 + 2
+    assert i0.n_split_slices == 0 and i1.n_split_slices == 5 + 2  # 9,001 and 3,001 elements
     assert all(np.all(np.isfinite(v)) for v in s0.values())
     np.testing.assert_array_equal(t0[:, 2], t1[:, 2])
     tol = 1e-11 if precision == 0 else 1e-5
@@ -113,7 +116,7 @@ def test_split_adjoint_matches_unsplit(lpm):
     close(grads[2048][1], grads[0][1], 1e-10, "db")
 
 
-@pytest.mark.parametrize("opts", SPLITS, ids=["default", "forced"])
+@pytest.mark.parametrize("opts", SPLITS, ids=SPLIT_IDS)
 def test_split_layout_device_matches_host(lpm, opts):
     data = dense_lp()
     out = {}
