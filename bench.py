@@ -63,6 +63,8 @@ def parse():
     p.add_argument("--no-ttk", action="store_true")
     p.add_argument("--no-mcf", action="store_true")
     p.add_argument("--no-long-row", action="store_true")
+    p.add_argument("--no-schemes", action="store_true")
+    p.add_argument("--schemes-cap", type=int, default=400_000)
     p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--adjoint-lps", type=int, default=4)
     p.add_argument("--no-ttk-large", action="store_true")
@@ -587,6 +589,34 @@ def run_ours(args):
             ttk8[name + "_omega1"] = ttk_run(small, 1e-8, prec, False, 3_000_000)
             ttk8[name] = ttk_run(small, 1e-8, prec, True, 3_000_000)
         mixed_error(ttk8)
+    schemes = None
+    if not args.no_ttk and not args.no_schemes:
+        # the shape of Table 3: restart schemes to relative KKT 1e-8 on the 5k x 25k LP at the
+        # primal weight the grid picked for it (FP64, setup included, cap in iterations)
+        from paper_2105_12715_gb300 import lpgen
+
+        small = lpgen.large_mixed(5, m=5000, n=25000)
+        w = ttk8["fp64"]["omega"] if ttk8 else 1.0
+        schemes = {"lp": f"large_mixed m={small.m} n={small.n} nnz={small.nnz} seed 5",
+                   "tol": 1e-8, "omega": w, "cap_iters": args.schemes_cap, "runs": {}}
+        runs = [("adaptive", dict(restart_scheme=lp.LP_RESTART_ADAPTIVE)),
+                ("flexible", dict(restart_scheme=lp.LP_RESTART_FLEXIBLE))]
+        runs += [(f"fixed_{L}", dict(restart_scheme=lp.LP_RESTART_FIXED, fixed_len=L))
+                 for L in (256, 1024, 4096, 16384)]
+        runs += [("no_restart", dict(restart_scheme=lp.LP_RESTART_NONE))]
+        for name, kw in runs:
+            barrier()
+            t0 = time.perf_counter()
+            gs = lp.LP(small, stream=stream, check_every=K_CHECK, max_iter=args.schemes_cap,
+                       omega=w, **kw)
+            st = gs.solve(1e-8)
+            torch.cuda.synchronize()
+            it = gs.info()
+            gs.close()
+            schemes["runs"][name] = {"iters": it.iters, "restarts": it.restarts,
+                                     "status": lp.STATUS_NAMES.get(st, st),
+                                     "rel_kkt": min(it.kkt_avg[4], it.kkt_cur[4]),
+                                     "seconds": time.perf_counter() - t0}
     if not args.no_ttk and not args.no_ttk_large and ws == 1:
         # the benchmark LP itself (m = 200k, n = 1M, nnz = 10M)
         ttk_large = {"lp": config_of(args, data)["workload"], "tol": 1e-8,
@@ -733,7 +763,8 @@ def run_ours(args):
                             "gather_bound": gather_bound},
                "clocks": clocks, "e2e": e2e, "mixed": mixed, "time_to_kkt": ttk,
                "time_to_kkt_1e8": ttk8, "time_to_kkt_1e8_large": ttk_large,
-               "multicommodity": mcf, "long_row": long_row, "adjoint": adjoint,
+               "multicommodity": mcf, "long_row": long_row, "restart_schemes": schemes,
+               "adjoint": adjoint,
                "batched": batched,
                "solver": {"eta": info0.eta, "sigma_max": info0.sigma_max,
                           "sigma_steps": info0.sigma_steps,
