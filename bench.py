@@ -615,6 +615,7 @@ def run_ours(args):
             gs.close()
             schemes["runs"][name] = {"iters": it.iters, "restarts": it.restarts,
                                      "status": lp.STATUS_NAMES.get(st, st),
+                                     "returned": "average" if it.returned == 0 else "current",
                                      "rel_kkt": min(it.kkt_avg[4], it.kkt_cur[4]),
                                      "seconds": time.perf_counter() - t0}
     if not args.no_ttk and not args.no_ttk_large and ws == 1:
