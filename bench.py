@@ -203,12 +203,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(args, data):
+def cpu_baseline(args, data, eta):
     """The oracle (plain C, 1 thread) on a bounded sample: cpu_iters iterations
-    with one check every 64 (the same workload)."""
+    with one check every 64 (the same workload, the GPU's step size)."""
     import oracle
 
-    eta = 0.9 / 11.0
     t = time.perf_counter()
     res = oracle.solve(data, eta, tol=1e-300, max_iter=args.cpu_iters, check_every=K_CHECK)
     dt = time.perf_counter() - t
@@ -225,7 +224,13 @@ def run_reference(args):
     import oracle
 
     oracle.build()
-    eta = 0.9 / 11.0
+    # a valid step size without a sigma_max estimate on the host: sigma_max(A) is at most
+    # sqrt(||A||_1 ||A||_inf) (largest column and row absolute sums)
+    a = np.abs(data.val)
+    row_sums = np.add.reduceat(a, data.row_ptr[:-1]) if data.nnz else np.zeros(1)
+    row_sums[np.diff(data.row_ptr) == 0] = 0.0
+    col_sums = np.bincount(data.col_idx, weights=a, minlength=data.n)
+    eta = 0.9 / max(float(np.sqrt(row_sums.max() * col_sums.max())), 1e-300)
     per_step = 4  # oracle iterations per step (bounded sample; a check every 64 iterations)
     olp = oracle.OracleLP(data)
     oracle.solve(olp, eta, tol=1e-300, max_iter=per_step * args.warmup, check_every=K_CHECK)
@@ -562,6 +567,7 @@ def run_ours(args):
         gt.close()
         pobj = it.kkt_avg[2] if it.returned == 0 else it.kkt_cur[2]
         out = {"seconds": dt, "omega": omega, "omega_select_seconds": t_sel, "iters": it.iters,
+               "eta": it.eta,
                "restarts": it.restarts, "status": lp.STATUS_NAMES.get(st, st),
                "rel_kkt": min(it.kkt_avg[4], it.kkt_cur[4]), "pobj": pobj}
         if d.obj_star is not None:  # the planted optimum's objective (unique)
@@ -647,6 +653,23 @@ def run_ours(args):
         long_row["speedup"] = (long_row["split_512"]["iters_per_s"]
                                / long_row["one_warp_per_row"]["iters_per_s"])
 
+    # the 200 x 400 LP (2,000 nonzeros): a step is launch- and latency-bound, not
+    # bandwidth-bound; microseconds per iteration, K iterations + check per graph replay
+    tiny, tiny_lp = None, None
+    if not args.no_mcf:
+        from paper_2105_12715_gb300 import lpgen
+
+        tiny_lp = lpgen.tiny_standard_form(0)
+        gt0 = lp.LP(tiny_lp, stream=stream, check_every=K_CHECK)
+        gt0.iterate(args.warmup, 1e-300)
+        barrier()
+        tms = time_steps(lp, gt0, stream, args.steps)
+        tiny = {"lp": f"tiny_standard_form seed 0: m={tiny_lp.m} n={tiny_lp.n} nnz={tiny_lp.nnz}",
+                "us_per_iter": 1000.0 * tms / (args.steps * K_CHECK),
+                "iters_per_s": args.steps * K_CHECK / (tms / 1000.0),
+                "graph_kernels_per_step": gt0.info().graph_kernels, "eta": gt0.info().eta}
+        gt0.close()
+
     # multicommodity flow LP (300 x 300 grid, 8 commodities): FP64 vs mixed throughput
     mcf = None
     if not args.no_mcf:
@@ -664,6 +687,7 @@ def run_ours(args):
                          "ms_per_step": msm / args.steps}
             if prec == lp.LP_PRECISION_FP64:
                 mcf[name]["achieved_gbs_per_iter"] = (mp + md) * mcf[name]["iters_per_s"] / 1e9
+                mcf["eta"] = gmc.info().eta
             gmc.close()
 
     # adjoint of the unrolled map on differentiable-LP-shaped instances
@@ -764,7 +788,8 @@ def run_ours(args):
                             "gather_bound": gather_bound},
                "clocks": clocks, "e2e": e2e, "mixed": mixed, "time_to_kkt": ttk,
                "time_to_kkt_1e8": ttk8, "time_to_kkt_1e8_large": ttk_large,
-               "multicommodity": mcf, "long_row": long_row, "restart_schemes": schemes,
+               "tiny": tiny, "multicommodity": mcf, "long_row": long_row,
+               "restart_schemes": schemes,
                "adjoint": adjoint,
                "batched": batched,
                "solver": {"eta": info0.eta, "sigma_max": info0.sigma_max,
@@ -775,13 +800,14 @@ def run_ours(args):
                           "rel_kkt_avg": info.kkt_avg[4], "rel_kkt_cur": info.kkt_cur[4],
                           "nnz_padded": info.nnz_padded}}
         if not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(args, data)
+            out["cpu_baseline"] = cpu_baseline(args, data, info0.eta)
             if ttk is not None:
                 import oracle
 
                 for key, entry, d_ in (("time_to_kkt", ttk, med), ("time_to_kkt_1e8", ttk8, small)):
                     t0 = time.perf_counter()
-                    r = oracle.solve(d_, 0.9 / 11.0, tol=1e-300, max_iter=256, check_every=K_CHECK)
+                    r = oracle.solve(d_, entry["fp64"]["eta"], tol=1e-300, max_iter=256,
+                                     check_every=K_CHECK)
                     rate = r.iters / (time.perf_counter() - t0)
                     entry["oracle_iters_per_s"] = rate
                     entry["oracle_extrapolated_seconds"] = entry["fp64"]["iters"] / rate
@@ -790,6 +816,22 @@ def run_ours(args):
             if ttk_large is not None:
                 rate = out["cpu_baseline"]["value"]
                 ttk_large["oracle_extrapolated_seconds"] = ttk_large["fp64"]["iters"] / rate
+            # the oracle on the other workloads (bounded samples, 1 thread)
+            import oracle
+
+            other = {}
+            if tiny is not None:
+                t0 = time.perf_counter()
+                r = oracle.solve(tiny_lp, tiny["eta"], tol=1e-300, max_iter=1024,
+                                 check_every=K_CHECK)
+                other["tiny_200x400"] = {"iters_per_s": r.iters / (time.perf_counter() - t0),
+                                         "sample": f"{r.iters} iterations"}
+            if mcf is not None:
+                t0 = time.perf_counter()
+                r = oracle.solve(mc, mcf["eta"], tol=1e-300, max_iter=16, check_every=K_CHECK)
+                other["multicommodity"] = {"iters_per_s": r.iters / (time.perf_counter() - t0),
+                                           "sample": f"{r.iters} iterations"}
+            out["cpu_baseline"]["other_workloads"] = other
         print(json.dumps(out))
     if ws > 1:
         torch.distributed.barrier()
