@@ -73,6 +73,8 @@ def parse():
     p.add_argument("--batch-count", type=int, default=512)
     p.add_argument("--batch-cap", type=int, default=100_000)
     p.add_argument("--batch-loop-sample", type=int, default=16)
+    p.add_argument("--batch-schemes", action="store_true",
+                   help="also solve the batch with the flexible and no-restart schemes")
     p.add_argument("--batch-only", action="store_true",
                    help="run only the batched section and print its JSON (profiling)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -409,6 +411,25 @@ def run_batched(args, lp, stream, barrier):
                     "converged": int(pdist.reduce_scalar(conv_m.sum(), "sum")),
                     "iters_median": float(np.median(its_m)),
                     "converged_both": int(pdist.reduce_scalar((conv & conv_m).sum(), "sum"))}
+    if args.batch_schemes:
+        # the shape of Table 3 on the batch: problems converged to relative KKT 1e-8 within the
+        # iteration cap with the adaptive, flexible and no-restart schemes (FP64, K = 64)
+        res["restart_schemes"] = {}
+        for name, scheme in (("adaptive", lp.LP_RESTART_ADAPTIVE),
+                             ("flexible", lp.LP_RESTART_FLEXIBLE),
+                             ("no_restart", lp.LP_RESTART_NONE)):
+            t0 = time.perf_counter()
+            gb = lp.LPBatch(probs, stream=stream, check_every=K_CHECK, max_iter=args.batch_cap,
+                            restart_scheme=scheme)
+            gb.solve(1e-8)
+            torch.cuda.synchronize()
+            _, per_s = gb.info()
+            gb.close()
+            its_s = [p["iters"] for p in per_s if p["status"] == lp.LP_OK]
+            res["restart_schemes"][name] = {
+                "converged": int(pdist.reduce_scalar(len(its_s), "sum")),
+                "median_iters_converged": float(np.median(its_s)) if its_s else None,
+                "seconds_with_setup": pdist.reduce_scalar(time.perf_counter() - t0, "max")}
     return res
 
 
