@@ -310,7 +310,8 @@ def test_kkt_planted_optimum_zero(oracle_mod):
 def test_planted_objective_is_lp_optimum():
     """The planted objective equals the LP optimum from an independent LP solver (HiGHS)."""
     linprog = pytest.importorskip("scipy.optimize").linprog
-    for lp in [lpgen.tiny_standard_form(1, m=40, n=80), lpgen.adversarial(4)]:
+    for lp in [lpgen.tiny_standard_form(1, m=40, n=80), lpgen.adversarial(4),
+               lpgen.with_dense_lines(lpgen.large_mixed(2, m=60, n=200), seed=3)]:
         A = lp.dense()
         eq, ge, le = (lp.row_type == 0), (lp.row_type == 1), (lp.row_type == 2)
         A_ub = np.vstack([-A[ge], A[le]])
@@ -320,6 +321,20 @@ def test_planted_objective_is_lp_optimum():
                       A_eq=A[eq], b_eq=lp.b[eq], bounds=bounds, method="highs")
         assert res.status == 0
         assert res.fun == pytest.approx(lp.obj_star, rel=1e-7, abs=1e-7)
+
+
+def test_dense_lines_keep_the_planted_optimum(oracle_mod):
+    """with_dense_lines adds a full row and a full column and keeps (x*, y*) optimal:
+    zero KKT error at the planted pair (complementary reduced costs, y* = 0 on the
+    new row, x* = 0 with a positive reduced cost on the new column)."""
+    base = lpgen.large_mixed(5, m=400, n=1500)
+    d = lpgen.with_dense_lines(base, seed=2)
+    assert (d.m, d.n) == (base.m + 1, base.n + 1)
+    assert np.diff(d.row_ptr)[-1] == d.n  # the new row: every old column and the new one
+    assert np.bincount(d.col_idx, minlength=d.n)[-1] == d.m  # the new column every row
+    k = oracle_mod.kkt(d, d.x_star, d.y_star)
+    assert k["rel"] < 1e-13
+    assert d.obj_star == pytest.approx(base.obj_star, rel=1e-14)
 
 
 def test_sigma_max_power_iteration(oracle_mod):
