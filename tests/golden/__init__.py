@@ -51,8 +51,8 @@ def lp_data(case):
     """The case's LP as an lpgen.LPData (CSR from the dense A; null bounds = infinite)."""
     from paper_2105_12715_gb300 import lpgen
 
-    A = np.array(case["A"], dtype=np.float64)
-    m, n = A.shape
+    m, n = len(case["b"]), len(case["c"])
+    A = np.array(case["A"], dtype=np.float64).reshape(m, n)
     rows, cols = np.nonzero(A)
     row_ptr = np.zeros(m + 1, dtype=np.int32)
     np.cumsum(np.bincount(rows, minlength=m), out=row_ptr[1:])

@@ -52,3 +52,31 @@ def test_bilinear_average_hand(oracle_mod):
     assert res.x[0] == pytest.approx(golden.value(BIL["iterates"][-1]["x"]), rel=1e-15)
     assert res.xbar[0] == pytest.approx(golden.value(BIL["average_t3"]["x"]), rel=1e-15)
     assert res.ybar[0] == pytest.approx(golden.value(BIL["average_t3"]["y"]), rel=1e-15)
+
+
+FLEX = golden.load("flexible_restart_hand.json")
+
+
+@pytest.mark.parametrize("case", FLEX["cases"], ids=[c["name"] for c in FLEX["cases"]])
+def test_flexible_restart_hand(oracle_mod, case):
+    """Remark (Flexible restarts): check by check, the chosen candidate's gap
+    and radius, the restart flag and the restart point, then the end state."""
+    lp = golden.lp_data(FLEX["lp"])
+    scheme = {"flexible": oracle_mod.RESTART_FLEXIBLE,
+              "adaptive": oracle_mod.RESTART_ADAPTIVE}[case["scheme"]]
+    kw = dict(tol=FLEX["tol"], check_every=FLEX["check_every"], tau0=FLEX["tau0"],
+              restart_scheme=scheme, x_init=np.array([FLEX["x_init"]]), y_init=np.zeros(0))
+    for i, ck in enumerate(case["checks"]):
+        r = oracle_mod.solve(lp, case["eta"], max_iter=ck["iter"], **kw)
+        row = r.trace[i]
+        assert row[0] == ck["iter"]
+        assert row[1] == pytest.approx(golden.value(ck["rho"]), rel=1e-15), ck
+        assert row[5] == pytest.approx(golden.value(ck["radius"]), rel=1e-15), ck
+        assert row[2] == ck["restarted"], ck
+        assert r.x0[0] == pytest.approx(golden.value(ck["x0_after"]), rel=1e-15), ck
+    r = oracle_mod.solve(lp, case["eta"], max_iter=1000, **kw)
+    f = case["final"]
+    assert r.status == oracle_mod.STATUS_OK
+    assert (r.iters, r.restarts, r.returned) == (f["iters"], f["restarts"], f["returned"])
+    for k in ("x", "xbar", "x0"):
+        assert getattr(r, k)[0] == pytest.approx(golden.value(f[k]), rel=1e-15, abs=1e-300), k

@@ -55,3 +55,40 @@ def test_bilinear_iterates_hand(lpm, t):
     if t == 3:
         assert st["xbar"][0] == pytest.approx(golden.value(BIL["average_t3"]["x"]), rel=1e-12)
         assert st["ybar"][0] == pytest.approx(golden.value(BIL["average_t3"]["y"]), rel=1e-12)
+
+
+FLEX = golden.load("flexible_restart_hand.json")
+
+
+@pytest.mark.parametrize("case", FLEX["cases"], ids=[c["name"] for c in FLEX["cases"]])
+def test_flexible_restart_hand(lpm, case):
+    """Remark (Flexible restarts) through the C ABI: per check the chosen
+    candidate's gap and radius, the restart flag and the restart point
+    (lp_get_trace, lp_get_state), then the end state."""
+    data = golden.lp_data(FLEX["lp"])
+    scheme = {"flexible": lpm.LP_RESTART_FLEXIBLE,
+              "adaptive": lpm.LP_RESTART_ADAPTIVE}[case["scheme"]]
+    opts = dict(eta=case["eta"], omega=1.0, check_every=FLEX["check_every"], tau0=FLEX["tau0"],
+                restart_scheme=scheme, autotune=0)
+    x_init = np.array([FLEX["x_init"]])
+    for i, ck in enumerate(case["checks"]):
+        with lpm.LP(data, max_iter=ck["iter"], **opts) as g:
+            g.set_state(x_init, np.zeros(0))
+            g.solve(FLEX["tol"])
+            tr = g.trace()
+            st = g.state()
+        row = tr[i]
+        assert row[0] == ck["iter"]
+        assert row[1] == pytest.approx(golden.value(ck["rho"]), rel=1e-12), ck
+        assert row[5] == pytest.approx(golden.value(ck["radius"]), rel=1e-12), ck
+        assert row[2] == ck["restarted"], ck
+        assert st["x0"][0] == pytest.approx(golden.value(ck["x0_after"]), rel=1e-12), ck
+    with lpm.LP(data, max_iter=1000, **opts) as g:
+        g.set_state(x_init, np.zeros(0))
+        assert g.solve(FLEX["tol"]) == lpm.LP_OK
+        info = g.info()
+        st = g.state()
+    f = case["final"]
+    assert (info.iters, info.restarts, info.returned) == (f["iters"], f["restarts"], f["returned"])
+    for k in ("x", "xbar", "x0"):
+        assert st[k][0] == pytest.approx(golden.value(f[k]), rel=1e-12, abs=1e-300), k
