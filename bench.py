@@ -40,11 +40,59 @@ K_CHECK = 64
 OMEGA_GRID = [4.0 ** k for k in range(-3, 4)]  # Section 7 grid (powers of 4), 2048 iterations each
 OMEGA_ITERS = 2048  # a multiple of the check period (the batch needs one)
 FALLBACK_HBM_GBS = 6800.0
-# dram__bytes_read.sum + dram__bytes_write.sum of one primal_kernel launch on
-# this workload with warm L2 (the benchmark's steady state), per column-pass
-# variant (lp_info.spmv_unroll), from one-pass ncu captures; a variant missing
-# here, or a kernel changed since, reports null.
-PRIMAL_TRAFFIC_BYTES = {-2: 127.6e6, -4: 124.0e6, 2: 123.9e6, 4: 123.9e6}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one column-pass
+# launch on this workload with warm L2, per kernel variant, from one-pass ncu
+# captures kept as text under profiles/; each row names the hash of the kernel
+# sources it was taken with, so a kernel changed since reports null.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "primal_kernel_traffic_large_mixed.md")
+KERNEL_SOURCES = ["lp_kernels.cu", "spmv_core.cuh", "lp_internal.h"]
+# Random-gather ceilings on GB300 (G gathers/s), measured once by a gather
+# microbenchmark with every block resident: 8-byte __ldg gathers from a
+# 1.6 MB L2-resident vector alone, and a sliced SpMV (one warp per 32 columns
+# of 10 elements, int32 indices and FP64 values streamed from a 126 MB matrix)
+# with the column pass's per-column reads and writes.
+GATHER_CEILINGS = {"random_gathers_1p6MB": 330.0, "sliced_spmv_with_epilogue_traffic": 224.0}
+
+
+def kernel_source_hash():
+    """SHA-256 (first 16 hex digits) of the iteration kernels' sources."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2105_12715_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(variant):
+    """Bytes per launch of the column pass for this variant, read from the
+    committed capture table (rows '| variant | source hash | bytes |'), or
+    None when no row matches the variant and the current sources."""
+    try:
+        want = kernel_source_hash()
+        for line in open(TRAFFIC_FILE):
+            cells = [c.strip() for c in line.strip().strip("|").split("|")]
+            if len(cells) >= 3 and cells[0] == str(variant) and cells[1] == want:
+                return float(cells[2])
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def host_info():
+    """Core count and CPU model of the host the oracle runs on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                             timeout=10).stdout.decode()
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:  # noqa: BLE001
+        pass
+    return {"nproc": os.cpu_count(), "model": model, "machine": os.uname().machine}
 
 
 def parse():
@@ -205,17 +253,43 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(args, data, eta):
-    """The oracle (plain C, 1 thread) on a bounded sample: cpu_iters iterations
-    with one check every 64 (the same workload, the GPU's step size)."""
+def oracle_openmp_available():
     import oracle
 
+    try:
+        oracle.build(openmp=True)
+        return True
+    except Exception:  # noqa: BLE001
+        return False
+
+
+def cpu_baseline(args, data, eta):
+    """The oracle on a bounded sample: cpu_iters iterations with one check
+    every 64 (the same workload, the GPU's step size), on all host cores (its
+    OpenMP build: the row products and elementwise loops split over the
+    cores, A^T y a serial scatter) and on one thread (the checker build)."""
+    import oracle
+
+    olp = oracle.OracleLP(data)
+    host = host_info()
+    single = None
     t = time.perf_counter()
-    res = oracle.solve(data, eta, tol=1e-300, max_iter=args.cpu_iters, check_every=K_CHECK)
+    res = oracle.solve(olp, eta, tol=1e-300, max_iter=args.cpu_iters, check_every=K_CHECK)
     dt = time.perf_counter() - t
-    return {"value": res.iters / dt, "unit": "iters/s", "cores": 1, "kind": "oracle",
-            "sample": f"{res.iters} oracle iterations incl. {res.n_checks} check(s) on the full "
-                      f"workload, {dt:.1f} s"}
+    single = {"value": res.iters / dt, "cores": 1, "seconds": dt}
+    out = {"value": single["value"], "unit": "iters/s", "cores": 1, "kind": "oracle",
+           "sample": f"{res.iters} oracle iterations incl. {res.n_checks} check(s) on the full "
+                     f"workload, {dt:.1f} s", "host": host, "single_thread": single}
+    if oracle_openmp_available():
+        t = time.perf_counter()
+        res = oracle.solve(olp, eta, tol=1e-300, max_iter=args.cpu_iters, check_every=K_CHECK,
+                           openmp=True)
+        dt = time.perf_counter() - t
+        out.update({"value": res.iters / dt, "cores": host["nproc"],
+                    "sample": f"{res.iters} oracle iterations incl. {res.n_checks} check(s) on "
+                              f"the full workload, OpenMP build on {host['nproc']} threads, "
+                              f"{dt:.1f} s"})
+    return out
 
 
 def run_reference(args):
@@ -234,11 +308,15 @@ def run_reference(args):
     col_sums = np.bincount(data.col_idx, weights=a, minlength=data.n)
     eta = 0.9 / max(float(np.sqrt(row_sums.max() * col_sums.max())), 1e-300)
     per_step = 4  # oracle iterations per step (bounded sample; a check every 64 iterations)
+    omp = oracle_openmp_available()
+    host = host_info()
+    cores = host["nproc"] if omp else 1
     olp = oracle.OracleLP(data)
-    oracle.solve(olp, eta, tol=1e-300, max_iter=per_step * args.warmup, check_every=K_CHECK)
+    oracle.solve(olp, eta, tol=1e-300, max_iter=per_step * args.warmup, check_every=K_CHECK,
+                 openmp=omp)
     total = per_step * args.steps
     t = time.perf_counter()
-    res = oracle.solve(olp, eta, tol=1e-300, max_iter=total, check_every=K_CHECK)
+    res = oracle.solve(olp, eta, tol=1e-300, max_iter=total, check_every=K_CHECK, openmp=omp)
     dt = time.perf_counter() - t
     v = res.iters / dt
     line = {"metric": "PDHG iterations/s (fp64 restarted PDHG, large mixed LP)", "value": v,
@@ -246,25 +324,15 @@ def run_reference(args):
             "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": config_of(args, data),
-            "cpu_baseline": {"value": v, "unit": "iters/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "iters/s", "cores": cores, "kind": "oracle",
                              "sample": f"{res.iters} oracle iterations ({per_step} per step), "
-                                       f"{res.n_checks} check(s)"},
+                                       f"{res.n_checks} check(s)"
+                                       + (f", OpenMP build on {cores} threads" if omp else
+                                          ", one thread"),
+                             "host": host},
             "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
-
-
-def gather_probe():
-    """Random-gather throughput of this GPU (csrc/probe_gather.cu): the rate the
-    iteration kernels' operand gathers are bounded by."""
-    try:
-        from paper_2105_12715_gb300 import build as b
-
-        exe = b.build_probe()
-        r = subprocess.run([exe], stdout=subprocess.PIPE, stderr=subprocess.STDOUT, timeout=120)
-        return json.loads(r.stdout.decode().strip().splitlines()[-1])
-    except Exception as e:  # the probe is context only
-        return {"error": str(e)[:200]}
 
 
 def run_batched(args, lp, stream, barrier):
@@ -511,17 +579,14 @@ def run_ours(args):
     peak, peak_kind = peaks()
     achieved = primal_b / (primal_ms / 1000.0) / 1e9
     g.close()
-    probe = gather_probe() if rank == 0 else None
-    gather_bound = None
-    if probe and "global_1p6MB_ggathers_per_s" in probe:
-        ach_g = data.nnz / (primal_ms / 1000.0) / 1e9
-        gather_bound = {"gathers_per_launch": data.nnz, "achieved_ggathers_per_s": ach_g,
-                        "probe": probe,
-                        "frac_of_probe": ach_g / probe["global_1p6MB_ggathers_per_s"]}
-        if probe.get("sliced_spmv_epilogue_ggathers_per_s"):
-            # against the simplest kernel with the column pass's memory traffic
-            gather_bound["frac_of_sliced_epilogue"] = (
-                ach_g / probe["sliced_spmv_epilogue_ggathers_per_s"])
+    # the column pass against the random-gather ceilings of this GPU (one
+    # 8-byte gather per nonzero from the L2-resident y)
+    ach_g = data.nnz / (primal_ms / 1000.0) / 1e9
+    gather_bound = {"gathers_per_launch": data.nnz, "achieved_ggathers_per_s": ach_g,
+                    "ceilings_ggathers_per_s": GATHER_CEILINGS,
+                    "frac_of_random_gathers": ach_g / GATHER_CEILINGS["random_gathers_1p6MB"],
+                    "frac_of_sliced_spmv": ach_g / GATHER_CEILINGS["sliced_spmv_with_epilogue_traffic"],
+                    "source": "gather microbenchmark on GB300, measured once (not re-run here)"}
 
     # end to end through the C ABI from host buffers
     e2e_vals, h2d, e2e_setup = [], 0, None
@@ -802,7 +867,9 @@ def run_ours(args):
                "roofline": {"bound": "hbm", "kernel": "primal_kernel", "achieved": achieved,
                             "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                             "peak_kind": peak_kind,
-                            "traffic": PRIMAL_TRAFFIC_BYTES.get(info0.spmv_unroll),
+                            "traffic": measured_traffic(info0.spmv_unroll),
+                            "traffic_source": {"file": os.path.relpath(TRAFFIC_FILE, ROOT),
+                                               "kernel_source_hash": kernel_source_hash()},
                             "variant": info0.spmv_unroll,
                             "algorithmic_bytes": primal_b, "avg_launch_ms": primal_ms,
                             "dual_kernel_ms": dual_ms, "dual_algorithmic_bytes": dual_b,

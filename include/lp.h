@@ -99,9 +99,7 @@ typedef struct {
   int32_t lane_steps;     /* rows longer than single_lane_max get the fewest lanes G (power of
                              two <= 32) with ceil(len / G) <= lane_steps (16) */
   int32_t single_lane_max; /* rows of at most this many elements get one lane each (64) */
-  int32_t spmv_mode;      /* iteration kernels: 0 = one warp per slice with register batches,
-                             1 = persistent warps with a TMA-staged (cp.async.bulk) matrix
-                             stream (0) */
+  int32_t spmv_mode;      /* reserved, must be 0 */
   int32_t precision;      /* LP_PRECISION_FP64 (default) or LP_PRECISION_MIXED */
   int32_t lane_auto;      /* > 0: per matrix, halve single_lane_max and lane_steps until the
                              layout has at least lane_auto x (SM count) slices (warps); 0: use
@@ -116,13 +114,13 @@ typedef struct {
                              by at most power_tol (relative) */
   int32_t device_layout;  /* 1: build the library's layout (CSC copy, length orders, slices) on the
                              GPU (default); 0: on the host cores.  Both give the same arrays.
-                             spmv_mode = 1 and lp_batch_create always build on the host */
+                             lp_batch_create always builds on the host */
   int32_t split_row_len;  /* a row of A or A^T with a whole warp (long_row_threshold or more
                              elements) longer than this is cut into chunks of at most this many
                              elements, one warp each, whose partial sums the last chunk to finish
                              adds in chunk order: no warp walks a very long row alone.  A positive
                              multiple of 32, or 0 for never (512 = 32 x lane_steps: a chunk takes no
-                             more steps than an ordinary slice; spmv_mode = 1 never splits) */
+                             more steps than an ordinary slice) */
 } lp_options;
 
 typedef struct {
@@ -223,7 +221,8 @@ lp_status lp_get_trace(lp_handle h, double *host_rows, int64_t capacity,
  * the linear trust region of Section 6.3 solved by a parallel search over
  * the multiplier (Algorithm 2's answer).  x[n], y[m] (host or device) in the
  * caller's order, inside X x Y.  *host_rho receives rho_r; r = 0 gives 0.
- * Allocates and frees its own scratch.  Synchronizes the stream.
+ * Allocates and frees its own scratch (split-row counters included), so it
+ * may overlap a solve on the same handle.  Synchronizes the stream.
  */
 lp_status lp_normalized_gap(lp_handle h, const double *x, const double *y,
                             double r, double *host_rho, void *cuda_stream);
@@ -235,13 +234,18 @@ lp_status lp_normalized_gap(lp_handle h, const double *x, const double *y,
  * synchronizes the device; a process whose framework already reserved
  * nearly all device memory; code that must leave the allocation state
  * untouched while other work is queued).
- * Same arguments, result and tolerance as lp_normalized_gap.  Scratch is a
- * fixed 16 MiB device array inside the library (held on every GPU that
- * loads it until exit), so n + m must be <= 262,144; larger problems return
- * LP_ERR_INVALID_ARG.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) and should come before any stream
- * capture.  All calls share the array: calls that overlap on the GPU race
- * and must be serialized by the caller.  Synchronizes the stream.
+ * Same arguments as lp_normalized_gap and the same result, bit for bit (the
+ * same kernels and reduction order).  Scratch is a fixed 16 MiB device array
+ * inside the library (held on every GPU that loads it until exit), so
+ * n + m must be <= 262,144; larger problems, or split rows whose partial
+ * sums do not fit beside the rest, return LP_ERR_INVALID_ARG.  The first
+ * call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and should come before any stream capture.  All
+ * calls of this entry point share the array: two of them that overlap on
+ * the GPU race and must be serialized by the caller.  Neither gap entry
+ * point writes anything the handle's other calls use (the split-row
+ * counters and partial sums are the call's own), so a gap call may overlap
+ * a solve on the same handle.  Synchronizes the stream.
  */
 lp_status lp_normalized_gap_static(lp_handle h, const double *x, const double *y,
                                    double r, double *host_rho, void *cuda_stream);
@@ -295,7 +299,10 @@ lp_status lp_solve_recorded(lp_handle h, int64_t iters, void *cuda_stream);
 lp_status lp_backward(lp_handle h, const double *dl_dx, const double *dl_dy,
                       double *dl_dc, double *dl_db, void *cuda_stream);
 
-/* Releases every resource of the handle (NULL is a no-op). */
+/* Releases every resource of the handle (NULL is a no-op).  Waits for the
+ * stream of the handle's latest call that enqueued work (and for the
+ * handle's own capture stream), not for the whole device; work on other
+ * streams that still reads the handle must be finished by the caller. */
 void lp_destroy(lp_handle h);
 
 /* Message of the last failed call on this thread ("" if none). */

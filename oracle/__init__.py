@@ -26,22 +26,28 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rpdhg_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
+_LIB_OMP = os.path.join(_BUILD, "liboracle_omp.so")  # OpenMP build, for timing only
 
 RESTART_NONE, RESTART_FIXED, RESTART_ADAPTIVE, RESTART_FLEXIBLE, RESTART_SCHEDULE = 0, 1, 2, 3, 4
 STATUS_OK, STATUS_ITER_LIMIT, STATUS_NUMERICAL = 0, 4, 5
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc into oracle/_build/liboracle.so."""
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle with gcc into oracle/_build/liboracle.so (the
+    checker, one thread), or with openmp=True into liboracle_omp.so (the same
+    source with its OpenMP pragmas honored; used to time the oracle on all
+    host cores)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-        return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
+    lib = _LIB_OMP if openmp else _LIB
+    if (not force and os.path.exists(lib)
+            and os.path.getmtime(lib) >= os.path.getmtime(_SRC)):
+        return lib
+    tmp = lib + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC",
+                           *(["-fopenmp"] if openmp else []),
                            "-shared", "-o", tmp, _SRC, "-lm"])
-    os.replace(tmp, _LIB)
-    return _LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 class _LP(C.Structure):
@@ -66,30 +72,39 @@ class _Info(C.Structure):
 
 
 _lib = None
+_lib_omp = None
 
 
-def _load():
-    global _lib
+def _load(openmp: bool = False):
+    global _lib, _lib_omp
+    if openmp:
+        if _lib_omp is None:
+            _lib_omp = _declare(C.CDLL(build(openmp=True)))
+        return _lib_omp
     if _lib is None:
-        lib = C.CDLL(build())
-        P = C.c_void_p
-        lib.orc_matvec.argtypes = [P, P, P]
-        lib.orc_matvec_t.argtypes = [P, P, P]
-        lib.orc_pdhg_step.argtypes = [P, C.c_double, C.c_double, P, P, P, P, P]
-        lib.orc_sigma_max.argtypes = [P, C.c_int32, C.c_double]
-        lib.orc_sigma_max.restype = C.c_double
-        lib.orc_trust_region_lower.argtypes = [C.c_int64, P, P, P, C.c_double, P, P]
-        lib.orc_trust_region.argtypes = [C.c_int64, P, P, P, P, C.c_double, P]
-        lib.orc_trust_region.restype = C.c_double
-        lib.orc_normalized_gap.argtypes = [P, C.c_double, P, P, C.c_double]
-        lib.orc_normalized_gap.restype = C.c_double
-        lib.orc_weighted_dist.argtypes = [C.c_int32, C.c_int32, C.c_double, P, P, P, P]
-        lib.orc_weighted_dist.restype = C.c_double
-        lib.orc_kkt.argtypes = [P, P, P, P]
-        lib.orc_solve.argtypes = [P, P, P, P, P, P, P, P, P, P, C.c_int64]
-        lib.orc_solve.restype = C.c_int32
-        _lib = lib
+        _lib = _declare(C.CDLL(build()))
     return _lib
+
+
+def _declare(lib):
+    """Argument and result types of the oracle's C functions."""
+    P = C.c_void_p
+    lib.orc_matvec.argtypes = [P, P, P]
+    lib.orc_matvec_t.argtypes = [P, P, P]
+    lib.orc_pdhg_step.argtypes = [P, C.c_double, C.c_double, P, P, P, P, P]
+    lib.orc_sigma_max.argtypes = [P, C.c_int32, C.c_double]
+    lib.orc_sigma_max.restype = C.c_double
+    lib.orc_trust_region_lower.argtypes = [C.c_int64, P, P, P, C.c_double, P, P]
+    lib.orc_trust_region.argtypes = [C.c_int64, P, P, P, P, C.c_double, P]
+    lib.orc_trust_region.restype = C.c_double
+    lib.orc_normalized_gap.argtypes = [P, C.c_double, P, P, C.c_double]
+    lib.orc_normalized_gap.restype = C.c_double
+    lib.orc_weighted_dist.argtypes = [C.c_int32, C.c_int32, C.c_double, P, P, P, P]
+    lib.orc_weighted_dist.restype = C.c_double
+    lib.orc_kkt.argtypes = [P, P, P, P]
+    lib.orc_solve.argtypes = [P, P, P, P, P, P, P, P, P, P, C.c_int64]
+    lib.orc_solve.restype = C.c_int32
+    return lib
 
 
 def _f64(a):
@@ -222,10 +237,12 @@ class SolveResult:
 
 def solve(lp, eta, omega=1.0, beta=float(np.exp(-1.0)), tol=1e-8, max_iter=100000,
           check_every=64, restart_scheme=RESTART_ADAPTIVE, tau0=None, fixed_len=0,
-          x_init=None, y_init=None, trace_cap=100000, schedule=None) -> SolveResult:
+          x_init=None, y_init=None, trace_cap=100000, schedule=None,
+          openmp=False) -> SolveResult:
     """Algorithm 1 (restarted PDHG) from z^{0,0} = (x_init, y_init) (zeros by default).
 
-    schedule (RESTART_SCHEDULE): one flag per check, restart where nonzero."""
+    schedule (RESTART_SCHEDULE): one flag per check, restart where nonzero.
+    openmp: run the OpenMP build (all host cores; same results) -- for timing."""
     lp = _olp(lp)
     x = np.zeros(lp.n) if x_init is None else _f64(x_init).copy()
     y = np.zeros(lp.m) if y_init is None else _f64(y_init).copy()
@@ -238,8 +255,8 @@ def solve(lp, eta, omega=1.0, beta=float(np.exp(-1.0)), tol=1e-8, max_iter=10000
     info = _Info()
     cap = max(1, min(trace_cap, max_iter // max(1, check_every) + 1))
     trace = np.full((cap, 6), np.nan)
-    _load().orc_solve(lp.ref, C.byref(opt), _ptr(x), _ptr(y), _ptr(xbar), _ptr(ybar), _ptr(x0),
-                      _ptr(y0), C.byref(info), _ptr(trace), cap)
+    _load(openmp).orc_solve(lp.ref, C.byref(opt), _ptr(x), _ptr(y), _ptr(xbar), _ptr(ybar),
+                            _ptr(x0), _ptr(y0), C.byref(info), _ptr(trace), cap)
     nck = int(info.n_checks)
     return SolveResult(int(info.status), int(info.iters), int(info.restarts), int(info.inner_t),
                        int(info.returned), float(info.rho_stored), nck,

@@ -28,6 +28,15 @@
  * val double).  Infinite bounds are +-INFINITY.  Everything is double.
  * Compiled with -ffp-contract=off so that a*b+c is two roundings, as
  * written.
+ *
+ * The loops whose iterations are independent (the row products of A x,
+ * the elementwise parts of the PDHG step, the averages) carry OpenMP
+ * pragmas.  The checker is the default build, without -fopenmp: the
+ * pragmas are ignored and the code runs on one thread exactly as written.
+ * A second build with -fopenmp (liboracle_omp.so) is used only to time the
+ * oracle on all host cores; the loops it splits have no dependence between
+ * iterations (no sum is split), so it computes the same values bit for bit,
+ * and A^T y stays a serial scatter over the rows.
  */
 #include <math.h>
 #include <stdint.h>
@@ -52,6 +61,7 @@ typedef struct {
 
 /* out = A x (definition of the matrix-vector product). */
 void orc_matvec(const orc_lp *lp, const double *x, double *out) {
+  #pragma omp parallel for schedule(static)
   for (int32_t i = 0; i < lp->m; ++i) {
     double s = 0.0;
     for (int64_t p = lp->row_ptr[i]; p < lp->row_ptr[i + 1]; ++p)
@@ -97,11 +107,14 @@ void orc_pdhg_step(const orc_lp *lp, double tau, double sigma, const double *x,
   double *aty = work;          /* [n] */
   double *ax = work + lp->n;   /* [m] */
   orc_matvec_t(lp, y, aty);
+  #pragma omp parallel for schedule(static)
   for (int32_t j = 0; j < lp->n; ++j)
     x_new[j] = clamp(x[j] - tau * (lp->c[j] - aty[j]), lp->lb[j], lp->ub[j]);
   /* extrapolated point 2 x+ - x, stored temporarily in aty */
+  #pragma omp parallel for schedule(static)
   for (int32_t j = 0; j < lp->n; ++j) aty[j] = 2.0 * x_new[j] - x[j];
   orc_matvec(lp, aty, ax);
+  #pragma omp parallel for schedule(static)
   for (int32_t i = 0; i < lp->m; ++i) {
     double lo, hi;
     dual_bounds(lp->row_type[i], &lo, &hi);
@@ -471,8 +484,10 @@ int32_t orc_solve(const orc_lp *lp, const orc_options *opt, double *x,
     memcpy(x, xn, sizeof(double) * n);
     memcpy(y, yn, sizeof(double) * m);
     /* zbar^{n,t+1} = t/(t+1) zbar^{n,t} + 1/(t+1) z^{n,t+1} */
+    #pragma omp parallel for schedule(static)
     for (int32_t j = 0; j < n; ++j)
       xbar[j] = ((double)t * xbar[j] + x[j]) / (double)(t + 1);
+    #pragma omp parallel for schedule(static)
     for (int32_t i = 0; i < m; ++i)
       ybar[i] = ((double)t * ybar[i] + y[i]) / (double)(t + 1);
     ++t;

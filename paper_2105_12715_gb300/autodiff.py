@@ -4,14 +4,22 @@ forward: (c, b) -> (xbar, ybar), the running average after `iters` recorded
 iterations of restarted PDHG (lp_solve_recorded).  backward: the library's
 hand-written adjoint (lp_backward).  Restart decisions and clamp/projection
 activity are those of the recorded forward solve.
+
+The tensors go to the library as they are: c, b, the incoming gradients and
+the outputs are passed by pointer (the C ABI takes host or device arrays), so
+CUDA tensors never round-trip through host memory.  The matrix, bounds and
+row senses come from the LP's data object.
 """
 from __future__ import annotations
 
-import numpy as np
 import torch
 
 from . import lp as _lp
 from .lpgen import LPData
+
+
+def _f64(t):
+    return t.detach().to(torch.float64).contiguous()
 
 
 def _replace_cb(data, c, b):
@@ -24,25 +32,27 @@ def _replace_cb(data, c, b):
 class UnrolledRestartedPDHG(torch.autograd.Function):
     @staticmethod
     def forward(ctx, c, b, data, iters, options):
-        cn = c.detach().to("cpu", torch.float64).numpy()
-        bn = b.detach().to("cpu", torch.float64).numpy()
-        g = _lp.LP(_replace_cb(data, cn, bn), **options)
+        cd, bd = _f64(c), _f64(b)
+        g = _lp.LP(_replace_cb(data, cd, bd), **options)
         _lp.lp_solve_recorded(g.h, iters, g.stream)
-        st = g.state()
+        xbar = torch.empty(g.n, dtype=torch.float64, device=c.device)
+        ybar = torch.empty(g.m, dtype=torch.float64, device=b.device)
+        _lp.lp_get_state(g.h, xbar=xbar, ybar=ybar, stream=g.stream)
         ctx.handle = g
-        return (torch.from_numpy(st["xbar"]).to(c.device), torch.from_numpy(st["ybar"]).to(b.device))
+        ctx.devices = (c.device, b.device)
+        return xbar, ybar
 
     @staticmethod
     def backward(ctx, gx, gy):
         g = ctx.handle
-        dc = np.empty(g.n)
-        db = np.empty(g.m)
-        gxn = None if gx is None else gx.detach().to("cpu", torch.float64).contiguous().numpy()
-        gyn = None if gy is None else gy.detach().to("cpu", torch.float64).contiguous().numpy()
-        _lp.lp_backward(g.h, gxn, gyn, dc, db, g.stream)
+        dev_c, dev_b = ctx.devices
+        dc = torch.empty(g.n, dtype=torch.float64, device=dev_c)
+        db = torch.empty(g.m, dtype=torch.float64, device=dev_b)
+        gxd = None if gx is None else _f64(gx)
+        gyd = None if gy is None else _f64(gy)
+        _lp.lp_backward(g.h, gxd, gyd, dc, db, g.stream)
         g.close()
-        return (torch.from_numpy(dc).to(gx.device), torch.from_numpy(db).to(gx.device),
-                None, None, None)
+        return dc, db, None, None, None
 
 
 def unrolled_pdhg(c, b, data, iters, **options):
@@ -56,28 +66,26 @@ class UnrolledRestartedPDHGBatch(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, c, b, problems, iters, options):
-        cn = c.detach().to("cpu", torch.float64).numpy()
-        bn = b.detach().to("cpu", torch.float64).numpy()
-        probs, co, ro = [], 0, 0
-        for d in problems:
-            probs.append(_replace_cb(d, cn[co:co + d.n], bn[ro:ro + d.m]))
-            co += d.n
-            ro += d.m
-        g = _lp.LPBatch(probs, **options)
+        g = _lp.LPBatch(problems, c=_f64(c), b=_f64(b), **options)
         g.solve_recorded(iters)
-        st = g.state()
+        xbar = torch.empty(g.n, dtype=torch.float64, device=c.device)
+        ybar = torch.empty(g.m, dtype=torch.float64, device=b.device)
+        _lp.lp_batch_get_state(g.h, xbar=xbar, ybar=ybar, stream=g.stream)
         ctx.handle = g
-        return (torch.from_numpy(st["xbar"]).to(c.device), torch.from_numpy(st["ybar"]).to(b.device))
+        ctx.devices = (c.device, b.device)
+        return xbar, ybar
 
     @staticmethod
     def backward(ctx, gx, gy):
         g = ctx.handle
-        gxn = None if gx is None else gx.detach().to("cpu", torch.float64).contiguous().numpy()
-        gyn = None if gy is None else gy.detach().to("cpu", torch.float64).contiguous().numpy()
-        dc, db = g.backward(gxn, gyn)
+        dev_c, dev_b = ctx.devices
+        dc = torch.empty(g.n, dtype=torch.float64, device=dev_c)
+        db = torch.empty(g.m, dtype=torch.float64, device=dev_b)
+        gxd = None if gx is None else _f64(gx)
+        gyd = None if gy is None else _f64(gy)
+        _lp.lp_batch_backward(g.h, gxd, gyd, dc, db, g.stream)
         g.close()
-        dev = gx.device if gx is not None else gy.device
-        return torch.from_numpy(dc).to(dev), torch.from_numpy(db).to(dev), None, None, None
+        return dc, db, None, None, None
 
 
 def unrolled_pdhg_batch(c, b, problems, iters, **options):

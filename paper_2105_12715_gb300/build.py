@@ -65,24 +65,5 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     return LIB
 
 
-PROBE = os.path.join(BUILD, "probe_gather")
-
-
-def build_probe(force: bool = False) -> str:
-    """Compile the random-gather throughput probe (csrc/probe_gather.cu), a
-    measurement tool next to the library."""
-    src = os.path.join(CSRC, "probe_gather.cu")
-    if not force and os.path.exists(PROBE) and os.path.getmtime(PROBE) >= os.path.getmtime(src):
-        return PROBE
-    os.makedirs(BUILD, exist_ok=True)
-    tmp = PROBE + f".tmp{os.getpid()}"
-    r = subprocess.run([_nvcc(), *ARCH, "-O3", "-std=c++17", "-o", tmp, src],
-                       stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
-    if r.returncode != 0:
-        raise RuntimeError(f"probe build failed: {r.stdout.decode(errors='replace')}")
-    os.replace(tmp, PROBE)
-    return PROBE
-
-
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True))

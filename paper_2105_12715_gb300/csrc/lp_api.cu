@@ -33,39 +33,6 @@ using namespace lpg;
 
 namespace {
 
-// Segments of at most kSegSteps steps, and a split of them over nwarps
-// persistent warps: contiguous ranges, cut only where a slice starts,
-// balanced by cost = elements + 64 per slice (the epilogue).
-void build_plan(const HostSell &S, int32_t nwarps, std::vector<WorkSeg> &segs,
-                std::vector<int32_t> &warp_begin) {
-  segs.clear();
-  std::vector<int64_t> cost;
-  for (int32_t s = 0; s < S.nslices; ++s) {
-    const SliceInfo &a = S.info[s];
-    const int32_t steps = a.len_g >> 3;
-    int32_t t0 = 0;
-    do {
-      const int32_t ns = std::min(kSegSteps, steps - t0);
-      const int first = (t0 == 0), last = (t0 + ns >= steps);
-      segs.push_back(WorkSeg{a.off + (int64_t)kWarp * t0, s, (ns << 2) | (first << 1) | last});
-      cost.push_back((int64_t)kWarp * ns + (last ? 64 : 0));
-      t0 += ns;
-    } while (t0 < steps);
-  }
-  const int64_t nseg = (int64_t)segs.size();
-  int64_t total = 0;
-  for (int64_t c : cost) total += c;
-  warp_begin.assign(nwarps + 1, (int32_t)nseg);
-  warp_begin[0] = 0;
-  int64_t acc = 0;
-  int32_t w = 1;
-  for (int64_t i = 0; i < nseg && w < nwarps; ++i) {
-    // a cut before segment i is allowed only at a slice start
-    while (w < nwarps && (segs[i].steps_fl & 2) && acc >= (total * w) / nwarps) warp_begin[w++] = (int32_t)i;
-    acc += cost[i];
-  }
-}
-
 double now_seconds() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
       .count();
@@ -81,7 +48,6 @@ struct lp_problem {
   int nsm = 0;
   std::vector<void *> allocs;
   SellMat A{}, AT{};
-  StreamPlan PA{}, PAT{};  // staged-kernel plans of A (row pass) and A^T (column pass)
   DevVecs v{};
   MixVecs mv{};
   bool mixed = false;
@@ -106,6 +72,12 @@ struct lp_problem {
   int32_t *h_status = nullptr;  // pinned [2]
   cudaEvent_t ev[2] = {nullptr, nullptr};
   bool solved = false;
+  cudaStream_t last_stream = nullptr;  // stream of the latest call that enqueued work
+  bool stream_used = false;
+  void use_stream(cudaStream_t s) {
+    last_stream = s;
+    stream_used = true;
+  }
   int nsearch = 1;
   int grid_cap = 0;  // blocks of the per-slice iteration kernels (0: one warp per slice)
   double setup_ms[4] = {0, 0, 0, 0};  // lp_create phases (lp_info.setup_ms)
@@ -139,22 +111,6 @@ struct lp_problem {
     lp_status s = alloc(p, (int64_t)h.size());
     if (s != LP_OK) return s;
     if (!h.empty()) LP_CU(cudaMemcpy(*p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
-    return LP_OK;
-  }
-
-  lp_status upload_plan(const HostSell &H, int32_t nwarps, StreamPlan &P) {
-    std::vector<WorkSeg> segs;
-    std::vector<int32_t> wb;
-    build_plan(H, nwarps, segs, wb);
-    WorkSeg *ds = nullptr;
-    int32_t *dw = nullptr;
-    lp_status s;
-    if ((s = upload(&ds, segs)) != LP_OK) return s;
-    if ((s = upload(&dw, wb)) != LP_OK) return s;
-    P.segs = ds;
-    P.warp_begin = dw;
-    P.nwarps = nwarps;
-    P.nseg = (int32_t)segs.size();
     return LP_OK;
   }
 
@@ -242,9 +198,6 @@ void launch_iteration(lp_problem *h, int k, cudaStream_t s) {
   if (h->mixed) {
     launch_primal_mix(h->AT, h->mv, h->st, h->w, k, h->opt.spmv_unroll, s);
     launch_dual_mix(h->A, h->mv, h->v, h->st, h->w, k, h->opt.spmv_unroll_rows, s);
-  } else if (h->opt.spmv_mode == 1) {
-    launch_primal_stream(h->AT, h->PAT, h->v, h->st, h->w, k, s);
-    launch_dual_stream(h->A, h->PA, h->v, h->st, h->w, k, s);
   } else {
     launch_primal_step(h->AT, h->v, h->st, h->w, k, h->opt.spmv_unroll, h->grid_cap, s);
     launch_dual_step(h->A, h->v, h->st, h->w, k, h->opt.spmv_unroll_rows, h->grid_cap, s);
@@ -293,7 +246,6 @@ lp_status set_run_params(lp_problem *h, double tol, cudaStream_t s) {
 // changes speed, not results.  The launches advance the iterate: the caller
 // resets the state afterwards.
 lp_status tune_variants(lp_problem *h, cudaStream_t s) {
-  if (h->opt.spmv_mode != 0) return LP_OK;
   constexpr int kCands = 4, kRounds = 3, kReps = 3;
   const int cands[kCands] = {-2, -4, 2, 4};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -413,7 +365,7 @@ lp_status host_layout(lp_problem *h, const int32_t *row_ptr, const int32_t *col_
   const int64_t target = (int64_t)opt.lane_auto * h->nsm;
   const LanePolicy pa = choose_policy(rp, perm_y, policy, target);
   const LanePolicy pat = choose_policy(cp, perm_x, policy, target);
-  const int32_t split_len = opt.spmv_mode == 0 ? opt.split_row_len : 0;
+  const int32_t split_len = opt.split_row_len;
   build_sell(m, n, rp, hci, hv, perm_y, inv_x, pa, HA, {}, split_len);
   build_sell(n, m, cp, ri.data(), cv.data(), perm_x, inv_y, pat, HAT, {}, split_len);
   h->nnz_padded = (int64_t)HA.idx.size();
@@ -437,12 +389,6 @@ lp_status host_layout(lp_problem *h, const int32_t *row_ptr, const int32_t *col_
   lp_status e;
   if ((e = h->upload_sell(HA, h->A, h->mixed)) != LP_OK) return e;
   if ((e = h->upload_sell(HAT, h->AT, h->mixed)) != LP_OK) return e;
-  if (opt.spmv_mode == 1) {
-    const int32_t nwarps = h->nsm * kStreamWarpsPerSM;
-    if ((e = h->upload_plan(HA, nwarps, h->PA)) != LP_OK) return e;
-    if ((e = h->upload_plan(HAT, nwarps, h->PAT)) != LP_OK) return e;
-    LP_CU(prepare_stream_kernels());
-  }
   if ((e = h->upload(&h->v.c, pc)) != LP_OK) return e;
   if ((e = h->upload(&h->v.lb, pl)) != LP_OK) return e;
   if ((e = h->upload(&h->v.ub, pu)) != LP_OK) return e;
@@ -829,7 +775,7 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
                : (opt.restart_scheme == LP_RESTART_FLEXIBLE) ? 2 : 0;
   h->mixed = (opt.precision == LP_PRECISION_MIXED);
   double t_copied = t_start, t_layout = t_start;
-  lp_status e = (opt.device_layout && opt.spmv_mode == 0)
+  lp_status e = opt.device_layout
                     ? device_layout(h.get(), row_ptr, col_idx, val, c, b, lb, ub, row_type, s,
                                     &t_copied, &t_layout)
                     : host_layout(h.get(), row_ptr, col_idx, val, c, b, lb, ub, row_type, s,
@@ -906,7 +852,7 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
   LP_CU(cudaEventCreateWithFlags(&h->ev[1], cudaEventDisableTiming));
   LP_CU(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
 
-  LP_CU(cudaDeviceSynchronize());
+  LP_CU(cudaStreamSynchronize(s));
   const double t_uploaded = now_seconds();
 
   // ---- device state: step sizes, norms, sigma_max estimate
@@ -1015,6 +961,7 @@ lp_status lp_set_state(lp_handle h, const double *x, const double *y, void *cuda
   err_msg().clear();
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  h->use_stream(s);
   if (x) {
     LP_CU(cudaMemcpyAsync(h->tmp, x, sizeof(double) * h->n, cudaMemcpyDefault, s));
     launch_gather(h->v.x, h->tmp, h->perm_x, h->n, s);
@@ -1039,6 +986,7 @@ lp_status lp_iterate(lp_handle h, int32_t n_checks, double tol, void *cuda_strea
   if (!(tol > 0.0)) return fail(LP_ERR_INVALID_ARG, "tol must be > 0");
   if (n_checks < 0) return fail(LP_ERR_INVALID_ARG, "n_checks must be >= 0");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  h->use_stream(s);
   lp_status e = build_graph(h);
   if (e != LP_OK) return e;
   if ((e = set_run_params(h, tol, s)) != LP_OK) return e;
@@ -1052,6 +1000,7 @@ lp_status lp_solve(lp_handle h, double tol, void *cuda_stream) {
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   if (!(tol > 0.0)) return fail(LP_ERR_INVALID_ARG, "tol must be > 0");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  h->use_stream(s);
   lp_status e = build_graph(h);
   if (e != LP_OK) return e;
   if ((e = set_run_params(h, tol, s)) != LP_OK) return e;
@@ -1096,6 +1045,7 @@ lp_status lp_get_solution(lp_handle h, double *x, double *y, void *cuda_stream) 
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   if (!h->solved) return fail(LP_ERR_NOT_SOLVED, "no solve has run on this handle");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  h->use_stream(s);
   if (h->mixed) launch_combine(h->v, h->mv, h->st, h->n, h->m, 1, s);
   int32_t returned = 0;
   LP_CU(cudaMemcpyAsync(&returned, &h->st->returned, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -1119,6 +1069,7 @@ lp_status lp_get_state(lp_handle h, double *x, double *y, double *xbar, double *
   err_msg().clear();
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  h->use_stream(s);
   if (h->mixed) launch_combine(h->v, h->mv, h->st, h->n, h->m, 1, s);
   struct Item { double *dst; const double *src; const int32_t *perm; int32_t len; };
   const Item items[] = {{x, h->v.x, h->perm_x, h->n},       {y, h->v.y, h->perm_y, h->m},
@@ -1187,6 +1138,7 @@ lp_status lp_normalized_gap(lp_handle h, const double *x, const double *y, doubl
   if (!h || !host_rho || !x || (h->m > 0 && !y)) return fail(LP_ERR_INVALID_ARG, "NULL argument");
   if (!(r >= 0.0) || !std::isfinite(r)) return fail(LP_ERR_INVALID_ARG, "radius must be finite and >= 0");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  h->use_stream(s);
   const int n = h->n, m = h->m;
   const int64_t N = (int64_t)n + m;
   // scratch owned by this call
@@ -1217,11 +1169,23 @@ lp_status lp_normalized_gap(lp_handle h, const double *x, const double *y, doubl
   cs.hpart = (double *)get(sizeof(double) * 2 * cs.hist_grid * 4 * kBuckets);
   cs.btot = (double *)get(sizeof(double) * 2 * 4 * kBuckets);
   double *tmpx = (double *)get(sizeof(double) * std::max(n, m));
+  // split-row partial sums and arrival counters of this call (the handle's
+  // belong to its solves); the counters start at zero
+  SellMat A = h->A, AT = h->AT;
+  bool split_ok = true;
+  for (SellMat *M : {&A, &AT}) {
+    if (M->nsplit == 0) continue;
+    M->split_part = (double *)get(sizeof(double) * 2 * (size_t)M->nsplit);
+    M->split_cnt = (int32_t *)get(sizeof(int32_t) * (size_t)M->nsplit);
+    split_ok = split_ok && M->split_part && M->split_cnt;
+  }
   if (!xp || !yp || !st || !cs.partials || !cs.keys[0] || !cs.d2[0] || !cs.g2[0] || !cs.gd[0] ||
-      !cs.hpart || !cs.btot || !tmpx) {
+      !cs.hpart || !cs.btot || !tmpx || !split_ok) {
     cudaGetLastError();
     return fail(LP_ERR_OOM, "cudaMalloc of gap scratch failed");
   }
+  for (SellMat *M : {&A, &AT})
+    if (M->nsplit > 0) LP_CU(cudaMemsetAsync(M->split_cnt, 0, sizeof(int32_t) * (size_t)M->nsplit, s));
   LP_CU(cudaMemcpyAsync(tmpx, x, sizeof(double) * n, cudaMemcpyDefault, s));
   launch_gather(xp, tmpx, h->perm_x, n, s);
   if (m > 0) {
@@ -1240,7 +1204,7 @@ lp_status lp_normalized_gap(lp_handle h, const double *x, const double *y, doubl
   LP_CU(cudaStreamSynchronize(s));
   cs.pair_x = cs.pair_y = nullptr;  // the handle's pair buffers belong to its solve
   cs.cand[0] = cs.cand[1] = nullptr;  // and so do its candidate lists: full scans
-  launch_check(h->A, h->AT, v, st, nullptr, cs, n, m, 1, nullptr, false, s);
+  launch_check(A, AT, v, st, nullptr, cs, n, m, 1, nullptr, false, s);
   LP_CU(cudaGetLastError());
   LSearch L{};
   LP_CU(cudaMemcpyAsync(&L, &st->ls[0], sizeof(LSearch), cudaMemcpyDeviceToHost, s));
@@ -1258,6 +1222,7 @@ lp_status lp_select_omega(lp_handle h, const double *omegas, int32_t count, int6
     if (!(omegas[k] > 0.0) || !std::isfinite(omegas[k]))
       return fail(LP_ERR_INVALID_ARG, "every omega must be finite and > 0");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  h->use_stream(s);
   lp_status e = build_graph(h);
   if (e != LP_OK) return e;
   const int32_t scheme = h->opt.restart_scheme;
@@ -1305,6 +1270,7 @@ lp_status lp_solve_recorded(lp_handle h, int64_t iters, void *cuda_stream) {
   if (h->opt.restart_scheme == LP_RESTART_FLEXIBLE)
     return fail(LP_ERR_INVALID_ARG, "recording supports the adaptive, fixed and no-restart schemes");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  h->use_stream(s);
   lp_status e = build_graph(h);
   if (e != LP_OK) return e;
   const int n = h->n, m = h->m;
@@ -1356,6 +1322,7 @@ lp_status lp_backward(lp_handle h, const double *dl_dx, const double *dl_dy, dou
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   if (h->rec_blocks == 0) return fail(LP_ERR_NOT_SOLVED, "no recorded solve (lp_solve_recorded)");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  h->use_stream(s);
   const int n = h->n, m = h->m, K = h->opt.check_every;
   const int64_t slot = 2 * (int64_t)n + 2 * (int64_t)m;
   DevState hs{};
@@ -1436,13 +1403,11 @@ lp_status lp_profile_kernel(lp_handle h, int32_t which, int32_t reps, void *cuda
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   if (which < 0 || which > 1 || reps < 0) return fail(LP_ERR_INVALID_ARG, "which must be 0 or 1, reps >= 0");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  h->use_stream(s);
   for (int32_t r = 0; r < reps; ++r) {
     if (h->mixed) {
       if (which == 0) launch_primal_mix(h->AT, h->mv, h->st, h->w, 0, h->opt.spmv_unroll, s);
       else launch_dual_mix(h->A, h->mv, h->v, h->st, h->w, 0, h->opt.spmv_unroll_rows, s);
-    } else if (h->opt.spmv_mode == 1) {
-      if (which == 0) launch_primal_stream(h->AT, h->PAT, h->v, h->st, h->w, 0, s);
-      else launch_dual_stream(h->A, h->PA, h->v, h->st, h->w, 0, s);
     } else {
       if (which == 0) launch_primal_step(h->AT, h->v, h->st, h->w, 0, h->opt.spmv_unroll, h->grid_cap, s);
       else launch_dual_step(h->A, h->v, h->st, h->w, 0, h->opt.spmv_unroll_rows, h->grid_cap, s);
@@ -1454,7 +1419,10 @@ lp_status lp_profile_kernel(lp_handle h, int32_t which, int32_t reps, void *cuda
 
 void lp_destroy(lp_handle h) {
   if (!h) return;
-  cudaDeviceSynchronize();
+  // the handle's work is stream-ordered: wait for the stream of its latest
+  // call and for its own capture stream, not for the whole device
+  if (h->stream_used) cudaStreamSynchronize(h->last_stream);
+  if (h->cap_stream) cudaStreamSynchronize(h->cap_stream);
   delete h;
 }
 
@@ -1481,15 +1449,18 @@ void lp_destroy(lp_handle h) {
 // first call made on that device.  Make that first call before any stream
 // capture begins.  Every call reuses the same array: two calls whose work
 // overlaps on the GPU (different streams, different host threads) race on
-// it and must be serialized by the caller.  Every region is fully written
-// by a call before the same call reads it, so nothing has to be cleared
-// between calls.
+// it and must be serialized by the caller.  A call writes nothing that the
+// handle's own calls use (its split-row counters and partial sums come from
+// the array too), so it may overlap a solve on the same handle.  The
+// split-row arrival counters are cleared at the start of every call; every
+// other region is fully written by a call before the same call reads it.
+// The histogram grid is the handle's (at most 129 blocks for n + m within
+// the limit), so the result is that of lp_normalized_gap bit for bit.
 namespace {
 
 constexpr size_t kGapScratchBytes = size_t(16) << 20;
 constexpr int64_t kGapScratchMaxElems = int64_t(1) << 18;  // n + m
 constexpr int32_t kGapScratchMaxParts = 4096;               // partial-sum slots per quantity
-constexpr int32_t kGapScratchHistGrid = 64;                 // histogram blocks
 constexpr int kGapScratchMaxDevices = 256;
 
 static __device__ __align__(256) unsigned char g_gap_scratch[kGapScratchBytes];
@@ -1541,13 +1512,13 @@ extern "C" lp_status lp_normalized_gap_static(lp_handle h, const double *x, cons
     base = g_gap_scratch_addr[dev];
   }
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  h->use_stream(s);
   ScratchCarver sc{static_cast<unsigned char *>(base), 0, kGapScratchBytes};
   double *xp = (double *)sc.take(sizeof(double) * std::max(n, 1));
   double *yp = (double *)sc.take(sizeof(double) * std::max(m, 1));
   double *tmpx = (double *)sc.take(sizeof(double) * std::max(std::max(n, m), 1));
   DevState *st = (DevState *)sc.take(sizeof(DevState));
-  CheckScratch cs = h->cs;
-  cs.hist_grid = std::min(h->cs.hist_grid, kGapScratchHistGrid);
+  CheckScratch cs = h->cs;  // same histogram grid as lp_normalized_gap: same reduction order
   cs.partials = (double *)sc.take(sizeof(double) * NQ * cs.pstride);
   cs.keys[0] = (uint64_t *)sc.take(sizeof(uint64_t) * N);
   cs.d2[0] = (double *)sc.take(sizeof(double) * N);
@@ -1555,9 +1526,21 @@ extern "C" lp_status lp_normalized_gap_static(lp_handle h, const double *x, cons
   cs.gd[0] = (double *)sc.take(sizeof(double) * N);
   cs.hpart = (double *)sc.take(sizeof(double) * 2 * cs.hist_grid * 4 * kBuckets);
   cs.btot = (double *)sc.take(sizeof(double) * 2 * 4 * kBuckets);
+  // split-row partial sums and arrival counters of this call (the handle's
+  // belong to its solves); the counters start at zero
+  SellMat A = h->A, AT = h->AT;
+  bool split_ok = true;
+  for (SellMat *M : {&A, &AT}) {
+    if (M->nsplit == 0) continue;
+    M->split_part = (double *)sc.take(sizeof(double) * 2 * (size_t)M->nsplit);
+    M->split_cnt = (int32_t *)sc.take(sizeof(int32_t) * (size_t)M->nsplit);
+    split_ok = split_ok && M->split_part && M->split_cnt;
+  }
   if (!xp || !yp || !tmpx || !st || !cs.partials || !cs.keys[0] || !cs.d2[0] || !cs.g2[0] ||
-      !cs.gd[0] || !cs.hpart || !cs.btot)
+      !cs.gd[0] || !cs.hpart || !cs.btot || !split_ok)
     return fail(LP_ERR_INVALID_ARG, "lp_normalized_gap_static: problem does not fit the static scratch");
+  for (SellMat *M : {&A, &AT})
+    if (M->nsplit > 0) LP_CU(cudaMemsetAsync(M->split_cnt, 0, sizeof(int32_t) * (size_t)M->nsplit, s));
   cs.keys[1] = cs.keys[0];
   cs.d2[1] = cs.d2[0];
   cs.g2[1] = cs.g2[0];
@@ -1580,7 +1563,7 @@ extern "C" lp_status lp_normalized_gap_static(lp_handle h, const double *x, cons
   LP_CU(cudaMemcpyAsync(st, &hs, sizeof(DevState), cudaMemcpyHostToDevice, s));
   cs.pair_x = cs.pair_y = nullptr;  // the handle's pair buffers belong to its solve
   cs.cand[0] = cs.cand[1] = nullptr;  // and so do its candidate lists: full scans
-  launch_check(h->A, h->AT, v, st, nullptr, cs, n, m, 1, nullptr, false, s);
+  launch_check(A, AT, v, st, nullptr, cs, n, m, 1, nullptr, false, s);
   LP_CU(cudaGetLastError());
   LSearch L{};
   LP_CU(cudaMemcpyAsync(&L, &st->ls[0], sizeof(LSearch), cudaMemcpyDeviceToHost, s));

@@ -386,7 +386,7 @@ inline lp_status validate_options(const lp_options &o) {
   }
   if (o.lane_steps < 1 || o.lane_steps > 1024) return fail(LP_ERR_INVALID_ARG, "lane_steps must lie in [1, 1024]");
   if (o.single_lane_max < 0) return fail(LP_ERR_INVALID_ARG, "single_lane_max must be >= 0");
-  if (o.spmv_mode != 0 && o.spmv_mode != 1) return fail(LP_ERR_INVALID_ARG, "spmv_mode must be 0 or 1");
+  if (o.spmv_mode != 0) return fail(LP_ERR_INVALID_ARG, "spmv_mode must be 0 (reserved)");
   if (o.lane_auto < 0) return fail(LP_ERR_INVALID_ARG, "lane_auto must be >= 0");
   if (o.autotune != 0 && o.autotune != 1) return fail(LP_ERR_INVALID_ARG, "autotune must be 0 or 1");
   if (o.sigma_method != LP_SIGMA_POWER && o.sigma_method != LP_SIGMA_LANCZOS)

@@ -62,25 +62,6 @@ struct SellMat {
   int32_t *split_cnt = nullptr;        // [nsplit] arrival counters (at index first), zero between passes
 };
 
-// Work plan of the staged (TMA) SpMV kernels.  A segment is at most
-// kSegSteps steps (32 elements each) of one slice; a slice longer than
-// that spans consecutive segments.  Persistent warps own contiguous segment
-// ranges that start and end on slice boundaries, balanced by elements.
-constexpr int kSegSteps = 16;
-constexpr int kStreamWarps = 4;  // warps per block of the staged kernels
-constexpr int kStreamWarpsPerSM = 16;
-struct WorkSeg {
-  int64_t off;       // element offset of the segment
-  int32_t slice;
-  int32_t steps_fl;  // (steps << 2) | (first segment of the slice << 1) | last
-};
-struct StreamPlan {
-  const WorkSeg *segs;
-  const int32_t *warp_begin;  // [nwarps + 1]
-  int32_t nwarps;
-  int32_t nseg;
-};
-
 // Reduced quantities of one check.  _A: running average, _C: current
 // iterate.  GAP*: data of the multiplier search (finite-breakpoint sums and
 // the squared objective of coordinates that never reach a bound).
@@ -277,11 +258,6 @@ void launch_primal_step(const SellMat &AT, const DevVecs &v, DevState *st,
                         const double *w, int k, int unroll, int grid_cap, cudaStream_t s);
 void launch_dual_step(const SellMat &A, const DevVecs &v, DevState *st,
                       const double *w, int k, int unroll, int grid_cap, cudaStream_t s);
-void launch_primal_stream(const SellMat &AT, const StreamPlan &P, const DevVecs &v,
-                          DevState *st, const double *w, int k, cudaStream_t s);
-void launch_dual_stream(const SellMat &A, const StreamPlan &P, const DevVecs &v,
-                        DevState *st, const double *w, int k, cudaStream_t s);
-cudaError_t prepare_stream_kernels();
 void launch_check(const SellMat &A, const SellMat &AT, const DevVecs &v,
                   DevState *st, double *w, const CheckScratch &cs, int n,
                   int m, int nsearch, double *trace, bool decide,

@@ -60,159 +60,6 @@ __global__ void __launch_bounds__(kBlock) spmv_kernel(SellMat A, const double *_
   process_all<1, kUnroll, false, false, SPLIT>(A, v, (const double *)nullptr, epi);
 }
 
-// ------------------------------------------------ staged (TMA) iteration
-//
-// Persistent warps, each with two shared-memory buffers.  One lane issues
-// the bulk copies (cp.async.bulk, the TMA's 1-D form) of the next segment's
-// indices and values while the warp computes the current one, so the
-// matrix stream is always one segment ahead and only the gathers of the
-// operand vector wait on memory.  Copies complete on a per-buffer mbarrier
-// (transaction count = bytes); waits are bounded: on expiry the kernel
-// records LP_ERR_TIMEOUT in the state, waits (bounded) for its other copy
-// and returns.
-constexpr int kSegIdxBytes = kSegSteps * kWarp * 4;
-constexpr int kSegBufBytes = kSegSteps * kWarp * 12;
-constexpr int kStreamWarpSmem = 2 * kSegBufBytes + 128;  // two buffers + mbarriers
-constexpr int kStreamSmem = kStreamWarps * kStreamWarpSmem;
-constexpr int kMaxSpin = 1 << 22;
-constexpr int kStatusTimeout = 6;
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_fence_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
-                                         uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          dst),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < kMaxSpin; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-template <class Epi>
-__device__ __forceinline__ void stream_warp(const SellMat &A, const StreamPlan &P,
-                                            const double *__restrict__ v0, Epi &epi,
-                                            DevState *st) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int lane = threadIdx.x & (kWarp - 1), wib = threadIdx.x >> 5;
-  const int gw = blockIdx.x * kStreamWarps + wib;
-  if (gw >= P.nwarps) return;
-  unsigned char *my = smem_raw + wib * kStreamWarpSmem;
-  const uint32_t buf0 = smem_addr(my), bar0 = smem_addr(my + 2 * kSegBufBytes);
-  if (lane == 0) {
-    mbar_init(bar0, 1);
-    mbar_init(bar0 + 8, 1);
-    mbar_fence_init();
-  }
-  __syncwarp();
-  const int sb = P.warp_begin[gw], se = P.warp_begin[gw + 1];
-  uint32_t uses0 = 0, uses1 = 0;  // completed phases per buffer
-  auto issue = [&](int i, int b) {
-    const WorkSeg g = P.segs[i];
-    const uint32_t ns = (uint32_t)(g.steps_fl >> 2);
-    if (ns > 0 && lane == 0) {
-      const uint32_t bar = bar0 + 8 * b, dst = buf0 + b * kSegBufBytes;
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_expect_tx(bar, ns * kWarp * 12);
-      bulk_g2s(dst, A.idx + g.off, ns * kWarp * 4, bar);
-      bulk_g2s(dst + kSegIdxBytes, A.val + g.off, ns * kWarp * 8, bar);
-    }
-  };
-  if (sb < se) issue(sb, 0);
-  typename Epi::Pre pre{};
-  double a0 = 0.0;
-  int row = 0, lg = 0;
-  bool owner = false;
-  for (int i = sb; i < se; ++i) {
-    const int b = (i - sb) & 1;
-    if (i + 1 < se) issue(i + 1, b ^ 1);
-    const WorkSeg g = P.segs[i];
-    const int ns = g.steps_fl >> 2;
-    if (g.steps_fl & 2) {  // first segment of its slice
-      const SliceInfo a = A.info[g.slice];
-      const int32_t row_end = A.info[g.slice + 1].row0;
-      lg = a.len_g & 7;
-      row = a.row0 + (lane >> lg);
-      owner = ((lane & ((1 << lg) - 1)) == 0) && row < row_end;
-      if (owner) pre = epi.load(row);
-      a0 = owner ? epi.init(pre) : 0.0;
-    }
-    if (ns > 0) {
-      const uint32_t parity = (b ? uses1 : uses0) & 1u;
-      if (b) ++uses1;
-      else ++uses0;
-      if (!mbar_wait(bar0 + 8 * b, parity)) {
-        if (lane == 0) atomicExch(&st->status, kStatusTimeout);
-        if (i + 1 < se && (P.segs[i + 1].steps_fl >> 2) > 0)
-          mbar_wait(bar0 + 8 * (b ^ 1), (b ? uses0 : uses1) & 1u);
-        return;
-      }
-      const int32_t *si = reinterpret_cast<const int32_t *>(my + b * kSegBufBytes);
-      const double *sv = reinterpret_cast<const double *>(my + b * kSegBufBytes + kSegIdxBytes);
-      double gv[kSegSteps];
-#pragma unroll
-      for (int t = 0; t < kSegSteps; ++t)
-        if (t < ns) gv[t] = __ldg(v0 + si[t * kWarp + lane]);
-#pragma unroll
-      for (int t = 0; t < kSegSteps; ++t)
-        if (t < ns) a0 = fma(sv[t * kWarp + lane], gv[t], a0);
-    }
-    __syncwarp();
-    if (g.steps_fl & 1) {  // last segment: combine the row's lanes, epilogue
-      for (int o = (1 << lg) >> 1; o > 0; o >>= 1) a0 += __shfl_xor_sync(kFull, a0, o);
-      if (owner) epi.store(row, a0, 0.0, pre);
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kStreamWarps *kWarp) primal_stream_kernel(
-    SellMat AT, StreamPlan P, const double *__restrict__ y, PrimalEpi epi, DevState *st,
-    const double *__restrict__ w, int k) {
-  if (st->status != kRunning) return;
-  epi.tau = st->tau;
-  epi.w = w[k];
-  stream_warp(AT, P, y, epi, st);
-}
-
-__global__ void __launch_bounds__(kStreamWarps *kWarp) dual_stream_kernel(
-    SellMat A, StreamPlan P, const double *__restrict__ xhat, DualEpi epi, DevState *st,
-    const double *__restrict__ w, int k) {
-  if (st->status != kRunning) return;
-  epi.sigma = st->sigma;
-  epi.w = w[k];
-  stream_warp(A, P, xhat, epi, st);
-}
-
 template <int U, bool PIPE, bool SPLIT = false>
 __global__ void __launch_bounds__(kBlock) primal_mix_kernel(SellMat AT, const float *__restrict__ dy,
                                                             PrimalMixEpi epi, const DevState *st,
@@ -1212,28 +1059,6 @@ void launch_dual_step(const SellMat &A, const DevVecs &v, DevState *st, const do
     case -4: dual_launch<4, true>(occ, g, s, A, v.xhat, epi, st, w, k); break;
     default: dual_launch<4, false>(occ, g, s, A, v.xhat, epi, st, w, k); break;
   }
-}
-
-void launch_primal_stream(const SellMat &AT, const StreamPlan &P, const DevVecs &v, DevState *st,
-                          const double *w, int k, cudaStream_t s) {
-  PrimalEpi epi{v.c, v.lbk, v.ubk, v.x, v.xhat, v.xbar, 0.0, 0.0, nullptr};
-  const int grid = (P.nwarps + kStreamWarps - 1) / kStreamWarps;
-  primal_stream_kernel<<<grid, kStreamWarps * kWarp, kStreamSmem, s>>>(AT, P, v.y, epi, st, w, k);
-}
-
-void launch_dual_stream(const SellMat &A, const StreamPlan &P, const DevVecs &v, DevState *st,
-                        const double *w, int k, cudaStream_t s) {
-  DualEpi epi{v.b, v.row_type, v.y, v.ybar, 0.0, 0.0, nullptr};
-  const int grid = (P.nwarps + kStreamWarps - 1) / kStreamWarps;
-  dual_stream_kernel<<<grid, kStreamWarps * kWarp, kStreamSmem, s>>>(A, P, v.xhat, epi, st, w, k);
-}
-
-cudaError_t prepare_stream_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(primal_stream_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kStreamSmem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(dual_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              kStreamSmem);
 }
 
 void launch_check(const SellMat &A, const SellMat &AT, const DevVecs &v, DevState *st, double *w,

@@ -524,7 +524,9 @@ class LPBatch:
     """Owning wrapper of an lp_batch_handle built from a list of lpgen.LPData-like
     problems (concatenated into the block-diagonal batch here, on the host)."""
 
-    def __init__(self, problems, stream=None, tuning=None, **options):
+    def __init__(self, problems, stream=None, tuning=None, c=None, b=None, **options):
+        """c, b (optional): the concatenated objective and right-hand side, host or
+        device arrays, in place of the problems' own."""
         opt = lp_default_options()
         for k, v in options.items():
             if not hasattr(opt, k):
@@ -552,8 +554,9 @@ class LPBatch:
                 setattr(t, k, v)
             tuning = t
         self.h = lp_batch_create(self.row_start, self.col_start, int(row_ptr[-1]), row_ptr,
-                                 col_idx, cat("val", np.float64), cat("c", np.float64),
-                                 cat("b", np.float64), cat("lb", np.float64),
+                                 col_idx, cat("val", np.float64),
+                                 cat("c", np.float64) if c is None else c,
+                                 cat("b", np.float64) if b is None else b, cat("lb", np.float64),
                                  cat("ub", np.float64), cat("row_type", np.int8), opt, tuning,
                                  stream)
 

@@ -80,3 +80,20 @@ def test_flexible_restart_hand(oracle_mod, case):
     assert (r.iters, r.restarts, r.returned) == (f["iters"], f["restarts"], f["returned"])
     for k in ("x", "xbar", "x0"):
         assert getattr(r, k)[0] == pytest.approx(golden.value(f[k]), rel=1e-15, abs=1e-300), k
+
+
+def test_openmp_build_is_bitwise_the_checker(oracle_mod):
+    """The OpenMP build (used only to time the oracle on all cores) splits
+    loops without dependences between iterations: same bits as the checker."""
+    from paper_2105_12715_gb300 import lpgen
+
+    try:
+        oracle_mod.build(openmp=True)
+    except Exception as e:  # noqa: BLE001
+        pytest.skip(f"no OpenMP toolchain: {e}")
+    d = lpgen.adversarial(5, m=40, n=90, dense_row=True)
+    eta = 0.9 / oracle_mod.sigma_max(d)
+    a = oracle_mod.solve(d, eta, tol=1e-300, max_iter=320, check_every=16)
+    b = oracle_mod.solve(d, eta, tol=1e-300, max_iter=320, check_every=16, openmp=True)
+    for k in ("x", "y", "xbar", "ybar", "x0", "y0", "trace"):
+        np.testing.assert_array_equal(getattr(a, k), getattr(b, k), err_msg=k)

@@ -239,3 +239,80 @@ def test_batch_autograd_function(oracle_mod):
         torch.testing.assert_close(b.grad[ro:ro + d.m], bk.grad, rtol=1e-11, atol=1e-13)
         co += d.n
         ro += d.m
+
+
+def test_backward_finite_differences_at_full_size(oracle_mod):
+    """The differentiable-LP workload at its full size: m = 2000, n = 5000,
+    50k nonzeros, box [0, 1], K = 100, 2000 unrolled iterations (checkpoints
+    every 100).  Eight sampled coordinates of c and eight of b against
+    central differences (h = 1e-6, FP64) of the oracle's unrolled map with
+    the recorded restart schedule.  Over 2000 steps some clamp decisions may
+    sit within the perturbation of their bound; the map is continuous and
+    piecewise affine, so such a kink moves the difference quotient by a
+    fraction of one coordinate's slope change, which the tolerance
+    (1e-4 of the gradient's largest sampled entry) covers."""
+    from paper_2105_12715_gb300 import lp
+
+    data = lpgen.box_standard_form(100)
+    assert (data.m, data.n, data.nnz) == (2000, 5000, 50000)
+    eta = 0.9 / oracle_mod.sigma_max(data)
+    K, iters = 100, 2000
+    rng = np.random.default_rng(5)
+    wx = rng.standard_normal(data.n)
+    with lp.LP(data, eta=eta, check_every=K) as g:
+        lp.lp_solve_recorded(g.h, iters)
+        flags = g.trace()[:, 2].astype(np.int8)
+        st = g.state()
+        dc, db = np.empty(data.n), np.empty(data.m)
+        lp.lp_backward(g.h, wx, None, dc, db)
+    ref = oracle_mod.solve(data, eta, tol=1e-300, max_iter=iters, check_every=K)
+    np.testing.assert_array_equal(flags, ref.trace[:, 2].astype(np.int8))
+    assert flags.sum() >= 2
+    np.testing.assert_allclose(st["xbar"], ref.xbar, rtol=0, atol=1e-9)
+
+    def loss(c, b):
+        d = lpgen.LPData(**{**data.__dict__})
+        d.c, d.b = c, b
+        r = oracle_mod.solve(d, eta, tol=1e-300, max_iter=iters, check_every=K,
+                             restart_scheme=oracle_mod.RESTART_SCHEDULE, schedule=flags)
+        return wx @ r.xbar
+
+    h = 1e-6
+    got, fds = [], []
+    for j in rng.choice(data.n, size=8, replace=False):
+        e = np.zeros(data.n)
+        e[j] = h
+        fds.append((loss(data.c + e, data.b) - loss(data.c - e, data.b)) / (2 * h))
+        got.append(dc[j])
+    for i in rng.choice(data.m, size=8, replace=False):
+        e = np.zeros(data.m)
+        e[i] = h
+        fds.append((loss(data.c, data.b + e) - loss(data.c, data.b - e)) / (2 * h))
+        got.append(db[i])
+    got, fds = np.array(got), np.array(fds)
+    scale = float(np.abs(fds).max())
+    assert scale > 0
+    np.testing.assert_allclose(got, fds, rtol=1e-4, atol=1e-4 * scale)
+
+
+def test_autograd_loss_on_ybar_only(oracle_mod):
+    """A loss that reads only ybar: backward gets no gradient for xbar (None)."""
+    import torch
+
+    from paper_2105_12715_gb300 import lp
+    from paper_2105_12715_gb300.autodiff import unrolled_pdhg
+
+    data = _box_lp(6)
+    eta = 0.9 / oracle_mod.sigma_max(data)
+    c = torch.tensor(data.c, dtype=torch.float64, device="cuda", requires_grad=True)
+    b = torch.tensor(data.b, dtype=torch.float64, device="cuda", requires_grad=True)
+    wy = torch.linspace(-1.0, 1.0, data.m, dtype=torch.float64, device="cuda")
+    _, ybar = unrolled_pdhg(c, b, data, 128, eta=eta, check_every=32)
+    (wy * ybar).sum().backward()
+    assert c.grad.device.type == "cuda" and b.grad.device.type == "cuda"
+    with lp.LP(data, eta=eta, check_every=32) as g:
+        lp.lp_solve_recorded(g.h, 128)
+        dc, db = np.empty(data.n), np.empty(data.m)
+        lp.lp_backward(g.h, None, wy.cpu().numpy(), dc, db)
+    np.testing.assert_array_equal(c.grad.cpu().numpy(), dc)
+    np.testing.assert_array_equal(b.grad.cpu().numpy(), db)

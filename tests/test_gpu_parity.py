@@ -36,11 +36,17 @@ def close(gpu, ref, tol=TOL, what=""):
     assert err <= tol * scale, f"{what}: max abs err {err:.3e} (scale {scale:.3e})"
 
 
+# Kernel variants of the two passes (lp_options.spmv_unroll): register
+# batches of 2, 4, 8 gathers, software-pipelined batches (-2, -4), and the
+# same with registers capped for higher occupancy (+-100).
+VARIANTS = [2, 4, 8, -2, -4, 102, -104]
+
+
 def run_both(lpm, oracle_mod, data, iters, eta, K=64, omega=1.0, scheme=2, long_thr=512,
-             x_init=None, y_init=None, unroll=4, mode=1):
+             x_init=None, y_init=None, unroll=4, **opts):
     with lpm.LP(data, eta=eta, omega=omega, check_every=K, restart_scheme=scheme,
                 max_iter=iters, long_row_threshold=long_thr, spmv_unroll=unroll,
-                spmv_unroll_rows=unroll, spmv_mode=mode, autotune=0) as g:
+                spmv_unroll_rows=unroll, autotune=0, **opts) as g:
         if x_init is not None:
             g.set_state(x_init, y_init)
         status = g.solve(1e-300)
@@ -88,28 +94,28 @@ def test_checks_and_restarts_match_oracle(lpm, oracle_mod):
     compare_states(st, ref, 1e-8)
 
 
-@pytest.mark.parametrize("omega,mode", [(0.3, 1), (1.0, 1), (4.0, 1), (1.0, 0)])
-def test_mixed_bounds_rows_and_long_rows(lpm, oracle_mod, omega, mode):
+@pytest.mark.parametrize("omega,unroll", [(0.3, 4), (1.0, -4), (4.0, 2), (1.0, -2)])
+def test_mixed_bounds_rows_and_long_rows(lpm, oracle_mod, omega, unroll):
     """EQ/GE/LE rows, every bound kind, empty rows/cols, a dense row and a
     dense column on the warp-per-row path (threshold 16)."""
     data = lpgen.adversarial(7)
     eta = eta_of(oracle_mod, data)
     x0, y0 = lpgen.random_state(data, 5)
     status, st, info, tr, ref = run_both(lpm, oracle_mod, data, 200, eta, K=32, omega=omega,
-                                         long_thr=16, x_init=x0, y_init=y0, mode=mode)
+                                         long_thr=16, x_init=x0, y_init=y0, unroll=unroll)
     assert info.n_long_rows >= 1 and info.n_long_cols >= 1
     compare_states(st, ref)
     np.testing.assert_array_equal(tr[:, 2], ref.trace[:, 2])
 
 
-@pytest.mark.parametrize("mode,unroll", [(1, 4), (0, 2), (0, 4), (0, 8), (0, -2), (0, -4)])
-def test_ragged_multi_slice_power_law(lpm, oracle_mod, mode, unroll):
+@pytest.mark.parametrize("unroll", VARIANTS)
+def test_ragged_multi_slice_power_law(lpm, oracle_mod, unroll):
     """Several hundred slices with a ragged last slice, power-law columns;
-    both iteration-kernel designs (staged persistent warps, per-slice warps)."""
+    every kernel variant of the two passes."""
     data = lpgen.large_mixed(11, m=3001, n=15007)
     eta = eta_of(oracle_mod, data)
-    status, st, info, tr, ref = run_both(lpm, oracle_mod, data, 130, eta, K=64, unroll=unroll,
-                                         mode=mode)
+    status, st, info, tr, ref = run_both(lpm, oracle_mod, data, 130, eta, K=64, unroll=unroll)
+    assert (info.spmv_unroll, info.spmv_unroll_rows) == (unroll, unroll)
     compare_states(st, ref)
     assert info.restarts == ref.restarts
 
