@@ -37,8 +37,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 K_CHECK = 64
-OMEGA_GRID = [4.0 ** k for k in range(-3, 4)]  # Section 7 grid (powers of 4), 2048 iterations each
+OMEGA_GRID = [4.0 ** k for k in range(-3, 4)]  # reduced Section 7 grid, 2048 iterations each
 OMEGA_ITERS = 2048  # a multiple of the check period (the batch needs one)
+PAPER_OMEGA_GRID = [4.0 ** k for k in range(-5, 6)]  # Section 7: 4^-5 .. 4^5
+PAPER_OMEGA_ITERS = 5000  # Section 7: 5,000 iterations without restarts per weight
 FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one column-pass
 # launch on this workload with warm L2, per kernel variant, from one-pass ncu
@@ -117,6 +119,11 @@ def parse():
     p.add_argument("--adjoint-lps", type=int, default=4)
     p.add_argument("--no-ttk-large", action="store_true")
     p.add_argument("--ttk-large-cap", type=int, default=1_500_000)
+    p.add_argument("--no-paper-grid", action="store_true",
+                   help="skip the benchmark LP solved with the paper's full primal-weight grid")
+    p.add_argument("--no-mcf-ttk", action="store_true",
+                   help="skip the multicommodity LP solved to relative KKT 1e-8")
+    p.add_argument("--mcf-cap", type=int, default=3_000_000)
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--batch-count", type=int, default=512)
     p.add_argument("--batch-cap", type=int, default=100_000)
@@ -261,6 +268,25 @@ def oracle_openmp_available():
         return True
     except Exception:  # noqa: BLE001
         return False
+
+
+def highs_objective(d):
+    """Optimal objective of an LP by SciPy's HiGHS (None if unavailable)."""
+    try:
+        import scipy.sparse as sp
+        from scipy.optimize import linprog
+    except ImportError:
+        return None
+    A = sp.csr_matrix((d.val, d.col_idx, d.row_ptr), shape=(d.m, d.n))
+    eq, ge, le = d.row_type == 0, d.row_type == 1, d.row_type == 2
+    A_ub = sp.vstack([A[le], -A[ge]]).tocsr()
+    b_ub = np.concatenate([d.b[le], -d.b[ge]])
+    bounds = [(lo if np.isfinite(lo) else None, hi if np.isfinite(hi) else None)
+              for lo, hi in zip(d.lb, d.ub)]
+    r = linprog(d.c, A_ub=A_ub if A_ub.shape[0] else None, b_ub=b_ub if b_ub.size else None,
+                A_eq=A[eq] if eq.any() else None, b_eq=d.b[eq] if eq.any() else None,
+                bounds=bounds, method="highs")
+    return float(r.fun) if r.status == 0 else None
 
 
 def cpu_baseline(args, data, eta):
@@ -414,12 +440,25 @@ def run_batched(args, lp, stream, barrier):
     g.close()
     t_batch = pdist.reduce_scalar(t_batch, "max")
     t_setup = pdist.reduce_scalar(t_setup, "max")
+    kkt_fin = np.array([min(p["kkt_avg"][4], p["kkt_cur"][4]) for p in per])
+    unconv = np.flatnonzero(~conv)
     res["solve"] = {"tol": 1e-8, "cap_iters": args.batch_cap, "seconds": t_batch,
                     "seconds_with_setup": t_batch + t_setup,
                     "converged": int(pdist.reduce_scalar(conv.sum(), "sum")),
                     "problems": int(pdist.reduce_scalar(len(probs), "sum")),
                     "iters_median": float(np.median(its)),
-                    "iters_sum": int(pdist.reduce_scalar(its.sum(), "sum")), "omega": 1.0}
+                    "iters_sum": int(pdist.reduce_scalar(its.sum(), "sum")), "omega": 1.0,
+                    # every problem that did not reach 1e-8 within the cap, with its final
+                    # relative KKT error (the smaller of its two candidates) and its rows
+                    "unconverged": {
+                        "count": int(unconv.size),
+                        "final_rel_kkt_quantiles_0_50_90_100": (
+                            [float(q) for q in np.quantile(kkt_fin[unconv], [0, 0.5, 0.9, 1])]
+                            if unconv.size else None),
+                        "below_1e6": int((kkt_fin[unconv] <= 1e-6).sum()),
+                        "below_1e7": int((kkt_fin[unconv] <= 1e-7).sum()),
+                        "problems": [[int(k), int(probs[k].m), float("%.3g" % kkt_fin[k])]
+                                     for k in unconv]}}
     # the plain FP64 path, one problem at a time, on a seeded sample
     rng = np.random.default_rng(0)
     idx = rng.choice(len(probs), size=min(max(args.batch_loop_sample, 1), len(probs)),
@@ -637,14 +676,14 @@ def run_ours(args):
 
     # time to relative KKT 1e-8 (the paper's recipe: primal weight by the grid search of
     # Section 7, then adaptive restarted PDHG), FP64 vs mixed, setup included
-    def ttk_run(d, tol, prec, select, cap):
+    def ttk_run(d, tol, prec, select, cap, grid=None, grid_iters=None):
         barrier()
         t0 = time.perf_counter()
         gt = lp.LP(d, stream=stream, check_every=K_CHECK, max_iter=cap, precision=prec)
         omega, t_sel = 1.0, 0.0
         if select:
             ts = time.perf_counter()
-            omega, _ = gt.select_omega(OMEGA_GRID, iters=OMEGA_ITERS)
+            omega, _ = gt.select_omega(grid or OMEGA_GRID, iters=grid_iters or OMEGA_ITERS)
             t_sel = time.perf_counter() - ts
         st = gt.solve(tol)
         torch.cuda.synchronize()
@@ -653,7 +692,8 @@ def run_ours(args):
         gt.close()
         pobj = it.kkt_avg[2] if it.returned == 0 else it.kkt_cur[2]
         out = {"seconds": dt, "omega": omega, "omega_select_seconds": t_sel, "iters": it.iters,
-               "eta": it.eta,
+               "eta": it.eta, "omega_grid": [min(grid or OMEGA_GRID), max(grid or OMEGA_GRID),
+                                             grid_iters or OMEGA_ITERS] if select else None,
                "restarts": it.restarts, "status": lp.STATUS_NAMES.get(st, st),
                "rel_kkt": min(it.kkt_avg[4], it.kkt_cur[4]), "pobj": pobj}
         if d.obj_star is not None:  # the planted optimum's objective (unique)
@@ -718,6 +758,11 @@ def run_ours(args):
             ttk_large[name] = ttk_run(data, 1e-8, prec, True, args.ttk_large_cap)
         ttk_large["mixed_speedup"] = ttk_large["fp64"]["seconds"] / ttk_large["mixed"]["seconds"]
         mixed_error(ttk_large)
+        if not args.no_paper_grid:
+            # Section 7's own recipe: 4^-5 .. 4^5, 5,000 iterations without restarts each
+            ttk_large["fp64_paper_grid"] = ttk_run(data, 1e-8, lp.LP_PRECISION_FP64, True,
+                                                   args.ttk_large_cap, PAPER_OMEGA_GRID,
+                                                   PAPER_OMEGA_ITERS)
 
     # an LP with one dense row and one dense column: split rows (lp_options.split_row_len)
     # against one warp per long row
@@ -775,6 +820,29 @@ def run_ours(args):
                 mcf[name]["achieved_gbs_per_iter"] = (mp + md) * mcf[name]["iters_per_s"] / 1e9
                 mcf["eta"] = gmc.info().eta
             gmc.close()
+        if not args.no_mcf_ttk and not args.no_ttk:
+            # FP32-mixed (FP64 restarts, checks and refinement) against plain FP64 to relative
+            # KKT 1e-8, omega by Section 7's grid (4^-5 .. 4^5, 5,000 iterations each), setup
+            # included; the mixed result's objective against the FP64 one
+            t8 = {"tol": 1e-8, "cap_iters": args.mcf_cap}
+            for name, prec in (("fp64", lp.LP_PRECISION_FP64), ("mixed", lp.LP_PRECISION_MIXED)):
+                t8[name] = ttk_run(mc, 1e-8, prec, True, args.mcf_cap, PAPER_OMEGA_GRID,
+                                   PAPER_OMEGA_ITERS)
+            mixed_error(t8)
+            t8["mixed_speedup"] = t8["fp64"]["seconds"] / t8["mixed"]["seconds"]
+            # a 30 x 30 grid with 4 commodities: both arms against HiGHS's optimum
+            small = lpgen.multicommodity_grid(4, side=30, commodities=4)
+            ref = highs_objective(small)
+            sm = {"lp": f"multicommodity grid 30x30, 4 commodities: m={small.m} n={small.n} "
+                        f"nnz={small.nnz}", "highs_objective": ref}
+            for name, prec in (("fp64", lp.LP_PRECISION_FP64), ("mixed", lp.LP_PRECISION_MIXED)):
+                r = ttk_run(small, 1e-8, prec, True, 3_000_000, PAPER_OMEGA_GRID,
+                            PAPER_OMEGA_ITERS)
+                if ref is not None:
+                    r["obj_rel_err_vs_highs"] = abs(r["pobj"] - ref) / max(1.0, abs(ref))
+                sm[name] = r
+            t8["small_vs_highs"] = sm
+            mcf["time_to_kkt_1e8"] = t8
 
     # adjoint of the unrolled map on differentiable-LP-shaped instances
     # (m=2000, n=5000, nnz=50k, box [0,1]; 2000 iterations, checkpoint every 100)
