@@ -122,12 +122,14 @@ def parse():
     p.add_argument("--no-paper-grid", action="store_true",
                    help="skip the benchmark LP solved with the paper's full primal-weight grid")
     p.add_argument("--no-mcf-ttk", action="store_true",
-                   help="skip the multicommodity LP solved to relative KKT 1e-8")
-    p.add_argument("--mcf-cap", type=int, default=3_000_000)
+                   help="skip the multicommodity LP solved to a relative KKT tolerance")
+    p.add_argument("--mcf-tol", type=float, default=1e-3,
+                   help="tolerance of the multicommodity time-to-tolerance runs")
+    p.add_argument("--mcf-cap", type=int, default=1_000_000)
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--batch-count", type=int, default=512)
-    p.add_argument("--batch-cap", type=int, default=100_000)
-    p.add_argument("--batch-loop-sample", type=int, default=16)
+    p.add_argument("--batch-cap", type=int, default=1_000_000)
+    p.add_argument("--batch-loop-sample", type=int, default=8)
     p.add_argument("--batch-schemes", action="store_true",
                    help="also solve the batch with the flexible and no-restart schemes")
     p.add_argument("--batch-only", action="store_true",
@@ -800,6 +802,36 @@ def run_ours(args):
                 "iters_per_s": args.steps * K_CHECK / (tms / 1000.0),
                 "graph_kernels_per_step": gt0.info().graph_kernels, "eta": gt0.info().eta}
         gt0.close()
+        # LPs this small belong in the batched solver: 512 such LPs (seeds 0..511) as one
+        # batch, aggregate throughput and all of them to relative KKT 1e-8
+        tl = [lpgen.tiny_standard_form(sd) for sd in range(512)]
+        gbt = lp.LPBatch(tl, stream=stream, check_every=K_CHECK, max_iter=args.batch_cap,
+                         tuning={"autotune": 1})
+        gbt.iterate(2, 1e-300)
+        barrier()
+        e0t, e1t = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0t.record(stream)
+        gbt.iterate(8, 1e-300)
+        e1t.record(stream)
+        torch.cuda.synchronize()
+        bms = e0t.elapsed_time(e1t) / 8
+        gbt.close()
+        barrier()
+        t0 = time.perf_counter()
+        gbt = lp.LPBatch(tl, stream=stream, check_every=K_CHECK, max_iter=args.batch_cap,
+                         tuning={"autotune": 1})
+        gbt.solve(1e-8)
+        torch.cuda.synchronize()
+        tsolve = time.perf_counter() - t0
+        _, pert = gbt.info()
+        gbt.close()
+        conv_t = [p_ for p_ in pert if p_["status"] == lp.LP_OK]
+        tiny["batch_512"] = {
+            "lp": "512 x tiny_standard_form (seeds 0..511), one batch",
+            "us_per_batch_iter": 1000.0 * bms / K_CHECK,
+            "problem_iters_per_s": 512 * K_CHECK / (bms / 1000.0),
+            "to_1e8_seconds_with_setup": tsolve, "converged": len(conv_t),
+            "iters_median": float(np.median([p_["iters"] for p_ in pert]))}
 
     # multicommodity flow LP (300 x 300 grid, 8 commodities): FP64 vs mixed throughput
     mcf = None
@@ -821,12 +853,14 @@ def run_ours(args):
                 mcf["eta"] = gmc.info().eta
             gmc.close()
         if not args.no_mcf_ttk and not args.no_ttk:
-            # FP32-mixed (FP64 restarts, checks and refinement) against plain FP64 to relative
-            # KKT 1e-8, omega by Section 7's grid (4^-5 .. 4^5, 5,000 iterations each), setup
-            # included; the mixed result's objective against the FP64 one
-            t8 = {"tol": 1e-8, "cap_iters": args.mcf_cap}
+            # FP32-mixed (FP64 restarts, checks and refinement) against plain FP64 to a relative
+            # KKT tolerance (mcf_tol), omega by Section 7's grid (4^-5 .. 4^5, 5,000 iterations
+            # each), setup included; the mixed result's objective against the FP64 one.  On this
+            # network LP restarted PDHG needs millions of iterations below 1e-4, so the default
+            # tolerance is one both arms reach within the cap.
+            t8 = {"tol": args.mcf_tol, "cap_iters": args.mcf_cap}
             for name, prec in (("fp64", lp.LP_PRECISION_FP64), ("mixed", lp.LP_PRECISION_MIXED)):
-                t8[name] = ttk_run(mc, 1e-8, prec, True, args.mcf_cap, PAPER_OMEGA_GRID,
+                t8[name] = ttk_run(mc, args.mcf_tol, prec, True, args.mcf_cap, PAPER_OMEGA_GRID,
                                    PAPER_OMEGA_ITERS)
             mixed_error(t8)
             t8["mixed_speedup"] = t8["fp64"]["seconds"] / t8["mixed"]["seconds"]
@@ -836,13 +870,13 @@ def run_ours(args):
             sm = {"lp": f"multicommodity grid 30x30, 4 commodities: m={small.m} n={small.n} "
                         f"nnz={small.nnz}", "highs_objective": ref}
             for name, prec in (("fp64", lp.LP_PRECISION_FP64), ("mixed", lp.LP_PRECISION_MIXED)):
-                r = ttk_run(small, 1e-8, prec, True, 3_000_000, PAPER_OMEGA_GRID,
+                r = ttk_run(small, 1e-8, prec, True, 1_000_000, PAPER_OMEGA_GRID,
                             PAPER_OMEGA_ITERS)
                 if ref is not None:
                     r["obj_rel_err_vs_highs"] = abs(r["pobj"] - ref) / max(1.0, abs(ref))
                 sm[name] = r
             t8["small_vs_highs"] = sm
-            mcf["time_to_kkt_1e8"] = t8
+            mcf["time_to_tolerance"] = t8
 
     # adjoint of the unrolled map on differentiable-LP-shaped instances
     # (m=2000, n=5000, nnz=50k, box [0,1]; 2000 iterations, checkpoint every 100)

@@ -811,7 +811,9 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
   CheckScratch &cs = h->cs;
   cs.cols_grid = check_grid_for(h->AT, h->nsm);
   cs.rows_grid = check_grid_for(h->A, h->nsm);
-  cs.pstride = std::max(cs.cols_grid + cs.rows_grid + split_grid(h->A) + split_grid(h->AT),
+  // one slot per block of the check passes, then one per chunk slice of split rows
+  cs.pstride = std::max(cs.cols_grid + cs.rows_grid + split_grid(h->A) + split_grid(h->AT) +
+                            h->A.nsplit + h->AT.nsplit,
                         8 * h->nsm);
   if ((e = h->alloc(&cs.partials, (int64_t)NQ * cs.pstride)) != LP_OK) return e;
   const int64_t N = (int64_t)n + m;
@@ -1460,7 +1462,7 @@ namespace {
 
 constexpr size_t kGapScratchBytes = size_t(16) << 20;
 constexpr int64_t kGapScratchMaxElems = int64_t(1) << 18;  // n + m
-constexpr int32_t kGapScratchMaxParts = 4096;               // partial-sum slots per quantity
+constexpr int32_t kGapScratchMaxParts = 65536;              // partial-sum slots per quantity
 constexpr int kGapScratchMaxDevices = 256;
 
 static __device__ __align__(256) unsigned char g_gap_scratch[kGapScratchBytes];

@@ -1103,6 +1103,13 @@ void launch_check(const SellMat &A, const SellMat &AT, const DevVecs &v, DevStat
   const double *r0 = pair ? cs.pair_x : v.xbar, *r1 = pair ? nullptr : v.x;
   double *P = cs.partials;
   const int ps = cs.pstride;
+  // after the blocks' slots, one reduction slot per chunk slice of each
+  // matrix's split rows (every one written by every check pass)
+  ce.split_slots = AT.nsplit > 0 ? P + gc + gr : nullptr;
+  ce.slot_stride = ps;
+  re.split_slots = A.nsplit > 0 ? P + gc + gr + AT.nsplit : nullptr;
+  re.slot_stride = ps;
+  const int nparts = gc + gr + AT.nsplit + A.nsplit;
   if (sc > 0 && pair)
     check_kernel<CheckColsEpi, true, true><<<gc, kBlock, 0, s>>>(AT, c0, c1, ce, st, P, ps, 0);
   else if (sc > 0)
@@ -1119,7 +1126,7 @@ void launch_check(const SellMat &A, const SellMat &AT, const DevVecs &v, DevStat
     check_kernel<CheckRowsEpi, true><<<gr, kBlock, 0, s>>>(A, r0, r1, re, st, P, ps, gc);
   else
     check_kernel<CheckRowsEpi, false><<<gr, kBlock, 0, s>>>(A, r0, r1, re, st, P, ps, gc);
-  check_finalize_kernel<<<NQ, kBlock, 0, s>>>(st, cs.partials, cs.pstride, gc + gr);
+  check_finalize_kernel<<<NQ, kBlock, 0, s>>>(st, cs.partials, cs.pstride, nparts);
   if (nsearch > 0) {
     const int64_t N = (int64_t)n + m;
     for (int p = 0; p < kSearchPasses; ++p) {

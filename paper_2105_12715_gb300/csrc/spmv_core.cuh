@@ -131,13 +131,29 @@ __device__ __forceinline__ void process_item(const SellMat &A, const T *__restri
   if (owner) epi.store(row, a0, a1, pre);
 }
 
+// Epilogues that accumulate reductions (the check's) declare kSplitSlots:
+// the reductions of a split row then go to a slot of their own instead of
+// the block of whichever chunk arrived last (see process_split_item).
+template <class E, class = void>
+struct SplitSlotsOf {
+  static constexpr bool value = false;
+};
+template <class E>
+struct SplitSlotsOf<E, decltype((void)E::kSplitSlots, void())> {
+  static constexpr bool value = E::kSplitSlots;
+};
+
 // One chunk slice of a split row (see SellMat): the warp sums its chunk in
 // the order of process_item (U loads, U gathers, U FMAs per lane, then the
 // 32-lane butterfly); chunk 0 starts from the epilogue's initial value.
 // Lane 0 publishes the partial sums; the last chunk of the row to arrive
 // adds all partials in chunk order and runs the epilogue, then resets the
 // row's counter for the next pass.  Every chunk's sum, and their order, is
-// fixed, so the result is deterministic.
+// fixed, so the result is deterministic.  For an accumulating epilogue,
+// every chunk slice first clears its own reduction slot, and the last
+// arrival moves the row's reductions into the slot of the row's first
+// chunk: each split row's terms land in a fixed slot, which the finalize
+// adds in slot order, whichever block arrived last.
 template <int NV, int U, bool PIPE, bool PAIR, typename T, class Epi>
 __device__ __forceinline__ void process_split_item(const SellMat &A, const T *__restrict__ v0,
                                                 const T *__restrict__ v1, int item, int lane,
@@ -189,6 +205,9 @@ __device__ __forceinline__ void process_split_item(const SellMat &A, const T *__
     if (NV == 2) a1 += __shfl_xor_sync(kFull, a1, o);
   }
   if (lane != 0) return;
+  if constexpr (SplitSlotsOf<Epi>::value) {
+    if (item != sp.first) epi.zero_split_slot(item);
+  }
   A.split_part[2 * (size_t)item] = (double)a0;
   A.split_part[2 * (size_t)item + 1] = (double)a1;
   __threadfence();
@@ -203,6 +222,7 @@ __device__ __forceinline__ void process_split_item(const SellMat &A, const T *__
   A.split_cnt[sp.first] = 0;
   const typename Epi::Pre pre = epi.load(row);
   epi.store(row, s0, s1, pre);
+  if constexpr (SplitSlotsOf<Epi>::value) epi.flush_split_slot(sp.first);
 }
 
 // The slices of a pass, one warp per slice.  SPLIT = false: matrices
@@ -432,6 +452,23 @@ struct CheckColsEpi {
   double sw, isw;
   int gap_a, gap_c;
   double q[NQ];
+  // split rows: the reductions of each split row go to
+  // split_slots[q * slot_stride + (slice of its first chunk)] (see
+  // process_split_item); null when the matrix has no split rows
+  static constexpr bool kSplitSlots = true;
+  double *split_slots = nullptr;
+  int slot_stride = 0;
+  __device__ __forceinline__ void zero_split_slot(int item) const {
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) split_slots[(size_t)i * slot_stride + item] = 0.0;
+  }
+  __device__ __forceinline__ void flush_split_slot(int first) {
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+      split_slots[(size_t)i * slot_stride + first] = q[i];
+      q[i] = 0.0;
+    }
+  }
   struct Pre { double c, lb, ub, xb, x, x0; };
   __device__ __forceinline__ Pre load(int j) const {
     return {c[j], lb[j], ub[j], xbar[j], x[j], x0[j]};
@@ -490,6 +527,23 @@ struct CheckRowsEpi {
   int64_t off;  // element offset of the y-part in the search arrays (= n)
   int gap_a, gap_c;
   double q[NQ];
+  // split rows: the reductions of each split row go to
+  // split_slots[q * slot_stride + (slice of its first chunk)] (see
+  // process_split_item); null when the matrix has no split rows
+  static constexpr bool kSplitSlots = true;
+  double *split_slots = nullptr;
+  int slot_stride = 0;
+  __device__ __forceinline__ void zero_split_slot(int item) const {
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) split_slots[(size_t)i * slot_stride + item] = 0.0;
+  }
+  __device__ __forceinline__ void flush_split_slot(int first) {
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+      split_slots[(size_t)i * slot_stride + first] = q[i];
+      q[i] = 0.0;
+    }
+  }
   struct Pre { double b, yb, y, y0; int t; };
   __device__ __forceinline__ Pre load(int i) const { return {b[i], ybar[i], y[i], y0[i], (int)rt[i]}; }
   __device__ __forceinline__ double init(const Pre &) const { return 0.0; }
