@@ -17,7 +17,10 @@ by a second copy of the branch:
   n = 0) fires at the first check with t >= tau^0, whatever the gaps;
 * a schedule of restart flags (the unrolled map the adjoint differentiates)
   reproduces the run whose decisions it copies, and an all-zero schedule is
-  the run without restarts.
+  the run without restarts;
+* restart points never move away from an optimum in the norm in which the
+  PDHG step is non-expansive, so they stay within twice the starting
+  distance of the starting point (the boundedness proposition of Section 4).
 """
 import numpy as np
 import pytest
@@ -238,3 +241,45 @@ def test_schedule_reproduces_the_runs_it_copies(oracle_mod):
                              schedule=np.ones(3, np.int8))
     assert short.restarts == 3
     assert list(np.nonzero(short.trace[:, 2])[0]) == [0, 1, 2]
+
+
+@pytest.mark.parametrize("scheme", ["adaptive", "flexible", "fixed"])
+def test_restart_points_stay_in_the_ball(oracle_mod, scheme):
+    """Proposition (restart points stay bounded) of Section 4, for PDHG: with
+    z* optimal and ||.||_M the norm in which the PDHG step is non-expansive,
+    every average satisfies ||z* - zbar^{n,t}|| <= ||z* - z^{n,0}||, so
+    ||z* - z^{n,0}|| never grows from one restart to the next and every
+    restart point lies within 2 ||z^{0,0} - z*|| of z^{0,0}.  Checked at
+    every one of 40 checks (the average before the decision and the restart
+    point after it) on a planted LP with EQ/GE/LE rows and every bound kind."""
+    lp = lpgen.adversarial(11, m=25, n=50)
+    A = lp.dense()
+    eta = 0.95 / np.linalg.norm(A, 2)
+    omega = 2.0
+    tau, sigma = eta / omega, eta * omega
+    M = np.block([[np.eye(lp.n) / tau, A.T], [A, np.eye(lp.m) / sigma]])
+    zs = np.concatenate([lp.x_star, lp.y_star])
+
+    def norm(d):
+        return float(np.sqrt(d @ M @ d))
+
+    sch = {"adaptive": oracle_mod.RESTART_ADAPTIVE, "flexible": oracle_mod.RESTART_FLEXIBLE,
+           "fixed": oracle_mod.RESTART_FIXED}[scheme]
+    x_init, y_init = lpgen.random_state(lp, 4, scale=3.0)
+    z00 = np.concatenate([x_init, y_init])
+    d0 = norm(z00 - zs)
+    K = 8
+    prev = d0
+    restarts = 0
+    for c in range(1, 41):
+        r = oracle_mod.solve(lp, eta, omega=omega, tol=NEVER, max_iter=K * c, check_every=K,
+                             restart_scheme=sch, fixed_len=3 * K, x_init=x_init, y_init=y_init)
+        zbar = np.concatenate([r.xbar, r.ybar])
+        z0 = np.concatenate([r.x0, r.y0])
+        dn = norm(z0 - zs)
+        assert norm(zbar - zs) <= prev * (1 + 1e-12) + 1e-12, c
+        assert dn <= prev * (1 + 1e-12) + 1e-12, c
+        assert norm(z0 - z00) <= 2 * d0 * (1 + 1e-12), c
+        prev = dn
+        restarts = r.restarts
+    assert restarts >= 4
