@@ -31,6 +31,7 @@
 
 using namespace lpg;
 
+
 namespace {
 
 double now_seconds() {
@@ -748,6 +749,7 @@ lp_status lp_create(int32_t m, int32_t n, int64_t nnz, const int32_t *row_ptr,
                     const double *lb, const double *ub, const int8_t *row_type,
                     const lp_options *opt_in, void *cuda_stream, lp_handle *out) {
   err_msg().clear();
+  NvtxRange nvtx_range("lp_create");
   if (!out) return fail(LP_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (m < 0 || n < 1) return fail(LP_ERR_INVALID_ARG, "need m >= 0 and n >= 1");
@@ -984,6 +986,7 @@ lp_status lp_set_state(lp_handle h, const double *x, const double *y, void *cuda
 
 lp_status lp_iterate(lp_handle h, int32_t n_checks, double tol, void *cuda_stream) {
   err_msg().clear();
+  NvtxRange nvtx_range("lp_iterate");
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   if (!(tol > 0.0)) return fail(LP_ERR_INVALID_ARG, "tol must be > 0");
   if (n_checks < 0) return fail(LP_ERR_INVALID_ARG, "n_checks must be >= 0");
@@ -999,6 +1002,7 @@ lp_status lp_iterate(lp_handle h, int32_t n_checks, double tol, void *cuda_strea
 
 lp_status lp_solve(lp_handle h, double tol, void *cuda_stream) {
   err_msg().clear();
+  NvtxRange nvtx_range("lp_solve");
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   if (!(tol > 0.0)) return fail(LP_ERR_INVALID_ARG, "tol must be > 0");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -1044,6 +1048,7 @@ lp_status lp_solve(lp_handle h, double tol, void *cuda_stream) {
 
 lp_status lp_get_solution(lp_handle h, double *x, double *y, void *cuda_stream) {
   err_msg().clear();
+  NvtxRange nvtx_range("lp_get_solution");
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   if (!h->solved) return fail(LP_ERR_NOT_SOLVED, "no solve has run on this handle");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -1137,6 +1142,7 @@ lp_status lp_get_trace(lp_handle h, double *rows, int64_t capacity, int64_t *cou
 lp_status lp_normalized_gap(lp_handle h, const double *x, const double *y, double r,
                             double *host_rho, void *cuda_stream) {
   err_msg().clear();
+  NvtxRange nvtx_range("lp_normalized_gap");
   if (!h || !host_rho || !x || (h->m > 0 && !y)) return fail(LP_ERR_INVALID_ARG, "NULL argument");
   if (!(r >= 0.0) || !std::isfinite(r)) return fail(LP_ERR_INVALID_ARG, "radius must be finite and >= 0");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -1218,6 +1224,7 @@ lp_status lp_normalized_gap(lp_handle h, const double *x, const double *y, doubl
 lp_status lp_select_omega(lp_handle h, const double *omegas, int32_t count, int64_t iters,
                           double *kkt_out, double *best_out, void *cuda_stream) {
   err_msg().clear();
+  NvtxRange nvtx_range("lp_select_omega");
   if (!h || !omegas || !kkt_out || count < 1) return fail(LP_ERR_INVALID_ARG, "bad arguments");
   if (iters < h->opt.check_every) return fail(LP_ERR_INVALID_ARG, "iters must be >= check_every");
   for (int32_t k = 0; k < count; ++k)
@@ -1265,6 +1272,7 @@ lp_status lp_select_omega(lp_handle h, const double *omegas, int32_t count, int6
 
 lp_status lp_solve_recorded(lp_handle h, int64_t iters, void *cuda_stream) {
   err_msg().clear();
+  NvtxRange nvtx_range("lp_solve_recorded");
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   const int K = h->opt.check_every;
   if (iters < K || iters % K != 0) return fail(LP_ERR_INVALID_ARG, "iters must be a positive multiple of check_every");
@@ -1321,6 +1329,7 @@ lp_status lp_solve_recorded(lp_handle h, int64_t iters, void *cuda_stream) {
 lp_status lp_backward(lp_handle h, const double *dl_dx, const double *dl_dy, double *dl_dc,
                       double *dl_db, void *cuda_stream) {
   err_msg().clear();
+  NvtxRange nvtx_range("lp_backward");
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   if (h->rec_blocks == 0) return fail(LP_ERR_NOT_SOLVED, "no recorded solve (lp_solve_recorded)");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -1488,6 +1497,7 @@ struct ScratchCarver {
 extern "C" lp_status lp_normalized_gap_static(lp_handle h, const double *x, const double *y,
                                               double r, double *host_rho, void *cuda_stream) {
   err_msg().clear();
+  NvtxRange nvtx_range("lp_normalized_gap_static");
   if (!h || !host_rho || !x || (h->m > 0 && !y)) return fail(LP_ERR_INVALID_ARG, "NULL argument");
   if (!(r >= 0.0) || !std::isfinite(r)) return fail(LP_ERR_INVALID_ARG, "radius must be finite and >= 0");
   const int n = h->n, m = h->m;

@@ -1618,6 +1618,7 @@ lp_status lp_batch_create(int32_t count, const int32_t *host_row_start,
                           const lp_batch_tuning *tuning, void *cuda_stream,
                           lp_batch_handle *out) {
   err_msg().clear();
+  NvtxRange nvtx_range("lp_batch_create");
   const auto t_start = std::chrono::steady_clock::now();
   if (!out) return fail(LP_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
@@ -2053,6 +2054,7 @@ lp_status lp_batch_select_omega(lp_batch_handle h, const double *host_omegas, in
                                 int64_t iters, double *host_kkt, double *host_best,
                                 void *cuda_stream) {
   err_msg().clear();
+  NvtxRange nvtx_range("lp_batch_select_omega");
   if (!h || !host_omegas || n_omegas < 1) return fail(LP_ERR_INVALID_ARG, "bad arguments");
   const int K = h->opt.check_every;
   if (iters < K || iters % K != 0)
@@ -2135,6 +2137,7 @@ lp_status lp_batch_set_check_every(lp_batch_handle h, const int32_t *host_k, voi
 
 lp_status lp_batch_iterate(lp_batch_handle h, int32_t n_blocks, double tol, void *cuda_stream) {
   err_msg().clear();
+  NvtxRange nvtx_range("lp_batch_iterate");
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   if (!(tol > 0.0)) return fail(LP_ERR_INVALID_ARG, "tol must be > 0");
   if (n_blocks < 0) return fail(LP_ERR_INVALID_ARG, "n_blocks must be >= 0");
@@ -2150,6 +2153,7 @@ lp_status lp_batch_iterate(lp_batch_handle h, int32_t n_blocks, double tol, void
 
 lp_status lp_batch_solve(lp_batch_handle h, double tol, void *cuda_stream) {
   err_msg().clear();
+  NvtxRange nvtx_range("lp_batch_solve");
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   if (!(tol > 0.0)) return fail(LP_ERR_INVALID_ARG, "tol must be > 0");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -2195,6 +2199,7 @@ lp_status lp_batch_solve(lp_batch_handle h, double tol, void *cuda_stream) {
 
 lp_status lp_batch_get_solution(lp_batch_handle h, double *x, double *y, void *cuda_stream) {
   err_msg().clear();
+  NvtxRange nvtx_range("lp_batch_get_solution");
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   if (!h->solved) return fail(LP_ERR_NOT_SOLVED, "no solve has run on this batch");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
@@ -2300,6 +2305,7 @@ lp_status lp_batch_get_info(lp_batch_handle h, lp_batch_info *info,
 
 lp_status lp_batch_solve_recorded(lp_batch_handle h, int64_t iters, void *cuda_stream) {
   err_msg().clear();
+  NvtxRange nvtx_range("lp_batch_solve_recorded");
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   const int K = h->opt.check_every;
   if (iters < K || iters % K != 0) return fail(LP_ERR_INVALID_ARG, "iters must be a positive multiple of check_every");
@@ -2375,6 +2381,7 @@ lp_status lp_batch_solve_recorded(lp_batch_handle h, int64_t iters, void *cuda_s
 lp_status lp_batch_backward(lp_batch_handle h, const double *dl_dx, const double *dl_dy,
                             double *dl_dc, double *dl_db, void *cuda_stream) {
   err_msg().clear();
+  NvtxRange nvtx_range("lp_batch_backward");
   if (!h) return fail(LP_ERR_INVALID_ARG, "NULL handle");
   if (h->rec_blocks == 0) return fail(LP_ERR_NOT_SOLVED, "no recorded solve (lp_batch_solve_recorded)");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);

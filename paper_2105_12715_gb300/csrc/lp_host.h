@@ -14,6 +14,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/lp.h"
 #include "lp_internal.h"
@@ -37,6 +38,15 @@ inline lp_status cuda_fail(cudaError_t e, const char *what) {
   return fail(e == cudaErrorMemoryAllocation ? LP_ERR_OOM : LP_ERR_CUDA,
               std::string(what) + ": " + cudaGetErrorString(e));
 }
+
+// NVTX range around an entry point (header-only NVTX3: a no-op unless a
+// profiler is attached), so a timeline shows the library's phases.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 #define LP_CU(call)                                   \
   do {                                                \
