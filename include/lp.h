@@ -275,8 +275,8 @@ lp_status lp_select_omega(lp_handle h, const double *host_omegas, int32_t count,
                           void *cuda_stream);
 
 /*
- * Unrolled forward for differentiation (spec extension; the paper
- * has no gradients): runs exactly `iters` iterations of Algorithm 1 from the
+ * Unrolled forward for differentiation (an extension: the paper has no
+ * gradients): runs exactly `iters` iterations of Algorithm 1 from the
  * current state (iters a multiple of K; FP64; adaptive, fixed or no
  * restarts; no termination test), keeping a checkpoint of (x, y, xbar, ybar)
  * and the inner iteration count at the start of every block of K
