@@ -295,7 +295,7 @@ def cpu_baseline(args, data, eta):
     """The oracle on a bounded sample: cpu_iters iterations with one check
     every 64 (the same workload, the GPU's step size), on all host cores (its
     OpenMP build: the row products and elementwise loops split over the
-    cores, A^T y a serial scatter) and on one thread (the checker build)."""
+    cores, A^T y a serial scatter) and on one thread (the default build)."""
     import oracle
 
     olp = oracle.OracleLP(data)

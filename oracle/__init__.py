@@ -33,10 +33,10 @@ STATUS_OK, STATUS_ITER_LIMIT, STATUS_NUMERICAL = 0, 4, 5
 
 
 def build(force: bool = False, openmp: bool = False) -> str:
-    """Compile the oracle with gcc into oracle/_build/liboracle.so (the
-    checker, one thread), or with openmp=True into liboracle_omp.so (the same
-    source with its OpenMP pragmas honored; used to time the oracle on all
-    host cores)."""
+    """Compile the oracle with gcc into oracle/_build/liboracle.so (the build
+    the tests use, one thread), or with openmp=True into liboracle_omp.so
+    (the same source with its OpenMP pragmas honored; used to time the
+    oracle on all host cores)."""
     os.makedirs(_BUILD, exist_ok=True)
     lib = _LIB_OMP if openmp else _LIB
     if (not force and os.path.exists(lib)

@@ -31,7 +31,7 @@
  *
  * The loops whose iterations are independent (the row products of A x,
  * the elementwise parts of the PDHG step, the averages) carry OpenMP
- * pragmas.  The checker is the default build, without -fopenmp: the
+ * pragmas.  The tests use the default build, without -fopenmp: the
  * pragmas are ignored and the code runs on one thread exactly as written.
  * A second build with -fopenmp (liboracle_omp.so) is used only to time the
  * oracle on all host cores; the loops it splits have no dependence between

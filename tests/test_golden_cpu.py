@@ -82,9 +82,9 @@ def test_flexible_restart_hand(oracle_mod, case):
         assert getattr(r, k)[0] == pytest.approx(golden.value(f[k]), rel=1e-15, abs=1e-300), k
 
 
-def test_openmp_build_is_bitwise_the_checker(oracle_mod):
+def test_openmp_build_is_bitwise_the_default_build(oracle_mod):
     """The OpenMP build (used only to time the oracle on all cores) splits
-    loops without dependences between iterations: same bits as the checker."""
+    loops without dependences between iterations: same bits as the default build."""
     from paper_2105_12715_gb300 import lpgen
 
     try:
