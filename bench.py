@@ -877,6 +877,16 @@ def run_ours(args):
                 sm[name] = r
             t8["small_vs_highs"] = sm
             mcf["time_to_tolerance"] = t8
+            # the same shape at a size it reaches 1e-8 at: a 100 x 100 grid, 8 commodities
+            mid = lpgen.multicommodity_grid(4, side=100, commodities=8)
+            t8m = {"lp": f"multicommodity grid 100x100, 8 commodities: m={mid.m} n={mid.n} "
+                         f"nnz={mid.nnz}", "tol": 1e-8, "cap_iters": 2_000_000}
+            for name, prec in (("fp64", lp.LP_PRECISION_FP64), ("mixed", lp.LP_PRECISION_MIXED)):
+                t8m[name] = ttk_run(mid, 1e-8, prec, True, 2_000_000, PAPER_OMEGA_GRID,
+                                    PAPER_OMEGA_ITERS)
+            mixed_error(t8m)
+            t8m["mixed_speedup"] = t8m["fp64"]["seconds"] / t8m["mixed"]["seconds"]
+            mcf["time_to_kkt_1e8_grid100"] = t8m
 
     # adjoint of the unrolled map on differentiable-LP-shaped instances
     # (m=2000, n=5000, nnz=50k, box [0,1]; 2000 iterations, checkpoint every 100)
