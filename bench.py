@@ -225,6 +225,9 @@ class ClockSampler:
         self.path = os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv")
 
     def start(self):
+        """Starts nvidia-smi and waits (up to 5 s) for its first sample, so the
+        samples of the region that follows are not lost to its start-up."""
+        self.skip = 0
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
@@ -232,6 +235,20 @@ class ClockSampler:
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 5.0 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.01)
+
+    def mark(self):
+        """Start of the timed region: samples written before it are dropped."""
+        try:
+            with open(self.path) as fh:
+                self.skip = sum(1 for _ in fh)
+        except OSError:
+            self.skip = 0
 
     def stop(self):
         if self.proc is None:
@@ -244,7 +261,11 @@ class ClockSampler:
         self.f.close()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        lines = open(self.path).read().splitlines()
+        # the samples of the timed region, and the one taken just before it
+        # when the region was shorter than the sampling interval
+        lines = lines[max(0, self.skip - 1):] if len(lines) > self.skip else lines[-1:]
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -587,6 +608,7 @@ def run_ours(args):
     barrier()
     sampler = ClockSampler(dev)
     sampler.start()
+    sampler.mark()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     g.iterate(args.steps, 1e-300)
