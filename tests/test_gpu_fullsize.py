@@ -2,7 +2,8 @@
 columns, ~10M nonzeros; mixed bounds and row senses, power-law column
 degrees) in the benchmark's launch configuration (K = 64, adaptive
 restarts): 128 iterations (two checks) of the CUDA path against the
-oracle, every state vector compared element by element."""
+oracle, every state vector compared element by element, in FP64 (1e-9) and
+in mixed precision (1e-5)."""
 import numpy as np
 import pytest
 
@@ -57,6 +58,19 @@ def test_full_size_two_checks(oracle_mod):
         assert err <= 1e-9 * scale, (k, err, scale)
     np.testing.assert_array_equal(tr[:, 2], ref.trace[:, 2])
     np.testing.assert_allclose(tr[:, 1], ref.trace[:, 1], rtol=1e-8)
+    # FP32-mixed iterations (FP64 averages, checks and refinement) on the same LP against the
+    # same FP64 oracle run: FP32 rounding, bounded by 1e-5 relative, same restart decisions
+    with lp.LP(data, eta=eta, check_every=64, max_iter=iters,
+               precision=lp.LP_PRECISION_MIXED) as g:
+        assert g.solve(1e-300) == lp.LP_ITER_LIMIT
+        st = g.state()
+        tr = g.trace()
+    for k in ["x", "y", "xbar", "ybar", "x0", "y0"]:
+        want = getattr(ref, k)
+        scale = max(1.0, float(np.abs(want).max()))
+        err = float(np.abs(st[k] - want).max())
+        assert err <= 1e-5 * scale, ("mixed", k, err, scale)
+    np.testing.assert_array_equal(tr[:, 2], ref.trace[:, 2])
 
 
 def test_full_size_batch_512_problems(oracle_mod):

@@ -120,6 +120,26 @@ def test_ragged_multi_slice_power_law(lpm, oracle_mod, unroll):
     assert info.restarts == ref.restarts
 
 
+@pytest.mark.parametrize("tau0_mult", [0, 2.5, 3])
+def test_first_restart_length_tau0(lpm, oracle_mod, tau0_mult):
+    """Eq. (adaptive-restart-scheme), n = 0: the first restart at the first
+    check with t >= tau^0 (tau^0 = 1, 2.5 K, 3 K), then the beta rule; the
+    CUDA path's restart flags, gaps and iterates against the oracle's."""
+    data = lpgen.tiny_standard_form(6)
+    eta = eta_of(oracle_mod, data)
+    K = 16
+    tau0 = 1 if tau0_mult == 0 else int(tau0_mult * K)
+    with lpm.LP(data, eta=eta, check_every=K, max_iter=20 * K, tau0=tau0, autotune=0) as g:
+        g.solve(1e-300)
+        st, tr = g.state(), g.trace()
+    ref = oracle_mod.solve(data, eta, tol=1e-300, max_iter=20 * K, check_every=K, tau0=tau0)
+    np.testing.assert_array_equal(tr[:, 2], ref.trace[:, 2])
+    first = int(np.flatnonzero(ref.trace[:, 2])[0]) + 1
+    assert first == max(1, -(-tau0 // K))  # first check with t >= tau0
+    close(tr[:, 1], ref.trace[:, 1], 1e-8, "rho")
+    compare_states(st, ref, 1e-8)
+
+
 def test_flexible_and_fixed_schemes(lpm, oracle_mod):
     data = lpgen.tiny_standard_form(4)
     eta = eta_of(oracle_mod, data)
