@@ -15,12 +15,17 @@ e2e   = the same metric through the C ABI from HOST buffers: lp_create
 
 Also reported (outside the timed region): time to relative KKT 1e-8 with the
 paper's recipe (primal weight by Section 7's grid search, then adaptive
-restarted PDHG), FP64 vs mixed, on the benchmark LP itself and on two
-smaller LPs; mixed-precision throughput; the multicommodity LP; the adjoint
-(single LP, implicit-KKT check, 64-LP batch); the 512-LP batched solver.
+restarted PDHG), FP64 vs mixed, on the benchmark LP itself (with the reduced
+and with the paper's own grid) and on two smaller LPs; mixed-precision
+throughput; the multicommodity LP (throughput, a 100 x 100 grid to 1e-8 FP64
+vs mixed, a small instance against HiGHS); the adjoint (single LP,
+implicit-KKT check, 64-LP batch); the 200 x 400 LP alone and 512 of them as
+one batch; the 512-LP batched solver to 1e-8; the column pass's roofline
+(traffic from a committed ncu capture keyed by the kernels' source hash) and
+its gather ceilings; the oracle on all host cores and on one.
 
---impl reference times the CPU oracle (plain C, FP64, 1 thread) on a
-bounded sample of the same workload and metric.
+--impl reference times the CPU oracle (plain C, FP64, its OpenMP build on
+all host cores) on a bounded sample of the same workload and metric.
 """
 from __future__ import annotations
 
